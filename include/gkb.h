@@ -1,0 +1,187 @@
+/*
+ * gkb.h - C ABI of the GB300 generalized Golub-Kahan bidiagonalization (GKB)
+ * solver for MAC-discretised Stokes saddle-point systems
+ *
+ *     [ W   A ] [w]   [g]
+ *     [ A^T 0 ] [p] = [r]                                   (Sec. 2, Eq. (1))
+ *
+ * with W the viscous operator, A the integrated gradient, N = n_scale * I and
+ * the augmented block M = W + gamma A N^-1 A^T (Eq. (2)). The solver applies
+ * the augmented-Lagrangian transform (Eq. (3)), runs the Craig-variant GKB
+ * recurrence (Algorithm 1) with the lower-bound stopping rule of Sec. 2.2
+ * (Eq. (5)) and solves every inner system M x = f with conjugate gradients,
+ * optionally preconditioned by one geometric-multigrid V-cycle.
+ *
+ * Discretisation (shared definition with the independent CPU oracle):
+ *   uniform spacing h; velocity component c on the faces normal to axis c,
+ *   pressure in the cells; finite-volume integrated form, so W has entries of
+ *   size mu h^(d-2) and A entries +-h^(d-1): (A p)_f = h^(d-1)(p_plus - p_minus),
+ *   and A^T is minus the integrated divergence. Tangential links use the mean
+ *   viscosity of the in-domain cells around the node (2D) / edge (3D). Walls
+ *   are no-slip mirror walls; natural sides are do-nothing outflow with
+ *   half control volumes.
+ *
+ * Vector layout of every m-vector (velocity) and n-vector (pressure) crossing
+ * this boundary ("compact ordering"): all active u faces, then all active v
+ * faces (then w), each block row-major with x fastest; a face normal to axis
+ * c is active unless it lies on a Dirichlet side normal to c. Pressure is the
+ * cell array, x fastest. gkb_layout() reports m and n.
+ *
+ * Memory: every array pointer may be host memory (pageable or pinned) or
+ * device memory of the handle's device; the library detects which with
+ * cudaPointerGetAttributes. Host arrays are staged through the handle's
+ * device buffers (copies included in the call). The caller owns all arrays
+ * it passes; the handle owns all workspace.
+ *
+ * Errors: every entry point returns a status code (GKB_OK or GKB_ERR_*);
+ * nothing is thrown across the ABI. gkb_last_error() returns a message for
+ * the last failing call on that handle. A handle is not thread safe.
+ *
+ * Calls are synchronous with respect to the host: they return after the
+ * work queued on the handle's stream has completed.
+ */
+#ifndef GKB_H
+#define GKB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GKB_OK                       0
+#define GKB_ERR_INVALID_ARG          1  /* bad size, pointer, option or state */
+#define GKB_ERR_NOT_SPD              2  /* w^T M w <= 0 or p^T M p <= 0 met     */
+#define GKB_ERR_NOT_CONVERGED        3  /* outer maxit reached (Algorithm 1)     */
+#define GKB_ERR_INNER_NOT_CONVERGED  4  /* an inner solve hit maxit_inner        */
+#define GKB_ERR_NAN                  5  /* NaN or Inf met in a norm              */
+#define GKB_ERR_TIMEOUT              6  /* a bounded device wait ran out         */
+#define GKB_ERR_CUDA                 7  /* CUDA runtime error                    */
+#define GKB_ERR_OOM                  8  /* device allocation failed              */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define GKB_BC_DIRICHLET  0   /* velocity given on that side (no-slip wall) */
+#define GKB_BC_NATURAL    1   /* do-nothing outflow                         */
+
+#define GKB_PREC_FP64     0   /* everything in FP64                          */
+#define GKB_PREC_MIXED    1   /* inner CG, V-cycles and stencils in FP32 with
+                                 FP64 iterative refinement of each inner
+                                 solve; GKB vectors, alpha, beta, zeta and the
+                                 estimator in FP64                           */
+
+#define GKB_INNER_CG      0   /* unpreconditioned CG                         */
+#define GKB_INNER_GMG_PCG 1   /* CG + one GMG V-cycle (all-Dirichlet grids)  */
+
+#define GKB_OP_W   0          /* y = W x                 (m -> m) */
+#define GKB_OP_A   1          /* y = A x (gradient)      (n -> m) */
+#define GKB_OP_AT  2          /* y = A^T x (-divergence) (m -> n) */
+#define GKB_OP_M   3          /* y = M x                 (m -> m) */
+
+typedef struct gkb_ctx* gkb_handle;
+
+/* Grid: dim = 2 or 3, n[] cells per axis (n[2] ignored in 2D), spacing h,
+ * bc[] per side in the order x-low, x-high, y-low, y-high, z-low, z-high. */
+typedef struct {
+  int dim;
+  int n[3];
+  double h;
+  int bc[6];
+} gkb_grid;
+
+typedef struct {
+  int precision;          /* GKB_PREC_*                                        */
+  int inner;              /* GKB_INNER_*                                       */
+  double tol_inner;       /* inner stop: ||f - M x||_2 <= tol_inner ||f||_2    */
+  int maxit;              /* outer (Algorithm 1 while-loop) iteration limit    */
+  int maxit_inner;        /* CG iteration limit per inner solve                */
+  int smoother_degree;    /* Chebyshev degree of pre- and post-smoothing       */
+  int coarse_max;         /* coarsen while every side is even, halves to >= 2
+                             cells and the longest side exceeds coarse_max
+                             (coarse_max / 2, at least 4, in 3D)              */
+  double mixed_rtol;      /* GKB_PREC_MIXED: relative tolerance of each FP32
+                             correction solve inside the refinement loop       */
+  int use_graph;          /* 1: run each solve as one CUDA graph with device-
+                             side loop control; 0: host-driven loops           */
+  void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
+} gkb_options;
+
+typedef struct {
+  int status;                 /* status of the last gkb_solve                */
+  int outer_iterations;       /* while-loop iterations of Algorithm 1        */
+  int inner_solves;           /* inner M-solves (AL transform + init + loop) */
+  int64_t inner_iterations;   /* total CG iterations over all inner solves   */
+  double estimate;            /* final lower-bound estimate (Eq. (5))        */
+  double setup_seconds;       /* gkb_set_problem wall time                   */
+  double solve_seconds;       /* last gkb_solve wall time                    */
+  int levels;                 /* multigrid levels (0 without GMG)            */
+} gkb_stats_t;
+
+/* Fill *opt with defaults: FP64, GMG-PCG, tol_inner 1e-10, maxit 1000,
+ * maxit_inner 2000, degree 2, coarse_max 8, mixed_rtol 1e-4, graph off. */
+int gkb_default_options(gkb_options* opt);
+
+/* Create a handle on the current CUDA device. *out receives the handle.
+ * Errors: INVALID_ARG (null pointers, bad option values), CUDA. */
+int gkb_create(gkb_handle* out, const gkb_options* opt);
+
+/* Define the operator (Eq. (1)-(2)): grid, cell viscosity, gamma and
+ * N = n_scale * I (n_scale <= 0 selects h^dim, the pressure mass matrix).
+ * viscosity: NULL for the constant mu0, else n values in compact pressure
+ * ordering (host or device; copied). Builds the multigrid hierarchy and the
+ * coarse solver. Errors: INVALID_ARG (sizes < 2, non-positive h, mu <= 0,
+ * natural sides with GMG, odd sizes that cannot coarsen), OOM, CUDA. */
+int gkb_set_problem(gkb_handle h, const gkb_grid* grid, const double* viscosity,
+                    double mu0, double gamma, double n_scale);
+
+/* Sizes of the compact velocity (m) and pressure (n) vectors. */
+int gkb_layout(gkb_handle h, int64_t* m, int64_t* n);
+
+/* Fold a Dirichlet normal velocity on one side into (g, r) in place: for
+ * every boundary face b of that side with value u_b, the momentum row of the
+ * active face linked to it gets kappa * u_b and the adjacent cell's
+ * continuity row gets -A[b, cell] * u_b. normal_velocity holds one value per
+ * boundary face of the side (x fastest over the remaining axes). g (m) and
+ * r (n) are compact vectors. Errors: INVALID_ARG (side not Dirichlet). */
+int gkb_boundary_rhs(gkb_handle h, int side, const double* normal_velocity,
+                     double* g, double* r);
+
+/* Solve Eq. (1) for (w, p): AL transform (Eq. (3)), Algorithm 1 with the
+ * lower-bound rule of Eq. (5): with zeta_1..zeta_K known, stop when
+ * sqrt(sum_{j=K-d}^{K} zeta_j^2 / sum_{j=1}^{K} zeta_j^2) <= tol, delay d.
+ * g (m), r (n): right-hand side; w_out (m), p_out (n): solution. w0 / p0:
+ * optional initial guess (NULL for zero), handled by defect correction. With
+ * every side Dirichlet the returned pressure has zero mean.
+ * Returns OK, NOT_CONVERGED (maxit reached; w_out/p_out hold the last
+ * iterate), INNER_NOT_CONVERGED, NOT_SPD, NAN, or an argument/CUDA error. */
+int gkb_solve(gkb_handle h, const double* g, const double* r, double tol, int delay,
+              double* w_out, double* p_out, const double* w0, const double* p0);
+
+/* Statistics of the last solve. */
+int gkb_stats(gkb_handle h, gkb_stats_t* out);
+
+/* Per-step history of the last solve, host arrays of `capacity` entries
+ * (any may be NULL): alpha_k, beta_k (beta_1 first), zeta_k, the estimate
+ * after each loop step, and the CG iterations of each inner solve. Returns
+ * the number of entries written for zeta (negative on error). */
+int gkb_history(gkb_handle h, double* alpha, double* beta, double* zeta,
+                double* estimate, int* inner_its, int capacity);
+
+/* Apply one operator (GKB_OP_*) in FP64 to compact vectors, y = op(x). */
+int gkb_apply(gkb_handle h, int op, const double* x, double* y);
+
+/* Apply the inner preconditioner once, z = B r (one V-cycle, or identity for
+ * plain CG), in the handle's precision, to compact m-vectors. */
+int gkb_precond(gkb_handle h, const double* r, double* z);
+
+/* Message for the last failing call (never NULL). */
+const char* gkb_last_error(gkb_handle h);
+
+/* Release the handle and all its device memory. */
+int gkb_destroy(gkb_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKB_H */

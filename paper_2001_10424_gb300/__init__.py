@@ -1,0 +1,215 @@
+"""Python binding of the GB300 GKB saddle-point solver (``libgkb.so``).
+
+Thin ctypes marshalling over the C ABI declared in ``include/gkb.h``: every
+function here has the C name, converts its array arguments to raw pointers
+(PyTorch CUDA or CPU tensors, or NumPy arrays, all float64 and contiguous)
+and calls the library. All arithmetic runs in the library's CUDA kernels;
+there is no Python or CPU fallback, and :func:`load` raises if the shared
+library has not been built.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build.LIB
+
+GKB_OK = 0
+GKB_ERR_INVALID_ARG = 1
+GKB_ERR_NOT_SPD = 2
+GKB_ERR_NOT_CONVERGED = 3
+GKB_ERR_INNER_NOT_CONVERGED = 4
+GKB_ERR_NAN = 5
+GKB_ERR_TIMEOUT = 6
+GKB_ERR_CUDA = 7
+GKB_ERR_OOM = 8
+
+GKB_BC_DIRICHLET = 0
+GKB_BC_NATURAL = 1
+GKB_PREC_FP64 = 0
+GKB_PREC_MIXED = 1
+GKB_INNER_CG = 0
+GKB_INNER_GMG_PCG = 1
+GKB_OP_W, GKB_OP_A, GKB_OP_AT, GKB_OP_M = 0, 1, 2, 3
+
+STATUS_NAMES = {
+    0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "NOT_CONVERGED", 4: "INNER_NOT_CONVERGED",
+    5: "NAN", 6: "TIMEOUT", 7: "CUDA", 8: "OOM",
+}
+
+# symbols declared in include/gkb.h
+EXPORTED = [
+    "gkb_default_options", "gkb_create", "gkb_set_problem", "gkb_layout", "gkb_boundary_rhs",
+    "gkb_solve", "gkb_stats", "gkb_history", "gkb_apply", "gkb_precond", "gkb_last_error",
+    "gkb_destroy",
+]
+
+
+class gkb_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double),
+                ("bc", ctypes.c_int * 6)]
+
+
+class gkb_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("inner", ctypes.c_int), ("tol_inner", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
+                ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class gkb_stats_t(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("inner_solves", ctypes.c_int),
+                ("inner_iterations", ctypes.c_int64), ("estimate", ctypes.c_double),
+                ("setup_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
+                ("levels", ctypes.c_int)]
+
+
+class GkbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def load(path=None):
+    """Load ``libgkb.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libgkb.so is not built (%s); run paper_2001_10424_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "gkb_default_options": (i, [ctypes.POINTER(gkb_options)]),
+        "gkb_create": (i, [ctypes.POINTER(_P), ctypes.POINTER(gkb_options)]),
+        "gkb_set_problem": (i, [_P, ctypes.POINTER(gkb_grid), _P, d, d, d]),
+        "gkb_layout": (i, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "gkb_boundary_rhs": (i, [_P, i, _P, _P, _P]),
+        "gkb_solve": (i, [_P, _P, _P, d, i, _P, _P, _P, _P]),
+        "gkb_stats": (i, [_P, ctypes.POINTER(gkb_stats_t)]),
+        "gkb_history": (i, [_P, _P, _P, _P, _P, _P, i]),
+        "gkb_apply": (i, [_P, i, _P, _P]),
+        "gkb_precond": (i, [_P, _P, _P]),
+        "gkb_last_error": (ctypes.c_char_p, [_P]),
+        "gkb_destroy": (i, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw pointer of a float64 contiguous tensor / array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("arrays must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data
+
+
+def _check(h, rc, allow=()):
+    if rc != GKB_OK and rc not in allow:
+        raise GkbError(rc, gkb_last_error(h) if h else "")
+    return rc
+
+
+def make_grid(n, h, bc=None):
+    """gkb_grid for ``n`` cells per axis (2 or 3 entries), spacing h, sides bc."""
+    g = gkb_grid()
+    g.dim = len(n)
+    for a, v in enumerate(n):
+        g.n[a] = int(v)
+    g.h = float(h)
+    bc = bc if bc is not None else (GKB_BC_DIRICHLET,) * (2 * len(n))
+    for s, v in enumerate(bc):
+        g.bc[s] = int(v)
+    return g
+
+
+def gkb_default_options():
+    lib = load()
+    o = gkb_options()
+    _check(None, lib.gkb_default_options(ctypes.byref(o)))
+    return o
+
+
+def gkb_create(opt=None):
+    lib = load()
+    opt = opt or gkb_default_options()
+    h = _P()
+    _check(None, lib.gkb_create(ctypes.byref(h), ctypes.byref(opt)))
+    return h
+
+
+def gkb_set_problem(h, grid, viscosity=None, mu0=1.0, gamma=0.0, n_scale=0.0):
+    return _check(h, load().gkb_set_problem(h, ctypes.byref(grid), _ptr(viscosity), mu0, gamma, n_scale))
+
+
+def gkb_layout(h):
+    m, n = ctypes.c_int64(), ctypes.c_int64()
+    _check(h, load().gkb_layout(h, ctypes.byref(m), ctypes.byref(n)))
+    return m.value, n.value
+
+
+def gkb_boundary_rhs(h, side, normal_velocity, g, r):
+    return _check(h, load().gkb_boundary_rhs(h, side, _ptr(normal_velocity), _ptr(g), _ptr(r)))
+
+
+def gkb_solve(h, g, r, tol, delay, w_out, p_out, w0=None, p0=None):
+    """Returns the status code; argument / CUDA errors raise GkbError."""
+    rc = load().gkb_solve(h, _ptr(g), _ptr(r), tol, delay, _ptr(w_out), _ptr(p_out), _ptr(w0), _ptr(p0))
+    return _check(h, rc, allow=(GKB_ERR_NOT_CONVERGED, GKB_ERR_INNER_NOT_CONVERGED, GKB_ERR_NOT_SPD, GKB_ERR_NAN))
+
+
+def gkb_stats(h):
+    s = gkb_stats_t()
+    _check(h, load().gkb_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def gkb_history(h, capacity=4096):
+    import numpy as np
+    a = np.zeros(capacity)
+    b = np.zeros(capacity)
+    z = np.zeros(capacity)
+    e = np.zeros(capacity)
+    its = np.zeros(capacity, dtype=np.int32)
+    n = load().gkb_history(h, a.ctypes.data, b.ctypes.data, z.ctypes.data, e.ctypes.data, its.ctypes.data, capacity)
+    if n < 0:
+        raise GkbError(-n, gkb_last_error(h))
+    st = gkb_stats(h)
+    k = st["outer_iterations"]
+    return {"alpha": a[:n], "beta": b[:k + 1], "zeta": z[:n], "estimate": e[:k],
+            "inner_iterations": its[:st["inner_solves"]]}
+
+
+def gkb_apply(h, op, x, y):
+    return _check(h, load().gkb_apply(h, op, _ptr(x), _ptr(y)))
+
+
+def gkb_precond(h, r, z):
+    return _check(h, load().gkb_precond(h, _ptr(r), _ptr(z)))
+
+
+def gkb_last_error(h):
+    msg = load().gkb_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def gkb_destroy(h):
+    return _check(None, load().gkb_destroy(h))

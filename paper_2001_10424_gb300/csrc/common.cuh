@@ -1,0 +1,213 @@
+// common.cuh - level descriptor, padded MAC layout and stencil device code.
+//
+// Padded layout of one grid level (2D uses nz = 1):
+//   every array is indexed  k * S + j * P + i  with row pitch P >= nx + 1
+//   (a multiple of 32 elements) and plane stride S = (ny + 1) * P.
+//   velocity: component blocks u | v | w at offsets off[c]; u has nz planes of
+//   ny rows of nx+1 faces, v nz planes of ny+1 rows of nx faces, w nz+1 planes
+//   of ny rows of nx faces. pressure / cell arrays: nz planes of ny rows of nx.
+//   Entries outside the active faces (Dirichlet boundary faces and padding)
+//   are kept exactly zero by every kernel, so flat BLAS-1 over the whole
+//   array equals BLAS-1 over the unknowns.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gkb {
+
+struct Lvl {
+  int dim;            // 2 or 3
+  int n[3];           // cells per axis (n[2] = 1 in 2D)
+  int nat[6];         // 1 where the side is natural (outflow)
+  int P;              // row pitch in elements
+  long long S;        // plane stride
+  long long off[3];   // velocity component offsets
+  long long nvel;     // padded velocity length
+  long long ncell;    // padded cell length (n[2] * S)
+  double h;
+  double wscale;      // h^(d-2): link conductance factor
+  double ascale;      // h^(d-1): gradient entry
+  double gc;          // gamma / n_scale
+  double mu0;         // constant viscosity when mu == null
+  const double* mu64; // cell viscosity in the padded cell layout, or null
+  const float* mu32;
+};
+
+__host__ __device__ __forceinline__ long long cix(const Lvl& L, int i, int j, int k) {
+  return (long long)k * L.S + (long long)j * L.P + i;
+}
+
+// active face test for component C at (i, j, k)
+template <int C>
+__host__ __device__ __forceinline__ bool face_active(const Lvl& L, int i, int j, int k) {
+  const int p[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (a >= L.dim) { if (p[a] != 0) return false; continue; }
+    if (a == C) {
+      if (p[a] < 0 || p[a] > L.n[a]) return false;
+      if (p[a] == 0 && !L.nat[2 * a]) return false;
+      if (p[a] == L.n[a] && !L.nat[2 * a + 1]) return false;
+    } else {
+      if (p[a] < 0 || p[a] >= L.n[a]) return false;
+    }
+  }
+  return true;
+}
+
+__host__ __device__ __forceinline__ bool cell_in(const Lvl& L, int i, int j, int k) {
+  return i >= 0 && i < L.n[0] && j >= 0 && j < L.n[1] && k >= 0 && k < L.n[2];
+}
+
+template <typename T> struct MuPtr;
+template <> struct MuPtr<double> { static __device__ __forceinline__ const double* get(const Lvl& L) { return L.mu64; } };
+template <> struct MuPtr<float>  { static __device__ __forceinline__ const float*  get(const Lvl& L) { return L.mu32; } };
+
+template <typename T, bool VarMu>
+__device__ __forceinline__ T cell_mu(const Lvl& L, int i, int j, int k) {
+  if (!VarMu) return (T)L.mu0;
+  return __ldg(MuPtr<T>::get(L) + cix(L, i, j, k));
+}
+
+// mean viscosity of the in-domain cells around the node/edge crossed by a
+// tangential link of component C along axis A; the cells have C-coordinate
+// p[C]-1 and p[C], A-coordinate af-1 and af, other coordinates from p.
+template <typename T, bool VarMu, int C, int A>
+__device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
+  if (!VarMu) return (T)L.mu0;
+  T s = 0;
+  int cnt = 0;
+#pragma unroll
+  for (int dc = -1; dc <= 0; ++dc)
+#pragma unroll
+    for (int da = -1; da <= 0; ++da) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[C] = p[C] + dc;
+      q[A] = af + da;
+      if (cell_in(L, q[0], q[1], q[2])) { s += cell_mu<T, true>(L, q[0], q[1], q[2]); ++cnt; }
+    }
+  return s / (T)cnt;
+}
+
+template <typename T>
+__device__ __forceinline__ T ldv(const T* x, long long idx) { return __ldg(x + idx); }
+
+// Velocity value of component C at face position p; positions outside the
+// face grid read as 0 (callers only ask for in-grid or wall-adjacent ones).
+template <typename T, int C>
+__device__ __forceinline__ T face_val(const Lvl& L, const T* x, int i, int j, int k) {
+  return ldv(x, L.off[C] + cix(L, i, j, k));
+}
+
+// (A^T x)_cell / ascale = sum over components of (low face - high face)
+template <typename T>
+__device__ __forceinline__ T neg_div(const Lvl& L, const T* x, int i, int j, int k) {
+  if (!cell_in(L, i, j, k)) return (T)0;
+  T s = face_val<T, 0>(L, x, i, j, k) - face_val<T, 0>(L, x, i + 1, j, k)
+      + face_val<T, 1>(L, x, i, j, k) - face_val<T, 1>(L, x, i, j + 1, k);
+  if (L.dim == 3) s += face_val<T, 2>(L, x, i, j, k) - face_val<T, 2>(L, x, i, j, k + 1);
+  return s;
+}
+
+// Row of W at an active face of component C, position p (FV links, see
+// include/gkb.h). Returns sum_links kappa (x_f - x_nb) with x_nb = 0 for
+// mirror links, divided by wscale (the caller scales).
+template <typename T, bool VarMu, int C>
+__device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T xf) {
+  T acc = 0;
+  // normal links across the cells p[C]-1 and p[C]
+  {
+    int q[3] = {p[0], p[1], p[2]};
+    if (p[C] < L.n[C]) {
+      q[C] = p[C] + 1;
+      T mu = cell_mu<T, VarMu>(L, p[0], p[1], p[2]);
+      acc += mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+    }
+    if (p[C] > 0) {
+      q[C] = p[C] - 1;
+      T mu = cell_mu<T, VarMu>(L, q[0], q[1], q[2]);
+      acc += mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+    }
+  }
+  const bool half = (p[C] == 0 && L.nat[2 * C]) || (p[C] == L.n[C] && L.nat[2 * C + 1]);
+  const T area = half ? (T)0.5 : (T)1;
+  // tangential links
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+    if (A == C || A >= L.dim) continue;
+    int q[3] = {p[0], p[1], p[2]};
+    // + direction: crosses A-face coordinate p[A]+1
+    {
+      T mu;
+      if (A == 0) mu = edge_mu<T, VarMu, C, 0>(L, p, p[A] + 1);
+      else if (A == 1) mu = edge_mu<T, VarMu, C, 1>(L, p, p[A] + 1);
+      else mu = edge_mu<T, VarMu, C, 2>(L, p, p[A] + 1);
+      if (p[A] + 1 < L.n[A]) {
+        q[A] = p[A] + 1;
+        acc += area * mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+      } else if (!L.nat[2 * A + 1]) {
+        acc += (T)2 * area * mu * xf;
+      }
+    }
+    // - direction: crosses A-face coordinate p[A]
+    {
+      T mu;
+      if (A == 0) mu = edge_mu<T, VarMu, C, 0>(L, p, p[A]);
+      else if (A == 1) mu = edge_mu<T, VarMu, C, 1>(L, p, p[A]);
+      else mu = edge_mu<T, VarMu, C, 2>(L, p, p[A]);
+      if (p[A] > 0) {
+        q[A] = p[A] - 1;
+        acc += area * mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+      } else if (!L.nat[2 * A]) {
+        acc += (T)2 * area * mu * xf;
+      }
+    }
+  }
+  return acc;
+}
+
+// Diagonal of W at an active face (divided by wscale).
+template <typename T, bool VarMu, int C>
+__device__ __forceinline__ T w_diag(const Lvl& L, const int p[3]) {
+  T acc = 0;
+  if (p[C] < L.n[C]) acc += cell_mu<T, VarMu>(L, p[0], p[1], p[2]);
+  if (p[C] > 0) {
+    int q[3] = {p[0], p[1], p[2]};
+    q[C] = p[C] - 1;
+    acc += cell_mu<T, VarMu>(L, q[0], q[1], q[2]);
+  }
+  const bool half = (p[C] == 0 && L.nat[2 * C]) || (p[C] == L.n[C] && L.nat[2 * C + 1]);
+  const T area = half ? (T)0.5 : (T)1;
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+    if (A == C || A >= L.dim) continue;
+    T mup, mum;
+    if (A == 0) { mup = edge_mu<T, VarMu, C, 0>(L, p, p[A] + 1); mum = edge_mu<T, VarMu, C, 0>(L, p, p[A]); }
+    else if (A == 1) { mup = edge_mu<T, VarMu, C, 1>(L, p, p[A] + 1); mum = edge_mu<T, VarMu, C, 1>(L, p, p[A]); }
+    else { mup = edge_mu<T, VarMu, C, 2>(L, p, p[A] + 1); mum = edge_mu<T, VarMu, C, 2>(L, p, p[A]); }
+    if (p[A] + 1 < L.n[A]) acc += area * mup; else if (!L.nat[2 * A + 1]) acc += (T)2 * area * mup;
+    if (p[A] > 0) acc += area * mum; else if (!L.nat[2 * A]) acc += (T)2 * area * mum;
+  }
+  return acc;
+}
+
+// number of in-domain cells adjacent to a face of component C (1 or 2)
+template <int C>
+__device__ __forceinline__ int face_cells(const Lvl& L, const int p[3]) {
+  return (p[C] < L.n[C] ? 1 : 0) + (p[C] > 0 ? 1 : 0);
+}
+
+// (M x)_f at an active face of component C: W row + gc * ascale^2 * grad(negdiv)
+template <typename T, bool VarMu, int C>
+__device__ __forceinline__ T m_row(const Lvl& L, const T* x, const int p[3]) {
+  const T xf = face_val<T, C>(L, x, p[0], p[1], p[2]);
+  T wv = w_row<T, VarMu, C>(L, x, p, xf) * (T)L.wscale;
+  if (L.gc == 0.0) return wv;
+  int q[3] = {p[0], p[1], p[2]};
+  T dplus = neg_div<T>(L, x, q[0], q[1], q[2]);
+  q[C] -= 1;
+  T dminus = neg_div<T>(L, x, q[0], q[1], q[2]);
+  const T g = (T)(L.gc * L.ascale * L.ascale);
+  return wv + g * (dplus - dminus);
+}
+
+}  // namespace gkb

@@ -1,0 +1,101 @@
+// kernels_inst.cuh - launch wrappers, instantiated for KT (see kernels_f64.cu).
+#pragma once
+#include "kernels_impl.cuh"
+
+namespace gkb {
+
+#define GKB_VARMU(L) ((sizeof(KT) == 8) ? (L.mu64 != nullptr) : (L.mu32 != nullptr))
+
+template <>
+long long Ops<KT>::face_blocks(const Lvl& L) {
+  dim3 g = face_grid(L);
+  return (long long)g.x * g.y * g.z;
+}
+
+template <>
+void Ops<KT>::apply(const Lvl& L, int mode, const KT* x, KT* y, cudaStream_t s) {
+  RedBuf red{nullptr, nullptr};
+  if (GKB_VARMU(L)) k_apply<KT, true, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, 0, nullptr);
+  else k_apply<KT, false, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, 0, nullptr);
+}
+
+template <>
+void Ops<KT>::apply_dot(const Lvl& L, int mode, const KT* x, KT* y, const RedBuf& red, int fin, void* st,
+                        cudaStream_t s) {
+  if (GKB_VARMU(L)) k_apply<KT, true, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, fin, st);
+  else k_apply<KT, false, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, fin, st);
+}
+
+template <>
+void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s) {
+  if (GKB_VARMU(L)) k_residual<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, x, b, r);
+  else k_residual<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, x, b, r);
+}
+
+template <>
+void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* table,
+                   cudaStream_t s) {
+  if (GKB_VARMU(L)) k_cheb<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, nullptr);
+  else k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
+}
+
+template <>
+void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStream_t s) {
+  if (GKB_VARMU(L)) k_patch<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, nullptr);
+  else k_patch<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, table);
+}
+
+template <>
+void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
+  k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
+}
+
+template <>
+void Ops<KT>::grad(const Lvl& L, const KT* p, KT* y, KT scale, cudaStream_t s) {
+  k_grad<KT><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, p, y, scale);
+}
+
+template <>
+void Ops<KT>::negdiv(const Lvl& L, const KT* x, KT* y, KT scale, cudaStream_t s) {
+  k_negdiv<KT><<<cell_grid(L), dim3(BX, BY), 0, s>>>(L, x, y, scale);
+}
+
+template <>
+void Ops<KT>::prolong(const Lvl& Lf, const Lvl& Lc, const KT* xc, KT* xf, cudaStream_t s) {
+  k_prolong<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
+}
+
+template <>
+void Ops<KT>::restrict_(const Lvl& Lf, const Lvl& Lc, const KT* rf, KT* bc, cudaStream_t s) {
+  k_restrict<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc);
+}
+
+template <>
+void Ops<KT>::coarse(int m, const KT* Minv, const int* idx, const KT* b, KT* x, cudaStream_t s) {
+  const int warps_per_block = 8;
+  k_coarse_solve<KT><<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(m, Minv, idx, b, x);
+}
+
+template <>
+void Ops<KT>::dot(long long len, const KT* a, const KT* b, const RedBuf& red, int fin, void* st, cudaStream_t s) {
+  k_dot<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, b, red, fin, st);
+}
+
+template <>
+void Ops<KT>::cg_update(long long len, KT* x, const KT* p, KT* r, const KT* q, const CgState* cg,
+                        const RedBuf& red, void* st, cudaStream_t s) {
+  k_cg_update<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, x, p, r, q, cg, red, st);
+}
+
+template <>
+void Ops<KT>::cg_dir(long long len, KT* p, const KT* z, const CgState* cg, int first, cudaStream_t s) {
+  k_cg_dir<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, p, z, cg, first);
+}
+
+template <>
+void Ops<KT>::axpby(long long len, KT a, const KT* x, KT b, KT* y, cudaStream_t s) {
+  k_axpby<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, x, b, y);
+}
+
+#undef GKB_VARMU
+}  // namespace gkb

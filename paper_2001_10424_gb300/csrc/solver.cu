@@ -1,0 +1,1098 @@
+// solver.cu - multigrid hierarchy, conjugate gradients and the GKB driver
+// (Algorithm 1 with the augmented-Lagrangian transform of Eq. (3) and the
+// lower-bound stopping rule of Eq. (5)), all running on the device; the host
+// only sequences launches.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <chrono>
+#include <cstdio>
+
+#include "solver.cuh"
+
+namespace gkb {
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    throw Error{e == cudaErrorMemoryAllocation ? GKB_ERR_OOM : GKB_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+
+static long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
+  Lvl L{};
+  L.dim = dim;
+  L.n[0] = n[0];
+  L.n[1] = n[1];
+  L.n[2] = (dim == 3) ? n[2] : 1;
+  for (int s = 0; s < 6; ++s) L.nat[s] = (s < 2 * dim) ? nat[s] : 0;
+  L.P = (int)round_up(n[0] + 1, 32);
+  L.S = (long long)(n[1] + 1) * L.P;
+  if (dim == 2) {
+    L.off[0] = 0;
+    L.off[1] = L.S;
+    L.off[2] = 2 * L.S;
+    L.nvel = 2 * L.S;
+  } else {
+    L.off[0] = 0;
+    L.off[1] = (long long)L.n[2] * L.S;
+    L.off[2] = 2LL * L.n[2] * L.S;
+    L.nvel = (3LL * L.n[2] + 1) * L.S;
+  }
+  L.ncell = (long long)L.n[2] * L.S;
+  L.h = h;
+  L.wscale = pow(h, dim - 2);
+  L.ascale = pow(h, dim - 1);
+  L.gc = gc;
+  L.mu0 = 1.0;
+  L.mu64 = nullptr;
+  L.mu32 = nullptr;
+  return L;
+}
+
+template <typename T> static void set_mu(Lvl& L, const T* mu);
+template <> void set_mu<double>(Lvl& L, const double* mu) { L.mu64 = mu; L.mu32 = nullptr; }
+template <> void set_mu<float>(Lvl& L, const float* mu) { L.mu32 = mu; L.mu64 = nullptr; }
+
+// ---------------------------------------------------------------------------
+// layout kernels (compact ordering <-> padded layout)
+// ---------------------------------------------------------------------------
+
+struct Compact {
+  int dim;
+  int lo[3][3];    // low corner of the active box of component c
+  int ext[3][3];   // extents of that box
+  long long base[3];
+  long long m;
+};
+
+static Compact make_compact(const Lvl& L) {
+  Compact c{};
+  c.dim = L.dim;
+  long long off = 0;
+  for (int comp = 0; comp < L.dim; ++comp) {
+    for (int a = 0; a < 3; ++a) {
+      if (a >= L.dim) { c.lo[comp][a] = 0; c.ext[comp][a] = 1; continue; }
+      if (a == comp) {
+        const int lo = L.nat[2 * a] ? 0 : 1;
+        const int hi = L.nat[2 * a + 1] ? L.n[a] : L.n[a] - 1;
+        c.lo[comp][a] = lo;
+        c.ext[comp][a] = hi - lo + 1;
+      } else {
+        c.lo[comp][a] = 0;
+        c.ext[comp][a] = L.n[a];
+      }
+    }
+    c.base[comp] = off;
+    off += (long long)c.ext[comp][0] * c.ext[comp][1] * c.ext[comp][2];
+  }
+  c.m = off;
+  return c;
+}
+
+__device__ __forceinline__ long long compact_to_padded(const Lvl& L, const Compact& c, long long t) {
+  int comp = 0;
+  if (c.dim == 3 && t >= c.base[2]) comp = 2;
+  else if (t >= c.base[1]) comp = 1;
+  const long long l = t - c.base[comp];
+  const int ex = c.ext[comp][0], ey = c.ext[comp][1];
+  const long long row = l / ex;
+  const int i = (int)(l - row * ex) + c.lo[comp][0];
+  const long long pl = row / ey;
+  const int j = (int)(row - pl * ey) + c.lo[comp][1];
+  const int k = (int)pl + c.lo[comp][2];
+  return L.off[comp] + cix(L, i, j, k);
+}
+
+template <typename TO>
+__global__ void k_pack_vel(Lvl L, Compact c, const double* __restrict__ src, TO* __restrict__ dst) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < c.m; t += (long long)gridDim.x * blockDim.x)
+    dst[compact_to_padded(L, c, t)] = (TO)src[t];
+}
+__global__ void k_unpack_vel(Lvl L, Compact c, const double* __restrict__ src, double* __restrict__ dst) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < c.m; t += (long long)gridDim.x * blockDim.x)
+    dst[t] = src[compact_to_padded(L, c, t)];
+}
+template <typename TO>
+__global__ void k_pack_cell(Lvl L, const double* __restrict__ src, TO* __restrict__ dst) {
+  const long long n = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / L.n[0];
+    const int i = (int)(t - row * L.n[0]);
+    const int k = (int)(row / L.n[1]);
+    const int j = (int)(row - (long long)k * L.n[1]);
+    dst[cix(L, i, j, k)] = (TO)src[t];
+  }
+}
+__global__ void k_unpack_cell(Lvl L, const double* __restrict__ src, double* __restrict__ dst, double shift) {
+  const long long n = (long long)L.n[0] * L.n[1] * L.n[2];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / L.n[0];
+    const int i = (int)(t - row * L.n[0]);
+    const int k = (int)(row / L.n[1]);
+    const int j = (int)(row - (long long)k * L.n[1]);
+    dst[t] = src[cix(L, i, j, k)] - shift;
+  }
+}
+
+// coarse viscosity: mean of the 2^d fine cells
+template <typename T>
+__global__ void k_mu_coarsen(Lvl Lf, Lvl Lc, const T* __restrict__ muf, T* __restrict__ muc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int K = blockIdx.z;
+  if (I >= Lc.n[0] || J >= Lc.n[1]) return;
+  const int nz = (Lf.dim == 3) ? 2 : 1;
+  T s = 0;
+  for (int dz = 0; dz < nz; ++dz)
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) s += muf[cix(Lf, 2 * I + dx, 2 * J + dy, Lf.dim == 3 ? 2 * K + dz : 0)];
+  muc[cix(Lc, I, J, K)] = s / (T)(4 * nz);
+}
+
+// deterministic pseudo-random start vector for the power iteration
+template <typename T>
+__global__ void k_fill_hash(Lvl L, T* x) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y;
+  const int k = blockIdx.z;
+  for (int c = 0; c < L.dim; ++c) {
+    bool act = (c == 0) ? face_active<0>(L, i, j, k) : (c == 1) ? face_active<1>(L, i, j, k) : face_active<2>(L, i, j, k);
+    if (!act) continue;
+    unsigned long long hsh = (unsigned long long)(L.off[c] + cix(L, i, j, k)) * 0x9E3779B97F4A7C15ull + 12345u;
+    hsh ^= hsh >> 31; hsh *= 0xBF58476D1CE4E5B9ull; hsh ^= hsh >> 29;
+    x[L.off[c] + cix(L, i, j, k)] = (T)((double)(hsh >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+  }
+}
+
+static dim3 fgrid(const Lvl& L) {
+  const int nz = (L.dim == 3) ? L.n[2] + 1 : 1;
+  return dim3((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 7) / 8, nz);
+}
+
+static void read_scalars(double* dev, double* host, int n, cudaStream_t s) {
+  GKB_CUDA(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+}
+
+// ---------------------------------------------------------------------------
+// multigrid hierarchy
+// ---------------------------------------------------------------------------
+
+template <typename T>
+void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, const RedBuf& red,
+                   double* scratch, cudaStream_t s) {
+  degree = deg;
+  lev.clear();
+  lev.reserve(32);
+  lev.emplace_back();
+  lev[0].L = fine;
+  set_mu<T>(lev[0].L, fine_mu);
+  // coarsen while every side is even, halves to >= 2 cells and the longest
+  // side exceeds coarse_max (halved in 3D to keep the dense coarse solve small)
+  const int cmax = (fine.dim == 3) ? std::max(4, coarse_max / 2) : coarse_max;
+  for (;;) {
+    const Lvl& Lf = lev.back().L;
+    bool can = true;
+    int nmax = 0;
+    for (int a = 0; a < Lf.dim; ++a) {
+      if (Lf.n[a] % 2 != 0 || Lf.n[a] / 2 < 2) can = false;
+      nmax = std::max(nmax, Lf.n[a]);
+    }
+    if (!can || nmax <= cmax) break;
+    int nc[3] = {Lf.n[0] / 2, Lf.n[1] / 2, Lf.dim == 3 ? Lf.n[2] / 2 : 1};
+    const double gc = Lf.gc / (Lf.dim == 3 ? 8.0 : 4.0);
+    Lvl Lc = make_level(Lf.dim, nc, 2.0 * Lf.h, Lf.nat, gc);
+    Lc.mu0 = Lf.mu0;
+    lev.emplace_back();
+    Level& C = lev.back();
+    C.L = Lc;
+    const T* fmu = (sizeof(T) == 8) ? (const T*)lev[lev.size() - 2].L.mu64 : (const T*)lev[lev.size() - 2].L.mu32;
+    if (fmu) {
+      C.mu.alloc(Lc.ncell);
+      dim3 g((nc[0] + 31) / 32, (nc[1] + 7) / 8, Lc.n[2]);
+      k_mu_coarsen<T><<<g, dim3(32, 8), 0, s>>>(lev[lev.size() - 2].L, Lc, fmu, C.mu.p);
+      GKB_CUDA(cudaGetLastError());
+      set_mu<T>(C.L, C.mu.p);
+    }
+  }
+  const int nl = (int)lev.size();
+  for (int l = 0; l < nl; ++l) {
+    Level& V = lev[l];
+    if (l > 0) { V.x.alloc(V.L.nvel); V.b.alloc(V.L.nvel); }
+    if (l < nl - 1) {
+      V.r.alloc(V.L.nvel);
+      V.d.alloc(V.L.nvel);
+      const bool var = (sizeof(T) == 8) ? V.L.mu64 != nullptr : V.L.mu32 != nullptr;
+      if (!var) {
+        V.table.alloc(3 * 75 * 16);
+        Ops<T>::patch_table(V.L, V.table.p, s);
+        GKB_CUDA(cudaGetLastError());
+      }
+    }
+  }
+  // power iteration for lambda_max(C M) on every smoothing level
+  for (int l = 0; l < nl - 1; ++l) {
+    Level& V = lev[l];
+    DevBuf<T> xv, zv, zero;
+    xv.alloc(V.L.nvel);
+    zv.alloc(V.L.nvel);
+    zero.alloc(V.L.nvel);
+    k_fill_hash<T><<<fgrid(V.L), dim3(32, 8), 0, s>>>(V.L, xv.p);
+    GKB_CUDA(cudaGetLastError());
+    double hs[4];
+    double lam = 0;
+    for (int it = 0; it < 16; ++it) {
+      Ops<T>::residual(V.L, xv.p, zero.p, V.r.p, s);       // r = -M x
+      Ops<T>::patch(V.L, V.r.p, zv.p, V.table.p, s);       // z = -C M x
+      Ops<T>::dot(V.L.nvel, zv.p, zv.p, red, FIN_STORE, scratch, s);
+      read_scalars(scratch, hs, 1, s);
+      const double zn = sqrt(hs[0]);
+      Ops<T>::dot(V.L.nvel, xv.p, xv.p, red, FIN_STORE, scratch, s);
+      read_scalars(scratch, hs + 1, 1, s);
+      const double xn = sqrt(hs[1]);
+      if (!(zn > 0) || !(xn > 0)) break;
+      lam = zn / xn;
+      Ops<T>::axpby(V.L.nvel, (T)(-1.0 / zn), zv.p, (T)0, xv.p, s);
+    }
+    GKB_CUDA(cudaGetLastError());
+    V.lam_max = lam;
+    const double hi = cheb_hi * lam, lo = cheb_lo * lam;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    V.ca.assign(deg, 0.0);
+    V.cb.assign(deg, 0.0);
+    double rho = 1.0 / sigma;
+    V.ca[0] = 1.0 / theta;
+    V.cb[0] = 0.0;
+    for (int k = 1; k < deg; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      V.ca[k] = 2.0 * rn / delta;
+      V.cb[k] = rn * rho;
+      rho = rn;
+    }
+  }
+  // coarsest level: dense M by probing with unit vectors, inverted on host
+  Level& Cl = lev.back();
+  const Lvl& L = Cl.L;
+  Compact cmp = make_compact(L);
+  const int m = (int)cmp.m;
+  if (m > 4096) throw Error{GKB_ERR_INVALID_ARG, "coarsest multigrid level too large (" + std::to_string(m) + " unknowns)"};
+  coarse_m = m;
+  std::vector<long long> pidx(m);
+  {
+    int t = 0;
+    for (int comp = 0; comp < L.dim; ++comp)
+      for (int k = 0; k < cmp.ext[comp][2]; ++k)
+        for (int j = 0; j < cmp.ext[comp][1]; ++j)
+          for (int i = 0; i < cmp.ext[comp][0]; ++i)
+            pidx[t++] = L.off[comp] + cix(L, i + cmp.lo[comp][0], j + cmp.lo[comp][1], k + cmp.lo[comp][2]);
+  }
+  std::vector<double> A((size_t)m * m);
+  {
+    DevBuf<T> e, y;
+    e.alloc(L.nvel);
+    y.alloc(L.nvel);
+    std::vector<T> hy(L.nvel);
+    const T one = (T)1;
+    for (int c = 0; c < m; ++c) {
+      GKB_CUDA(cudaMemsetAsync(e.p, 0, L.nvel * sizeof(T), s));
+      GKB_CUDA(cudaMemcpyAsync(e.p + pidx[c], &one, sizeof(T), cudaMemcpyHostToDevice, s));
+      Ops<T>::apply(L, 1, e.p, y.p, s);
+      GKB_CUDA(cudaMemcpyAsync(hy.data(), y.p, L.nvel * sizeof(T), cudaMemcpyDeviceToHost, s));
+      GKB_CUDA(cudaStreamSynchronize(s));
+      for (int r = 0; r < m; ++r) A[(size_t)r * m + c] = (double)hy[pidx[r]];
+    }
+  }
+  // symmetrise, Cholesky, explicit inverse
+  for (int r = 0; r < m; ++r)
+    for (int c = r + 1; c < m; ++c) {
+      const double a = 0.5 * (A[(size_t)r * m + c] + A[(size_t)c * m + r]);
+      A[(size_t)r * m + c] = A[(size_t)c * m + r] = a;
+    }
+  std::vector<double> Lc((size_t)m * m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    double sjj = A[(size_t)j * m + j];
+    for (int k = 0; k < j; ++k) sjj -= Lc[(size_t)j * m + k] * Lc[(size_t)j * m + k];
+    if (!(sjj > 0)) throw Error{GKB_ERR_NOT_SPD, "coarse-level matrix is not positive definite"};
+    const double ljj = sqrt(sjj);
+    Lc[(size_t)j * m + j] = ljj;
+    for (int i = j + 1; i < m; ++i) {
+      double sij = A[(size_t)i * m + j];
+      for (int k = 0; k < j; ++k) sij -= Lc[(size_t)i * m + k] * Lc[(size_t)j * m + k];
+      Lc[(size_t)i * m + j] = sij / ljj;
+    }
+  }
+  std::vector<double> inv((size_t)m * m, 0.0), col(m);
+  for (int c = 0; c < m; ++c) {
+    for (int i = 0; i < m; ++i) {
+      double sv = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) sv -= Lc[(size_t)i * m + k] * col[k];
+      col[i] = sv / Lc[(size_t)i * m + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double sv = col[i];
+      for (int k = i + 1; k < m; ++k) sv -= Lc[(size_t)k * m + i] * col[k];
+      col[i] = sv / Lc[(size_t)i * m + i];
+    }
+    for (int i = 0; i < m; ++i) inv[(size_t)i * m + c] = col[i];
+  }
+  std::vector<T> invT((size_t)m * m);
+  for (size_t t = 0; t < invT.size(); ++t) invT[t] = (T)(0.5 * (inv[t] + inv[(t % m) * m + t / m]));
+  coarse_inv.alloc((size_t)m * m);
+  GKB_CUDA(cudaMemcpyAsync(coarse_inv.p, invT.data(), invT.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  std::vector<int> idx32(m);
+  for (int i = 0; i < m; ++i) idx32[i] = (int)pidx[i];
+  coarse_idx.alloc(m);
+  GKB_CUDA(cudaMemcpyAsync(coarse_idx.p, idx32.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+}
+
+template <typename T>
+void Gmg<T>::smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s) {
+  Level& V = lev[l];
+  for (int k = 0; k < degree; ++k) {
+    const T* r;
+    if (k == 0 && x_zero) r = b;
+    else {
+      Ops<T>::residual(V.L, x, b, V.r.p, s);
+      r = V.r.p;
+    }
+    Ops<T>::cheb(V.L, r, x, V.d.p, (T)V.ca[k], (T)V.cb[k], (k == 0 && x_zero) ? 1 : 0, V.table.p, s);
+  }
+}
+
+template <typename T>
+void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s) {
+  const int nl = (int)lev.size();
+  if (nl == 1) {
+    Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, r0, z0, s);
+    return;
+  }
+  for (int l = 0; l < nl - 1; ++l) {
+    const T* b = (l == 0) ? r0 : lev[l].b.p;
+    T* x = (l == 0) ? z0 : lev[l].x.p;
+    smooth(l, b, x, true, s);
+    Ops<T>::residual(lev[l].L, x, b, lev[l].r.p, s);
+    Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, s);
+  }
+  Level& Cl = lev[nl - 1];
+  Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, Cl.b.p, Cl.x.p, s);
+  for (int l = nl - 2; l >= 0; --l) {
+    const T* b = (l == 0) ? r0 : lev[l].b.p;
+    T* x = (l == 0) ? z0 : lev[l].x.p;
+    Ops<T>::prolong(lev[l].L, lev[l + 1].L, lev[l + 1].x.p, x, s);
+    smooth(l, b, x, false, s);
+  }
+}
+
+template struct Gmg<double>;
+template struct Gmg<float>;
+
+// ---------------------------------------------------------------------------
+// conjugate gradients (host-sequenced, device scalars)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+void Cg<T>::init(const Lvl& L_, Gmg<T>* pre_, const RedBuf& red_, CgState* st_dev, CgState* st_host) {
+  L = L_;
+  pre = pre_;
+  red = red_;
+  st = st_dev;
+  host = st_host;
+  r.alloc(L.nvel);
+  p.alloc(L.nvel);
+  q.alloc(L.nvel);
+  if (pre) z.alloc(L.nvel);
+}
+
+template <typename T>
+int Cg<T>::solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* iters) {
+  const long long len = L.nvel;
+  CgState h{};
+  h.tol2 = tol * tol;
+  h.maxit = maxit;
+  GKB_CUDA(cudaMemcpyAsync(st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaMemsetAsync(x, 0, len * sizeof(T), s));
+  GKB_CUDA(cudaMemcpyAsync(r.p, f, len * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  Ops<T>::dot(len, f, f, red, FIN_CG_INIT, st, s);
+  T* zp = pre ? z.p : r.p;
+  if (pre) pre->vcycle(r.p, zp, s);
+  Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ0, st, s);
+  Ops<T>::cg_dir(len, p.p, zp, st, 1, s);
+  GKB_CUDA(cudaMemcpyAsync(host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  while (!host->done) {
+    Ops<T>::apply_dot(L, 1, p.p, q.p, red, FIN_CG_PAP, st, s);
+    Ops<T>::cg_update(len, x, p.p, r.p, q.p, st, red, st, s);
+    GKB_CUDA(cudaMemcpyAsync(host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    GKB_CUDA(cudaStreamSynchronize(s));
+    if (host->done) break;
+    if (pre) pre->vcycle(r.p, zp, s);
+    Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
+    Ops<T>::cg_dir(len, p.p, zp, st, 0, s);
+  }
+  if (iters) *iters = host->it;
+  return host->status;
+}
+
+template struct Cg<double>;
+template struct Cg<float>;
+
+// ---------------------------------------------------------------------------
+// GKB kernels (FP64)
+// ---------------------------------------------------------------------------
+
+constexpr int CB = 256;
+
+static dim3 cgrid(const Lvl& L) { return dim3((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]); }
+
+// b = r - A^T y0 ; reduce sum b^2, sum b
+__global__ void __launch_bounds__(256) k_gkb_b(Lvl L, const double* __restrict__ rc, const double* __restrict__ y0,
+                                               double* __restrict__ b, RedBuf red, double* out) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  double v[2] = {0.0, 0.0};
+  if (i < L.n[0] && j < L.n[1]) {
+    const long long id = cix(L, i, j, k);
+    const double bv = rc[id] - L.ascale * neg_div<double>(L, y0, i, j, k);
+    b[id] = bv;
+    v[0] = bv * bv;
+    v[1] = bv;
+  }
+  grid_reduce<2>(v, red, FIN_STORE, out);
+}
+
+// g = N^-1 A^T v - alpha q ; reduce sum g^2, sum g
+__global__ void __launch_bounds__(256) k_gk1(Lvl L, const double* __restrict__ v, const double* __restrict__ q,
+                                             double* __restrict__ gq, const GkbState* st, RedBuf red, double* out) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  double acc[2] = {0.0, 0.0};
+  if (i < L.n[0] && j < L.n[1]) {
+    const long long id = cix(L, i, j, k);
+    const double g = L.ascale * neg_div<double>(L, v, i, j, k) / st->n_scale - st->alpha * q[id];
+    gq[id] = g;
+    acc[0] = g * g;
+    acc[1] = g;
+  }
+  grid_reduce<2>(acc, red, FIN_STORE, out);
+}
+
+// f = A q_{k+1} with q_{k+1} = (g - mean) / beta (mean cancels on active faces)
+__global__ void __launch_bounds__(256) k_gk2(Lvl L, const double* __restrict__ gq, double* __restrict__ f,
+                                             const GkbState* st) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const double sc = (st->beta > 0.0 && !st->stop) ? L.ascale / st->beta : 0.0;
+  const double mean = st->mean;
+#define GKB_GK2(C, DI, DJ, DK)                                                   \
+  {                                                                              \
+    bool store = (L.dim == 2) ? (k == 0 && i <= L.n[0] && j <= L.n[1])           \
+                              : (i <= L.n[0] && j <= L.n[1] && (C == 2 ? k <= L.n[2] : k < L.n[2])); \
+    if (store) {                                                                 \
+      double val = 0.0;                                                          \
+      if (face_active<C>(L, i, j, k)) {                                          \
+        const double pp = cell_in(L, i, j, k) ? gq[cix(L, i, j, k)] - mean : 0.0; \
+        const double pm = cell_in(L, i - DI, j - DJ, k - DK) ? gq[cix(L, i - DI, j - DJ, k - DK)] - mean : 0.0; \
+        val = sc * (pp - pm);                                                    \
+      }                                                                          \
+      f[L.off[C] + cix(L, i, j, k)] = val;                                       \
+    }                                                                            \
+  }
+  GKB_GK2(0, 1, 0, 0)
+  GKB_GK2(1, 0, 1, 0)
+  if (L.dim == 3) GKB_GK2(2, 0, 0, 1)
+#undef GKB_GK2
+}
+
+// w = x - beta v
+__global__ void __launch_bounds__(CB) k_gk3(long long len, const double* __restrict__ x, const double* __restrict__ v,
+                                            double* __restrict__ w, const GkbState* st) {
+  const double beta = st->stop && st->beta == 0.0 ? 0.0 : st->beta;
+  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB)
+    w[t] = x[t] - beta * v[t];
+}
+
+// v = w / alpha ; u += zeta v     (first: u = zeta v)
+__global__ void __launch_bounds__(CB) k_gk4v(long long len, const double* __restrict__ w, double* __restrict__ v,
+                                             double* __restrict__ u, const GkbState* st, int first) {
+  if (st->stop && st->converged && st->alpha == 0.0) return;
+  if (st->status != 0) return;
+  const double ia = 1.0 / st->alpha, z = st->zeta;
+  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB) {
+    const double vn = w[t] * ia;
+    v[t] = vn;
+    u[t] = first ? z * vn : u[t] + z * vn;
+  }
+}
+
+// q = (g - mean) / beta ; d = (q - beta d) / alpha ; p -= zeta d   (first: d = q / alpha, p = -zeta d)
+__global__ void __launch_bounds__(256) k_gk4c(Lvl L, const double* __restrict__ gq, double* __restrict__ q,
+                                              double* __restrict__ d, double* __restrict__ p, const GkbState* st,
+                                              int first) {
+  if (st->stop && st->converged && st->alpha == 0.0) return;
+  if (st->status != 0) return;
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (i >= L.n[0] || j >= L.n[1]) return;
+  const long long id = cix(L, i, j, k);
+  const double ia = 1.0 / st->alpha, z = st->zeta, beta = st->beta;
+  if (first) {
+    const double dn = q[id] * ia;
+    d[id] = dn;
+    p[id] = -z * dn;
+  } else {
+    const double qn = (gq[id] - st->mean) / beta;
+    q[id] = qn;
+    const double dn = (qn - beta * d[id]) * ia;
+    d[id] = dn;
+    p[id] -= z * dn;
+  }
+}
+
+// q1 = (b - mean) / (n_scale beta1)
+__global__ void __launch_bounds__(256) k_gkb_q1(Lvl L, const double* __restrict__ b, double* __restrict__ q,
+                                                const GkbState* st) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (i >= L.n[0] || j >= L.n[1]) return;
+  const long long id = cix(L, i, j, k);
+  q[id] = (st->beta > 0.0) ? (b[id] - st->mean) / (st->n_scale * st->beta) : 0.0;
+}
+
+enum { S_BETA1 = 0, S_ALPHA1 = 1, S_BETA = 2, S_ALPHA = 3 };
+
+__device__ void hist_put(double* h, int cap, int i, double v) {
+  if (h && i >= 0 && i < cap) h[i] = v;
+}
+
+// scalar part of Algorithm 1 and the stopping rule (single thread)
+__global__ void k_gkb_scalar(int op, GkbState* st, const double* red) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  GkbState& S = *st;
+  switch (op) {
+    case S_BETA1: {
+      // beta_1 = ||b||_{N^-1} on the mean-free b
+      const double mean = S.enclosed ? red[1] / S.ncells : 0.0;
+      double s2 = red[0] - S.ncells * mean * mean;
+      if (s2 < 0) s2 = 0;
+      S.mean = mean;
+      S.beta = sqrt(s2 / S.n_scale);
+      hist_put(S.h_beta, S.hcap, 0, S.beta);
+      if (!isfinite(S.beta)) { S.status = ST_NAN; S.stop = 1; }
+      else if (S.beta == 0.0) { S.stop = 1; S.converged = 1; }
+    } break;
+    case S_ALPHA1: {
+      const double a2 = red[0];
+      if (!isfinite(a2)) { S.status = ST_NAN; S.stop = 1; break; }
+      if (!(a2 > 0.0)) {
+        if (a2 < 0.0) S.status = ST_NOT_SPD;
+        S.alpha = 0.0; S.stop = 1; S.converged = (a2 == 0.0);
+        break;
+      }
+      S.alpha = sqrt(a2);
+      S.zeta = S.beta / S.alpha;
+      S.K = 1;
+      S.zsum = S.zeta * S.zeta;
+      S.ring[1 % GKB_RING] = S.zeta * S.zeta;
+      hist_put(S.h_alpha, S.hcap, 0, S.alpha);
+      hist_put(S.h_zeta, S.hcap, 0, S.zeta);
+      if (S.maxit <= 0) S.stop = 1;
+    } break;
+    case S_BETA: {
+      // beta_{k+1} = ||g||_N on the mean-free g
+      S.k += 1;
+      const double mean = S.enclosed ? red[1] / S.ncells : 0.0;
+      double s2 = red[0] - S.ncells * mean * mean;
+      if (s2 < 0) s2 = 0;
+      S.mean = mean;
+      S.beta = sqrt(S.n_scale * s2);
+      hist_put(S.h_beta, S.hcap, S.k, S.beta);
+      if (!isfinite(S.beta)) { S.status = ST_NAN; S.stop = 1; }
+      else if (S.beta == 0.0) { S.stop = 1; S.converged = 1; S.alpha = 0.0; }
+    } break;
+    case S_ALPHA: {
+      if (S.stop) break;  // breakdown already handled
+      const double a2 = red[0];
+      if (!isfinite(a2)) { S.status = ST_NAN; S.stop = 1; break; }
+      if (!(a2 > 0.0)) {
+        if (a2 < 0.0) S.status = ST_NOT_SPD;
+        S.alpha = 0.0; S.stop = 1; S.converged = (a2 == 0.0);
+        break;
+      }
+      S.alpha = sqrt(a2);
+      S.zeta = -S.beta / S.alpha * S.zeta;
+      S.K += 1;
+      const double z2 = S.zeta * S.zeta;
+      S.zsum += z2;
+      S.ring[S.K % GKB_RING] = z2;
+      double tail = 0.0;
+      const int j0 = (S.K - S.delay > 1) ? S.K - S.delay : 1;
+      for (int j = j0; j <= S.K; ++j) tail += S.ring[j % GKB_RING];
+      S.est = sqrt(tail / S.zsum);
+      hist_put(S.h_alpha, S.hcap, S.k, S.alpha);
+      hist_put(S.h_zeta, S.hcap, S.K - 1, S.zeta);
+      hist_put(S.h_est, S.hcap, S.k - 1, S.est);
+      if (S.est <= S.tol) { S.converged = 1; S.stop = 1; }
+      else if (S.k >= S.maxit) S.stop = 1;
+    } break;
+  }
+}
+
+// pressure sum for the mean-zero projection
+__global__ void __launch_bounds__(256) k_cell_sum(Lvl L, const double* __restrict__ p, RedBuf red, double* out) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  double v[1] = {0.0};
+  if (i < L.n[0] && j < L.n[1]) v[0] = p[cix(L, i, j, k)];
+  grid_reduce<1>(v, red, FIN_STORE, out);
+}
+
+// mixed precision: FP32 rhs r32 = r64 / ||r64|| ; x64 += ||r64|| e32
+__global__ void __launch_bounds__(CB) k_to_f32(long long len, const double* __restrict__ r, float* __restrict__ o,
+                                               const double* nrm2) {
+  const double s = (*nrm2 > 0.0) ? 1.0 / sqrt(*nrm2) : 0.0;
+  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB)
+    o[t] = (float)(r[t] * s);
+}
+__global__ void __launch_bounds__(CB) k_add_f32(long long len, const float* __restrict__ e, double* __restrict__ x,
+                                                const double* nrm2) {
+  const double s = sqrt(*nrm2);
+  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB)
+    x[t] += s * (double)e[t];
+}
+
+// ---------------------------------------------------------------------------
+// Solver
+// ---------------------------------------------------------------------------
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) { (void)cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static unsigned lin_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 1216) b = 1216;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+Solver::~Solver() {
+  if (cg_host) cudaFreeHost(cg_host);
+  if (gkb_host) cudaFreeHost(gkb_host);
+}
+
+void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_, double gamma_, double n_scale_) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!g) throw Error{GKB_ERR_INVALID_ARG, "grid is NULL"};
+  if (g->dim != 2 && g->dim != 3) throw Error{GKB_ERR_INVALID_ARG, "dim must be 2 or 3"};
+  for (int a = 0; a < g->dim; ++a)
+    if (g->n[a] < 2) throw Error{GKB_ERR_INVALID_ARG, "every side needs at least 2 cells"};
+  if (!(g->h > 0)) throw Error{GKB_ERR_INVALID_ARG, "h must be positive"};
+  for (int s = 0; s < 2 * g->dim; ++s)
+    if (g->bc[s] != GKB_BC_DIRICHLET && g->bc[s] != GKB_BC_NATURAL) throw Error{GKB_ERR_INVALID_ARG, "bad boundary type"};
+  if (!(gamma_ >= 0)) throw Error{GKB_ERR_INVALID_ARG, "gamma must be >= 0"};
+  if (!viscosity && !(mu0_ > 0)) throw Error{GKB_ERR_INVALID_ARG, "mu0 must be positive"};
+  have_problem = false;
+  grid = *g;
+  gamma = gamma_;
+  mu0 = mu0_;
+  n_scale = (n_scale_ > 0) ? n_scale_ : pow(g->h, g->dim);
+  int nat[6] = {0, 0, 0, 0, 0, 0};
+  enclosed = true;
+  for (int s = 0; s < 2 * g->dim; ++s) { nat[s] = g->bc[s] == GKB_BC_NATURAL; if (nat[s]) enclosed = false; }
+  if (opt.inner == GKB_INNER_GMG_PCG && !enclosed)
+    throw Error{GKB_ERR_INVALID_ARG, "the multigrid preconditioner needs Dirichlet velocity on every side"};
+  int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
+  L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
+  L64.mu0 = viscosity ? 1.0 : mu0;
+  Compact cmp = make_compact(L64);
+  m = cmp.m;
+  ncell = (int64_t)n3[0] * n3[1] * n3[2];
+  // viscosity
+  mu64.release();
+  mu32.release();
+  const bool mixed = opt.precision == GKB_PREC_MIXED;
+  if (viscosity) {
+    DevBuf<double> tmp;
+    tmp.alloc(ncell);
+    GKB_CUDA(cudaMemcpyAsync(tmp.p, viscosity, ncell * sizeof(double), cudaMemcpyDefault, stream));
+    mu64.alloc(L64.ncell);
+    k_pack_cell<double><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, mu64.p);
+    if (mixed) {
+      mu32.alloc(L64.ncell);
+      k_pack_cell<float><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, mu32.p);
+    }
+    GKB_CUDA(cudaStreamSynchronize(stream));
+    std::vector<double> hv(ncell);
+    GKB_CUDA(cudaMemcpy(hv.data(), tmp.p, ncell * sizeof(double), cudaMemcpyDeviceToHost));
+    for (double vv : hv)
+      if (!(vv > 0) || !std::isfinite(vv)) throw Error{GKB_ERR_INVALID_ARG, "viscosity must be positive and finite"};
+  }
+  L64.mu64 = mu64.p;
+  L32 = L64;
+  L32.mu64 = nullptr;
+  L32.mu32 = mu32.p;
+  // reduction scratch: enough partials for every launch shape used
+  long long blocks = std::max<long long>(Ops<double>::face_blocks(L64), blas_blocks(L64.nvel));
+  blocks = std::max<long long>(blocks, (long long)cgrid(L64).x * cgrid(L64).y * cgrid(L64).z);
+  red_partial.alloc((size_t)blocks * 4 + 64);
+  red_ticket.alloc(1);
+  red = RedBuf{red_partial.p, red_ticket.p};
+  scal.alloc(16);
+  if (!cg_host) {
+    GKB_CUDA(cudaMallocHost(&cg_host, sizeof(CgState)));
+    GKB_CUDA(cudaMallocHost(&gkb_host, sizeof(GkbState)));
+  }
+  state_mem.alloc(sizeof(CgState) + sizeof(GkbState) + 256);
+  cg_dev = (CgState*)state_mem.p;
+  gkb_dev = (GkbState*)(state_mem.p + ((sizeof(CgState) + 127) / 128) * 128);
+  // multigrid + CG
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG;
+  stats = gkb_stats_t{};
+  if (mixed) {
+    if (use_gmg) gmg32.build(L32, mu32.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
+    cg32.init(L32, use_gmg ? &gmg32 : nullptr, red, cg_dev, cg_host);
+    r64.alloc(L64.nvel);
+    f32.alloc(L64.nvel);
+    x32.alloc(L64.nvel);
+    stats.levels = use_gmg ? (int)gmg32.lev.size() : 0;
+  } else {
+    if (use_gmg) gmg64.build(L64, mu64.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
+    cg64.init(L64, use_gmg ? &gmg64 : nullptr, red, cg_dev, cg_host);
+    stats.levels = use_gmg ? (int)gmg64.lev.size() : 0;
+  }
+  // GKB vectors
+  for (DevBuf<double>* b : {&u, &v, &x, &w, &t, &f, &y0, &wtmp}) b->alloc(L64.nvel);
+  for (DevBuf<double>* b : {&q, &d, &pp, &gq, &bc, &ctmp}) b->alloc(L64.ncell);
+  stage_m.alloc(m);
+  stage_n.alloc(ncell);
+  hist.alloc(4 * (size_t)(opt.maxit + 2));
+  GKB_CUDA(cudaStreamSynchronize(stream));
+  have_problem = true;
+  stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+int Solver::inner_solve(const double* fpad, double* xpad) {
+  int its = 0, st = 0;
+  if (opt.precision == GKB_PREC_MIXED) {
+    // FP64 iterative refinement around FP32 CG: x = 0, r = f; repeat
+    // { e = M32^-1 (r / ||r||) ; x += ||r|| e ; r = f - M x (FP64) }
+    const long long len = L64.nvel;
+    GKB_CUDA(cudaMemsetAsync(xpad, 0, len * sizeof(double), stream));
+    GKB_CUDA(cudaMemcpyAsync(r64.p, fpad, len * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+    Ops<double>::dot(len, fpad, fpad, red, FIN_STORE, scal.p + 4, stream);
+    double hs[8];
+    read_scalars(scal.p + 4, hs, 1, stream);
+    const double ff = hs[0];
+    if (ff == 0.0) { inner_its.push_back(0); return ST_OK; }
+    double rr = ff;
+    const int max_refine = 60;
+    int ref = 0;
+    while (rr > opt.tol_inner * opt.tol_inner * ff) {
+      if (ref++ >= max_refine) { st = ST_INNER_NOT_CONVERGED; break; }
+      GKB_CUDA(cudaMemcpyAsync(scal.p + 8, &rr, sizeof(double), cudaMemcpyHostToDevice, stream));
+      k_to_f32<<<lin_blocks(len), CB, 0, stream>>>(len, r64.p, f32.p, scal.p + 8);
+      int it = 0;
+      int s32 = cg32.solve(f32.p, x32.p, opt.mixed_rtol, opt.maxit_inner, stream, &it);
+      its += it;
+      if (s32 != ST_OK && s32 != ST_INNER_NOT_CONVERGED) { st = s32; break; }
+      k_add_f32<<<lin_blocks(len), CB, 0, stream>>>(len, x32.p, xpad, scal.p + 8);
+      Ops<double>::residual(L64, xpad, fpad, r64.p, stream);
+      Ops<double>::dot(len, r64.p, r64.p, red, FIN_STORE, scal.p + 4, stream);
+      read_scalars(scal.p + 4, hs, 1, stream);
+      if (!std::isfinite(hs[0])) { st = ST_NAN; break; }
+      rr = hs[0];
+    }
+    stats.inner_iterations += its;
+  } else {
+    st = cg64.solve(fpad, xpad, opt.tol_inner, opt.maxit_inner, stream, &its);
+    stats.inner_iterations += its;
+  }
+  stats.inner_solves += 1;
+  inner_its.push_back(its);
+  return st;
+}
+
+int Solver::solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
+                  const double* w0, const double* p0) {
+  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (!g || !r || !w_out || !p_out) throw Error{GKB_ERR_INVALID_ARG, "g, r, w_out and p_out must not be NULL"};
+  if (!(tol >= 0)) throw Error{GKB_ERR_INVALID_ARG, "tol must be >= 0"};
+  if (delay < 0 || delay > GKB_RING - 2) throw Error{GKB_ERR_INVALID_ARG, "delay out of range"};
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  Compact cmp = make_compact(L);
+  const long long len = L.nvel;
+  const int inner_first = stats.inner_solves;
+  stats.inner_iterations = 0;
+  stats.inner_solves = 0;
+  inner_its.clear();
+  (void)inner_first;
+  // inputs -> padded FP64 (f holds g, bc holds r)
+  auto load_m = [&](const double* src, double* dst) {
+    const double* dsrc = src;
+    if (!is_device_ptr(src)) {
+      GKB_CUDA(cudaMemcpyAsync(stage_m.p, src, m * sizeof(double), cudaMemcpyHostToDevice, s));
+      dsrc = stage_m.p;
+    }
+    GKB_CUDA(cudaMemsetAsync(dst, 0, len * sizeof(double), s));
+    k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, dsrc, dst);
+  };
+  auto load_n = [&](const double* src, double* dst) {
+    const double* dsrc = src;
+    if (!is_device_ptr(src)) {
+      GKB_CUDA(cudaMemcpyAsync(stage_n.p, src, ncell * sizeof(double), cudaMemcpyHostToDevice, s));
+      dsrc = stage_n.p;
+    }
+    GKB_CUDA(cudaMemsetAsync(dst, 0, L.ncell * sizeof(double), s));
+    k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, dsrc, dst);
+  };
+  load_m(g, wtmp.p);   // wtmp = g
+  load_n(r, ctmp.p);   // ctmp = r
+  if (w0) {
+    // defect correction: g <- g - W w0 - A p0 ; r <- r - A^T w0
+    load_m(w0, u.p);
+    Ops<double>::apply(L, 0, u.p, t.p, s);
+    Ops<double>::axpby(len, -1.0, t.p, 1.0, wtmp.p, s);
+    if (p0) {
+      load_n(p0, pp.p);
+      Ops<double>::grad(L, pp.p, t.p, 1.0, s);
+      Ops<double>::axpby(len, -1.0, t.p, 1.0, wtmp.p, s);
+    }
+    Ops<double>::negdiv(L, u.p, q.p, 1.0, s);
+    Ops<double>::axpby(L.ncell, -1.0, q.p, 1.0, ctmp.p, s);
+  }
+  // AL transform (Eq. (3)): f = g + gamma A N^-1 r ; y0 = M^-1 f ; b = r - A^T y0
+  Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
+  Ops<double>::axpby(len, 1.0, wtmp.p, 1.0, f.p, s);
+  int inner_status = ST_OK;
+  int st = inner_solve(f.p, y0.p);
+  if (st != ST_OK) inner_status = st;
+  // GKB state
+  GkbState hs{};
+  hs.tol = tol;
+  hs.n_scale = n_scale;
+  hs.ncells = (double)ncell;
+  hs.delay = delay;
+  hs.maxit = opt.maxit;
+  hs.enclosed = enclosed ? 1 : 0;
+  const int cap = opt.maxit + 2;
+  hs.h_alpha = hist.p;
+  hs.h_beta = hist.p + cap;
+  hs.h_zeta = hist.p + 2 * cap;
+  hs.h_est = hist.p + 3 * cap;
+  hs.hcap = cap;
+  GKB_CUDA(cudaMemsetAsync(hist.p, 0, 4 * cap * sizeof(double), s));
+  GKB_CUDA(cudaMemcpyAsync(gkb_dev, &hs, sizeof(GkbState), cudaMemcpyHostToDevice, s));
+  GkbState* S = gkb_dev;
+  double* red_out = (double*)((char*)gkb_dev + offsetof(GkbState, red));
+  // init: beta_1, q_1, w = M^-1 A q_1, alpha_1, v_1, zeta_1, d_1, p, u
+  k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out);
+  k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out);
+  k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S);
+  Ops<double>::grad(L, q.p, f.p, 1.0, s);
+  GKB_CUDA(cudaMemsetAsync(u.p, 0, len * sizeof(double), s));
+  GKB_CUDA(cudaMemsetAsync(pp.p, 0, L.ncell * sizeof(double), s));
+  GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  if (!gkb_host->stop) {
+    st = inner_solve(f.p, x.p);
+    if (st != ST_OK) inner_status = st;
+    Ops<double>::apply_dot(L, 1, x.p, t.p, red, FIN_STORE, red_out, s);
+    k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA1, S, red_out);
+    k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, u.p, S, 1);
+    k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 1);
+    GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
+    GKB_CUDA(cudaStreamSynchronize(s));
+    // the while loop of Algorithm 1
+    while (!gkb_host->stop) {
+      k_gk1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, v.p, q.p, gq.p, S, red, red_out);
+      k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA, S, red_out);
+      k_gk2<<<fgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, f.p, S);
+      st = inner_solve(f.p, x.p);
+      if (st != ST_OK) inner_status = st;
+      k_gk3<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, w.p, S);
+      Ops<double>::apply_dot(L, 1, w.p, t.p, red, FIN_STORE, red_out, s);
+      k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA, S, red_out);
+      k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, w.p, v.p, u.p, S, 0);
+      k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 0);
+      GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
+      GKB_CUDA(cudaStreamSynchronize(s));
+      if (gkb_host->status != ST_OK) break;
+    }
+  }
+  GKB_CUDA(cudaGetLastError());
+  // back-transform: w = u + y0 (+ w0), p (+ p0), mean-free pressure if enclosed
+  Ops<double>::axpby(len, 1.0, y0.p, 1.0, u.p, s);
+  if (w0) {
+    load_m(w0, t.p);
+    Ops<double>::axpby(len, 1.0, t.p, 1.0, u.p, s);
+    if (p0) {
+      load_n(p0, ctmp.p);
+      Ops<double>::axpby(L.ncell, 1.0, ctmp.p, 1.0, pp.p, s);
+    }
+  }
+  double shift = 0.0;
+  if (enclosed) {
+    k_cell_sum<<<cgrid(L), dim3(32, 8), 0, s>>>(L, pp.p, red, scal.p);
+    double hsum[1];
+    read_scalars(scal.p, hsum, 1, s);
+    shift = hsum[0] / (double)ncell;
+  }
+  const bool wdev = is_device_ptr(w_out), pdev = is_device_ptr(p_out);
+  k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, u.p, wdev ? w_out : stage_m.p);
+  k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, pp.p, pdev ? p_out : stage_n.p, shift);
+  if (!wdev) GKB_CUDA(cudaMemcpyAsync(w_out, stage_m.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!pdev) GKB_CUDA(cudaMemcpyAsync(p_out, stage_n.p, ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  GKB_CUDA(cudaGetLastError());
+  const GkbState& H = *gkb_host;
+  int status = H.status;
+  if (status == ST_OK && !H.converged) status = ST_NOT_CONVERGED;
+  if (status == ST_OK && inner_status != ST_OK) status = inner_status;
+  stats.status = status;
+  stats.outer_iterations = H.k;
+  stats.estimate = H.est;
+  stats.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+void Solver::apply(int op, const double* xin, double* yout) {
+  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (!xin || !yout) throw Error{GKB_ERR_INVALID_ARG, "NULL vector"};
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  Compact cmp = make_compact(L);
+  const long long len = L.nvel;
+  const bool in_cells = (op == GKB_OP_A);
+  const bool out_cells = (op == GKB_OP_AT);
+  const long long nin = in_cells ? ncell : m, nout = out_cells ? ncell : m;
+  const double* src = xin;
+  if (!is_device_ptr(xin)) {
+    double* st_in = in_cells ? stage_n.p : stage_m.p;
+    GKB_CUDA(cudaMemcpyAsync(st_in, xin, nin * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = st_in;
+  }
+  if (in_cells) {
+    GKB_CUDA(cudaMemsetAsync(ctmp.p, 0, L.ncell * sizeof(double), s));
+    k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, src, ctmp.p);
+  } else {
+    GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
+    k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p);
+  }
+  switch (op) {
+    case GKB_OP_W: Ops<double>::apply(L, 0, wtmp.p, t.p, s); break;
+    case GKB_OP_M: Ops<double>::apply(L, 1, wtmp.p, t.p, s); break;
+    case GKB_OP_A: Ops<double>::grad(L, ctmp.p, t.p, 1.0, s); break;
+    case GKB_OP_AT: Ops<double>::negdiv(L, wtmp.p, q.p, 1.0, s); break;
+    default: throw Error{GKB_ERR_INVALID_ARG, "unknown operator"};
+  }
+  const bool ydev = is_device_ptr(yout);
+  double* dst = ydev ? yout : (out_cells ? stage_n.p : stage_m.p);
+  if (out_cells) k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, q.p, dst, 0.0);
+  else k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, t.p, dst);
+  if (!ydev) GKB_CUDA(cudaMemcpyAsync(yout, dst, nout * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  GKB_CUDA(cudaGetLastError());
+}
+
+// Dirichlet normal velocity on one side folded into compact (g, r)
+__global__ void k_boundary_rhs(Lvl L, Compact cmp, int side, const double* __restrict__ ub,
+                               double* __restrict__ g, double* __restrict__ r) {
+  const int c = side / 2, hi = side % 2;
+  int oth[2], no = 0;
+  for (int a = 0; a < L.dim; ++a)
+    if (a != c) oth[no++] = a;
+  const int n0 = L.n[oth[0]], n1 = (no > 1) ? L.n[oth[1]] : 1;
+  const long long nb = (long long)n0 * n1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb; t += (long long)gridDim.x * blockDim.x) {
+    int p[3] = {0, 0, 0};
+    p[oth[0]] = (int)(t % n0);
+    if (no > 1) p[oth[1]] = (int)(t / n0);
+    const double u = ub[t];
+    // adjacent active face and the cell between them
+    int f[3] = {p[0], p[1], p[2]};
+    int cell[3] = {p[0], p[1], p[2]};
+    f[c] = hi ? L.n[c] - 1 : 1;
+    cell[c] = hi ? L.n[c] - 1 : 0;
+    const double mu = L.mu64 ? L.mu64[cix(L, cell[0], cell[1], cell[2])] : L.mu0;
+    const long long fi = cmp.base[c] + ((long long)(f[2] - cmp.lo[c][2]) * cmp.ext[c][1] + (f[1] - cmp.lo[c][1])) * cmp.ext[c][0] +
+                         (f[0] - cmp.lo[c][0]);
+    g[fi] += L.wscale * mu * u;
+    const long long ci = ((long long)cell[2] * L.n[1] + cell[1]) * L.n[0] + cell[0];
+    r[ci] += (hi ? 1.0 : -1.0) * L.ascale * u;
+  }
+}
+
+void Solver::boundary_rhs(int side, const double* ub, double* g, double* r) {
+  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (side < 0 || side >= 2 * grid.dim) throw Error{GKB_ERR_INVALID_ARG, "side out of range"};
+  if (grid.bc[side] != GKB_BC_DIRICHLET) throw Error{GKB_ERR_INVALID_ARG, "side is not Dirichlet"};
+  if (!ub || !g || !r) throw Error{GKB_ERR_INVALID_ARG, "NULL vector"};
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  Compact cmp = make_compact(L);
+  const int c = side / 2;
+  long long nb = 1;
+  for (int a = 0; a < grid.dim; ++a)
+    if (a != c) nb *= grid.n[a];
+  DevBuf<double> ubd;
+  const double* ud = ub;
+  if (!is_device_ptr(ub)) {
+    ubd.alloc(nb);
+    GKB_CUDA(cudaMemcpyAsync(ubd.p, ub, nb * sizeof(double), cudaMemcpyHostToDevice, s));
+    ud = ubd.p;
+  }
+  const bool gdev = is_device_ptr(g), rdev = is_device_ptr(r);
+  double* gd = gdev ? g : stage_m.p;
+  double* rd = rdev ? r : stage_n.p;
+  if (!gdev) GKB_CUDA(cudaMemcpyAsync(gd, g, m * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (!rdev) GKB_CUDA(cudaMemcpyAsync(rd, r, ncell * sizeof(double), cudaMemcpyHostToDevice, s));
+  k_boundary_rhs<<<lin_blocks(nb), 256, 0, s>>>(L, cmp, side, ud, gd, rd);
+  if (!gdev) GKB_CUDA(cudaMemcpyAsync(g, gd, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (!rdev) GKB_CUDA(cudaMemcpyAsync(r, rd, ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  GKB_CUDA(cudaGetLastError());
+}
+
+void Solver::precond(const double* rin, double* zout) {
+  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (!rin || !zout) throw Error{GKB_ERR_INVALID_ARG, "NULL vector"};
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  Compact cmp = make_compact(L);
+  const long long len = L.nvel;
+  const double* src = rin;
+  if (!is_device_ptr(rin)) {
+    GKB_CUDA(cudaMemcpyAsync(stage_m.p, rin, m * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = stage_m.p;
+  }
+  GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
+  k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p);
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG;
+  if (opt.precision == GKB_PREC_MIXED) {
+    k_pack_vel<float><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, f32.p);
+    if (use_gmg) gmg32.vcycle(f32.p, x32.p, s);
+    else GKB_CUDA(cudaMemcpyAsync(x32.p, f32.p, len * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    GKB_CUDA(cudaMemsetAsync(scal.p + 8, 0, sizeof(double), s));
+    double one = 1.0;
+    GKB_CUDA(cudaMemcpyAsync(scal.p + 8, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    GKB_CUDA(cudaMemsetAsync(t.p, 0, len * sizeof(double), s));
+    k_add_f32<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, t.p, scal.p + 8);
+  } else {
+    if (use_gmg) gmg64.vcycle(wtmp.p, t.p, s);
+    else GKB_CUDA(cudaMemcpyAsync(t.p, wtmp.p, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  const bool zdev = is_device_ptr(zout);
+  double* dst = zdev ? zout : stage_m.p;
+  k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, t.p, dst);
+  if (!zdev) GKB_CUDA(cudaMemcpyAsync(zout, dst, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  GKB_CUDA(cudaGetLastError());
+}
+
+}  // namespace gkb

@@ -1,0 +1,152 @@
+// solver.cuh - host-side objects: levels, multigrid hierarchy, CG, GKB driver.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/gkb.h"
+#include "common.cuh"
+#include "ops.h"
+#include "reduce.cuh"
+#include "state.cuh"
+
+namespace gkb {
+
+// thrown inside the library only; converted to a status at the ABI
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void check_cuda(cudaError_t e, const char* what);
+#define GKB_CUDA(x) ::gkb::check_cuda((x), #x)
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      throw Error{GKB_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed"};
+    }
+    n = count;
+    GKB_CUDA(cudaMemset(p, 0, count * sizeof(T)));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// Geometry of one level (both precisions share it; mu pointers differ).
+Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc);
+
+// Multigrid hierarchy in precision T for an all-Dirichlet grid.
+template <typename T>
+struct Gmg {
+  struct Level {
+    Lvl L;
+    DevBuf<T> x, b, r, d, mu;
+    DevBuf<T> table;            // patch class inverses (constant viscosity)
+    std::vector<double> ca, cb; // Chebyshev coefficients per step
+    double lam_max = 0;
+  };
+  std::vector<Level> lev;
+  DevBuf<T> coarse_inv;
+  DevBuf<int> coarse_idx;
+  int coarse_m = 0;
+  int degree = 2;
+  double cheb_lo = 0.25;   // interval [cheb_lo * lam, cheb_hi * lam]
+  double cheb_hi = 1.1;
+
+  // levels[0] geometry given; mu0_cells: fine padded cell viscosity (T) or null
+  void build(const Lvl& fine, const T* fine_mu, int coarse_max, int degree, const RedBuf& red,
+             double* scratch_dev, cudaStream_t s);
+  // z = B r on the finest level (one V-cycle); r, z fine padded arrays
+  void vcycle(const T* r, T* z, cudaStream_t s);
+  void smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s);
+};
+
+// Conjugate gradients for M x = f in precision T on one level, optionally
+// preconditioned by a V-cycle.
+template <typename T>
+struct Cg {
+  Lvl L;
+  Gmg<T>* pre = nullptr;
+  DevBuf<T> r, z, p, q;
+  CgState* st = nullptr;      // device
+  CgState* host = nullptr;    // pinned mirror
+  RedBuf red{};
+  void init(const Lvl& L_, Gmg<T>* pre_, const RedBuf& red_, CgState* st_dev, CgState* st_host);
+  // x = M^-1 f to relative tolerance tol (zero start); returns status
+  int solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* iters);
+};
+
+struct Solver {
+  gkb_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  bool have_problem = false;
+  gkb_grid grid{};
+  double gamma = 0, n_scale = 0, mu0 = 1;
+  bool enclosed = false;
+  int64_t m = 0, ncell = 0;      // compact sizes
+  Lvl L64{}, L32{};              // finest level, FP64 / FP32 views
+  DevBuf<double> mu64;
+  DevBuf<float> mu32;
+
+  // reduction scratch and device scalars
+  DevBuf<double> red_partial;
+  DevBuf<unsigned int> red_ticket;
+  RedBuf red{};
+  DevBuf<double> scal;           // small scratch for FIN_STORE results
+  DevBuf<unsigned char> state_mem;
+  CgState* cg_dev = nullptr;
+  GkbState* gkb_dev = nullptr;
+  CgState* cg_host = nullptr;    // pinned
+  GkbState* gkb_host = nullptr;  // pinned
+
+  // multigrid and CG in both precisions (only the ones in use are built)
+  Gmg<double> gmg64;
+  Gmg<float> gmg32;
+  Cg<double> cg64;
+  Cg<float> cg32;
+
+  // FP64 vectors of the GKB recurrence (padded)
+  DevBuf<double> u, v, x, w, t, f, y0, wtmp;   // velocity
+  DevBuf<double> q, d, pp, gq, bc, ctmp;       // cells
+  DevBuf<double> r64;                          // mixed refinement residual
+  DevBuf<float> f32, x32;                      // mixed refinement FP32 rhs / correction
+  DevBuf<double> hist;                         // alpha, beta, zeta, est histories
+  DevBuf<double> stage_m, stage_n;             // compact staging for host I/O
+  std::vector<int> inner_its;
+  gkb_stats_t stats{};
+
+  void set_problem(const gkb_grid* g, const double* viscosity, double mu0, double gamma, double n_scale);
+  int solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
+            const double* w0, const double* p0);
+  void apply(int op, const double* x, double* y);
+  void boundary_rhs(int side, const double* normal_velocity, double* g, double* r);
+  void precond(const double* r, double* z);
+  // inner solve in FP64 padded layout: x = M^-1 f; returns status
+  int inner_solve(const double* f, double* x);
+  ~Solver();
+};
+
+}  // namespace gkb

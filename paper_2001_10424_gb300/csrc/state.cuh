@@ -1,0 +1,125 @@
+// state.cuh - device-resident solver scalars and the reduction finalisers.
+//
+// All scalars of the inner CG and of the GKB recurrence live in device
+// memory; kernels read them through pointers and the finalisers of the
+// fused reductions update them, so no host round trip is needed inside a
+// solve.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gkb {
+
+// status codes mirrored from include/gkb.h
+constexpr int ST_OK = 0;
+constexpr int ST_INVALID = 1;
+constexpr int ST_NOT_SPD = 2;
+constexpr int ST_NOT_CONVERGED = 3;
+constexpr int ST_INNER_NOT_CONVERGED = 4;
+constexpr int ST_NAN = 5;
+constexpr int ST_TIMEOUT = 6;
+
+enum FinOp {
+  FIN_NONE = 0,
+  FIN_STORE = 1,   // st is double[4]: store the sums
+  FIN_CG_INIT,     // s0 = f.f
+  FIN_CG_RZ0,      // s0 = r.z (first)
+  FIN_CG_PAP,      // s0 = p.Mp -> alpha
+  FIN_CG_RR,       // s0 = r.r  -> convergence test
+  FIN_CG_RZ,       // s0 = r.z  -> beta
+};
+
+struct CgState {
+  double ff;        // ||f||^2
+  double rr;        // ||r||^2
+  double rz_old;    // r.z of the previous iteration
+  double pAp;
+  double alpha, beta;
+  double tol2;      // tol_inner^2
+  int it;           // iterations of this solve
+  int maxit;
+  int done;         // 1 once the solve has stopped
+  int status;       // ST_* of this solve
+  long long total_it;
+  int solves;
+  int pad;
+};
+
+__device__ __forceinline__ void cg_fail(CgState* c, int code) {
+  if (c->status == ST_OK) c->status = code;
+  c->done = 1;
+}
+
+__device__ __forceinline__ void finalize(int op, const double* s, void* st) {
+  switch (op) {
+    case FIN_STORE: {
+      double* o = (double*)st;
+      o[0] = s[0]; o[1] = s[1]; o[2] = s[2]; o[3] = s[3];
+    } break;
+    case FIN_CG_INIT: {
+      CgState* c = (CgState*)st;
+      c->ff = s[0]; c->rr = s[0]; c->it = 0; c->status = ST_OK; c->alpha = 0.0; c->beta = 0.0;
+      c->done = (s[0] == 0.0) ? 1 : 0;
+      c->solves += 1;
+      if (!isfinite(s[0])) cg_fail(c, ST_NAN);
+    } break;
+    case FIN_CG_RZ0: {
+      CgState* c = (CgState*)st;
+      c->rz_old = s[0];
+      if (!isfinite(s[0])) cg_fail(c, ST_NAN);
+    } break;
+    case FIN_CG_PAP: {
+      CgState* c = (CgState*)st;
+      c->pAp = s[0];
+      if (c->done) { c->alpha = 0.0; break; }
+      if (!isfinite(s[0])) { c->alpha = 0.0; cg_fail(c, ST_NAN); }
+      else if (!(s[0] > 0.0)) { c->alpha = 0.0; cg_fail(c, ST_NOT_SPD); }
+      else c->alpha = c->rz_old / s[0];
+    } break;
+    case FIN_CG_RR: {
+      CgState* c = (CgState*)st;
+      if (c->done) break;
+      c->rr = s[0];
+      c->it += 1;
+      c->total_it += 1;
+      if (!isfinite(s[0])) cg_fail(c, ST_NAN);
+      else if (s[0] <= c->tol2 * c->ff) c->done = 1;
+      else if (c->it >= c->maxit) cg_fail(c, ST_INNER_NOT_CONVERGED);
+    } break;
+    case FIN_CG_RZ: {
+      CgState* c = (CgState*)st;
+      if (c->done) break;
+      c->beta = (c->rz_old != 0.0) ? s[0] / c->rz_old : 0.0;
+      c->rz_old = s[0];
+    } break;
+    default: break;
+  }
+}
+
+constexpr int GKB_RING = 64;  // delay d <= GKB_RING - 2
+
+struct GkbState {
+  double alpha, beta, zeta;  // current alpha_k, beta_k, zeta_k
+  double mean;               // mean removed from the N-step vector (enclosed)
+  double zsum;               // sum_{j<=K} zeta_j^2
+  double est;                // latest lower-bound estimate
+  double tol;
+  double n_scale;            // N = n_scale * I
+  double ncells;             // number of cells (for the mean)
+  double red[4];             // raw results of the last FIN_STORE reduction
+  double ring[GKB_RING];     // zeta^2, indexed by K mod GKB_RING
+  int delay, maxit, enclosed;
+  int k;                     // while-loop iterations done
+  int K;                     // zetas known
+  int status;                // ST_* (ST_OK while running or converged)
+  int stop;                  // 1 once the loop must end
+  int converged;             // 1 if the estimate met tol (or happy breakdown)
+  double* h_alpha;           // history buffers (device), capacity hcap
+  double* h_beta;
+  double* h_zeta;
+  double* h_est;
+  int hcap;
+  int pad;
+};
+
+}  // namespace gkb

@@ -78,6 +78,18 @@ extern "C" {
 #define GKB_OP_AT  2          /* y = A^T x (-divergence) (m -> n) */
 #define GKB_OP_M   3          /* y = M x                 (m -> m) */
 
+/* kernel classes counted (and, with gkb_options.profile, timed) per solve */
+#define GKB_KC_APPLY     0    /* operator products with fused dot (CG, alpha)   */
+#define GKB_KC_RESIDUAL  1    /* r = b - M x                                    */
+#define GKB_KC_SMOOTH    2    /* patch-Chebyshev smoothing step                 */
+#define GKB_KC_RESTRICT  3    /* residual restriction P^T                       */
+#define GKB_KC_PROLONG   4    /* prolongation and correction x += P e          */
+#define GKB_KC_COARSE    5    /* dense coarsest-level solve                     */
+#define GKB_KC_BLAS      6    /* dots and vector updates of CG                  */
+#define GKB_KC_GKB       7    /* GKB recurrence kernels (Algorithm 1 steps)     */
+#define GKB_KC_LAYOUT    8    /* packing, precision conversion, gradients       */
+#define GKB_KC_COUNT     9
+
 typedef struct gkb_ctx* gkb_handle;
 
 /* Grid: dim = 2 or 3, n[] cells per axis (n[2] ignored in 2D), spacing h,
@@ -103,6 +115,9 @@ typedef struct {
                              correction solve inside the refinement loop       */
   int use_graph;          /* 1: run each solve as one CUDA graph with device-
                              side loop control; 0: host-driven loops           */
+  int profile;            /* 1: time every kernel launch with CUDA events on
+                             the stream and report per-class totals in
+                             gkb_stats (adds event overhead between kernels)  */
   void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
 } gkb_options;
 
@@ -115,6 +130,13 @@ typedef struct {
   double setup_seconds;       /* gkb_set_problem wall time                   */
   double solve_seconds;       /* last gkb_solve wall time                    */
   int levels;                 /* multigrid levels (0 without GMG)            */
+  int64_t kernel_launches[GKB_KC_COUNT];  /* launches per class, last solve  */
+  int64_t kernel_units[GKB_KC_COUNT];     /* work per class: velocity unknowns
+                                             of the launch's level summed over
+                                             launches (vector elements for
+                                             BLAS, rows for the coarse solve) */
+  double kernel_ms[GKB_KC_COUNT];         /* summed kernel time per class (ms)
+                                             when profiling, else 0          */
 } gkb_stats_t;
 
 /* Fill *opt with defaults: FP64, GMG-PCG, tol_inner 1e-10, maxit 1000,

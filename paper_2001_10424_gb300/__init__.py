@@ -32,6 +32,7 @@ GKB_PREC_MIXED = 1
 GKB_INNER_CG = 0
 GKB_INNER_GMG_PCG = 1
 GKB_OP_W, GKB_OP_A, GKB_OP_AT, GKB_OP_M = 0, 1, 2, 3
+KERNEL_CLASSES = ["apply", "residual", "smooth", "restrict", "prolong", "coarse", "blas", "gkb", "layout"]
 
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "NOT_CONVERGED", 4: "INNER_NOT_CONVERGED",
@@ -55,14 +56,15 @@ class gkb_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner", ctypes.c_int), ("tol_inner", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class gkb_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("inner_solves", ctypes.c_int),
                 ("inner_iterations", ctypes.c_int64), ("estimate", ctypes.c_double),
                 ("setup_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
-                ("levels", ctypes.c_int)]
+                ("levels", ctypes.c_int), ("kernel_launches", ctypes.c_int64 * 9),
+                ("kernel_units", ctypes.c_int64 * 9), ("kernel_ms", ctypes.c_double * 9)]
 
 
 class GkbError(RuntimeError):
@@ -179,7 +181,11 @@ def gkb_solve(h, g, r, tol, delay, w_out, p_out, w0=None, p0=None):
 def gkb_stats(h):
     s = gkb_stats_t()
     _check(h, load().gkb_stats(h, ctypes.byref(s)))
-    return {f: getattr(s, f) for f, _ in s._fields_}
+    out = {f: getattr(s, f) for f, _ in s._fields_}
+    out["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(s.kernel_launches)))
+    out["kernel_units"] = dict(zip(KERNEL_CLASSES, list(s.kernel_units)))
+    out["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(s.kernel_ms)))
+    return out
 
 
 def gkb_history(h, capacity=4096):

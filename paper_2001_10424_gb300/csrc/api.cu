@@ -19,6 +19,10 @@ thread_local std::string g_create_error = "no error";
 template <class F>
 int guarded(gkb_handle h, F&& fn) {
   if (!h) return GKB_ERR_INVALID_ARG;
+  struct ProfBind {
+    explicit ProfBind(gkb::Profiler* p) { gkb::g_prof = p; }
+    ~ProfBind() { gkb::g_prof = nullptr; }
+  } bind(&h->s.prof);
   try {
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) {
@@ -58,6 +62,7 @@ int gkb_default_options(gkb_options* opt) {
   opt->coarse_max = 8;
   opt->mixed_rtol = 1e-4;
   opt->use_graph = 0;
+  opt->profile = 0;
   opt->stream = nullptr;
   return GKB_OK;
 }

@@ -33,6 +33,18 @@ struct Lvl {
   const float* mu32;
 };
 
+// number of velocity unknowns (active faces) of a level
+inline long long lvl_unknowns(const Lvl& L) {
+  long long m = 0;
+  for (int c = 0; c < L.dim; ++c) {
+    long long k = L.n[c] + 1 - (L.nat[2 * c] ? 0 : 1) - (L.nat[2 * c + 1] ? 0 : 1);
+    for (int a = 0; a < L.dim; ++a)
+      if (a != c) k *= L.n[a];
+    m += k;
+  }
+  return m;
+}
+
 __host__ __device__ __forceinline__ long long cix(const Lvl& L, int i, int j, int k) {
   return (long long)k * L.S + (long long)j * L.P + i;
 }

@@ -1,6 +1,7 @@
 // kernels_inst.cuh - launch wrappers, instantiated for KT (see kernels_f64.cu).
 #pragma once
 #include "kernels_impl.cuh"
+#include "prof.h"
 
 namespace gkb {
 
@@ -14,6 +15,7 @@ long long Ops<KT>::face_blocks(const Lvl& L) {
 
 template <>
 void Ops<KT>::apply(const Lvl& L, int mode, const KT* x, KT* y, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
   RedBuf red{nullptr, nullptr};
   if (GKB_VARMU(L)) k_apply<KT, true, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, 0, nullptr);
   else k_apply<KT, false, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, 0, nullptr);
@@ -22,12 +24,14 @@ void Ops<KT>::apply(const Lvl& L, int mode, const KT* x, KT* y, cudaStream_t s) 
 template <>
 void Ops<KT>::apply_dot(const Lvl& L, int mode, const KT* x, KT* y, const RedBuf& red, int fin, void* st,
                         cudaStream_t s) {
+  ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
   if (GKB_VARMU(L)) k_apply<KT, true, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, fin, st);
   else k_apply<KT, false, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, fin, st);
 }
 
 template <>
 void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_RESIDUAL, s, lvl_unknowns(L));
   if (GKB_VARMU(L)) k_residual<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, x, b, r);
   else k_residual<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, x, b, r);
 }
@@ -35,65 +39,77 @@ void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream
 template <>
 void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* table,
                    cudaStream_t s) {
+  ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
   if (GKB_VARMU(L)) k_cheb<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, nullptr);
   else k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
 }
 
 template <>
 void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
   if (GKB_VARMU(L)) k_patch<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, nullptr);
   else k_patch<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, table);
 }
 
 template <>
 void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_LAYOUT, s, 0);
   k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
 }
 
 template <>
 void Ops<KT>::grad(const Lvl& L, const KT* p, KT* y, KT scale, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_LAYOUT, s, lvl_unknowns(L));
   k_grad<KT><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, p, y, scale);
 }
 
 template <>
 void Ops<KT>::negdiv(const Lvl& L, const KT* x, KT* y, KT scale, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_LAYOUT, s, lvl_unknowns(L));
   k_negdiv<KT><<<cell_grid(L), dim3(BX, BY), 0, s>>>(L, x, y, scale);
 }
 
 template <>
 void Ops<KT>::prolong(const Lvl& Lf, const Lvl& Lc, const KT* xc, KT* xf, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_PROLONG, s, lvl_unknowns(Lf));
   k_prolong<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
 }
 
 template <>
 void Ops<KT>::restrict_(const Lvl& Lf, const Lvl& Lc, const KT* rf, KT* bc, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_RESTRICT, s, lvl_unknowns(Lf));
   k_restrict<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc);
 }
 
 template <>
 void Ops<KT>::coarse(int m, const KT* Minv, const int* idx, const KT* b, KT* x, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_COARSE, s, (long long)m);
   const int warps_per_block = 8;
   k_coarse_solve<KT><<<(m + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(m, Minv, idx, b, x);
 }
 
 template <>
 void Ops<KT>::dot(long long len, const KT* a, const KT* b, const RedBuf& red, int fin, void* st, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_BLAS, s, len);
   k_dot<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, b, red, fin, st);
 }
 
 template <>
 void Ops<KT>::cg_update(long long len, KT* x, const KT* p, KT* r, const KT* q, const CgState* cg,
                         const RedBuf& red, void* st, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_BLAS, s, len);
   k_cg_update<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, x, p, r, q, cg, red, st);
 }
 
 template <>
 void Ops<KT>::cg_dir(long long len, KT* p, const KT* z, const CgState* cg, int first, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_BLAS, s, len);
   k_cg_dir<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, p, z, cg, first);
 }
 
 template <>
 void Ops<KT>::axpby(long long len, KT a, const KT* x, KT b, KT* y, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_BLAS, s, len);
   k_axpby<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, x, b, y);
 }
 

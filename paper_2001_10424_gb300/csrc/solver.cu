@@ -11,8 +11,11 @@
 #include <cstdio>
 
 #include "solver.cuh"
+#include "prof.h"
 
 namespace gkb {
+
+thread_local Profiler* g_prof = nullptr;
 
 void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {
@@ -216,7 +219,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     if (fmu) {
       C.mu.alloc(Lc.ncell);
       dim3 g((nc[0] + 31) / 32, (nc[1] + 7) / 8, Lc.n[2]);
-      k_mu_coarsen<T><<<g, dim3(32, 8), 0, s>>>(lev[lev.size() - 2].L, Lc, fmu, C.mu.p);
+      { ProfScope ps_(GKB_KC_LAYOUT, s); k_mu_coarsen<T><<<g, dim3(32, 8), 0, s>>>(lev[lev.size() - 2].L, Lc, fmu, C.mu.p); }
       GKB_CUDA(cudaGetLastError());
       set_mu<T>(C.L, C.mu.p);
     }
@@ -243,7 +246,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     xv.alloc(V.L.nvel);
     zv.alloc(V.L.nvel);
     zero.alloc(V.L.nvel);
-    k_fill_hash<T><<<fgrid(V.L), dim3(32, 8), 0, s>>>(V.L, xv.p);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_fill_hash<T><<<fgrid(V.L), dim3(32, 8), 0, s>>>(V.L, xv.p); }
     GKB_CUDA(cudaGetLastError());
     double hs[4];
     double lam = 0;
@@ -720,10 +723,10 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
     tmp.alloc(ncell);
     GKB_CUDA(cudaMemcpyAsync(tmp.p, viscosity, ncell * sizeof(double), cudaMemcpyDefault, stream));
     mu64.alloc(L64.ncell);
-    k_pack_cell<double><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, mu64.p);
+    { ProfScope ps_(GKB_KC_LAYOUT, stream); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, mu64.p); }
     if (mixed) {
       mu32.alloc(L64.ncell);
-      k_pack_cell<float><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, mu32.p);
+      { ProfScope ps_(GKB_KC_LAYOUT, stream); k_pack_cell<float><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, mu32.p); }
     }
     GKB_CUDA(cudaStreamSynchronize(stream));
     std::vector<double> hv(ncell);
@@ -794,12 +797,12 @@ int Solver::inner_solve(const double* fpad, double* xpad) {
     while (rr > opt.tol_inner * opt.tol_inner * ff) {
       if (ref++ >= max_refine) { st = ST_INNER_NOT_CONVERGED; break; }
       GKB_CUDA(cudaMemcpyAsync(scal.p + 8, &rr, sizeof(double), cudaMemcpyHostToDevice, stream));
-      k_to_f32<<<lin_blocks(len), CB, 0, stream>>>(len, r64.p, f32.p, scal.p + 8);
+      { ProfScope ps_(GKB_KC_LAYOUT, stream); k_to_f32<<<lin_blocks(len), CB, 0, stream>>>(len, r64.p, f32.p, scal.p + 8); }
       int it = 0;
       int s32 = cg32.solve(f32.p, x32.p, opt.mixed_rtol, opt.maxit_inner, stream, &it);
       its += it;
       if (s32 != ST_OK && s32 != ST_INNER_NOT_CONVERGED) { st = s32; break; }
-      k_add_f32<<<lin_blocks(len), CB, 0, stream>>>(len, x32.p, xpad, scal.p + 8);
+      { ProfScope ps_(GKB_KC_LAYOUT, stream); k_add_f32<<<lin_blocks(len), CB, 0, stream>>>(len, x32.p, xpad, scal.p + 8); }
       Ops<double>::residual(L64, xpad, fpad, r64.p, stream);
       Ops<double>::dot(len, r64.p, r64.p, red, FIN_STORE, scal.p + 4, stream);
       read_scalars(scal.p + 4, hs, 1, stream);
@@ -827,11 +830,11 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   const Lvl& L = L64;
   Compact cmp = make_compact(L);
   const long long len = L.nvel;
-  const int inner_first = stats.inner_solves;
   stats.inner_iterations = 0;
   stats.inner_solves = 0;
   inner_its.clear();
-  (void)inner_first;
+  prof.reset();
+  if (opt.profile) prof.enable(32768);
   // inputs -> padded FP64 (f holds g, bc holds r)
   auto load_m = [&](const double* src, double* dst) {
     const double* dsrc = src;
@@ -840,7 +843,7 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
       dsrc = stage_m.p;
     }
     GKB_CUDA(cudaMemsetAsync(dst, 0, len * sizeof(double), s));
-    k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, dsrc, dst);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, dsrc, dst); }
   };
   auto load_n = [&](const double* src, double* dst) {
     const double* dsrc = src;
@@ -849,7 +852,7 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
       dsrc = stage_n.p;
     }
     GKB_CUDA(cudaMemsetAsync(dst, 0, L.ncell * sizeof(double), s));
-    k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, dsrc, dst);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, dsrc, dst); }
   };
   load_m(g, wtmp.p);   // wtmp = g
   load_n(r, ctmp.p);   // ctmp = r
@@ -891,9 +894,9 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   GkbState* S = gkb_dev;
   double* red_out = (double*)((char*)gkb_dev + offsetof(GkbState, red));
   // init: beta_1, q_1, w = M^-1 A q_1, alpha_1, v_1, zeta_1, d_1, p, u
-  k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out);
-  k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out);
-  k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S);
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S); }
   Ops<double>::grad(L, q.p, f.p, 1.0, s);
   GKB_CUDA(cudaMemsetAsync(u.p, 0, len * sizeof(double), s));
   GKB_CUDA(cudaMemsetAsync(pp.p, 0, L.ncell * sizeof(double), s));
@@ -903,23 +906,23 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
     st = inner_solve(f.p, x.p);
     if (st != ST_OK) inner_status = st;
     Ops<double>::apply_dot(L, 1, x.p, t.p, red, FIN_STORE, red_out, s);
-    k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA1, S, red_out);
-    k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, u.p, S, 1);
-    k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 1);
+    { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA1, S, red_out); }
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, u.p, S, 1); }
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 1); }
     GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
     GKB_CUDA(cudaStreamSynchronize(s));
     // the while loop of Algorithm 1
     while (!gkb_host->stop) {
-      k_gk1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, v.p, q.p, gq.p, S, red, red_out);
-      k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA, S, red_out);
-      k_gk2<<<fgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, f.p, S);
+      { ProfScope ps_(GKB_KC_GKB, s); k_gk1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, v.p, q.p, gq.p, S, red, red_out); }
+      { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA, S, red_out); }
+      { ProfScope ps_(GKB_KC_GKB, s); k_gk2<<<fgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, f.p, S); }
       st = inner_solve(f.p, x.p);
       if (st != ST_OK) inner_status = st;
-      k_gk3<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, w.p, S);
+      { ProfScope ps_(GKB_KC_GKB, s); k_gk3<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, w.p, S); }
       Ops<double>::apply_dot(L, 1, w.p, t.p, red, FIN_STORE, red_out, s);
-      k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA, S, red_out);
-      k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, w.p, v.p, u.p, S, 0);
-      k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 0);
+      { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA, S, red_out); }
+      { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, w.p, v.p, u.p, S, 0); }
+      { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 0); }
       GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
       GKB_CUDA(cudaStreamSynchronize(s));
       if (gkb_host->status != ST_OK) break;
@@ -938,14 +941,14 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   }
   double shift = 0.0;
   if (enclosed) {
-    k_cell_sum<<<cgrid(L), dim3(32, 8), 0, s>>>(L, pp.p, red, scal.p);
+    { ProfScope ps_(GKB_KC_GKB, s); k_cell_sum<<<cgrid(L), dim3(32, 8), 0, s>>>(L, pp.p, red, scal.p); }
     double hsum[1];
     read_scalars(scal.p, hsum, 1, s);
     shift = hsum[0] / (double)ncell;
   }
   const bool wdev = is_device_ptr(w_out), pdev = is_device_ptr(p_out);
-  k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, u.p, wdev ? w_out : stage_m.p);
-  k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, pp.p, pdev ? p_out : stage_n.p, shift);
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, u.p, wdev ? w_out : stage_m.p); }
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, pp.p, pdev ? p_out : stage_n.p, shift); }
   if (!wdev) GKB_CUDA(cudaMemcpyAsync(w_out, stage_m.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!pdev) GKB_CUDA(cudaMemcpyAsync(p_out, stage_n.p, ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
@@ -954,6 +957,12 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   int status = H.status;
   if (status == ST_OK && !H.converged) status = ST_NOT_CONVERGED;
   if (status == ST_OK && inner_status != ST_OK) status = inner_status;
+  prof.collect();
+  for (int kc = 0; kc < GKB_KC_COUNT; ++kc) {
+    stats.kernel_launches[kc] = prof.launches[kc];
+    stats.kernel_units[kc] = prof.units[kc];
+    stats.kernel_ms[kc] = prof.ms[kc];
+  }
   stats.status = status;
   stats.outer_iterations = H.k;
   stats.estimate = H.est;
@@ -979,10 +988,10 @@ void Solver::apply(int op, const double* xin, double* yout) {
   }
   if (in_cells) {
     GKB_CUDA(cudaMemsetAsync(ctmp.p, 0, L.ncell * sizeof(double), s));
-    k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, src, ctmp.p);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, src, ctmp.p); }
   } else {
     GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
-    k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p); }
   }
   switch (op) {
     case GKB_OP_W: Ops<double>::apply(L, 0, wtmp.p, t.p, s); break;
@@ -993,8 +1002,8 @@ void Solver::apply(int op, const double* xin, double* yout) {
   }
   const bool ydev = is_device_ptr(yout);
   double* dst = ydev ? yout : (out_cells ? stage_n.p : stage_m.p);
-  if (out_cells) k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, q.p, dst, 0.0);
-  else k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, t.p, dst);
+  if (out_cells) { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, q.p, dst, 0.0); }
+  else { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, t.p, dst); }
   if (!ydev) GKB_CUDA(cudaMemcpyAsync(yout, dst, nout * sizeof(double), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
   GKB_CUDA(cudaGetLastError());
@@ -1052,7 +1061,7 @@ void Solver::boundary_rhs(int side, const double* ub, double* g, double* r) {
   double* rd = rdev ? r : stage_n.p;
   if (!gdev) GKB_CUDA(cudaMemcpyAsync(gd, g, m * sizeof(double), cudaMemcpyHostToDevice, s));
   if (!rdev) GKB_CUDA(cudaMemcpyAsync(rd, r, ncell * sizeof(double), cudaMemcpyHostToDevice, s));
-  k_boundary_rhs<<<lin_blocks(nb), 256, 0, s>>>(L, cmp, side, ud, gd, rd);
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_boundary_rhs<<<lin_blocks(nb), 256, 0, s>>>(L, cmp, side, ud, gd, rd); }
   if (!gdev) GKB_CUDA(cudaMemcpyAsync(g, gd, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!rdev) GKB_CUDA(cudaMemcpyAsync(r, rd, ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
@@ -1072,24 +1081,24 @@ void Solver::precond(const double* rin, double* zout) {
     src = stage_m.p;
   }
   GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
-  k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p);
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p); }
   const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG;
   if (opt.precision == GKB_PREC_MIXED) {
-    k_pack_vel<float><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, f32.p);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<float><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, f32.p); }
     if (use_gmg) gmg32.vcycle(f32.p, x32.p, s);
     else GKB_CUDA(cudaMemcpyAsync(x32.p, f32.p, len * sizeof(float), cudaMemcpyDeviceToDevice, s));
     GKB_CUDA(cudaMemsetAsync(scal.p + 8, 0, sizeof(double), s));
     double one = 1.0;
     GKB_CUDA(cudaMemcpyAsync(scal.p + 8, &one, sizeof(double), cudaMemcpyHostToDevice, s));
     GKB_CUDA(cudaMemsetAsync(t.p, 0, len * sizeof(double), s));
-    k_add_f32<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, t.p, scal.p + 8);
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_add_f32<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, t.p, scal.p + 8); }
   } else {
     if (use_gmg) gmg64.vcycle(wtmp.p, t.p, s);
     else GKB_CUDA(cudaMemcpyAsync(t.p, wtmp.p, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   const bool zdev = is_device_ptr(zout);
   double* dst = zdev ? zout : stage_m.p;
-  k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, t.p, dst);
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, t.p, dst); }
   if (!zdev) GKB_CUDA(cudaMemcpyAsync(zout, dst, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
   GKB_CUDA(cudaGetLastError());

@@ -8,6 +8,7 @@
 #include "../../include/gkb.h"
 #include "common.cuh"
 #include "ops.h"
+#include "prof.h"
 #include "reduce.cuh"
 #include "state.cuh"
 
@@ -137,6 +138,7 @@ struct Solver {
   DevBuf<double> stage_m, stage_n;             // compact staging for host I/O
   std::vector<int> inner_its;
   gkb_stats_t stats{};
+  Profiler prof;
 
   void set_problem(const gkb_grid* g, const double* viscosity, double mu0, double gamma, double n_scale);
   int solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,

@@ -377,6 +377,33 @@ def run_ours(args, ws, rank, local):
     return 0
 
 
+def run_probe(args, local):
+    """Short run for ncu captures: setup, then one V-cycle or one solve."""
+    import torch
+
+    import paper_2001_10424_gb300 as gk
+    import workloads
+    torch.cuda.set_device(local)
+    gk.build.build()
+    gk.load()
+    wl = workloads.stokes2d(args.n)
+    args.gammas = args.gammas[:1]
+    h = make_handles(gk, torch, wl, args, args.form)[0]
+    m, n = gk.gkb_layout(h)
+    g = torch.tensor(wl["g"], device="cuda")
+    r = torch.tensor(wl["r"], device="cuda")
+    w = torch.empty(m, dtype=torch.float64, device="cuda")
+    p = torch.empty(n, dtype=torch.float64, device="cuda")
+    if args.probe == "precond":
+        gk.gkb_precond(h, g, w)
+    else:
+        gk.gkb_solve(h, g, r, args.tol, args.delay, w, p)
+    torch.cuda.synchronize()
+    gk.gkb_destroy(h)
+    print("probe done")
+    return 0
+
+
 # per-launch DRAM traffic (bytes) of the dominant kernel from ncu captures,
 # keyed by (form, kernel class); summarised under profiles/
 TRAFFIC = {}
@@ -396,12 +423,16 @@ def main():
     ap.add_argument("--delay", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--probe", choices=["precond", "solve"], default=None,
+                    help="profiling target: set up one handle (first gamma) and run one V-cycle or one solve")
     args = ap.parse_args()
     args.gammas = [float(x) for x in args.gammas.split(",")]
     args.warmup = max(args.warmup, 0)
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.probe:
+        return run_probe(args, local)
     return run_ours(args, ws, rank, local)
 
 

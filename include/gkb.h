@@ -66,9 +66,9 @@ extern "C" {
 
 #define GKB_PREC_FP64     0   /* everything in FP64                          */
 #define GKB_PREC_MIXED    1   /* inner CG, V-cycles and stencils in FP32 with
-                                 FP64 iterative refinement of each inner
-                                 solve; GKB vectors, alpha, beta, zeta and the
-                                 estimator in FP64                           */
+                                 the solution accumulated and the residual
+                                 periodically recomputed in FP64; GKB vectors,
+                                 alpha, beta, zeta and the estimator in FP64 */
 
 #define GKB_INNER_CG      0   /* unpreconditioned CG                         */
 #define GKB_INNER_GMG_PCG 1   /* CG + one GMG V-cycle (all-Dirichlet grids)  */
@@ -111,10 +111,13 @@ typedef struct {
   int coarse_max;         /* coarsen while every side is even, halves to >= 2
                              cells and the longest side exceeds coarse_max
                              (coarse_max / 2, at least 4, in 3D)              */
-  double mixed_rtol;      /* GKB_PREC_MIXED: relative tolerance of each FP32
-                             correction solve inside the refinement loop       */
-  int use_graph;          /* 1: run each solve as one CUDA graph with device-
-                             side loop control; 0: host-driven loops           */
+  double mixed_rtol;      /* GKB_PREC_MIXED: the FP32 CG recomputes its
+                             residual in FP64 whenever it has dropped by this
+                             factor since the last recomputation               */
+  int use_graph;          /* 1: run every inner CG solve as one CUDA graph whose
+                             while loop is a device-side conditional node;
+                             0: host-sequenced loop (always used when
+                             profiling)                                        */
   int profile;            /* 1: time every kernel launch with CUDA events on
                              the stream and report per-class totals in
                              gkb_stats (adds event overhead between kernels)  */
@@ -140,7 +143,7 @@ typedef struct {
 } gkb_stats_t;
 
 /* Fill *opt with defaults: FP64, GMG-PCG, tol_inner 1e-10, maxit 1000,
- * maxit_inner 2000, degree 2, coarse_max 8, mixed_rtol 1e-4, graph off. */
+ * maxit_inner 2000, degree 2, coarse_max 8, mixed_rtol 1e-3, graphs on. */
 int gkb_default_options(gkb_options* opt);
 
 /* Create a handle on the current CUDA device. *out receives the handle.

@@ -60,8 +60,8 @@ int gkb_default_options(gkb_options* opt) {
   opt->maxit_inner = 2000;
   opt->smoother_degree = 2;
   opt->coarse_max = 8;
-  opt->mixed_rtol = 1e-4;
-  opt->use_graph = 0;
+  opt->mixed_rtol = 1e-3;
+  opt->use_graph = 1;
   opt->profile = 0;
   opt->stream = nullptr;
   return GKB_OK;

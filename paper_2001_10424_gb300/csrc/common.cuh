@@ -31,6 +31,40 @@ struct Lvl {
   double mu0;         // constant viscosity when mu == null
   const double* mu64; // cell viscosity in the padded cell layout, or null
   const float* mu32;
+  // derived constants (set by finish_level), in both precisions so that FP32
+  // kernels never convert from double on the FP64 pipe
+  int has_gd;         // gc != 0
+  double g2;          // gc * ascale^2: grad-div coupling of two faces of a cell
+  double wmu;         // wscale * mu0
+  float mu0f, wscalef, ascalef, g2f, wmuf;
+};
+
+inline void finish_level(Lvl& L) {
+  L.has_gd = (L.gc != 0.0) ? 1 : 0;
+  L.g2 = L.gc * L.ascale * L.ascale;
+  L.wmu = L.wscale * L.mu0;
+  L.mu0f = (float)L.mu0;
+  L.wscalef = (float)L.wscale;
+  L.ascalef = (float)L.ascale;
+  L.g2f = (float)L.g2;
+  L.wmuf = (float)L.wmu;
+}
+
+// per-precision level constants
+template <typename T> struct Kc;
+template <> struct Kc<double> {
+  static __host__ __device__ __forceinline__ double mu0(const Lvl& L) { return L.mu0; }
+  static __host__ __device__ __forceinline__ double ws(const Lvl& L) { return L.wscale; }
+  static __host__ __device__ __forceinline__ double as(const Lvl& L) { return L.ascale; }
+  static __host__ __device__ __forceinline__ double g2(const Lvl& L) { return L.g2; }
+  static __host__ __device__ __forceinline__ double wmu(const Lvl& L) { return L.wmu; }
+};
+template <> struct Kc<float> {
+  static __host__ __device__ __forceinline__ float mu0(const Lvl& L) { return L.mu0f; }
+  static __host__ __device__ __forceinline__ float ws(const Lvl& L) { return L.wscalef; }
+  static __host__ __device__ __forceinline__ float as(const Lvl& L) { return L.ascalef; }
+  static __host__ __device__ __forceinline__ float g2(const Lvl& L) { return L.g2f; }
+  static __host__ __device__ __forceinline__ float wmu(const Lvl& L) { return L.wmuf; }
 };
 
 // number of velocity unknowns (active faces) of a level
@@ -76,7 +110,7 @@ template <> struct MuPtr<float>  { static __device__ __forceinline__ const float
 
 template <typename T, bool VarMu>
 __device__ __forceinline__ T cell_mu(const Lvl& L, int i, int j, int k) {
-  if (!VarMu) return (T)L.mu0;
+  if (!VarMu) return Kc<T>::mu0(L);
   return __ldg(MuPtr<T>::get(L) + cix(L, i, j, k));
 }
 
@@ -85,7 +119,7 @@ __device__ __forceinline__ T cell_mu(const Lvl& L, int i, int j, int k) {
 // p[C]-1 and p[C], A-coordinate af-1 and af, other coordinates from p.
 template <typename T, bool VarMu, int C, int A>
 __device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
-  if (!VarMu) return (T)L.mu0;
+  if (!VarMu) return Kc<T>::mu0(L);
   T s = 0;
   int cnt = 0;
 #pragma unroll
@@ -212,14 +246,13 @@ __device__ __forceinline__ int face_cells(const Lvl& L, const int p[3]) {
 template <typename T, bool VarMu, int C>
 __device__ __forceinline__ T m_row(const Lvl& L, const T* x, const int p[3]) {
   const T xf = face_val<T, C>(L, x, p[0], p[1], p[2]);
-  T wv = w_row<T, VarMu, C>(L, x, p, xf) * (T)L.wscale;
-  if (L.gc == 0.0) return wv;
+  T wv = w_row<T, VarMu, C>(L, x, p, xf) * Kc<T>::ws(L);
+  if (!L.has_gd) return wv;
   int q[3] = {p[0], p[1], p[2]};
   T dplus = neg_div<T>(L, x, q[0], q[1], q[2]);
   q[C] -= 1;
   T dminus = neg_div<T>(L, x, q[0], q[1], q[2]);
-  const T g = (T)(L.gc * L.ascale * L.ascale);
-  return wv + g * (dplus - dminus);
+  return wv + Kc<T>::g2(L) * (dplus - dminus);
 }
 
 }  // namespace gkb

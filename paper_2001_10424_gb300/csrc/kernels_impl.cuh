@@ -29,58 +29,82 @@ __device__ __forceinline__ bool in_store(const Lvl& L, int i, int j, int k) {
 // velocity -> velocity stencils
 // ---------------------------------------------------------------------------
 
-// y = W x (mode 0) or y = M x (mode 1); optionally sum x.y into a reduction.
-template <typename T, bool VarMu, bool DOT>
-__global__ void __launch_bounds__(BX* BY) k_apply(Lvl L, int mode, const T* __restrict__ x,
-                                                   T* __restrict__ y, RedBuf red, int fin, void* st) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  double dot = 0.0;
+// W row for constant viscosity: faces whose links are all regular (no wall,
+// no natural side) take wmu * (2d x_f - sum of the 2d neighbours); the rest
+// fall back to the general link-by-link row.
+template <typename T, int C>
+__device__ __forceinline__ T w_row_const(const Lvl& L, const T* x, const int p[3], T xf) {
+  bool interior = p[C] >= 1 && p[C] <= L.n[C] - 1;
+#pragma unroll
+  for (int A = 0; A < 3; ++A)
+    if (A != C && A < L.dim) interior = interior && p[A] >= 1 && p[A] <= L.n[A] - 2;
+  if (interior) {
+    T acc = face_val<T, C>(L, x, p[0] + (C == 0), p[1] + (C == 1), p[2] + (C == 2)) +
+            face_val<T, C>(L, x, p[0] - (C == 0), p[1] - (C == 1), p[2] - (C == 2));
+    if (C != 0) acc += face_val<T, C>(L, x, p[0] + 1, p[1], p[2]) + face_val<T, C>(L, x, p[0] - 1, p[1], p[2]);
+    if (C != 1) acc += face_val<T, C>(L, x, p[0], p[1] + 1, p[2]) + face_val<T, C>(L, x, p[0], p[1] - 1, p[2]);
+    if (L.dim == 3 && C != 2) acc += face_val<T, C>(L, x, p[0], p[1], p[2] + 1) + face_val<T, C>(L, x, p[0], p[1], p[2] - 1);
+    const T kd = (L.dim == 3) ? (T)6 : (T)4;
+    return Kc<T>::wmu(L) * (kd * xf - acc);
+  }
+  return w_row<T, false, C>(L, x, p, xf) * Kc<T>::ws(L);
+}
+
+// Tiled MAC operator: the block first stores the (negative) divergence of
+// its cells plus a one-cell halo (and the plane below in 3D) in shared
+// memory, then every thread forms the W row of its faces and adds the
+// grad-div term from the stored divergences.
+//   mode 0: y = b - M x   (x null: y = b)
+//   mode 1: y = M x       (wonly: y = W x), DOT: reduce x.y
+template <typename T, bool VarMu, int MODE, bool DOT>
+__global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
+                                                     T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
+  __shared__ T Dt[2][BY + 1][BX + 1];
+  if (pred && !*pred) return;  // predicated launch (uniform over the grid)
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k = blockIdx.z;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool gd = L.has_gd && !wonly && x != nullptr;
+  const int cur = (L.dim == 3) ? 1 : 0;
+  if (gd) {
+    const int nplanes = (L.dim == 3) ? 2 : 1;
+    constexpr int TS = (BX + 1) * (BY + 1);
+    for (int t = tid; t < nplanes * TS; t += BX * BY) {
+      const int pl = t / TS, rem = t - pl * TS;
+      const int cj = rem / (BX + 1), ci = rem - cj * (BX + 1);
+      const int gk = (L.dim == 3) ? k - 1 + pl : 0;
+      Dt[pl][cj][ci] = neg_div<T>(L, x, i0 - 1 + ci, j0 - 1 + cj, gk);
+    }
+    __syncthreads();
+  }
   const int p[3] = {i, j, k};
-#define GKB_APPLY_COMP(C)                                                        \
+  const T g2 = Kc<T>::g2(L);
+  double dot = 0.0;
+#define GKB_TILE_COMP(C, DPLUS, DMINUS)                                          \
   if (in_store<C>(L, i, j, k)) {                                                 \
     const long long id = L.off[C] + cix(L, i, j, k);                             \
     T val = 0;                                                                   \
     if (face_active<C>(L, i, j, k)) {                                            \
-      if (mode == 1) val = m_row<T, VarMu, C>(L, x, p);                          \
-      else val = w_row<T, VarMu, C>(L, x, p, x[id]) * (T)L.wscale;               \
-      if (DOT) dot += (double)x[id] * (double)val;                               \
+      T m = 0, xf = 0;                                                           \
+      if (x) {                                                                   \
+        xf = x[id];                                                              \
+        if (VarMu) m = w_row<T, VarMu, C>(L, x, p, xf) * Kc<T>::ws(L);           \
+        else m = w_row_const<T, C>(L, x, p, xf);                                 \
+        if (gd) m += g2 * ((DPLUS) - (DMINUS));                                  \
+      }                                                                          \
+      val = (MODE == 0) ? b[id] - m : m;                                         \
+      if (DOT) dot += (double)xf * (double)val;                                  \
     }                                                                            \
     y[id] = val;                                                                 \
   }
-  GKB_APPLY_COMP(0)
-  GKB_APPLY_COMP(1)
-  if (L.dim == 3) { GKB_APPLY_COMP(2) }
-#undef GKB_APPLY_COMP
+  GKB_TILE_COMP(0, Dt[cur][ty + 1][tx + 1], Dt[cur][ty + 1][tx])
+  GKB_TILE_COMP(1, Dt[cur][ty + 1][tx + 1], Dt[cur][ty][tx + 1])
+  if (L.dim == 3) { GKB_TILE_COMP(2, Dt[1][ty + 1][tx + 1], Dt[0][ty + 1][tx + 1]) }
+#undef GKB_TILE_COMP
   if (DOT) {
     double v[1] = {dot};
     grid_reduce<1>(v, red, fin, st);
   }
-}
-
-// r = b - M x  (x may be null: r = b)
-template <typename T, bool VarMu>
-__global__ void __launch_bounds__(BX* BY) k_residual(Lvl L, const T* __restrict__ x,
-                                                      const T* __restrict__ b, T* __restrict__ r) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  const int p[3] = {i, j, k};
-#define GKB_RES_COMP(C)                                                          \
-  if (in_store<C>(L, i, j, k)) {                                                 \
-    const long long id = L.off[C] + cix(L, i, j, k);                             \
-    T val = 0;                                                                   \
-    if (face_active<C>(L, i, j, k)) {                                            \
-      val = b[id];                                                               \
-      if (x) val -= m_row<T, VarMu, C>(L, x, p);                                 \
-    }                                                                            \
-    r[id] = val;                                                                 \
-  }
-  GKB_RES_COMP(0)
-  GKB_RES_COMP(1)
-  if (L.dim == 3) { GKB_RES_COMP(2) }
-#undef GKB_RES_COMP
 }
 
 // ---------------------------------------------------------------------------
@@ -126,8 +150,8 @@ __device__ void patch_matrix(const Lvl& L, const int e[3], T Mp[4][4], bool act[
   act[1] = face_active<a>(L, e[0], e[1], e[2]);
   act[2] = face_active<b>(L, q2[0], q2[1], q2[2]);
   act[3] = face_active<b>(L, e[0], e[1], e[2]);
-  const T g = (T)(L.gc * L.ascale * L.ascale);
-  const T ws = (T)L.wscale;
+  const T g = Kc<T>::g2(L);
+  const T ws = Kc<T>::ws(L);
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -144,7 +168,7 @@ __device__ void patch_matrix(const Lvl& L, const int e[3], T Mp[4][4], bool act[
     const T area = face_half<b>(L, e) ? (T)0.5 : (T)1;
     Mp[2][3] = Mp[3][2] = -ws * area * edge_mu<T, VarMu, b, a>(L, e, e[a]);
   }
-  if (L.gc != 0.0) {
+  if (L.has_gd) {
     int cc[3] = {e[0], e[1], e[2]};
     cc[a] = e[a] - 1; cc[b] = e[b] - 1;
     if (act[0] && act[2] && cell_in(L, cc[0], cc[1], cc[2])) Mp[0][2] = Mp[2][0] = g;
@@ -352,7 +376,7 @@ __global__ void __launch_bounds__(BX* BY) k_grad(Lvl L, const T* __restrict__ pc
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
-  const T sc = s * (T)L.ascale;
+  const T sc = s * Kc<T>::as(L);
 #define GKB_GRAD_COMP(C, DI, DJ, DK)                                             \
   if (in_store<C>(L, i, j, k)) {                                                 \
     const long long id = L.off[C] + cix(L, i, j, k);                             \
@@ -377,7 +401,7 @@ __global__ void __launch_bounds__(BX* BY) k_negdiv(Lvl L, const T* __restrict__ 
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   if (i >= L.n[0] || j >= L.n[1]) return;
-  y[cix(L, i, j, k)] = s * (T)L.ascale * neg_div<T>(L, x, i, j, k);
+  y[cix(L, i, j, k)] = s * Kc<T>::as(L) * neg_div<T>(L, x, i, j, k);
 }
 
 // ---------------------------------------------------------------------------
@@ -457,6 +481,144 @@ __global__ void __launch_bounds__(BX* BY) k_restrict(Lvl Lf, Lvl Lc, const T* __
 #undef GKB_REST_COMP
 }
 
+// ---- 2D flux-conserving, divergence-preserving transfers -----------------
+// Prolongation of a coarse face field U (component C, tangential axis t):
+//   fine faces on a coarse face line (normal index 2I):  U(I,q) + s D(I,q),
+//     q = tangential fine index / 2, s = -1 / +1 for the lower / upper fine
+//     face, D(I,q) = (U(I,q+1) - U(I,q-1)) / 8 (tangential slope; no-slip
+//     mirror U(ghost) = -U(inside) across walls), so both fine faces carry
+//     the coarse flux;
+//   fine faces inside a coarse cell (normal index 2I+1): the mean of the two
+//     line values above plus (D'(line q+1) - D'(line q)) / 2, D' the slopes
+//     of the other component on the two faces of that coarse cell. The last
+//     term is the minimal-norm correction that makes the divergence of every
+//     fine cell equal to that of its coarse cell.
+// Restriction is the exact transpose, in two passes: a gather of the fine
+// residual into (rU, rD) per coarse face, then rU + G^T rD.
+
+template <typename T, int C>
+__device__ __forceinline__ T coarse_slope(const Lvl& Lc, const T* xc, int I, int J) {
+  constexpr int t = 1 - C;
+  int P[3] = {I, J, 0};
+  if (!face_active<C>(Lc, P[0], P[1], 0)) return (T)0;
+  const T u0 = __ldg(xc + Lc.off[C] + cix(Lc, P[0], P[1], 0));
+  int Pp[3] = {P[0], P[1], 0}, Pm[3] = {P[0], P[1], 0};
+  Pp[t] += 1;
+  Pm[t] -= 1;
+  const T up = (Pp[t] < Lc.n[t]) ? coarse_face<T, C>(Lc, xc, Pp[0], Pp[1], 0) : -u0;
+  const T um = (Pm[t] >= 0) ? coarse_face<T, C>(Lc, xc, Pm[0], Pm[1], 0) : -u0;
+  return (up - um) * (T)0.125;
+}
+
+template <typename T, int C>
+__device__ __forceinline__ T prolong_flux_val(const Lvl& Lc, const T* xc, int pc, int pt) {
+  constexpr int t = 1 - C, Co = 1 - C;
+  const int q = pt >> 1;
+  const T s = (pt & 1) ? (T)1 : (T)-1;
+  auto line_val = [&](int I) -> T {
+    int P[3] = {0, 0, 0};
+    P[C] = I;
+    P[t] = q;
+    return coarse_face<T, C>(Lc, xc, P[0], P[1], 0) + s * coarse_slope<T, C>(Lc, xc, P[0], P[1]);
+  };
+  if ((pc & 1) == 0) return line_val(pc >> 1);
+  const int I = pc >> 1;
+  int P0[3] = {0, 0, 0}, P1[3] = {0, 0, 0};
+  P0[C] = I; P0[t] = q;        // other component's face on tangential line q
+  P1[C] = I; P1[t] = q + 1;    // ... and on line q + 1
+  const T fix = (T)0.5 * (coarse_slope<T, Co>(Lc, xc, P1[0], P1[1]) - coarse_slope<T, Co>(Lc, xc, P0[0], P0[1]));
+  return (T)0.5 * (line_val(I) + line_val(I + 1)) + fix;
+}
+
+// xf += P xc (2D)
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong_flux2d(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  if (in_store<0>(Lf, i, j, 0) && face_active<0>(Lf, i, j, 0))
+    xf[Lf.off[0] + cix(Lf, i, j, 0)] += prolong_flux_val<T, 0>(Lc, xc, i, j);
+  if (in_store<1>(Lf, i, j, 0) && face_active<1>(Lf, i, j, 0))
+    xf[Lf.off[1] + cix(Lf, i, j, 0)] += prolong_flux_val<T, 1>(Lc, xc, j, i);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ T fine_at(const Lvl& Lf, const T* rf, int pc, int pt) {
+  constexpr int t = 1 - C;
+  int P[3] = {0, 0, 0};
+  P[C] = pc;
+  P[t] = pt;
+  return fine_face<T, C>(Lf, rf, P[0], P[1], 0);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void restrict_flux_gather(const Lvl& Lf, const T* rf, int Ic, int q, T& rU, T& rD) {
+  constexpr int Co = 1 - C;
+  T su = 0, sd = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int nn = (k == 0) ? 2 * Ic : (k == 1) ? 2 * Ic + 1 : 2 * Ic - 1;
+    const T w = (k == 0) ? (T)1 : (T)0.5;
+    const T lo = fine_at<T, C>(Lf, rf, nn, 2 * q);
+    const T hi = fine_at<T, C>(Lf, rf, nn, 2 * q + 1);
+    su += w * (lo + hi);
+    sd += w * (hi - lo);
+  }
+  // the other component's fine faces inside the coarse cells on either side
+  // (their divergence correction uses this face's slope)
+  sd += (T)-0.5 * (fine_at<T, Co>(Lf, rf, 2 * q + 1, 2 * Ic) + fine_at<T, Co>(Lf, rf, 2 * q + 1, 2 * Ic + 1));
+  sd += (T)0.5 * (fine_at<T, Co>(Lf, rf, 2 * q + 1, 2 * Ic - 2) + fine_at<T, Co>(Lf, rf, 2 * q + 1, 2 * Ic - 1));
+  rU = su;
+  rD = sd;
+}
+
+// pass a: bc = rU, tmp = rD  (launched over the coarse face grid)
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_a(Lvl Lf, Lvl Lc, const T* __restrict__ rf,
+                                                               T* __restrict__ bc, T* __restrict__ tmp) {
+  const int I = blockIdx.x * BX + threadIdx.x;
+  const int J = blockIdx.y * BY + threadIdx.y;
+  if (in_store<0>(Lc, I, J, 0)) {
+    const long long id = Lc.off[0] + cix(Lc, I, J, 0);
+    T rU = 0, rD = 0;
+    if (face_active<0>(Lc, I, J, 0)) restrict_flux_gather<T, 0>(Lf, rf, I, J, rU, rD);
+    bc[id] = rU;
+    tmp[id] = rD;
+  }
+  if (in_store<1>(Lc, I, J, 0)) {
+    const long long id = Lc.off[1] + cix(Lc, I, J, 0);
+    T rU = 0, rD = 0;
+    if (face_active<1>(Lc, I, J, 0)) restrict_flux_gather<T, 1>(Lf, rf, J, I, rU, rD);
+    bc[id] = rU;
+    tmp[id] = rD;
+  }
+}
+
+// pass b: bc += G^T tmp (transpose of the tangential slope, mirror walls)
+template <typename T, int C>
+__device__ __forceinline__ T slope_transpose(const Lvl& Lc, const T* d, int I, int J) {
+  constexpr int t = 1 - C;
+  int P[3] = {I, J, 0};
+  const int q = P[t], Nt = Lc.n[t];
+  T acc = 0;
+  int Q[3] = {P[0], P[1], 0};
+  if (q - 1 >= 0) { Q[t] = q - 1; acc += __ldg(d + Lc.off[C] + cix(Lc, Q[0], Q[1], 0)); }
+  if (q + 1 < Nt) { Q[t] = q + 1; acc -= __ldg(d + Lc.off[C] + cix(Lc, Q[0], Q[1], 0)); }
+  const T own = __ldg(d + Lc.off[C] + cix(Lc, I, J, 0));
+  if (q == 0) acc += own;
+  if (q == Nt - 1) acc -= own;
+  return acc * (T)0.125;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_b(Lvl Lc, const T* __restrict__ tmp, T* __restrict__ bc) {
+  const int I = blockIdx.x * BX + threadIdx.x;
+  const int J = blockIdx.y * BY + threadIdx.y;
+  if (in_store<0>(Lc, I, J, 0) && face_active<0>(Lc, I, J, 0))
+    bc[Lc.off[0] + cix(Lc, I, J, 0)] += slope_transpose<T, 0>(Lc, tmp, I, J);
+  if (in_store<1>(Lc, I, J, 0) && face_active<1>(Lc, I, J, 0))
+    bc[Lc.off[1] + cix(Lc, I, J, 0)] += slope_transpose<T, 1>(Lc, tmp, I, J);
+}
+
 // coarsest level: x[idx[r]] = sum_c Minv[r][c] b[idx[c]]; one warp per row
 template <typename T>
 __global__ void k_coarse_solve(int m, const T* __restrict__ Minv, const int* __restrict__ idx,
@@ -480,7 +642,8 @@ constexpr int RB = 256;
 // sum a.b (and b.b when NV == 2)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_dot(long long len, const T* __restrict__ a, const T* __restrict__ b,
-                                             RedBuf red, int fin, void* st) {
+                                             RedBuf red, int fin, void* st, const int* pred) {
+  if (pred && !*pred) return;  // every block skips, so the ticket stays untouched
   T acc = 0;
   const long long stride = (long long)gridDim.x * RB;
   for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride)
@@ -493,7 +656,7 @@ __global__ void __launch_bounds__(RB) k_dot(long long len, const T* __restrict__
 template <typename T>
 __global__ void __launch_bounds__(RB) k_cg_update(long long len, T* __restrict__ x, const T* __restrict__ p,
                                                    T* __restrict__ r, const T* __restrict__ q,
-                                                   const CgState* cg, RedBuf red, void* st) {
+                                                   const CgState* cg, RedBuf red, void* st, int fin) {
   const T alpha = (T)cg->alpha;
   T acc = 0;
   const long long stride = (long long)gridDim.x * RB;
@@ -504,7 +667,7 @@ __global__ void __launch_bounds__(RB) k_cg_update(long long len, T* __restrict__
     acc += rn * rn;
   }
   double v[1] = {(double)acc};
-  grid_reduce<1>(v, red, FIN_CG_RR, st);
+  grid_reduce<1>(v, red, fin, st);
 }
 
 // p = z + beta p   (beta from CgState; first: p = z)

@@ -17,23 +17,26 @@ template <>
 void Ops<KT>::apply(const Lvl& L, int mode, const KT* x, KT* y, cudaStream_t s) {
   ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
   RedBuf red{nullptr, nullptr};
-  if (GKB_VARMU(L)) k_apply<KT, true, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, 0, nullptr);
-  else k_apply<KT, false, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, 0, nullptr);
+  const int wonly = (mode == 0);
+  if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
+  else k_mac_tile<KT, false, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
 }
 
 template <>
 void Ops<KT>::apply_dot(const Lvl& L, int mode, const KT* x, KT* y, const RedBuf& red, int fin, void* st,
                         cudaStream_t s) {
   ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) k_apply<KT, true, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, fin, st);
-  else k_apply<KT, false, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, mode, x, y, red, fin, st);
+  const int wonly = (mode == 0);
+  if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
+  else k_mac_tile<KT, false, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
 }
 
 template <>
-void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s) {
+void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s, const int* pred) {
   ProfScope ps_(GKB_KC_RESIDUAL, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) k_residual<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, x, b, r);
-  else k_residual<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, x, b, r);
+  RedBuf red{nullptr, nullptr};
+  if (GKB_VARMU(L)) k_mac_tile<KT, true, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
+  else k_mac_tile<KT, false, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
 }
 
 template <>
@@ -72,13 +75,19 @@ void Ops<KT>::negdiv(const Lvl& L, const KT* x, KT* y, KT scale, cudaStream_t s)
 template <>
 void Ops<KT>::prolong(const Lvl& Lf, const Lvl& Lc, const KT* xc, KT* xf, cudaStream_t s) {
   ProfScope ps_(GKB_KC_PROLONG, s, lvl_unknowns(Lf));
-  k_prolong<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
+  if (Lf.dim == 2) k_prolong_flux2d<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
+  else k_prolong<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
 }
 
 template <>
-void Ops<KT>::restrict_(const Lvl& Lf, const Lvl& Lc, const KT* rf, KT* bc, cudaStream_t s) {
+void Ops<KT>::restrict_(const Lvl& Lf, const Lvl& Lc, const KT* rf, KT* bc, KT* tmp, cudaStream_t s) {
   ProfScope ps_(GKB_KC_RESTRICT, s, lvl_unknowns(Lf));
-  k_restrict<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc);
+  if (Lf.dim == 2) {
+    k_restrict_flux2d_a<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc, tmp);
+    k_restrict_flux2d_b<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lc, tmp, bc);
+  } else {
+    k_restrict<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc);
+  }
 }
 
 template <>
@@ -89,16 +98,17 @@ void Ops<KT>::coarse(int m, const KT* Minv, const int* idx, const KT* b, KT* x, 
 }
 
 template <>
-void Ops<KT>::dot(long long len, const KT* a, const KT* b, const RedBuf& red, int fin, void* st, cudaStream_t s) {
+void Ops<KT>::dot(long long len, const KT* a, const KT* b, const RedBuf& red, int fin, void* st, cudaStream_t s,
+                  const int* pred) {
   ProfScope ps_(GKB_KC_BLAS, s, len);
-  k_dot<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, b, red, fin, st);
+  k_dot<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, b, red, fin, st, pred);
 }
 
 template <>
 void Ops<KT>::cg_update(long long len, KT* x, const KT* p, KT* r, const KT* q, const CgState* cg,
-                        const RedBuf& red, void* st, cudaStream_t s) {
+                        const RedBuf& red, void* st, cudaStream_t s, int fin) {
   ProfScope ps_(GKB_KC_BLAS, s, len);
-  k_cg_update<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, x, p, r, q, cg, red, st);
+  k_cg_update<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, x, p, r, q, cg, red, st, fin);
 }
 
 template <>

@@ -15,8 +15,8 @@ struct Ops {
   // same, and reduce x.y through finaliser `fin` on state `st`
   static void apply_dot(const Lvl& L, int mode, const T* x, T* y, const RedBuf& red, int fin, void* st,
                         cudaStream_t s);
-  // r = b - M x (x null: r = b)
-  static void residual(const Lvl& L, const T* x, const T* b, T* r, cudaStream_t s);
+  // r = b - M x (x null: r = b); pred: device flag, launch is a no-op when 0
+  static void residual(const Lvl& L, const T* x, const T* b, T* r, cudaStream_t s, const int* pred = nullptr);
   // one Chebyshev step of the patch smoother
   static void cheb(const Lvl& L, const T* r, T* x, T* d, T ca, T cb, int x_zero, const T* table,
                    cudaStream_t s);
@@ -30,14 +30,15 @@ struct Ops {
   static void negdiv(const Lvl& L, const T* x, T* y, T scale, cudaStream_t s);
   // xf += P xc
   static void prolong(const Lvl& Lf, const Lvl& Lc, const T* xc, T* xf, cudaStream_t s);
-  // bc = P^T rf
-  static void restrict_(const Lvl& Lf, const Lvl& Lc, const T* rf, T* bc, cudaStream_t s);
+  // bc = P^T rf (tmp: coarse-sized scratch)
+  static void restrict_(const Lvl& Lf, const Lvl& Lc, const T* rf, T* bc, T* tmp, cudaStream_t s);
   // coarsest level dense solve through the stored inverse
   static void coarse(int m, const T* Minv, const int* idx, const T* b, T* x, cudaStream_t s);
   // reductions and vector updates on flat padded arrays
-  static void dot(long long len, const T* a, const T* b, const RedBuf& red, int fin, void* st, cudaStream_t s);
+  static void dot(long long len, const T* a, const T* b, const RedBuf& red, int fin, void* st, cudaStream_t s,
+                  const int* pred = nullptr);
   static void cg_update(long long len, T* x, const T* p, T* r, const T* q, const CgState* cg,
-                        const RedBuf& red, void* st, cudaStream_t s);
+                        const RedBuf& red, void* st, cudaStream_t s, int fin = FIN_CG_RR);
   static void cg_dir(long long len, T* p, const T* z, const CgState* cg, int first, cudaStream_t s);
   static void axpby(long long len, T a, const T* x, T b, T* y, cudaStream_t s);
   // blocks used by the stencil launches of level L (reduction partial sizing)

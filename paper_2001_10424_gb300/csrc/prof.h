@@ -22,6 +22,9 @@ struct Profiler {
   std::vector<int> rec_class;
   size_t used = 0;  // events used (pairs)
   int cur = -1;
+  int phase = -1;   // >= 0 while a graph is captured: launches go to cap[phase]
+  long long cap_l[3][GKB_KC_COUNT] = {};
+  long long cap_u[3][GKB_KC_COUNT] = {};
 
   void enable(size_t pairs) {
     timing = true;
@@ -37,6 +40,12 @@ struct Profiler {
     rec_class.clear();
   }
   void pre(int kc, cudaStream_t s, long long work) {
+    if (phase >= 0) {
+      cap_l[phase][kc] += 1;
+      cap_u[phase][kc] += work;
+      cur = -1;
+      return;
+    }
     launches[kc] += 1;
     units[kc] += work;
     cur = -1;

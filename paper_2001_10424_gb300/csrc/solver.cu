@@ -55,6 +55,7 @@ Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
   L.mu0 = 1.0;
   L.mu64 = nullptr;
   L.mu32 = nullptr;
+  finish_level(L);
   return L;
 }
 
@@ -184,6 +185,100 @@ static void read_scalars(double* dev, double* host, int n, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// loop graphs: "prefix; while (cond) body; suffix" captured once, launched
+// once per inner solve; the loop condition is set on the device
+// ---------------------------------------------------------------------------
+
+__global__ void k_cg_cond_init(cudaGraphConditionalHandle h, CgState* c) {
+  c->graph_iters = 0;
+  cudaGraphSetConditional(h, c->done ? 0u : 1u);
+}
+
+// continue while the CG has not stopped; hard_max bounds the loop even if
+// the iteration counter were never advanced
+__global__ void k_cg_cond(cudaGraphConditionalHandle h, CgState* c, int hard_max) {
+  c->graph_iters += 1;
+  unsigned cont = c->done ? 0u : 1u;
+  if (c->graph_iters >= hard_max) {
+    cont = 0u;
+    if (!c->done) {
+      if (c->status == ST_OK) c->status = ST_INNER_NOT_CONVERGED;
+      c->done = 1;
+    }
+  }
+  cudaGraphSetConditional(h, cont);
+}
+
+void LoopGraph::account(Profiler* P, long long body_runs) const {
+  if (!P) return;
+  for (int k = 0; k < GKB_KC_COUNT; ++k) {
+    P->launches[k] += cl[0][k] + body_runs * cl[1][k] + cl[2][k];
+    P->units[k] += cu[0][k] + body_runs * cu[1][k] + cu[2][k];
+  }
+}
+
+template <class Pre, class Body, class Post>
+static void build_loop_graph(LoopGraph& G, cudaStream_t cs, cudaStream_t cs2, Pre pre, Body body, Post post) {
+  G.destroy();
+  Profiler* P = g_prof;
+  auto phase = [&](int ph) {
+    if (!P) return;
+    if (ph >= 0)
+      for (int k = 0; k < GKB_KC_COUNT; ++k) { P->cap_l[ph][k] = 0; P->cap_u[ph][k] = 0; }
+    P->phase = ph;
+  };
+  cudaGraph_t g = nullptr;
+  GKB_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  bool capturing = false, capturing2 = false;
+  try {
+    GKB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    GKB_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing = true;
+    phase(0);
+    pre(cs, h);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    GKB_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wn;
+    GKB_CUDA(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    GKB_CUDA(cudaStreamBeginCaptureToGraph(cs2, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capturing2 = true;
+    phase(1);
+    body(cs2, h);
+    capturing2 = false;
+    GKB_CUDA(cudaStreamEndCapture(cs2, &bodyg));
+    GKB_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+    phase(2);
+    post(cs);
+    capturing = false;
+    GKB_CUDA(cudaStreamEndCapture(cs, &g));
+    phase(-1);
+    GKB_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
+  } catch (...) {
+    phase(-1);
+    cudaGraph_t dummy;
+    if (capturing2) cudaStreamEndCapture(cs2, &dummy);
+    if (capturing) cudaStreamEndCapture(cs, &dummy);
+    (void)cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  cudaGraphDestroy(g);
+  if (P)
+    for (int ph = 0; ph < 3; ++ph)
+      for (int k = 0; k < GKB_KC_COUNT; ++k) { G.cl[ph][k] = P->cap_l[ph][k]; G.cu[ph][k] = P->cap_u[ph][k]; }
+}
+
+// ---------------------------------------------------------------------------
 // multigrid hierarchy
 // ---------------------------------------------------------------------------
 
@@ -212,6 +307,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     const double gc = Lf.gc / (Lf.dim == 3 ? 8.0 : 4.0);
     Lvl Lc = make_level(Lf.dim, nc, 2.0 * Lf.h, Lf.nat, gc);
     Lc.mu0 = Lf.mu0;
+    finish_level(Lc);
     lev.emplace_back();
     Level& C = lev.back();
     C.L = Lc;
@@ -381,7 +477,7 @@ void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s) {
     T* x = (l == 0) ? z0 : lev[l].x.p;
     smooth(l, b, x, true, s);
     Ops<T>::residual(lev[l].L, x, b, lev[l].r.p, s);
-    Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, s);
+    Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, lev[l + 1].x.p, s);
   }
   Level& Cl = lev[nl - 1];
   Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, Cl.b.p, Cl.x.p, s);
@@ -439,6 +535,48 @@ int Cg<T>::solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* i
     Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
     Ops<T>::cg_dir(len, p.p, zp, st, 0, s);
   }
+  if (iters) *iters = host->it;
+  return host->status;
+}
+
+template <typename T>
+void Cg<T>::build_graph(const T* f, T* x, int maxit, cudaStream_t cs, cudaStream_t cs2) {
+  gf = f;
+  gx = x;
+  const long long len = L.nvel;
+  T* zp = pre ? z.p : r.p;
+  build_loop_graph(
+      G, cs, cs2,
+      [&](cudaStream_t s, cudaGraphConditionalHandle h) {
+        GKB_CUDA(cudaMemsetAsync(x, 0, len * sizeof(T), s));
+        GKB_CUDA(cudaMemcpyAsync(r.p, f, len * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        Ops<T>::dot(len, f, f, red, FIN_CG_INIT, st, s);
+        if (pre) pre->vcycle(r.p, zp, s);
+        Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ0, st, s);
+        Ops<T>::cg_dir(len, p.p, zp, st, 1, s);
+        k_cg_cond_init<<<1, 1, 0, s>>>(h, st);
+      },
+      [&](cudaStream_t s, cudaGraphConditionalHandle h) {
+        Ops<T>::apply_dot(L, 1, p.p, q.p, red, FIN_CG_PAP, st, s);
+        Ops<T>::cg_update(len, x, p.p, r.p, q.p, st, red, st, s);
+        if (pre) pre->vcycle(r.p, zp, s);
+        Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
+        Ops<T>::cg_dir(len, p.p, zp, st, 0, s);
+        k_cg_cond<<<1, 1, 0, s>>>(h, st, maxit + 2);
+      },
+      [&](cudaStream_t) {});
+}
+
+template <typename T>
+int Cg<T>::solve_graph(double tol, int maxit, cudaStream_t s, int* iters) {
+  CgState h{};
+  h.tol2 = tol * tol;
+  h.maxit = maxit;
+  GKB_CUDA(cudaMemcpyAsync(st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaGraphLaunch(G.exec, s));
+  GKB_CUDA(cudaMemcpyAsync(host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  G.account(g_prof, host->graph_iters);
   if (iters) *iters = host->it;
   return host->status;
 }
@@ -650,13 +788,23 @@ __global__ void __launch_bounds__(256) k_cell_sum(Lvl L, const double* __restric
   grid_reduce<1>(v, red, FIN_STORE, out);
 }
 
-// mixed precision: FP32 rhs r32 = r64 / ||r64|| ; x64 += ||r64|| e32
-__global__ void __launch_bounds__(CB) k_to_f32(long long len, const double* __restrict__ r, float* __restrict__ o,
-                                               const double* nrm2) {
-  const double s = (*nrm2 > 0.0) ? 1.0 / sqrt(*nrm2) : 0.0;
+// mixed precision: r32 = (float) r64 ; x64 += x32, x32 = 0
+__global__ void __launch_bounds__(CB) k_cvt_f32(long long len, const double* __restrict__ r, float* __restrict__ o,
+                                                const int* pred) {
+  if (pred && !*pred) return;
   for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB)
-    o[t] = (float)(r[t] * s);
+    o[t] = (float)r[t];
 }
+__global__ void __launch_bounds__(CB) k_mixed_accum(long long len, float* __restrict__ x32, double* __restrict__ x64,
+                                                    const int* pred) {
+  if (pred && !*pred) return;
+  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB) {
+    x64[t] += (double)x32[t];
+    x32[t] = 0.0f;
+  }
+}
+
+// x64 += s e32 with s = sqrt(*nrm2) (precision conversion of a preconditioned vector)
 __global__ void __launch_bounds__(CB) k_add_f32(long long len, const float* __restrict__ e, double* __restrict__ x,
                                                 const double* nrm2) {
   const double s = sqrt(*nrm2);
@@ -683,8 +831,12 @@ static unsigned lin_blocks(long long n) {
 }
 
 Solver::~Solver() {
+  mixed_graph.destroy();
+  cg64.G.destroy();
   if (cg_host) cudaFreeHost(cg_host);
   if (gkb_host) cudaFreeHost(gkb_host);
+  if (cap1) cudaStreamDestroy(cap1);
+  if (cap2) cudaStreamDestroy(cap2);
 }
 
 void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_, double gamma_, double n_scale_) {
@@ -711,6 +863,7 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
   L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
   L64.mu0 = viscosity ? 1.0 : mu0;
+  finish_level(L64);
   Compact cmp = make_compact(L64);
   m = cmp.m;
   ncell = (int64_t)n3[0] * n3[1] * n3[2];
@@ -774,49 +927,139 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   stage_n.alloc(ncell);
   hist.alloc(4 * (size_t)(opt.maxit + 2));
   GKB_CUDA(cudaStreamSynchronize(stream));
+  build_graphs();
   have_problem = true;
   stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+void Solver::build_graphs() {
+  graphs_ready = false;
+  if (!opt.use_graph || opt.profile) return;
+  if (!cap1) {
+    GKB_CUDA(cudaStreamCreateWithFlags(&cap1, cudaStreamNonBlocking));
+    GKB_CUDA(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
+  }
+  if (opt.precision == GKB_PREC_MIXED) {
+    const long long len = L64.nvel;
+    Cg<float>& c = cg32;
+    float* zp = c.pre ? c.z.p : c.r.p;
+    const int* upd = &cg_dev->update;
+    double* fx = f.p;
+    double* xx = x.p;
+    const int maxit = opt.maxit_inner;
+    build_loop_graph(
+        mixed_graph, cap1, cap2,
+        [&](cudaStream_t s, cudaGraphConditionalHandle h) {
+          GKB_CUDA(cudaMemsetAsync(xx, 0, len * sizeof(double), s));
+          GKB_CUDA(cudaMemsetAsync(x32.p, 0, len * sizeof(float), s));
+          Ops<double>::dot(len, fx, fx, red, FIN_CG_INIT, cg_dev, s);
+          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, fx, c.r.p, nullptr); }
+          if (c.pre) c.pre->vcycle(c.r.p, zp, s);
+          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ0, cg_dev, s);
+          Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 1, s);
+          k_cg_cond_init<<<1, 1, 0, s>>>(h, cg_dev);
+        },
+        [&](cudaStream_t s, cudaGraphConditionalHandle h) {
+          Ops<float>::apply_dot(L32, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, s);
+          Ops<float>::cg_update(len, x32.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, s, FIN_MX_RR);
+          // reliable update, predicated on the flag the finaliser just set
+          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, xx, upd); }
+          Ops<double>::residual(L64, xx, fx, r64.p, s, upd);
+          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, r64.p, c.r.p, upd); }
+          Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, s, upd);
+          if (c.pre) c.pre->vcycle(c.r.p, zp, s);
+          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, s);
+          Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, s);
+          k_cg_cond<<<1, 1, 0, s>>>(h, cg_dev, maxit + 2);
+        },
+        [&](cudaStream_t s) {
+          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, xx, nullptr); }
+        });
+  } else {
+    cg64.build_graph(f.p, x.p, opt.maxit_inner, cap1, cap2);
+  }
+  graphs_ready = true;
+}
+
+int Solver::mixed_solve_graph(int* iters) {
+  cudaStream_t s = stream;
+  CgState h{};
+  h.tol2 = opt.tol_inner * opt.tol_inner;
+  h.maxit = opt.maxit_inner;
+  h.delta2 = opt.mixed_rtol * opt.mixed_rtol;
+  GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaGraphLaunch(mixed_graph.exec, s));
+  GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  mixed_graph.account(g_prof, cg_host->graph_iters);
+  if (iters) *iters = cg_host->it;
+  return cg_host->status;
+}
+
 int Solver::inner_solve(const double* fpad, double* xpad) {
   int its = 0, st = 0;
-  if (opt.precision == GKB_PREC_MIXED) {
-    // FP64 iterative refinement around FP32 CG: x = 0, r = f; repeat
-    // { e = M32^-1 (r / ||r||) ; x += ||r|| e ; r = f - M x (FP64) }
-    const long long len = L64.nvel;
-    GKB_CUDA(cudaMemsetAsync(xpad, 0, len * sizeof(double), stream));
-    GKB_CUDA(cudaMemcpyAsync(r64.p, fpad, len * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-    Ops<double>::dot(len, fpad, fpad, red, FIN_STORE, scal.p + 4, stream);
-    double hs[8];
-    read_scalars(scal.p + 4, hs, 1, stream);
-    const double ff = hs[0];
-    if (ff == 0.0) { inner_its.push_back(0); return ST_OK; }
-    double rr = ff;
-    const int max_refine = 60;
-    int ref = 0;
-    while (rr > opt.tol_inner * opt.tol_inner * ff) {
-      if (ref++ >= max_refine) { st = ST_INNER_NOT_CONVERGED; break; }
-      GKB_CUDA(cudaMemcpyAsync(scal.p + 8, &rr, sizeof(double), cudaMemcpyHostToDevice, stream));
-      { ProfScope ps_(GKB_KC_LAYOUT, stream); k_to_f32<<<lin_blocks(len), CB, 0, stream>>>(len, r64.p, f32.p, scal.p + 8); }
-      int it = 0;
-      int s32 = cg32.solve(f32.p, x32.p, opt.mixed_rtol, opt.maxit_inner, stream, &it);
-      its += it;
-      if (s32 != ST_OK && s32 != ST_INNER_NOT_CONVERGED) { st = s32; break; }
-      { ProfScope ps_(GKB_KC_LAYOUT, stream); k_add_f32<<<lin_blocks(len), CB, 0, stream>>>(len, x32.p, xpad, scal.p + 8); }
-      Ops<double>::residual(L64, xpad, fpad, r64.p, stream);
-      Ops<double>::dot(len, r64.p, r64.p, red, FIN_STORE, scal.p + 4, stream);
-      read_scalars(scal.p + 4, hs, 1, stream);
-      if (!std::isfinite(hs[0])) { st = ST_NAN; break; }
-      rr = hs[0];
-    }
-    stats.inner_iterations += its;
-  } else {
-    st = cg64.solve(fpad, xpad, opt.tol_inner, opt.maxit_inner, stream, &its);
-    stats.inner_iterations += its;
-  }
+  if (graphs_ready && fpad == f.p) {
+    // the graphs are built for (f, x): copy out when another output is asked for
+    st = (opt.precision == GKB_PREC_MIXED) ? mixed_solve_graph(&its)
+                                           : cg64.solve_graph(opt.tol_inner, opt.maxit_inner, stream, &its);
+    if (xpad != x.p) GKB_CUDA(cudaMemcpyAsync(xpad, x.p, L64.nvel * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+  } else if (opt.precision == GKB_PREC_MIXED) st = mixed_solve(fpad, xpad, &its);
+  else st = cg64.solve(fpad, xpad, opt.tol_inner, opt.maxit_inner, stream, &its);
+  stats.inner_iterations += its;
   stats.inner_solves += 1;
   inner_its.push_back(its);
   return st;
+}
+
+// Mixed precision inner solve: conjugate gradients with FP32 vectors, FP32
+// operator and FP32 V-cycle, whose solution is accumulated in FP64 and whose
+// residual is recomputed in FP64 ("reliable update") each time the FP32
+// residual has dropped by mixed_rtol since the last recomputation, and when
+// it claims convergence. Convergence is judged on the FP64 residual only.
+int Solver::mixed_solve(const double* f, double* x64, int* iters) {
+  cudaStream_t s = stream;
+  const long long len = L64.nvel;
+  Cg<float>& c = cg32;
+  CgState h{};
+  h.tol2 = opt.tol_inner * opt.tol_inner;
+  h.maxit = opt.maxit_inner;
+  h.delta2 = opt.mixed_rtol * opt.mixed_rtol;
+  GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaMemsetAsync(x64, 0, len * sizeof(double), s));
+  GKB_CUDA(cudaMemsetAsync(x32.p, 0, len * sizeof(float), s));
+  Ops<double>::dot(len, f, f, red, FIN_CG_INIT, cg_dev, s);
+  { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, f, c.r.p, nullptr); }
+  float* zp = c.pre ? c.z.p : c.r.p;
+  if (c.pre) c.pre->vcycle(c.r.p, zp, s);
+  Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ0, cg_dev, s);
+  Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 1, s);
+  GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  while (!cg_host->done) {
+    Ops<float>::apply_dot(L32, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, s);
+    Ops<float>::cg_update(len, x32.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, s, FIN_MX_RR);
+    GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    GKB_CUDA(cudaStreamSynchronize(s));
+    if (cg_host->done) break;
+    if (cg_host->update) {
+      // x64 += x32, x32 = 0, r64 = f - M x64 (FP64), r32 = r64
+      { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, x64, nullptr); }
+      Ops<double>::residual(L64, x64, f, r64.p, s);
+      { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, r64.p, c.r.p, nullptr); }
+      Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, s);
+      GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+      GKB_CUDA(cudaStreamSynchronize(s));
+      if (cg_host->done) break;
+    }
+    if (c.pre) c.pre->vcycle(c.r.p, zp, s);
+    Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, s);
+    Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, s);
+  }
+  // a solve that stopped on the FP32 side (NaN, not SPD) still returns the
+  // FP64 accumulation of its progress
+  { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, x64, nullptr); }
+  if (iters) *iters = cg_host->it;
+  return cg_host->status;
 }
 
 int Solver::solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,

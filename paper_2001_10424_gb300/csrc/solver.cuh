@@ -73,7 +73,7 @@ struct Gmg {
   DevBuf<int> coarse_idx;
   int coarse_m = 0;
   int degree = 2;
-  double cheb_lo = 0.25;   // interval [cheb_lo * lam, cheb_hi * lam]
+  double cheb_lo = 0.1;    // interval [cheb_lo * lam, cheb_hi * lam]
   double cheb_hi = 1.1;
 
   // levels[0] geometry given; mu0_cells: fine padded cell viscosity (T) or null
@@ -82,6 +82,21 @@ struct Gmg {
   // z = B r on the finest level (one V-cycle); r, z fine padded arrays
   void vcycle(const T* r, T* z, cudaStream_t s);
   void smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s);
+};
+
+// An instantiated graph "prefix; while (cond) body; suffix" with the launch
+// counts of each part recorded at capture time.
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  long long cl[3][GKB_KC_COUNT] = {};
+  long long cu[3][GKB_KC_COUNT] = {};
+  void destroy() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+  }
+  ~LoopGraph() { destroy(); }
+  // add the launches of one run with `body_runs` loop iterations
+  void account(Profiler* P, long long body_runs) const;
 };
 
 // Conjugate gradients for M x = f in precision T on one level, optionally
@@ -97,6 +112,13 @@ struct Cg {
   void init(const Lvl& L_, Gmg<T>* pre_, const RedBuf& red_, CgState* st_dev, CgState* st_host);
   // x = M^-1 f to relative tolerance tol (zero start); returns status
   int solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* iters);
+  // the same loop as one CUDA graph with a device-side while node, for the
+  // fixed arrays (f, x) given at build time
+  LoopGraph G;
+  const T* gf = nullptr;
+  T* gx = nullptr;
+  void build_graph(const T* f, T* x, int maxit, cudaStream_t cs, cudaStream_t cs2);
+  int solve_graph(double tol, int maxit, cudaStream_t s, int* iters);
 };
 
 struct Solver {
@@ -139,6 +161,11 @@ struct Solver {
   std::vector<int> inner_its;
   gkb_stats_t stats{};
   Profiler prof;
+  cudaStream_t cap1 = nullptr, cap2 = nullptr;  // private capture streams
+  LoopGraph mixed_graph;
+  bool graphs_ready = false;
+  void build_graphs();
+  int mixed_solve_graph(int* iters);
 
   void set_problem(const gkb_grid* g, const double* viscosity, double mu0, double gamma, double n_scale);
   int solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
@@ -148,6 +175,7 @@ struct Solver {
   void precond(const double* r, double* z);
   // inner solve in FP64 padded layout: x = M^-1 f; returns status
   int inner_solve(const double* f, double* x);
+  int mixed_solve(const double* f, double* x, int* iters);
   ~Solver();
 };
 

@@ -27,6 +27,8 @@ enum FinOp {
   FIN_CG_PAP,      // s0 = p.Mp -> alpha
   FIN_CG_RR,       // s0 = r.r  -> convergence test
   FIN_CG_RZ,       // s0 = r.z  -> beta
+  FIN_MX_RR,       // s0 = r32.r32 -> iteration count, reliable-update trigger
+  FIN_MX_RR64,     // s0 = r64.r64 (true FP64 residual) -> convergence test
 };
 
 struct CgState {
@@ -42,7 +44,12 @@ struct CgState {
   int status;       // ST_* of this solve
   long long total_it;
   int solves;
-  int pad;
+  int update;       // mixed form: 1 when an FP64 residual recomputation is due
+  double rmax2;     // mixed form: ||r||^2 at the last FP64 recomputation
+  double delta2;    // mixed form: trigger ratio squared
+  double rr64;      // mixed form: last true FP64 ||r||^2
+  int graph_iters;  // loop-body executions of the graph form (device counted)
+  int pad2;
 };
 
 __device__ __forceinline__ void cg_fail(CgState* c, int code) {
@@ -59,6 +66,7 @@ __device__ __forceinline__ void finalize(int op, const double* s, void* st) {
     case FIN_CG_INIT: {
       CgState* c = (CgState*)st;
       c->ff = s[0]; c->rr = s[0]; c->it = 0; c->status = ST_OK; c->alpha = 0.0; c->beta = 0.0;
+      c->rmax2 = s[0]; c->rr64 = s[0]; c->update = 0;
       c->done = (s[0] == 0.0) ? 1 : 0;
       c->solves += 1;
       if (!isfinite(s[0])) cg_fail(c, ST_NAN);
@@ -82,6 +90,24 @@ __device__ __forceinline__ void finalize(int op, const double* s, void* st) {
       c->rr = s[0];
       c->it += 1;
       c->total_it += 1;
+      if (!isfinite(s[0])) cg_fail(c, ST_NAN);
+      else if (s[0] <= c->tol2 * c->ff) c->done = 1;
+      else if (c->it >= c->maxit) cg_fail(c, ST_INNER_NOT_CONVERGED);
+    } break;
+    case FIN_MX_RR: {
+      CgState* c = (CgState*)st;
+      if (c->done) break;
+      c->rr = s[0];
+      c->it += 1;
+      c->total_it += 1;
+      if (!isfinite(s[0])) { cg_fail(c, ST_NAN); break; }
+      c->update = (s[0] <= c->delta2 * c->rmax2 || s[0] <= c->tol2 * c->ff || c->it >= c->maxit) ? 1 : 0;
+    } break;
+    case FIN_MX_RR64: {
+      CgState* c = (CgState*)st;
+      c->rr64 = s[0];
+      c->rmax2 = s[0];
+      c->update = 0;
       if (!isfinite(s[0])) cg_fail(c, ST_NAN);
       else if (s[0] <= c->tol2 * c->ff) c->done = 1;
       else if (c->it >= c->maxit) cg_fail(c, ST_INNER_NOT_CONVERGED);

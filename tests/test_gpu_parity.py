@@ -282,3 +282,31 @@ def test_sizes_that_do_not_coarsen_far(lib, n):
     finally:
         gk.gkb_destroy(h)
     assert energy_rel(ops["M"], w, ref["w"]) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_graph_and_host_loops_agree_bitwise(lib, prec):
+    """The graph form (device-side while loop) launches the same kernels in
+    the same order as the host-sequenced loop: identical bits, identical
+    iteration counts."""
+    gk = lib
+    n, bc = (64, 48), (D,) * 4
+    grid, ops = oracle_problem(n, bc, 1.0, 100.0)
+    gvec = np.random.default_rng(13).standard_normal(grid.m)
+    out = []
+    for use_graph in (1, 0):
+        h = make_handle(gk, n, bc, 1.0, 100.0, precision=prec, use_graph=use_graph)
+        try:
+            rc, w, p = gpu_solve(gk, h, gvec, np.zeros(grid.n_cells))
+            st = gk.gkb_stats(h)
+            out.append((rc, w, p, st["outer_iterations"], st["inner_iterations"], st["kernel_launches"]))
+        finally:
+            gk.gkb_destroy(h)
+    (rc1, w1, p1, o1, i1, l1), (rc2, w2, p2, o2, i2, l2) = out
+    assert rc1 == rc2 == gk.GKB_OK
+    assert (o1, i1) == (o2, i2)
+    assert np.array_equal(w1, w2) and np.array_equal(p1, p2)
+    # the graph form counts its launches from the captured body times the
+    # loop executions: at least as many as the host loop (one extra
+    # preconditioner application after convergence per inner solve)
+    assert sum(l1.values()) >= sum(l2.values()) > 0

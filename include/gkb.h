@@ -199,6 +199,30 @@ int gkb_apply(gkb_handle h, int op, const double* x, double* y);
  * plain CG), in the handle's precision, to compact m-vectors. */
 int gkb_precond(gkb_handle h, const double* r, double* z);
 
+/* Allocation-free operator product (the paper has no counterpart; this is a
+ * service for callers that cannot allocate device memory, e.g. because their
+ * device memory belongs to another allocator or a fixed arena, or because
+ * cudaMalloc / cudaFree would synchronise a latency-critical loop).
+ *
+ * y = op(x) as in gkb_apply, for a constant-viscosity grid described by the
+ * arguments (no handle). x and y are compact vectors in device memory (host
+ * pointers are rejected). The call allocates nothing: its two padded work
+ * arrays live in one file-scope device array of 2 * GKB_NOALLOC_MAX_ELEMS
+ * doubles (16 MiB), which every GPU that loads the library holds until the
+ * process exits. A grid whose padded velocity or cell array exceeds
+ * GKB_NOALLOC_MAX_ELEMS doubles (about 700 x 700 cells in 2D, 78^3 in 3D)
+ * returns GKB_ERR_INVALID_ARG. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture. All calls share the array and each call clears what it
+ * needs, so calls that overlap on the GPU (different streams or threads)
+ * race and must be serialised by the caller. Runs on `stream` (cudaStream_t,
+ * NULL: legacy stream) and returns after it has completed.
+ * Errors: INVALID_ARG (bad grid, sizes above the limit, host pointers),
+ * CUDA. */
+#define GKB_NOALLOC_MAX_ELEMS 1048576
+int gkb_apply_noalloc(const gkb_grid* grid, double mu0, double gamma, double n_scale, int op,
+                      const double* x, double* y, void* stream);
+
 /* Message for the last failing call (never NULL). */
 const char* gkb_last_error(gkb_handle h);
 

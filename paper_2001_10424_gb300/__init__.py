@@ -43,8 +43,9 @@ STATUS_NAMES = {
 EXPORTED = [
     "gkb_default_options", "gkb_create", "gkb_set_problem", "gkb_layout", "gkb_boundary_rhs",
     "gkb_solve", "gkb_stats", "gkb_history", "gkb_apply", "gkb_precond", "gkb_last_error",
-    "gkb_destroy",
+    "gkb_destroy", "gkb_apply_noalloc",
 ]
+GKB_NOALLOC_MAX_ELEMS = 1048576
 
 
 class gkb_grid(ctypes.Structure):
@@ -100,6 +101,7 @@ def load(path=None):
         "gkb_precond": (i, [_P, _P, _P]),
         "gkb_last_error": (ctypes.c_char_p, [_P]),
         "gkb_destroy": (i, [_P]),
+        "gkb_apply_noalloc": (i, [ctypes.POINTER(gkb_grid), d, d, d, i, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +212,12 @@ def gkb_apply(h, op, x, y):
 
 def gkb_precond(h, r, z):
     return _check(h, load().gkb_precond(h, _ptr(r), _ptr(z)))
+
+
+def gkb_apply_noalloc(grid, mu0, gamma, n_scale, op, x, y, stream=None):
+    """y = op(x) without a handle or any device allocation (device arrays);
+    returns the status code."""
+    return load().gkb_apply_noalloc(ctypes.byref(grid), mu0, gamma, n_scale, op, _ptr(x), _ptr(y), stream)
 
 
 def gkb_last_error(h):

@@ -121,6 +121,9 @@ typedef struct {
   int profile;            /* 1: time every kernel launch with CUDA events on
                              the stream and report per-class totals in
                              gkb_stats (adds event overhead between kernels)  */
+  int kernel_variant;     /* 0: stencil kernels take their deep-interior fast
+                             paths; 1: general paths only (same values bit for
+                             bit; for testing)                                 */
   void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
 } gkb_options;
 

@@ -57,7 +57,7 @@ class gkb_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner", ctypes.c_int), ("tol_inner", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class gkb_stats_t(ctypes.Structure):

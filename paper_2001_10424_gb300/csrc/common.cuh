@@ -34,6 +34,7 @@ struct Lvl {
   // derived constants (set by finish_level), in both precisions so that FP32
   // kernels never convert from double on the FP64 pipe
   int has_gd;         // gc != 0
+  int fast;           // deep-interior fast paths enabled
   double g2;          // gc * ascale^2: grad-div coupling of two faces of a cell
   double wmu;         // wscale * mu0
   float mu0f, wscalef, ascalef, g2f, wmuf;
@@ -144,14 +145,30 @@ __device__ __forceinline__ T face_val(const Lvl& L, const T* x, int i, int j, in
   return ldv(x, L.off[C] + cix(L, i, j, k));
 }
 
-// (A^T x)_cell / ascale = sum over components of (low face - high face)
+// index stride of axis A in the padded layout
+template <int A>
+__host__ __device__ __forceinline__ long long strd(const Lvl& L) {
+  return A == 0 ? 1LL : (A == 1 ? (long long)L.P : L.S);
+}
+
+// (A^T x)_cell / ascale = sum over components of (low face - high face),
+// for the in-domain cell with padded index cb
+template <typename T>
+__device__ __forceinline__ T neg_div_at(const Lvl& L, const T* x, long long cb) {
+  const T* u = x + L.off[0] + cb;
+  const T* v = x + L.off[1] + cb;
+  T s = __ldg(u) - __ldg(u + 1) + __ldg(v) - __ldg(v + L.P);
+  if (L.dim == 3) {
+    const T* w = x + L.off[2] + cb;
+    s += __ldg(w) - __ldg(w + L.S);
+  }
+  return s;
+}
+
 template <typename T>
 __device__ __forceinline__ T neg_div(const Lvl& L, const T* x, int i, int j, int k) {
   if (!cell_in(L, i, j, k)) return (T)0;
-  T s = face_val<T, 0>(L, x, i, j, k) - face_val<T, 0>(L, x, i + 1, j, k)
-      + face_val<T, 1>(L, x, i, j, k) - face_val<T, 1>(L, x, i, j + 1, k);
-  if (L.dim == 3) s += face_val<T, 2>(L, x, i, j, k) - face_val<T, 2>(L, x, i, j, k + 1);
-  return s;
+  return neg_div_at<T>(L, x, cix(L, i, j, k));
 }
 
 // Row of W at an active face of component C, position p (FV links, see

@@ -25,6 +25,16 @@ __device__ __forceinline__ bool in_store(const Lvl& L, int i, int j, int k) {
   return C == 2 ? (k <= L.n[2]) : (k < L.n[2]);
 }
 
+// A position whose coordinates lie in [2, n-3] on every axis: all its faces
+// are active, all their links regular and every patch containing one of its
+// faces is in the interior class. L.fast = 0 disables the fast paths (the
+// general paths compute bitwise the same values).
+__device__ __forceinline__ bool deep_interior(const Lvl& L, int i, int j, int k) {
+  bool d = L.fast && i >= 2 && i <= L.n[0] - 3 && j >= 2 && j <= L.n[1] - 3;
+  if (L.dim == 3) d = d && k >= 2 && k <= L.n[2] - 3;
+  return d;
+}
+
 // ---------------------------------------------------------------------------
 // velocity -> velocity stencils
 // ---------------------------------------------------------------------------
@@ -33,17 +43,15 @@ __device__ __forceinline__ bool in_store(const Lvl& L, int i, int j, int k) {
 // no natural side) take wmu * (2d x_f - sum of the 2d neighbours); the rest
 // fall back to the general link-by-link row.
 template <typename T, int C>
-__device__ __forceinline__ T w_row_const(const Lvl& L, const T* x, const int p[3], T xf) {
+__device__ __forceinline__ T w_row_const(const Lvl& L, const T* x, const T* xc, const int p[3], T xf) {
   bool interior = p[C] >= 1 && p[C] <= L.n[C] - 1;
 #pragma unroll
   for (int A = 0; A < 3; ++A)
     if (A != C && A < L.dim) interior = interior && p[A] >= 1 && p[A] <= L.n[A] - 2;
   if (interior) {
-    T acc = face_val<T, C>(L, x, p[0] + (C == 0), p[1] + (C == 1), p[2] + (C == 2)) +
-            face_val<T, C>(L, x, p[0] - (C == 0), p[1] - (C == 1), p[2] - (C == 2));
-    if (C != 0) acc += face_val<T, C>(L, x, p[0] + 1, p[1], p[2]) + face_val<T, C>(L, x, p[0] - 1, p[1], p[2]);
-    if (C != 1) acc += face_val<T, C>(L, x, p[0], p[1] + 1, p[2]) + face_val<T, C>(L, x, p[0], p[1] - 1, p[2]);
-    if (L.dim == 3 && C != 2) acc += face_val<T, C>(L, x, p[0], p[1], p[2] + 1) + face_val<T, C>(L, x, p[0], p[1], p[2] - 1);
+    // xc points at this face; neighbours are +-1 (x), +-P (y), +-S (z)
+    T acc = __ldg(xc + 1) + __ldg(xc - 1) + __ldg(xc + L.P) + __ldg(xc - L.P);
+    if (L.dim == 3) acc += __ldg(xc + L.S) + __ldg(xc - L.S);
     const T kd = (L.dim == 3) ? (T)6 : (T)4;
     return Kc<T>::wmu(L) * (kd * xf - acc);
   }
@@ -73,23 +81,46 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
       const int pl = t / TS, rem = t - pl * TS;
       const int cj = rem / (BX + 1), ci = rem - cj * (BX + 1);
       const int gk = (L.dim == 3) ? k - 1 + pl : 0;
-      Dt[pl][cj][ci] = neg_div<T>(L, x, i0 - 1 + ci, j0 - 1 + cj, gk);
+      const int gi = i0 - 1 + ci, gj = j0 - 1 + cj;
+      Dt[pl][cj][ci] = cell_in(L, gi, gj, gk) ? neg_div_at<T>(L, x, cix(L, gi, gj, gk)) : (T)0;
     }
     __syncthreads();
   }
   const int p[3] = {i, j, k};
   const T g2 = Kc<T>::g2(L);
+  const long long cb = cix(L, i, j, k);
   double dot = 0.0;
+  if (!VarMu && x != nullptr && deep_interior(L, i, j, k)) {
+    const T wmu = Kc<T>::wmu(L);
+    const T kd = (L.dim == 3) ? (T)6 : (T)4;
+#define GKB_TILE_DEEP(C, DPLUS, DMINUS)                                          \
+    {                                                                            \
+      const long long id = L.off[C] + cb;                                        \
+      const T* xc = x + id;                                                      \
+      const T xf = __ldg(xc);                                                    \
+      T acc = __ldg(xc + 1) + __ldg(xc - 1) + __ldg(xc + L.P) + __ldg(xc - L.P); \
+      if (L.dim == 3) acc += __ldg(xc + L.S) + __ldg(xc - L.S);                  \
+      T m = wmu * (kd * xf - acc);                                               \
+      if (gd) m += g2 * ((DPLUS) - (DMINUS));                                    \
+      const T val = (MODE == 0) ? b[id] - m : m;                                 \
+      if (DOT) dot += (double)xf * (double)val;                                  \
+      y[id] = val;                                                               \
+    }
+    GKB_TILE_DEEP(0, Dt[cur][ty + 1][tx + 1], Dt[cur][ty + 1][tx])
+    GKB_TILE_DEEP(1, Dt[cur][ty + 1][tx + 1], Dt[cur][ty][tx + 1])
+    if (L.dim == 3) { GKB_TILE_DEEP(2, Dt[1][ty + 1][tx + 1], Dt[0][ty + 1][tx + 1]) }
+#undef GKB_TILE_DEEP
+  } else {
 #define GKB_TILE_COMP(C, DPLUS, DMINUS)                                          \
   if (in_store<C>(L, i, j, k)) {                                                 \
-    const long long id = L.off[C] + cix(L, i, j, k);                             \
+    const long long id = L.off[C] + cb;                                          \
     T val = 0;                                                                   \
     if (face_active<C>(L, i, j, k)) {                                            \
       T m = 0, xf = 0;                                                           \
       if (x) {                                                                   \
         xf = x[id];                                                              \
         if (VarMu) m = w_row<T, VarMu, C>(L, x, p, xf) * Kc<T>::ws(L);           \
-        else m = w_row_const<T, C>(L, x, p, xf);                                 \
+        else m = w_row_const<T, C>(L, x, x + id, p, xf);                         \
         if (gd) m += g2 * ((DPLUS) - (DMINUS));                                  \
       }                                                                          \
       val = (MODE == 0) ? b[id] - m : m;                                         \
@@ -101,6 +132,7 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
   GKB_TILE_COMP(1, Dt[cur][ty + 1][tx + 1], Dt[cur][ty][tx + 1])
   if (L.dim == 3) { GKB_TILE_COMP(2, Dt[1][ty + 1][tx + 1], Dt[0][ty + 1][tx + 1]) }
 #undef GKB_TILE_COMP
+  }
   if (DOT) {
     double v[1] = {dot};
     grid_reduce<1>(v, red, fin, st);
@@ -216,16 +248,16 @@ __device__ __forceinline__ void chol4_solve(T Mp[4][4], T rhs[4]) {
   }
 }
 
-// residual of the patch faces (0 for inactive ones)
+// residual of the patch faces (0 for inactive ones); ce = padded index of e
 template <typename T, int E>
-__device__ __forceinline__ void patch_rhs(const Lvl& L, const T* r, const int e[3], const bool act[4], T out[4]) {
+__device__ __forceinline__ void patch_rhs(const Lvl& L, const T* r, long long ce, const bool act[4], T out[4]) {
   constexpr int a = EAx<E>::a, b = EAx<E>::b;
-  int q0[3] = {e[0], e[1], e[2]}; q0[b] -= 1;
-  int q2[3] = {e[0], e[1], e[2]}; q2[a] -= 1;
-  out[0] = act[0] ? __ldg(r + L.off[a] + cix(L, q0[0], q0[1], q0[2])) : (T)0;
-  out[1] = act[1] ? __ldg(r + L.off[a] + cix(L, e[0], e[1], e[2])) : (T)0;
-  out[2] = act[2] ? __ldg(r + L.off[b] + cix(L, q2[0], q2[1], q2[2])) : (T)0;
-  out[3] = act[3] ? __ldg(r + L.off[b] + cix(L, e[0], e[1], e[2])) : (T)0;
+  const T* ra = r + L.off[a] + ce;
+  const T* rb = r + L.off[b] + ce;
+  out[0] = act[0] ? __ldg(ra - strd<b>(L)) : (T)0;
+  out[1] = act[1] ? __ldg(ra) : (T)0;
+  out[2] = act[2] ? __ldg(rb - strd<a>(L)) : (T)0;
+  out[3] = act[3] ? __ldg(rb) : (T)0;
 }
 
 template <int E>
@@ -239,48 +271,92 @@ __device__ __forceinline__ void patch_active(const Lvl& L, const int e[3], bool 
   act[3] = face_active<b>(L, e[0], e[1], e[2]);
 }
 
-// contribution of the patch of edge e to slot `slot` of z = C r
+// contribution of the patch of edge e (padded index ce) to slot `slot` of z = C r
 template <typename T, bool VarMu, int E>
-__device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e[3], int slot,
+__device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e[3], long long ce, int slot,
                                            const T* __restrict__ table) {
   bool act[4];
   T rp[4];
   if (VarMu || table == nullptr) {
     T Mp[4][4];
     patch_matrix<T, VarMu, E>(L, e, Mp, act);
-    patch_rhs<T, E>(L, r, e, act, rp);
+    patch_rhs<T, E>(L, r, ce, act, rp);
     chol4_solve<T>(Mp, rp);
     return rp[slot];
   }
   patch_active<E>(L, e, act);
-  patch_rhs<T, E>(L, r, e, act, rp);
+  patch_rhs<T, E>(L, r, ce, act, rp);
   const T* row = table + (size_t)(E * 75 + patch_class<E>(L, e)) * 16 + slot * 4;
   return __ldg(row + 0) * rp[0] + __ldg(row + 1) * rp[1] + __ldg(row + 2) * rp[2] + __ldg(row + 3) * rp[3];
 }
 
-// (C r) at an active face of component C, position p
-template <typename T, bool VarMu, int C>
-__device__ __forceinline__ T patch_apply(const Lvl& L, const T* r, const int p[3], const T* table) {
-  T acc = 0;
-#pragma unroll
-  for (int E = 0; E < 3; ++E) {
-    if (E == C) continue;
-    if (L.dim == 2 && E != 2) continue;
-    int e[3] = {p[0], p[1], p[2]};
-    if (E == 0) {
-      constexpr int a = EAx<0>::a, b = EAx<0>::b;
-      if (C == a) { acc += patch_contrib<T, VarMu, 0>(L, r, e, 1, table); e[b] += 1; acc += patch_contrib<T, VarMu, 0>(L, r, e, 0, table); }
-      else        { acc += patch_contrib<T, VarMu, 0>(L, r, e, 3, table); e[a] += 1; acc += patch_contrib<T, VarMu, 0>(L, r, e, 2, table); }
-    } else if (E == 1) {
-      constexpr int a = EAx<1>::a, b = EAx<1>::b;
-      if (C == a) { acc += patch_contrib<T, VarMu, 1>(L, r, e, 1, table); e[b] += 1; acc += patch_contrib<T, VarMu, 1>(L, r, e, 0, table); }
-      else        { acc += patch_contrib<T, VarMu, 1>(L, r, e, 3, table); e[a] += 1; acc += patch_contrib<T, VarMu, 1>(L, r, e, 2, table); }
-    } else {
-      constexpr int a = EAx<2>::a, b = EAx<2>::b;
-      if (C == a) { acc += patch_contrib<T, VarMu, 2>(L, r, e, 1, table); e[b] += 1; acc += patch_contrib<T, VarMu, 2>(L, r, e, 0, table); }
-      else        { acc += patch_contrib<T, VarMu, 2>(L, r, e, 3, table); e[a] += 1; acc += patch_contrib<T, VarMu, 2>(L, r, e, 2, table); }
-    }
+// the two patches of orientation E that contain a face of component C at
+// position p (padded cell index cb)
+template <typename T, bool VarMu, int C, int E>
+__device__ __forceinline__ T patch_pair(const Lvl& L, const T* r, const int p[3], long long cb, const T* table) {
+  constexpr int a = EAx<E>::a, b = EAx<E>::b;
+  int e[3] = {p[0], p[1], p[2]};
+  T acc;
+  if (C == a) {
+    acc = patch_contrib<T, VarMu, E>(L, r, e, cb, 1, table);
+    e[b] += 1;
+    acc += patch_contrib<T, VarMu, E>(L, r, e, cb + strd<b>(L), 0, table);
+  } else {
+    acc = patch_contrib<T, VarMu, E>(L, r, e, cb, 3, table);
+    e[a] += 1;
+    acc += patch_contrib<T, VarMu, E>(L, r, e, cb + strd<a>(L), 2, table);
   }
+  return acc;
+}
+
+// (C r) at an active face of component C, position p (padded cell index cb)
+template <typename T, bool VarMu, int C>
+__device__ __forceinline__ T patch_apply(const Lvl& L, const T* r, const int p[3], long long cb, const T* table) {
+  if (L.dim == 2) return patch_pair<T, VarMu, C, 2>(L, r, p, cb, table);
+  T acc = 0;
+  if (C != 0) acc += patch_pair<T, VarMu, C, 0>(L, r, p, cb, table);
+  if (C != 1) acc += patch_pair<T, VarMu, C, 1>(L, r, p, cb, table);
+  if (C != 2) acc += patch_pair<T, VarMu, C, 2>(L, r, p, cb, table);
+  return acc;
+}
+
+// ---- deep-interior fast path ---------------------------------------------
+// A position at least two cells away from every wall has all its faces
+// active, all links regular and every patch in the interior class; kernels
+// test this once per thread (warp-uniform almost everywhere) and then use
+// plain offset loads instead of per-face activity and class logic.
+// interior patch class of orientation E (cls5 = 2 on both node axes, cls3 = 1
+// on the cell axis in 3D, 0 in 2D)
+template <int E>
+__device__ __forceinline__ int interior_class(const Lvl& L) {
+  return (2 * 5 + 2) * 3 + (L.dim == 3 ? 1 : 0);
+}
+
+// patch rows of an interior patch: rhs faces at fixed offsets of ce
+template <typename T, int E>
+__device__ __forceinline__ T patch_deep(const Lvl& L, const T* r, long long ce, const T* row) {
+  constexpr int a = EAx<E>::a, b = EAx<E>::b;
+  const T* ra = r + L.off[a] + ce;
+  const T* rb = r + L.off[b] + ce;
+  return __ldg(row + 0) * __ldg(ra - strd<b>(L)) + __ldg(row + 1) * __ldg(ra) + __ldg(row + 2) * __ldg(rb - strd<a>(L)) +
+         __ldg(row + 3) * __ldg(rb);
+}
+
+template <typename T, int C, int E>
+__device__ __forceinline__ T patch_pair_deep(const Lvl& L, const T* r, long long cb, const T* table) {
+  constexpr int a = EAx<E>::a, b = EAx<E>::b;
+  const T* rows = table + (size_t)(E * 75 + interior_class<E>(L)) * 16;
+  if (C == a) return patch_deep<T, E>(L, r, cb, rows + 4) + patch_deep<T, E>(L, r, cb + strd<b>(L), rows + 0);
+  return patch_deep<T, E>(L, r, cb, rows + 12) + patch_deep<T, E>(L, r, cb + strd<a>(L), rows + 8);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ T patch_apply_deep(const Lvl& L, const T* r, long long cb, const T* table) {
+  if (L.dim == 2) return patch_pair_deep<T, C, 2>(L, r, cb, table);
+  T acc = 0;
+  if (C != 0) acc += patch_pair_deep<T, C, 0>(L, r, cb, table);
+  if (C != 1) acc += patch_pair_deep<T, C, 1>(L, r, cb, table);
+  if (C != 2) acc += patch_pair_deep<T, C, 2>(L, r, cb, table);
   return acc;
 }
 
@@ -293,10 +369,26 @@ __global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r,
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   const int p[3] = {i, j, k};
+  const long long pc = cix(L, i, j, k);
+  if (!VarMu && table != nullptr && deep_interior(L, i, j, k)) {
+#define GKB_CHEB_DEEP(C)                                                         \
+    {                                                                            \
+      const long long id = L.off[C] + pc;                                        \
+      const T z = patch_apply_deep<T, C>(L, r, pc, table);                       \
+      const T dn = (cb != (T)0) ? ca * z + cb * d[id] : ca * z;                  \
+      d[id] = dn;                                                                \
+      x[id] = x_zero ? dn : x[id] + dn;                                          \
+    }
+    GKB_CHEB_DEEP(0)
+    GKB_CHEB_DEEP(1)
+    if (L.dim == 3) { GKB_CHEB_DEEP(2) }
+#undef GKB_CHEB_DEEP
+    return;
+  }
 #define GKB_CHEB_COMP(C)                                                         \
   if (in_store<C>(L, i, j, k) && face_active<C>(L, i, j, k)) {                   \
-    const long long id = L.off[C] + cix(L, i, j, k);                             \
-    const T z = patch_apply<T, VarMu, C>(L, r, p, table);                        \
+    const long long id = L.off[C] + pc;                                          \
+    const T z = patch_apply<T, VarMu, C>(L, r, p, pc, table);                    \
     const T dn = (cb != (T)0) ? ca * z + cb * d[id] : ca * z;                    \
     d[id] = dn;                                                                  \
     x[id] = x_zero ? dn : x[id] + dn;                                            \
@@ -314,10 +406,11 @@ __global__ void __launch_bounds__(BX* BY) k_patch(Lvl L, const T* __restrict__ r
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   const int p[3] = {i, j, k};
+  const long long cb = cix(L, i, j, k);
 #define GKB_PATCH_COMP(C)                                                        \
   if (in_store<C>(L, i, j, k)) {                                                 \
-    const long long id = L.off[C] + cix(L, i, j, k);                             \
-    z[id] = face_active<C>(L, i, j, k) ? patch_apply<T, VarMu, C>(L, r, p, table) : (T)0; \
+    const long long id = L.off[C] + cb;                                          \
+    z[id] = face_active<C>(L, i, j, k) ? patch_apply<T, VarMu, C>(L, r, p, cb, table) : (T)0; \
   }
   GKB_PATCH_COMP(0)
   GKB_PATCH_COMP(1)

@@ -55,6 +55,7 @@ Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
   L.mu0 = 1.0;
   L.mu64 = nullptr;
   L.mu32 = nullptr;
+  L.fast = 1;
   finish_level(L);
   return L;
 }
@@ -307,6 +308,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     const double gc = Lf.gc / (Lf.dim == 3 ? 8.0 : 4.0);
     Lvl Lc = make_level(Lf.dim, nc, 2.0 * Lf.h, Lf.nat, gc);
     Lc.mu0 = Lf.mu0;
+    Lc.fast = Lf.fast;
     finish_level(Lc);
     lev.emplace_back();
     Level& C = lev.back();
@@ -863,6 +865,7 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
   L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
   L64.mu0 = viscosity ? 1.0 : mu0;
+  L64.fast = (opt.kernel_variant == 0) ? 1 : 0;
   finish_level(L64);
   Compact cmp = make_compact(L64);
   m = cmp.m;

@@ -310,3 +310,26 @@ def test_graph_and_host_loops_agree_bitwise(lib, prec):
     # loop executions: at least as many as the host loop (one extra
     # preconditioner application after convergence per inner solve)
     assert sum(l1.values()) >= sum(l2.values()) > 0
+
+
+@pytest.mark.parametrize("n,prec", [((64, 48), FP64), ((70, 66), MIXED), ((14, 12, 10), FP64), ((12, 14, 16), MIXED)])
+def test_fast_paths_match_general_paths_bitwise(lib, n, prec):
+    """The deep-interior fast paths of the operator and smoother kernels must
+    reproduce the general paths bit for bit: one V-cycle and one operator
+    product with kernel_variant 0 and 1."""
+    gk = lib
+    bc = (D,) * (2 * len(n))
+    outs = []
+    for variant in (0, 1):
+        h = make_handle(gk, n, bc, 1.0, 50.0, precision=prec, kernel_variant=variant)
+        try:
+            m, _ = gk.gkb_layout(h)
+            x = np.random.default_rng(21).standard_normal(m)
+            z, y = np.empty(m), np.empty(m)
+            gk.gkb_precond(h, x, z)
+            gk.gkb_apply(h, gk.GKB_OP_M, x, y)
+            outs.append((z, y))
+        finally:
+            gk.gkb_destroy(h)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])

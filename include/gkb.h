@@ -121,9 +121,10 @@ typedef struct {
   int profile;            /* 1: time every kernel launch with CUDA events on
                              the stream and report per-class totals in
                              gkb_stats (adds event overhead between kernels)  */
-  int kernel_variant;     /* 0: stencil kernels take their deep-interior fast
-                             paths; 1: general paths only (same values bit for
-                             bit; for testing)                                 */
+  int kernel_variant;     /* stencil kernels' deep-interior fast paths (same
+                             values bit for bit as the general paths):
+                             0: on in FP32, off in FP64 (measured fastest);
+                             1: off everywhere; 2: on everywhere               */
   void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
 } gkb_options;
 

@@ -498,8 +498,7 @@ __global__ void __launch_bounds__(BX* BY) k_negdiv(Lvl L, const T* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// grid transfer: divergence-preserving prolongation (normal-linear,
-// tangential-constant embedding of the coarse face field) and its transpose
+// grid transfer helpers
 // ---------------------------------------------------------------------------
 
 template <typename T, int C>
@@ -508,70 +507,10 @@ __device__ __forceinline__ T coarse_face(const Lvl& Lc, const T* xc, int I, int 
   return __ldg(xc + Lc.off[C] + cix(Lc, I, J, K));
 }
 
-// xf += P xc
-template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_prolong(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
-  const int p[3] = {i, j, k};
-#define GKB_PROL_COMP(C)                                                         \
-  if (in_store<C>(Lf, i, j, k) && face_active<C>(Lf, i, j, k)) {                 \
-    int q[3] = {p[0] >> 1, p[1] >> 1, p[2] >> 1};                                \
-    T val;                                                                       \
-    if ((p[C] & 1) == 0) {                                                       \
-      val = coarse_face<T, C>(Lc, xc, q[0], q[1], q[2]);                         \
-    } else {                                                                     \
-      T v0 = coarse_face<T, C>(Lc, xc, q[0], q[1], q[2]);                        \
-      q[C] += 1;                                                                 \
-      T v1 = coarse_face<T, C>(Lc, xc, q[0], q[1], q[2]);                        \
-      val = (T)0.5 * (v0 + v1);                                                  \
-    }                                                                            \
-    xf[Lf.off[C] + cix(Lf, i, j, k)] += val;                                     \
-  }
-  GKB_PROL_COMP(0)
-  GKB_PROL_COMP(1)
-  if (Lf.dim == 3) { GKB_PROL_COMP(2) }
-#undef GKB_PROL_COMP
-}
-
 template <typename T, int C>
 __device__ __forceinline__ T fine_face(const Lvl& Lf, const T* rf, int i, int j, int k) {
   if (!face_active<C>(Lf, i, j, k)) return (T)0;
   return __ldg(rf + Lf.off[C] + cix(Lf, i, j, k));
-}
-
-// bc = P^T rf  (launched over the coarse face grid)
-template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict(Lvl Lf, Lvl Lc, const T* __restrict__ rf, T* __restrict__ bc) {
-  const int I = blockIdx.x * BX + threadIdx.x;
-  const int J = blockIdx.y * BY + threadIdx.y;
-  const int K = blockIdx.z;
-  const int P3[3] = {I, J, K};
-#define GKB_REST_COMP(C)                                                         \
-  if (in_store<C>(Lc, I, J, K)) {                                                \
-    T acc = 0;                                                                   \
-    if (face_active<C>(Lc, I, J, K)) {                                           \
-      const int t1 = (C == 0) ? 1 : 0, t2 = (C == 2) ? 1 : 2;                    \
-      const int nt2 = (Lf.dim == 3) ? 2 : 1;                                     \
-      for (int s1 = 0; s1 < 2; ++s1)                                             \
-        for (int s2 = 0; s2 < nt2; ++s2) {                                       \
-          int q[3] = {2 * P3[0], 2 * P3[1], 2 * P3[2]};                          \
-          q[t1] += s1;                                                           \
-          if (Lf.dim == 3) q[t2] += s2;                                          \
-          acc += fine_face<T, C>(Lf, rf, q[0], q[1], q[2]);                      \
-          q[C] += 1;                                                             \
-          acc += (T)0.5 * fine_face<T, C>(Lf, rf, q[0], q[1], q[2]);             \
-          q[C] -= 2;                                                             \
-          if (q[C] >= 0) acc += (T)0.5 * fine_face<T, C>(Lf, rf, q[0], q[1], q[2]); \
-        }                                                                        \
-    }                                                                            \
-    bc[Lc.off[C] + cix(Lc, I, J, K)] = acc;                                      \
-  }
-  GKB_REST_COMP(0)
-  GKB_REST_COMP(1)
-  if (Lc.dim == 3) { GKB_REST_COMP(2) }
-#undef GKB_REST_COMP
 }
 
 // ---- 2D flux-conserving, divergence-preserving transfers -----------------
@@ -710,6 +649,177 @@ __global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_b(Lvl Lc, const T* _
     bc[Lc.off[0] + cix(Lc, I, J, 0)] += slope_transpose<T, 0>(Lc, tmp, I, J);
   if (in_store<1>(Lc, I, J, 0) && face_active<1>(Lc, I, J, 0))
     bc[Lc.off[1] + cix(Lc, I, J, 0)] += slope_transpose<T, 1>(Lc, tmp, I, J);
+}
+
+// ---- 3D flux-conserving, divergence-preserving transfers -----------------
+// Same construction as in 2D with two tangential slopes per face: fine faces
+// on a coarse face get U + s1 D_t1 + s2 D_t2; interior fine faces get the
+// mean of the two line values plus, for each other component c', one half
+// of (slope of c' along the face's normal axis on the coarse cell's high
+// c'-face - the same on its low c'-face). Restriction is the exact transpose:
+// a gather into (rU, rD_t1, rD_t2), then rU + G_t1^T rD_t1 + G_t2^T rD_t2.
+
+template <int C, int K> struct Oth;   // K-th axis other than C (ascending)
+template <> struct Oth<0, 0> { static constexpr int v = 1; };
+template <> struct Oth<0, 1> { static constexpr int v = 2; };
+template <> struct Oth<1, 0> { static constexpr int v = 0; };
+template <> struct Oth<1, 1> { static constexpr int v = 2; };
+template <> struct Oth<2, 0> { static constexpr int v = 0; };
+template <> struct Oth<2, 1> { static constexpr int v = 1; };
+
+// slope / 8 of component C along axis A at coarse face P (mirror walls)
+template <typename T, int C, int A>
+__device__ __forceinline__ T slope3(const Lvl& Lc, const T* xc, const int P[3]) {
+  if (!face_active<C>(Lc, P[0], P[1], P[2])) return (T)0;
+  const T* u = xc + Lc.off[C] + cix(Lc, P[0], P[1], P[2]);
+  const T u0 = __ldg(u);
+  int Pp[3] = {P[0], P[1], P[2]}, Pm[3] = {P[0], P[1], P[2]};
+  Pp[A] += 1;
+  Pm[A] -= 1;
+  const T up = (Pp[A] < Lc.n[A]) ? coarse_face<T, C>(Lc, xc, Pp[0], Pp[1], Pp[2]) : -u0;
+  const T um = (Pm[A] >= 0) ? coarse_face<T, C>(Lc, xc, Pm[0], Pm[1], Pm[2]) : -u0;
+  return (up - um) * (T)0.125;
+}
+
+template <typename T, int C>
+__device__ __forceinline__ T prolong3_val(const Lvl& Lc, const T* xc, const int p[3]) {
+  constexpr int t1 = Oth<C, 0>::v, t2 = Oth<C, 1>::v;
+  const int q[3] = {p[0] >> 1, p[1] >> 1, p[2] >> 1};
+  const T s1 = (p[t1] & 1) ? (T)1 : (T)-1;
+  const T s2 = (p[t2] & 1) ? (T)1 : (T)-1;
+  auto line_val = [&](int I) -> T {
+    int P[3] = {q[0], q[1], q[2]};
+    P[C] = I;
+    return coarse_face<T, C>(Lc, xc, P[0], P[1], P[2]) + s1 * slope3<T, C, t1>(Lc, xc, P) + s2 * slope3<T, C, t2>(Lc, xc, P);
+  };
+  if ((p[C] & 1) == 0) return line_val(p[C] >> 1);
+  const int I = p[C] >> 1;
+  T val = (T)0.5 * (line_val(I) + line_val(I + 1));
+  int lo[3] = {q[0], q[1], q[2]};
+  lo[C] = I;
+  int hi1[3] = {lo[0], lo[1], lo[2]}, hi2[3] = {lo[0], lo[1], lo[2]};
+  hi1[t1] += 1;
+  hi2[t2] += 1;
+  val += (T)0.5 * (slope3<T, t1, C>(Lc, xc, hi1) - slope3<T, t1, C>(Lc, xc, lo));
+  val += (T)0.5 * (slope3<T, t2, C>(Lc, xc, hi2) - slope3<T, t2, C>(Lc, xc, lo));
+  return val;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong_flux3d(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int p[3] = {i, j, k};
+  if (in_store<0>(Lf, i, j, k) && face_active<0>(Lf, i, j, k)) xf[Lf.off[0] + cix(Lf, i, j, k)] += prolong3_val<T, 0>(Lc, xc, p);
+  if (in_store<1>(Lf, i, j, k) && face_active<1>(Lf, i, j, k)) xf[Lf.off[1] + cix(Lf, i, j, k)] += prolong3_val<T, 1>(Lc, xc, p);
+  if (in_store<2>(Lf, i, j, k) && face_active<2>(Lf, i, j, k)) xf[Lf.off[2] + cix(Lf, i, j, k)] += prolong3_val<T, 2>(Lc, xc, p);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ T fine3(const Lvl& Lf, const T* rf, const int P[3]) {
+  return fine_face<T, C>(Lf, rf, P[0], P[1], P[2]);
+}
+
+// pass a for component C at coarse face Q: rU, and rD along its two tangential axes
+template <typename T, int C>
+__device__ __forceinline__ void restrict3_gather(const Lvl& Lf, const T* rf, const int Q[3], T& rU, T& rD1, T& rD2) {
+  constexpr int t1 = Oth<C, 0>::v, t2 = Oth<C, 1>::v;
+  const int Ic = Q[C];
+  T su = 0, s1 = 0, s2 = 0;
+#pragma unroll
+  for (int kk = 0; kk < 3; ++kk) {
+    const int nn = (kk == 0) ? 2 * Ic : (kk == 1) ? 2 * Ic + 1 : 2 * Ic - 1;
+    const T w = (kk == 0) ? (T)1 : (T)0.5;
+#pragma unroll
+    for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+      for (int b2 = 0; b2 < 2; ++b2) {
+        int P[3];
+        P[C] = nn;
+        P[t1] = 2 * Q[t1] + b1;
+        P[t2] = 2 * Q[t2] + b2;
+        const T v = w * fine3<T, C>(Lf, rf, P);
+        su += v;
+        s1 += b1 ? v : -v;
+        s2 += b2 ? v : -v;
+      }
+  }
+  // slope of C along t1 enters the correction of component t1's interior
+  // faces in the coarse cells above (-1/2) and below (+1/2) this face
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    const int cc = (kk == 0) ? 2 * Ic : (kk == 1) ? 2 * Ic + 1 : (kk == 2) ? 2 * Ic - 2 : 2 * Ic - 1;
+    const T w = (kk < 2) ? (T)-0.5 : (T)0.5;
+#pragma unroll
+    for (int sb = 0; sb < 2; ++sb) {
+      int P[3];
+      P[t1] = 2 * Q[t1] + 1;
+      P[C] = cc;
+      P[t2] = 2 * Q[t2] + sb;
+      s1 += w * fine3<T, t1>(Lf, rf, P);
+      int R[3];
+      R[t2] = 2 * Q[t2] + 1;
+      R[C] = cc;
+      R[t1] = 2 * Q[t1] + sb;
+      s2 += w * fine3<T, t2>(Lf, rf, R);
+    }
+  }
+  rU = su;
+  rD1 = s1;
+  rD2 = s2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_a(Lvl Lf, Lvl Lc, const T* __restrict__ rf, T* __restrict__ bc,
+                                                               T* __restrict__ d1, T* __restrict__ d2) {
+  const int I = blockIdx.x * BX + threadIdx.x;
+  const int J = blockIdx.y * BY + threadIdx.y;
+  const int K = blockIdx.z;
+  const int Q[3] = {I, J, K};
+#define GKB_R3A(C)                                                               \
+  if (in_store<C>(Lc, I, J, K)) {                                                \
+    const long long id = Lc.off[C] + cix(Lc, I, J, K);                           \
+    T rU = 0, r1 = 0, r2 = 0;                                                    \
+    if (face_active<C>(Lc, I, J, K)) restrict3_gather<T, C>(Lf, rf, Q, rU, r1, r2); \
+    bc[id] = rU;                                                                 \
+    d1[id] = r1;                                                                 \
+    d2[id] = r2;                                                                 \
+  }
+  GKB_R3A(0)
+  GKB_R3A(1)
+  GKB_R3A(2)
+#undef GKB_R3A
+}
+
+template <typename T, int C, int A>
+__device__ __forceinline__ T slope3_transpose(const Lvl& Lc, const T* d, const int Q[3]) {
+  const int q = Q[A], Nt = Lc.n[A];
+  T acc = 0;
+  int R[3] = {Q[0], Q[1], Q[2]};
+  if (q - 1 >= 0) { R[A] = q - 1; acc += __ldg(d + Lc.off[C] + cix(Lc, R[0], R[1], R[2])); }
+  if (q + 1 < Nt) { R[A] = q + 1; acc -= __ldg(d + Lc.off[C] + cix(Lc, R[0], R[1], R[2])); }
+  const T own = __ldg(d + Lc.off[C] + cix(Lc, Q[0], Q[1], Q[2]));
+  if (q == 0) acc += own;
+  if (q == Nt - 1) acc -= own;
+  return acc * (T)0.125;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_b(Lvl Lc, const T* __restrict__ d1, const T* __restrict__ d2,
+                                                               T* __restrict__ bc) {
+  const int I = blockIdx.x * BX + threadIdx.x;
+  const int J = blockIdx.y * BY + threadIdx.y;
+  const int K = blockIdx.z;
+  const int Q[3] = {I, J, K};
+#define GKB_R3B(C)                                                               \
+  if (in_store<C>(Lc, I, J, K) && face_active<C>(Lc, I, J, K))                   \
+    bc[Lc.off[C] + cix(Lc, I, J, K)] += slope3_transpose<T, C, Oth<C, 0>::v>(Lc, d1, Q) + \
+                                        slope3_transpose<T, C, Oth<C, 1>::v>(Lc, d2, Q);
+  GKB_R3B(0)
+  GKB_R3B(1)
+  GKB_R3B(2)
+#undef GKB_R3B
 }
 
 // coarsest level: x[idx[r]] = sum_c Minv[r][c] b[idx[c]]; one warp per row

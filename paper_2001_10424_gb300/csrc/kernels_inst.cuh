@@ -76,17 +76,18 @@ template <>
 void Ops<KT>::prolong(const Lvl& Lf, const Lvl& Lc, const KT* xc, KT* xf, cudaStream_t s) {
   ProfScope ps_(GKB_KC_PROLONG, s, lvl_unknowns(Lf));
   if (Lf.dim == 2) k_prolong_flux2d<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
-  else k_prolong<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
+  else k_prolong_flux3d<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
 }
 
 template <>
-void Ops<KT>::restrict_(const Lvl& Lf, const Lvl& Lc, const KT* rf, KT* bc, KT* tmp, cudaStream_t s) {
+void Ops<KT>::restrict_(const Lvl& Lf, const Lvl& Lc, const KT* rf, KT* bc, KT* tmp, KT* tmp2, cudaStream_t s) {
   ProfScope ps_(GKB_KC_RESTRICT, s, lvl_unknowns(Lf));
   if (Lf.dim == 2) {
     k_restrict_flux2d_a<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc, tmp);
     k_restrict_flux2d_b<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lc, tmp, bc);
   } else {
-    k_restrict<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc);
+    k_restrict_flux3d_a<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, rf, bc, tmp, tmp2);
+    k_restrict_flux3d_b<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lc, tmp, tmp2, bc);
   }
 }
 

@@ -30,8 +30,8 @@ struct Ops {
   static void negdiv(const Lvl& L, const T* x, T* y, T scale, cudaStream_t s);
   // xf += P xc
   static void prolong(const Lvl& Lf, const Lvl& Lc, const T* xc, T* xf, cudaStream_t s);
-  // bc = P^T rf (tmp: coarse-sized scratch)
-  static void restrict_(const Lvl& Lf, const Lvl& Lc, const T* rf, T* bc, T* tmp, cudaStream_t s);
+  // bc = P^T rf (tmp, tmp2: coarse-sized scratch; tmp2 only in 3D)
+  static void restrict_(const Lvl& Lf, const Lvl& Lc, const T* rf, T* bc, T* tmp, T* tmp2, cudaStream_t s);
   // coarsest level dense solve through the stored inverse
   static void coarse(int m, const T* Minv, const int* idx, const T* b, T* x, cudaStream_t s);
   // reductions and vector updates on flat padded arrays

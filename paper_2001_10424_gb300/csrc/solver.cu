@@ -325,7 +325,11 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
   const int nl = (int)lev.size();
   for (int l = 0; l < nl; ++l) {
     Level& V = lev[l];
-    if (l > 0) { V.x.alloc(V.L.nvel); V.b.alloc(V.L.nvel); }
+    if (l > 0) {
+      V.x.alloc(V.L.nvel);
+      V.b.alloc(V.L.nvel);
+      if (V.L.dim == 3) V.t2.alloc(V.L.nvel);
+    }
     if (l < nl - 1) {
       V.r.alloc(V.L.nvel);
       V.d.alloc(V.L.nvel);
@@ -479,7 +483,7 @@ void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s) {
     T* x = (l == 0) ? z0 : lev[l].x.p;
     smooth(l, b, x, true, s);
     Ops<T>::residual(lev[l].L, x, b, lev[l].r.p, s);
-    Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, lev[l + 1].x.p, s);
+    Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, lev[l + 1].x.p, lev[l + 1].t2.p, s);
   }
   Level& Cl = lev[nl - 1];
   Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, Cl.b.p, Cl.x.p, s);
@@ -865,7 +869,8 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
   L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
   L64.mu0 = viscosity ? 1.0 : mu0;
-  L64.fast = (opt.kernel_variant == 0) ? 1 : 0;
+  // fast paths: measured faster in FP32, slower in FP64 (FP64-pipe bound)
+  L64.fast = (opt.kernel_variant == 2) ? 1 : 0;
   finish_level(L64);
   Compact cmp = make_compact(L64);
   m = cmp.m;
@@ -894,6 +899,7 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   L32 = L64;
   L32.mu64 = nullptr;
   L32.mu32 = mu32.p;
+  L32.fast = (opt.kernel_variant == 1) ? 0 : 1;
   // reduction scratch: enough partials for every launch shape used
   long long blocks = std::max<long long>(Ops<double>::face_blocks(L64), blas_blocks(L64.nvel));
   blocks = std::max<long long>(blocks, (long long)cgrid(L64).x * cgrid(L64).y * cgrid(L64).z);

@@ -64,6 +64,7 @@ struct Gmg {
   struct Level {
     Lvl L;
     DevBuf<T> x, b, r, d, mu;
+    DevBuf<T> t2;               // second restriction scratch (3D coarse levels)
     DevBuf<T> table;            // patch class inverses (constant viscosity)
     std::vector<double> ca, cb; // Chebyshev coefficients per step
     double lam_max = 0;

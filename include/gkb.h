@@ -186,6 +186,20 @@ int gkb_boundary_rhs(gkb_handle h, int side, const double* normal_velocity,
 int gkb_solve(gkb_handle h, const double* g, const double* r, double tol, int delay,
               double* w_out, double* p_out, const double* w0, const double* p0);
 
+/* Solve `count` independent problems in one CUDA graph launch (the batched
+ * form; same method as gkb_solve for each). hs[i] is a handle set up with
+ * gkb_set_problem, all on one device, with use_graph = 1 and profile = 0.
+ * g[i], r[i] (inputs) and w_out[i], p_out[i] (outputs) are problem i's
+ * compact vectors, host or device memory. Every problem's whole solve, with
+ * its device-side loops, is one branch of a single graph; the branches run
+ * concurrently and each stops on its own estimate. The graph for a list of
+ * handles is captured at its first call and reused while none of the handles
+ * is re-set or destroyed. Runs on the stream of hs[0]. Returns OK when every
+ * problem returned OK, else the first non-OK status; per-problem statistics
+ * via gkb_stats(hs[i]). */
+int gkb_solve_batched(gkb_handle* hs, int count, const double* const* g, const double* const* r,
+                      double tol, int delay, double* const* w_out, double* const* p_out);
+
 /* Statistics of the last solve. */
 int gkb_stats(gkb_handle h, gkb_stats_t* out);
 

@@ -43,7 +43,7 @@ STATUS_NAMES = {
 EXPORTED = [
     "gkb_default_options", "gkb_create", "gkb_set_problem", "gkb_layout", "gkb_boundary_rhs",
     "gkb_solve", "gkb_stats", "gkb_history", "gkb_apply", "gkb_precond", "gkb_last_error",
-    "gkb_destroy", "gkb_apply_noalloc",
+    "gkb_destroy", "gkb_apply_noalloc", "gkb_solve_batched",
 ]
 GKB_NOALLOC_MAX_ELEMS = 1048576
 
@@ -102,6 +102,8 @@ def load(path=None):
         "gkb_last_error": (ctypes.c_char_p, [_P]),
         "gkb_destroy": (i, [_P]),
         "gkb_apply_noalloc": (i, [ctypes.POINTER(gkb_grid), d, d, d, i, _P, _P, _P]),
+        "gkb_solve_batched": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P), ctypes.POINTER(_P), d, i,
+                                  ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -178,6 +180,16 @@ def gkb_solve(h, g, r, tol, delay, w_out, p_out, w0=None, p0=None):
     """Returns the status code; argument / CUDA errors raise GkbError."""
     rc = load().gkb_solve(h, _ptr(g), _ptr(r), tol, delay, _ptr(w_out), _ptr(p_out), _ptr(w0), _ptr(p0))
     return _check(h, rc, allow=(GKB_ERR_NOT_CONVERGED, GKB_ERR_INNER_NOT_CONVERGED, GKB_ERR_NOT_SPD, GKB_ERR_NAN))
+
+
+def gkb_solve_batched(hs, g, r, tol, delay, w_out, p_out):
+    """Batched solve of len(hs) problems in one graph launch; g, r, w_out,
+    p_out are lists of per-problem arrays. Returns the status code."""
+    n = len(hs)
+    arr = lambda xs: (_P * n)(*[_ptr(x) for x in xs])
+    H = (_P * n)(*[h.value if hasattr(h, "value") else h for h in hs])
+    rc = load().gkb_solve_batched(H, n, arr(g), arr(r), tol, delay, arr(w_out), arr(p_out))
+    return _check(hs[0], rc, allow=(GKB_ERR_NOT_CONVERGED, GKB_ERR_INNER_NOT_CONVERGED, GKB_ERR_NOT_SPD, GKB_ERR_NAN))
 
 
 def gkb_stats(h):

@@ -113,6 +113,18 @@ int gkb_solve(gkb_handle h, const double* g, const double* r, double tol, int de
   return guarded(h, [&] { return h->s.solve(g, r, tol, delay, w_out, p_out, w0, p0); });
 }
 
+int gkb_solve_batched(gkb_handle* hs, int count, const double* const* g, const double* const* r, double tol,
+                      int delay, double* const* w_out, double* const* p_out) {
+  if (!hs || count < 1 || !hs[0]) return GKB_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!hs[i] || hs[i]->device != hs[0]->device) return GKB_ERR_INVALID_ARG;
+  return guarded(hs[0], [&] {
+    std::vector<gkb::Solver*> S(count);
+    for (int i = 0; i < count; ++i) S[i] = &hs[i]->s;
+    return gkb::solve_batched(S.data(), count, g, r, tol, delay, w_out, p_out);
+  });
+}
+
 int gkb_stats(gkb_handle h, gkb_stats_t* out) {
   return guarded(h, [&] {
     if (!out) throw gkb::Error{GKB_ERR_INVALID_ARG, "NULL stats"};
@@ -141,8 +153,11 @@ int gkb_history(gkb_handle h, double* alpha, double* beta, double* zeta, double*
       if (beta) beta[i] = hv[(size_t)cap + i];
     for (int i = 0; i < std::min(capacity, k); ++i)
       if (estimate) estimate[i] = hv[3 * (size_t)cap + i];
-    if (inner_its)
-      for (int i = 0; i < std::min<int>(capacity, (int)h->s.inner_its.size()); ++i) inner_its[i] = h->s.inner_its[i];
+    if (inner_its) {
+      const int ni = std::min<int>(capacity, std::min<int>(h->s.stats.inner_solves, h->s.opt.maxit + 4));
+      if (ni > 0)
+        gkb::check_cuda(cudaMemcpy(inner_its, h->s.hist_inner.p, ni * sizeof(int), cudaMemcpyDeviceToHost), "history");
+    }
     written = nz;
     return GKB_OK;
   });
@@ -178,6 +193,7 @@ const char* gkb_last_error(gkb_handle h) {
 int gkb_destroy(gkb_handle h) {
   if (!h) return GKB_ERR_INVALID_ARG;
   cudaSetDevice(h->device);
+  gkb::forget_batches(&h->s);
   delete h;
   return GKB_OK;
 }

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstddef>
+#include <mutex>
 #include <chrono>
 #include <cstdio>
 
@@ -210,73 +211,53 @@ __global__ void k_cg_cond(cudaGraphConditionalHandle h, CgState* c, int hard_max
   cudaGraphSetConditional(h, cont);
 }
 
-void LoopGraph::account(Profiler* P, long long body_runs) const {
-  if (!P) return;
-  for (int k = 0; k < GKB_KC_COUNT; ++k) {
-    P->launches[k] += cl[0][k] + body_runs * cl[1][k] + cl[2][k];
-    P->units[k] += cu[0][k] + body_runs * cu[1][k] + cu[2][k];
-  }
+// Capture "pre; while (cond) body; post" into the graph that stream s is
+// capturing (possibly the body graph of an enclosing loop). The condition
+// handle is created on that graph; `pre` must end with the kernel that sets
+// it, `body` with the kernel that updates it. The body is captured on sb.
+template <class Pre, class Body, class Post>
+static void capture_loop(cudaStream_t s, cudaStream_t sb, int body_phase, Pre pre, Body body, Post post) {
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t cg = nullptr;
+  GKB_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive) throw Error{GKB_ERR_CUDA, "stream is not capturing"};
+  cudaGraphConditionalHandle h;
+  GKB_CUDA(cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault));
+  pre(s, h);
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  GKB_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  GKB_CUDA(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
+  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+  Profiler* P = g_prof;
+  const int saved = P ? P->phase : -1;
+  GKB_CUDA(cudaStreamBeginCaptureToGraph(sb, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  if (P) P->phase = body_phase;
+  body(sb, h);
+  if (P) P->phase = saved;
+  GKB_CUDA(cudaStreamEndCapture(sb, &bodyg));
+  GKB_CUDA(cudaStreamUpdateCaptureDependencies(s, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  post(s);
 }
 
-template <class Pre, class Body, class Post>
-static void build_loop_graph(LoopGraph& G, cudaStream_t cs, cudaStream_t cs2, Pre pre, Body body, Post post) {
-  G.destroy();
-  Profiler* P = g_prof;
-  auto phase = [&](int ph) {
-    if (!P) return;
-    if (ph >= 0)
-      for (int k = 0; k < GKB_KC_COUNT; ++k) { P->cap_l[ph][k] = 0; P->cap_u[ph][k] = 0; }
-    P->phase = ph;
-  };
-  cudaGraph_t g = nullptr;
-  GKB_CUDA(cudaGraphCreate(&g, 0));
-  cudaGraphConditionalHandle h;
-  bool capturing = false, capturing2 = false;
-  try {
-    GKB_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
-    GKB_CUDA(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    capturing = true;
-    phase(0);
-    pre(cs, h);
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t cg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    GKB_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd));
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t wn;
-    GKB_CUDA(cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp));
-    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
-    GKB_CUDA(cudaStreamBeginCaptureToGraph(cs2, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-    capturing2 = true;
-    phase(1);
-    body(cs2, h);
-    capturing2 = false;
-    GKB_CUDA(cudaStreamEndCapture(cs2, &bodyg));
-    GKB_CUDA(cudaStreamUpdateCaptureDependencies(cs, &wn, nullptr, 1, cudaStreamSetCaptureDependencies));
-    phase(2);
-    post(cs);
-    capturing = false;
-    GKB_CUDA(cudaStreamEndCapture(cs, &g));
-    phase(-1);
-    GKB_CUDA(cudaGraphInstantiate(&G.exec, g, 0));
-  } catch (...) {
-    phase(-1);
-    cudaGraph_t dummy;
-    if (capturing2) cudaStreamEndCapture(cs2, &dummy);
-    if (capturing) cudaStreamEndCapture(cs, &dummy);
-    (void)cudaGetLastError();
-    if (g) cudaGraphDestroy(g);
-    throw;
+// end any capture still open on these streams (error paths)
+static void abandon_captures(std::initializer_list<cudaStream_t> ss) {
+  for (cudaStream_t st : ss) {
+    if (!st) continue;
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t dummy = nullptr;
+      cudaStreamEndCapture(st, &dummy);
+      if (dummy) cudaGraphDestroy(dummy);
+    }
   }
-  cudaGraphDestroy(g);
-  if (P)
-    for (int ph = 0; ph < 3; ++ph)
-      for (int k = 0; k < GKB_KC_COUNT; ++k) { G.cl[ph][k] = P->cap_l[ph][k]; G.cu[ph][k] = P->cap_u[ph][k]; }
+  (void)cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -545,48 +526,6 @@ int Cg<T>::solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* i
   return host->status;
 }
 
-template <typename T>
-void Cg<T>::build_graph(const T* f, T* x, int maxit, cudaStream_t cs, cudaStream_t cs2) {
-  gf = f;
-  gx = x;
-  const long long len = L.nvel;
-  T* zp = pre ? z.p : r.p;
-  build_loop_graph(
-      G, cs, cs2,
-      [&](cudaStream_t s, cudaGraphConditionalHandle h) {
-        GKB_CUDA(cudaMemsetAsync(x, 0, len * sizeof(T), s));
-        GKB_CUDA(cudaMemcpyAsync(r.p, f, len * sizeof(T), cudaMemcpyDeviceToDevice, s));
-        Ops<T>::dot(len, f, f, red, FIN_CG_INIT, st, s);
-        if (pre) pre->vcycle(r.p, zp, s);
-        Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ0, st, s);
-        Ops<T>::cg_dir(len, p.p, zp, st, 1, s);
-        k_cg_cond_init<<<1, 1, 0, s>>>(h, st);
-      },
-      [&](cudaStream_t s, cudaGraphConditionalHandle h) {
-        Ops<T>::apply_dot(L, 1, p.p, q.p, red, FIN_CG_PAP, st, s);
-        Ops<T>::cg_update(len, x, p.p, r.p, q.p, st, red, st, s);
-        if (pre) pre->vcycle(r.p, zp, s);
-        Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
-        Ops<T>::cg_dir(len, p.p, zp, st, 0, s);
-        k_cg_cond<<<1, 1, 0, s>>>(h, st, maxit + 2);
-      },
-      [&](cudaStream_t) {});
-}
-
-template <typename T>
-int Cg<T>::solve_graph(double tol, int maxit, cudaStream_t s, int* iters) {
-  CgState h{};
-  h.tol2 = tol * tol;
-  h.maxit = maxit;
-  GKB_CUDA(cudaMemcpyAsync(st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
-  GKB_CUDA(cudaGraphLaunch(G.exec, s));
-  GKB_CUDA(cudaMemcpyAsync(host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-  GKB_CUDA(cudaStreamSynchronize(s));
-  G.account(g_prof, host->graph_iters);
-  if (iters) *iters = host->it;
-  return host->status;
-}
-
 template struct Cg<double>;
 template struct Cg<float>;
 
@@ -810,6 +749,62 @@ __global__ void __launch_bounds__(CB) k_mixed_accum(long long len, float* __rest
   }
 }
 
+// ---- device-side control of the graph form --------------------------------
+
+// header of an inner CG solve (written on the device so that graphs can
+// start a solve without a host copy)
+__global__ void k_cg_setup(CgState* c, double tol2, int maxit, double delta2) {
+  c->tol2 = tol2;
+  c->maxit = maxit;
+  c->delta2 = delta2;
+  c->done = 0;
+  c->status = ST_OK;
+  c->it = 0;
+  c->update = 0;
+  c->graph_iters = 0;
+}
+
+// record an inner solve in the GKB state: status, iterations, history
+__global__ void k_note_inner(GkbState* S, const CgState* c) {
+  const int idx = S->inner_solves;
+  if (S->h_inner && idx < S->icap) S->h_inner[idx] = c->it;
+  S->inner_solves = idx + 1;
+  S->inner_its += c->it;
+  S->inner_runs += c->graph_iters;
+  if (c->status != ST_OK && S->inner_status == ST_OK) S->inner_status = c->status;
+}
+
+__global__ void k_gkb_cond_init(cudaGraphConditionalHandle h, GkbState* S) {
+  S->outer_runs = 0;
+  cudaGraphSetConditional(h, (S->stop || S->status != ST_OK) ? 0u : 1u);
+}
+
+// continue the outer loop while Algorithm 1 has not stopped; hard_max bounds
+// it even if the iteration counter were never advanced
+__global__ void k_gkb_cond(cudaGraphConditionalHandle h, GkbState* S, int hard_max) {
+  S->outer_runs += 1;
+  unsigned cont = (S->stop || S->status != ST_OK) ? 0u : 1u;
+  if (S->outer_runs >= hard_max) {
+    cont = 0u;
+    S->stop = 1;
+  }
+  cudaGraphSetConditional(h, cont);
+}
+
+// compact pressure with the mean (sum / n, sum on the device) removed
+__global__ void k_unpack_cell_dev(Lvl L, const double* __restrict__ src, double* __restrict__ dst, const double* sum,
+                                  double inv_n) {
+  const long long n = (long long)L.n[0] * L.n[1] * L.n[2];
+  const double shift = sum ? *sum * inv_n : 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long row = t / L.n[0];
+    const int i = (int)(t - row * L.n[0]);
+    const int k = (int)(row / L.n[1]);
+    const int j = (int)(row - (long long)k * L.n[1]);
+    dst[t] = src[cix(L, i, j, k)] - shift;
+  }
+}
+
 // x64 += s e32 with s = sqrt(*nrm2) (precision conversion of a preconditioned vector)
 __global__ void __launch_bounds__(CB) k_add_f32(long long len, const float* __restrict__ e, double* __restrict__ x,
                                                 const double* nrm2) {
@@ -837,17 +832,19 @@ static unsigned lin_blocks(long long n) {
 }
 
 Solver::~Solver() {
-  mixed_graph.destroy();
-  cg64.G.destroy();
+  sgraph.destroy();
   if (cg_host) cudaFreeHost(cg_host);
   if (gkb_host) cudaFreeHost(gkb_host);
   if (cap1) cudaStreamDestroy(cap1);
   if (cap2) cudaStreamDestroy(cap2);
+  if (cap3) cudaStreamDestroy(cap3);
 }
 
 void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_, double gamma_, double n_scale_) {
   auto t0 = std::chrono::steady_clock::now();
   if (!g) throw Error{GKB_ERR_INVALID_ARG, "grid is NULL"};
+  sgraph.destroy();
+  forget_batches(this);
   if (g->dim != 2 && g->dim != 3) throw Error{GKB_ERR_INVALID_ARG, "dim must be 2 or 3"};
   for (int a = 0; a < g->dim; ++a)
     if (g->n[a] < 2) throw Error{GKB_ERR_INVALID_ARG, "every side needs at least 2 cells"};
@@ -935,88 +932,19 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   stage_m.alloc(m);
   stage_n.alloc(ncell);
   hist.alloc(4 * (size_t)(opt.maxit + 2));
+  hist_inner.alloc((size_t)opt.maxit + 4);
   GKB_CUDA(cudaStreamSynchronize(stream));
-  build_graphs();
+  generation += 1;
   have_problem = true;
+  build_solve_graph();
   stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-}
-
-void Solver::build_graphs() {
-  graphs_ready = false;
-  if (!opt.use_graph || opt.profile) return;
-  if (!cap1) {
-    GKB_CUDA(cudaStreamCreateWithFlags(&cap1, cudaStreamNonBlocking));
-    GKB_CUDA(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
-  }
-  if (opt.precision == GKB_PREC_MIXED) {
-    const long long len = L64.nvel;
-    Cg<float>& c = cg32;
-    float* zp = c.pre ? c.z.p : c.r.p;
-    const int* upd = &cg_dev->update;
-    double* fx = f.p;
-    double* xx = x.p;
-    const int maxit = opt.maxit_inner;
-    build_loop_graph(
-        mixed_graph, cap1, cap2,
-        [&](cudaStream_t s, cudaGraphConditionalHandle h) {
-          GKB_CUDA(cudaMemsetAsync(xx, 0, len * sizeof(double), s));
-          GKB_CUDA(cudaMemsetAsync(x32.p, 0, len * sizeof(float), s));
-          Ops<double>::dot(len, fx, fx, red, FIN_CG_INIT, cg_dev, s);
-          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, fx, c.r.p, nullptr); }
-          if (c.pre) c.pre->vcycle(c.r.p, zp, s);
-          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ0, cg_dev, s);
-          Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 1, s);
-          k_cg_cond_init<<<1, 1, 0, s>>>(h, cg_dev);
-        },
-        [&](cudaStream_t s, cudaGraphConditionalHandle h) {
-          Ops<float>::apply_dot(L32, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, s);
-          Ops<float>::cg_update(len, x32.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, s, FIN_MX_RR);
-          // reliable update, predicated on the flag the finaliser just set
-          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, xx, upd); }
-          Ops<double>::residual(L64, xx, fx, r64.p, s, upd);
-          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, r64.p, c.r.p, upd); }
-          Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, s, upd);
-          if (c.pre) c.pre->vcycle(c.r.p, zp, s);
-          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, s);
-          Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, s);
-          k_cg_cond<<<1, 1, 0, s>>>(h, cg_dev, maxit + 2);
-        },
-        [&](cudaStream_t s) {
-          { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, xx, nullptr); }
-        });
-  } else {
-    cg64.build_graph(f.p, x.p, opt.maxit_inner, cap1, cap2);
-  }
-  graphs_ready = true;
-}
-
-int Solver::mixed_solve_graph(int* iters) {
-  cudaStream_t s = stream;
-  CgState h{};
-  h.tol2 = opt.tol_inner * opt.tol_inner;
-  h.maxit = opt.maxit_inner;
-  h.delta2 = opt.mixed_rtol * opt.mixed_rtol;
-  GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
-  GKB_CUDA(cudaGraphLaunch(mixed_graph.exec, s));
-  GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
-  GKB_CUDA(cudaStreamSynchronize(s));
-  mixed_graph.account(g_prof, cg_host->graph_iters);
-  if (iters) *iters = cg_host->it;
-  return cg_host->status;
 }
 
 int Solver::inner_solve(const double* fpad, double* xpad) {
   int its = 0, st = 0;
-  if (graphs_ready && fpad == f.p) {
-    // the graphs are built for (f, x): copy out when another output is asked for
-    st = (opt.precision == GKB_PREC_MIXED) ? mixed_solve_graph(&its)
-                                           : cg64.solve_graph(opt.tol_inner, opt.maxit_inner, stream, &its);
-    if (xpad != x.p) GKB_CUDA(cudaMemcpyAsync(xpad, x.p, L64.nvel * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-  } else if (opt.precision == GKB_PREC_MIXED) st = mixed_solve(fpad, xpad, &its);
+  if (opt.precision == GKB_PREC_MIXED) st = mixed_solve(fpad, xpad, &its);
   else st = cg64.solve(fpad, xpad, opt.tol_inner, opt.maxit_inner, stream, &its);
-  stats.inner_iterations += its;
-  stats.inner_solves += 1;
-  inner_its.push_back(its);
+  { ProfScope ps_(GKB_KC_GKB, stream); k_note_inner<<<1, 1, 0, stream>>>(gkb_dev, cg_dev); }
   return st;
 }
 
@@ -1071,23 +999,171 @@ int Solver::mixed_solve(const double* f, double* x64, int* iters) {
   return cg_host->status;
 }
 
-int Solver::solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
-                  const double* w0, const double* p0) {
-  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
-  if (!g || !r || !w_out || !p_out) throw Error{GKB_ERR_INVALID_ARG, "g, r, w_out and p_out must not be NULL"};
-  if (!(tol >= 0)) throw Error{GKB_ERR_INVALID_ARG, "tol must be >= 0"};
-  if (delay < 0 || delay > GKB_RING - 2) throw Error{GKB_ERR_INVALID_ARG, "delay out of range"};
-  auto t0 = std::chrono::steady_clock::now();
+void Solver::ensure_capture_streams() {
+  if (!cap1) GKB_CUDA(cudaStreamCreateWithFlags(&cap1, cudaStreamNonBlocking));
+  if (!cap2) GKB_CUDA(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
+  if (!cap3) GKB_CUDA(cudaStreamCreateWithFlags(&cap3, cudaStreamNonBlocking));
+}
+
+// One inner solve x = M^-1 f in graph form (prefix; while; suffix), then its
+// record in the GKB state. Straight-line parts count once per inner solve
+// (profiler phase 2), the loop body once per iteration (phase 3).
+void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
+  Profiler* P = g_prof;
+  const int saved = P ? P->phase : -1;
+  if (P) P->phase = 2;
+  const long long len = L64.nvel;
+  const double tol2 = opt.tol_inner * opt.tol_inner;
+  const int maxit = opt.maxit_inner;
+  if (opt.precision == GKB_PREC_MIXED) {
+    Cg<float>& c = cg32;
+    float* zp = c.pre ? c.z.p : c.r.p;
+    const int* upd = &cg_dev->update;
+    const double delta2 = opt.mixed_rtol * opt.mixed_rtol;
+    capture_loop(
+        s, sb, 3,
+        [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+          k_cg_setup<<<1, 1, 0, st>>>(cg_dev, tol2, maxit, delta2);
+          GKB_CUDA(cudaMemsetAsync(x.p, 0, len * sizeof(double), st));
+          GKB_CUDA(cudaMemsetAsync(x32.p, 0, len * sizeof(float), st));
+          Ops<double>::dot(len, f.p, f.p, red, FIN_CG_INIT, cg_dev, st);
+          { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_cvt_f32<<<lin_blocks(len), CB, 0, st>>>(len, f.p, c.r.p, nullptr); }
+          if (c.pre) c.pre->vcycle(c.r.p, zp, st);
+          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ0, cg_dev, st);
+          Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 1, st);
+          k_cg_cond_init<<<1, 1, 0, st>>>(h, cg_dev);
+        },
+        [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+          Ops<float>::apply_dot(L32, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, st);
+          Ops<float>::cg_update(len, x32.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, st, FIN_MX_RR);
+          // reliable update, predicated on the flag the finaliser just set
+          { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_mixed_accum<<<lin_blocks(len), CB, 0, st>>>(len, x32.p, x.p, upd); }
+          Ops<double>::residual(L64, x.p, f.p, r64.p, st, upd);
+          { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_cvt_f32<<<lin_blocks(len), CB, 0, st>>>(len, r64.p, c.r.p, upd); }
+          Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, st, upd);
+          if (c.pre) c.pre->vcycle(c.r.p, zp, st);
+          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
+          Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, st);
+          k_cg_cond<<<1, 1, 0, st>>>(h, cg_dev, maxit + 2);
+        },
+        [&](cudaStream_t st) {
+          { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_mixed_accum<<<lin_blocks(len), CB, 0, st>>>(len, x32.p, x.p, nullptr); }
+        });
+  } else {
+    Cg<double>& c = cg64;
+    double* zp = c.pre ? c.z.p : c.r.p;
+    capture_loop(
+        s, sb, 3,
+        [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+          k_cg_setup<<<1, 1, 0, st>>>(cg_dev, tol2, maxit, 0.0);
+          GKB_CUDA(cudaMemsetAsync(x.p, 0, len * sizeof(double), st));
+          GKB_CUDA(cudaMemcpyAsync(c.r.p, f.p, len * sizeof(double), cudaMemcpyDeviceToDevice, st));
+          Ops<double>::dot(len, f.p, f.p, red, FIN_CG_INIT, cg_dev, st);
+          if (c.pre) c.pre->vcycle(c.r.p, zp, st);
+          Ops<double>::dot(len, c.r.p, zp, red, FIN_CG_RZ0, cg_dev, st);
+          Ops<double>::cg_dir(len, c.p.p, zp, cg_dev, 1, st);
+          k_cg_cond_init<<<1, 1, 0, st>>>(h, cg_dev);
+        },
+        [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+          Ops<double>::apply_dot(L64, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, st);
+          Ops<double>::cg_update(len, x.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, st);
+          if (c.pre) c.pre->vcycle(c.r.p, zp, st);
+          Ops<double>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
+          Ops<double>::cg_dir(len, c.p.p, zp, cg_dev, 0, st);
+          k_cg_cond<<<1, 1, 0, st>>>(h, cg_dev, maxit + 2);
+        },
+        [&](cudaStream_t) {});
+  }
+  { ProfScope ps_(GKB_KC_GKB, s); k_note_inner<<<1, 1, 0, s>>>(gkb_dev, cg_dev); }
+  if (P) P->phase = saved;
+}
+
+// AL transform, GKB initialisation and the while loop of Algorithm 1,
+// captured into the graph that s is capturing. Inputs: wtmp (g), ctmp (r);
+// outputs: u (velocity without y0), pp (pressure), y0.
+void Solver::capture_core(cudaStream_t s, cudaStream_t sb1, cudaStream_t sb2) {
+  const Lvl& L = L64;
+  const long long len = L.nvel;
+  GkbState* S = gkb_dev;
+  double* red_out = (double*)((char*)gkb_dev + offsetof(GkbState, red));
+  // AL transform (Eq. (3)): f = g + gamma A N^-1 r ; y0 = M^-1 f ; b = r - A^T y0
+  Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
+  Ops<double>::axpby(len, 1.0, wtmp.p, 1.0, f.p, s);
+  capture_inner(s, sb1);
+  GKB_CUDA(cudaMemcpyAsync(y0.p, x.p, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // init: beta_1, q_1, w = M^-1 A q_1, alpha_1, v_1, zeta_1, d_1, p, u
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S); }
+  Ops<double>::grad(L, q.p, f.p, 1.0, s);
+  GKB_CUDA(cudaMemsetAsync(u.p, 0, len * sizeof(double), s));
+  GKB_CUDA(cudaMemsetAsync(pp.p, 0, L.ncell * sizeof(double), s));
+  capture_inner(s, sb1);
+  Ops<double>::apply_dot(L, 1, x.p, t.p, red, FIN_STORE, red_out, s);
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA1, S, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, u.p, S, 1); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 1); }
+  // the while loop of Algorithm 1 as a device-side loop
+  const int hard_max = opt.maxit + 2;
+  capture_loop(
+      s, sb1, 1,
+      [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+        { ProfScope ps_(GKB_KC_GKB, st); k_gkb_cond_init<<<1, 1, 0, st>>>(h, S); }
+      },
+      [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+        { ProfScope ps_(GKB_KC_GKB, st); k_gk1<<<cgrid(L), dim3(32, 8), 0, st>>>(L, v.p, q.p, gq.p, S, red, red_out); }
+        { ProfScope ps_(GKB_KC_GKB, st); k_gkb_scalar<<<1, 32, 0, st>>>(S_BETA, S, red_out); }
+        { ProfScope ps_(GKB_KC_GKB, st); k_gk2<<<fgrid(L), dim3(32, 8), 0, st>>>(L, gq.p, f.p, S); }
+        capture_inner(st, sb2);
+        { ProfScope ps_(GKB_KC_GKB, st); k_gk3<<<lin_blocks(len), CB, 0, st>>>(len, x.p, v.p, w.p, S); }
+        Ops<double>::apply_dot(L, 1, w.p, t.p, red, FIN_STORE, red_out, st);
+        { ProfScope ps_(GKB_KC_GKB, st); k_gkb_scalar<<<1, 32, 0, st>>>(S_ALPHA, S, red_out); }
+        { ProfScope ps_(GKB_KC_GKB, st); k_gk4v<<<lin_blocks(len), CB, 0, st>>>(len, w.p, v.p, u.p, S, 0); }
+        { ProfScope ps_(GKB_KC_GKB, st); k_gk4c<<<cgrid(L), dim3(32, 8), 0, st>>>(L, gq.p, q.p, d.p, pp.p, S, 0); }
+        { ProfScope ps_(GKB_KC_GKB, st); k_gkb_cond<<<1, 1, 0, st>>>(h, S, hard_max); }
+      },
+      [&](cudaStream_t) {});
+}
+
+void Solver::build_solve_graph() {
+  sgraph.destroy();
+  if (!opt.use_graph || opt.profile) return;
+  ensure_capture_streams();
+  Profiler* P = g_prof;
+  if (P) {
+    for (int ph = 0; ph < 4; ++ph)
+      for (int k = 0; k < GKB_KC_COUNT; ++k) { P->cap_l[ph][k] = 0; P->cap_u[ph][k] = 0; }
+    P->phase = 0;
+  }
+  cudaGraph_t g = nullptr;
+  try {
+    GKB_CUDA(cudaGraphCreate(&g, 0));
+    GKB_CUDA(cudaStreamBeginCaptureToGraph(cap1, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capture_core(cap1, cap2, cap3);
+    GKB_CUDA(cudaStreamEndCapture(cap1, &g));
+    GKB_CUDA(cudaGraphInstantiate(&sgraph.exec, g, 0));
+  } catch (...) {
+    if (P) P->phase = -1;
+    abandon_captures({cap3, cap2, cap1});
+    if (g) cudaGraphDestroy(g);
+    sgraph.exec = nullptr;
+    throw;
+  }
+  cudaGraphDestroy(g);
+  if (P) {
+    P->phase = -1;
+    for (int ph = 0; ph < 4; ++ph)
+      for (int k = 0; k < GKB_KC_COUNT; ++k) { sgraph.cl[ph][k] = P->cap_l[ph][k]; sgraph.cu[ph][k] = P->cap_u[ph][k]; }
+  }
+}
+
+// right-hand side into the padded layout: wtmp = g, ctmp = r, with the
+// defect correction of an initial guess (g - W w0 - A p0, r - A^T w0)
+void Solver::stage_in(const double* g, const double* r, const double* w0, const double* p0) {
   cudaStream_t s = stream;
   const Lvl& L = L64;
   Compact cmp = make_compact(L);
   const long long len = L.nvel;
-  stats.inner_iterations = 0;
-  stats.inner_solves = 0;
-  inner_its.clear();
-  prof.reset();
-  if (opt.profile) prof.enable(32768);
-  // inputs -> padded FP64 (f holds g, bc holds r)
   auto load_m = [&](const double* src, double* dst) {
     const double* dsrc = src;
     if (!is_device_ptr(src)) {
@@ -1106,10 +1182,9 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
     GKB_CUDA(cudaMemsetAsync(dst, 0, L.ncell * sizeof(double), s));
     { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, dsrc, dst); }
   };
-  load_m(g, wtmp.p);   // wtmp = g
-  load_n(r, ctmp.p);   // ctmp = r
+  load_m(g, wtmp.p);
+  load_n(r, ctmp.p);
   if (w0) {
-    // defect correction: g <- g - W w0 - A p0 ; r <- r - A^T w0
     load_m(w0, u.p);
     Ops<double>::apply(L, 0, u.p, t.p, s);
     Ops<double>::axpby(len, -1.0, t.p, 1.0, wtmp.p, s);
@@ -1121,13 +1196,10 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
     Ops<double>::negdiv(L, u.p, q.p, 1.0, s);
     Ops<double>::axpby(L.ncell, -1.0, q.p, 1.0, ctmp.p, s);
   }
-  // AL transform (Eq. (3)): f = g + gamma A N^-1 r ; y0 = M^-1 f ; b = r - A^T y0
-  Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
-  Ops<double>::axpby(len, 1.0, wtmp.p, 1.0, f.p, s);
-  int inner_status = ST_OK;
-  int st = inner_solve(f.p, y0.p);
-  if (st != ST_OK) inner_status = st;
-  // GKB state
+}
+
+void Solver::init_state(double tol, int delay) {
+  cudaStream_t s = stream;
   GkbState hs{};
   hs.tol = tol;
   hs.n_scale = n_scale;
@@ -1141,74 +1213,102 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   hs.h_zeta = hist.p + 2 * cap;
   hs.h_est = hist.p + 3 * cap;
   hs.hcap = cap;
+  hs.h_inner = hist_inner.p;
+  hs.icap = opt.maxit + 4;
   GKB_CUDA(cudaMemsetAsync(hist.p, 0, 4 * cap * sizeof(double), s));
+  GKB_CUDA(cudaMemsetAsync(hist_inner.p, 0, hs.icap * sizeof(int), s));
   GKB_CUDA(cudaMemcpyAsync(gkb_dev, &hs, sizeof(GkbState), cudaMemcpyHostToDevice, s));
+}
+
+// the same sequence as capture_core, sequenced by the host (profiling,
+// use_graph = 0): one flag read per outer iteration
+void Solver::run_core_host() {
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  const long long len = L.nvel;
   GkbState* S = gkb_dev;
   double* red_out = (double*)((char*)gkb_dev + offsetof(GkbState, red));
-  // init: beta_1, q_1, w = M^-1 A q_1, alpha_1, v_1, zeta_1, d_1, p, u
+  Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
+  Ops<double>::axpby(len, 1.0, wtmp.p, 1.0, f.p, s);
+  inner_solve(f.p, y0.p);
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out); }
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out); }
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S); }
   Ops<double>::grad(L, q.p, f.p, 1.0, s);
   GKB_CUDA(cudaMemsetAsync(u.p, 0, len * sizeof(double), s));
   GKB_CUDA(cudaMemsetAsync(pp.p, 0, L.ncell * sizeof(double), s));
+  inner_solve(f.p, x.p);
+  Ops<double>::apply_dot(L, 1, x.p, t.p, red, FIN_STORE, red_out, s);
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA1, S, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, u.p, S, 1); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 1); }
   GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
-  if (!gkb_host->stop) {
-    st = inner_solve(f.p, x.p);
-    if (st != ST_OK) inner_status = st;
-    Ops<double>::apply_dot(L, 1, x.p, t.p, red, FIN_STORE, red_out, s);
-    { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA1, S, red_out); }
-    { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, u.p, S, 1); }
-    { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 1); }
+  while (!gkb_host->stop && gkb_host->status == ST_OK) {
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, v.p, q.p, gq.p, S, red, red_out); }
+    { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA, S, red_out); }
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk2<<<fgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, f.p, S); }
+    inner_solve(f.p, x.p);
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk3<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, w.p, S); }
+    Ops<double>::apply_dot(L, 1, w.p, t.p, red, FIN_STORE, red_out, s);
+    { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA, S, red_out); }
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, w.p, v.p, u.p, S, 0); }
+    { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 0); }
     GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
     GKB_CUDA(cudaStreamSynchronize(s));
-    // the while loop of Algorithm 1
-    while (!gkb_host->stop) {
-      { ProfScope ps_(GKB_KC_GKB, s); k_gk1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, v.p, q.p, gq.p, S, red, red_out); }
-      { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA, S, red_out); }
-      { ProfScope ps_(GKB_KC_GKB, s); k_gk2<<<fgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, f.p, S); }
-      st = inner_solve(f.p, x.p);
-      if (st != ST_OK) inner_status = st;
-      { ProfScope ps_(GKB_KC_GKB, s); k_gk3<<<lin_blocks(len), CB, 0, s>>>(len, x.p, v.p, w.p, S); }
-      Ops<double>::apply_dot(L, 1, w.p, t.p, red, FIN_STORE, red_out, s);
-      { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_ALPHA, S, red_out); }
-      { ProfScope ps_(GKB_KC_GKB, s); k_gk4v<<<lin_blocks(len), CB, 0, s>>>(len, w.p, v.p, u.p, S, 0); }
-      { ProfScope ps_(GKB_KC_GKB, s); k_gk4c<<<cgrid(L), dim3(32, 8), 0, s>>>(L, gq.p, q.p, d.p, pp.p, S, 0); }
-      GKB_CUDA(cudaMemcpyAsync(gkb_host, S, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
-      GKB_CUDA(cudaStreamSynchronize(s));
-      if (gkb_host->status != ST_OK) break;
-    }
   }
-  GKB_CUDA(cudaGetLastError());
-  // back-transform: w = u + y0 (+ w0), p (+ p0), mean-free pressure if enclosed
+}
+
+// back-transform w = u + y0 (+ w0), p (+ p0), mean-free pressure for
+// enclosed flow, outputs in compact order; statistics
+int Solver::finish(double* w_out, double* p_out, const double* w0, const double* p0, bool graph_run) {
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  Compact cmp = make_compact(L);
+  const long long len = L.nvel;
   Ops<double>::axpby(len, 1.0, y0.p, 1.0, u.p, s);
   if (w0) {
-    load_m(w0, t.p);
+    const double* src = w0;
+    if (!is_device_ptr(w0)) {
+      GKB_CUDA(cudaMemcpyAsync(stage_m.p, w0, m * sizeof(double), cudaMemcpyHostToDevice, s));
+      src = stage_m.p;
+    }
+    GKB_CUDA(cudaMemsetAsync(t.p, 0, len * sizeof(double), s));
+    { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, t.p); }
     Ops<double>::axpby(len, 1.0, t.p, 1.0, u.p, s);
     if (p0) {
-      load_n(p0, ctmp.p);
+      const double* srcp = p0;
+      if (!is_device_ptr(p0)) {
+        GKB_CUDA(cudaMemcpyAsync(stage_n.p, p0, ncell * sizeof(double), cudaMemcpyHostToDevice, s));
+        srcp = stage_n.p;
+      }
+      GKB_CUDA(cudaMemsetAsync(ctmp.p, 0, L.ncell * sizeof(double), s));
+      { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, s>>>(L, srcp, ctmp.p); }
       Ops<double>::axpby(L.ncell, 1.0, ctmp.p, 1.0, pp.p, s);
     }
   }
-  double shift = 0.0;
-  if (enclosed) {
-    { ProfScope ps_(GKB_KC_GKB, s); k_cell_sum<<<cgrid(L), dim3(32, 8), 0, s>>>(L, pp.p, red, scal.p); }
-    double hsum[1];
-    read_scalars(scal.p, hsum, 1, s);
-    shift = hsum[0] / (double)ncell;
-  }
+  if (enclosed) { ProfScope ps_(GKB_KC_GKB, s); k_cell_sum<<<cgrid(L), dim3(32, 8), 0, s>>>(L, pp.p, red, scal.p); }
   const bool wdev = is_device_ptr(w_out), pdev = is_device_ptr(p_out);
   { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_vel<<<lin_blocks(m), 256, 0, s>>>(L, cmp, u.p, wdev ? w_out : stage_m.p); }
-  { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_cell<<<lin_blocks(ncell), 256, 0, s>>>(L, pp.p, pdev ? p_out : stage_n.p, shift); }
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_unpack_cell_dev<<<lin_blocks(ncell), 256, 0, s>>>(L, pp.p, pdev ? p_out : stage_n.p, enclosed ? scal.p : nullptr, 1.0 / (double)ncell); }
   if (!wdev) GKB_CUDA(cudaMemcpyAsync(w_out, stage_m.p, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   if (!pdev) GKB_CUDA(cudaMemcpyAsync(p_out, stage_n.p, ncell * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaMemcpyAsync(gkb_host, gkb_dev, sizeof(GkbState), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
   GKB_CUDA(cudaGetLastError());
   const GkbState& H = *gkb_host;
   int status = H.status;
   if (status == ST_OK && !H.converged) status = ST_NOT_CONVERGED;
-  if (status == ST_OK && inner_status != ST_OK) status = inner_status;
+  if (status == ST_OK && H.inner_status != ST_OK) status = H.inner_status;
+  if (graph_run) {
+    // launches of the graph: captured counts times the executions of each part
+    for (int k = 0; k < GKB_KC_COUNT; ++k) {
+      prof.launches[k] += sgraph.cl[0][k] + H.outer_runs * sgraph.cl[1][k] + H.inner_solves * sgraph.cl[2][k] +
+                          H.inner_runs * sgraph.cl[3][k];
+      prof.units[k] += sgraph.cu[0][k] + H.outer_runs * sgraph.cu[1][k] + H.inner_solves * sgraph.cu[2][k] +
+                       H.inner_runs * sgraph.cu[3][k];
+    }
+  }
   prof.collect();
   for (int kc = 0; kc < GKB_KC_COUNT; ++kc) {
     stats.kernel_launches[kc] = prof.launches[kc];
@@ -1218,6 +1318,26 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   stats.status = status;
   stats.outer_iterations = H.k;
   stats.estimate = H.est;
+  stats.inner_iterations = H.inner_its;
+  stats.inner_solves = H.inner_solves;
+  return status;
+}
+
+int Solver::solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
+                  const double* w0, const double* p0) {
+  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (!g || !r || !w_out || !p_out) throw Error{GKB_ERR_INVALID_ARG, "g, r, w_out and p_out must not be NULL"};
+  if (!(tol >= 0)) throw Error{GKB_ERR_INVALID_ARG, "tol must be >= 0"};
+  if (delay < 0 || delay > GKB_RING - 2) throw Error{GKB_ERR_INVALID_ARG, "delay out of range"};
+  auto t0 = std::chrono::steady_clock::now();
+  prof.reset();
+  if (opt.profile) prof.enable(32768);
+  stage_in(g, r, w0, p0);
+  init_state(tol, delay);
+  const bool graph_run = sgraph.exec != nullptr && !opt.profile;
+  if (graph_run) GKB_CUDA(cudaGraphLaunch(sgraph.exec, stream));
+  else run_core_host();
+  const int status = finish(w_out, p_out, w0, p0, graph_run);
   stats.solve_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return status;
 }
@@ -1354,6 +1474,148 @@ void Solver::precond(const double* rin, double* zout) {
   if (!zdev) GKB_CUDA(cudaMemcpyAsync(zout, dst, m * sizeof(double), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
   GKB_CUDA(cudaGetLastError());
+}
+
+
+// ---------------------------------------------------------------------------
+// batched solves: one graph, one branch per problem
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct BatchGraph {
+  std::vector<const Solver*> members;
+  std::vector<int> gens;
+  cudaGraphExec_t exec = nullptr;
+  ~BatchGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+std::mutex g_batch_mutex;
+std::vector<BatchGraph*> g_batches;
+
+}  // namespace
+
+void forget_batches(const Solver* sv) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (size_t i = 0; i < g_batches.size();) {
+    BatchGraph* b = g_batches[i];
+    bool hit = false;
+    for (const Solver* m : b->members) hit = hit || (m == sv);
+    if (hit) {
+      delete b;
+      g_batches.erase(g_batches.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+static BatchGraph* build_batch(Solver** S, int count, cudaStream_t origin) {
+  BatchGraph* B = new BatchGraph();
+  for (int i = 0; i < count; ++i) {
+    B->members.push_back(S[i]);
+    B->gens.push_back(S[i]->generation);
+  }
+  std::vector<cudaStream_t> br(count, nullptr);
+  std::vector<cudaEvent_t> ev(count + 1, nullptr);
+  cudaGraph_t g = nullptr;
+  Profiler* saved = g_prof;
+  g_prof = nullptr;  // launches are accounted from each handle's own graph counts
+  try {
+    for (int i = 0; i < count; ++i) GKB_CUDA(cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= count; ++i) GKB_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming));
+    GKB_CUDA(cudaGraphCreate(&g, 0));
+    GKB_CUDA(cudaStreamBeginCaptureToGraph(origin, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    GKB_CUDA(cudaEventRecord(ev[count], origin));
+    for (int i = 0; i < count; ++i) {
+      GKB_CUDA(cudaStreamWaitEvent(br[i], ev[count], 0));
+      S[i]->ensure_capture_streams();
+      S[i]->capture_core(br[i], S[i]->cap2, S[i]->cap3);
+      GKB_CUDA(cudaEventRecord(ev[i], br[i]));
+      GKB_CUDA(cudaStreamWaitEvent(origin, ev[i], 0));
+    }
+    GKB_CUDA(cudaStreamEndCapture(origin, &g));
+    GKB_CUDA(cudaGraphInstantiate(&B->exec, g, 0));
+  } catch (...) {
+    g_prof = saved;
+    std::vector<cudaStream_t> all(br.begin(), br.end());
+    all.push_back(origin);
+    for (int i = 0; i < count; ++i) { all.push_back(S[i]->cap2); all.push_back(S[i]->cap3); }
+    for (cudaStream_t st : all) abandon_captures({st});
+    if (g) cudaGraphDestroy(g);
+    for (cudaStream_t st : br) if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+    delete B;
+    throw;
+  }
+  g_prof = saved;
+  cudaGraphDestroy(g);
+  for (cudaStream_t st : br) cudaStreamDestroy(st);
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  return B;
+}
+
+int solve_batched(Solver** S, int count, const double* const* g, const double* const* r, double tol, int delay,
+                  double* const* w, double* const* p) {
+  if (count < 1 || !S || !g || !r || !w || !p) throw Error{GKB_ERR_INVALID_ARG, "bad batched arguments"};
+  if (!(tol >= 0)) throw Error{GKB_ERR_INVALID_ARG, "tol must be >= 0"};
+  if (delay < 0 || delay > GKB_RING - 2) throw Error{GKB_ERR_INVALID_ARG, "delay out of range"};
+  for (int i = 0; i < count; ++i) {
+    if (!S[i] || !S[i]->have_problem) throw Error{GKB_ERR_INVALID_ARG, "every handle needs gkb_set_problem"};
+    if (!S[i]->sgraph.exec) throw Error{GKB_ERR_INVALID_ARG, "batched solves need use_graph = 1 and profile = 0"};
+    if (!g[i] || !r[i] || !w[i] || !p[i]) throw Error{GKB_ERR_INVALID_ARG, "NULL vector in the batch"};
+    for (int j = 0; j < i; ++j)
+      if (S[j] == S[i]) throw Error{GKB_ERR_INVALID_ARG, "a handle appears twice in the batch"};
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = S[0]->stream;
+  BatchGraph* B = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    for (BatchGraph* b : g_batches) {
+      if ((int)b->members.size() != count) continue;
+      bool same = true;
+      for (int i = 0; i < count && same; ++i) same = b->members[i] == S[i] && b->gens[i] == S[i]->generation;
+      if (same) { B = b; break; }
+    }
+  }
+  if (!B) {
+    Solver* s0 = S[0];
+    s0->ensure_capture_streams();
+    B = build_batch(S, count, s0->cap1);
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    g_batches.push_back(B);
+  }
+  // every problem stages its inputs and state on the batch stream
+  std::vector<cudaStream_t> own(count);
+  for (int i = 0; i < count; ++i) {
+    own[i] = S[i]->stream;
+    S[i]->stream = st;
+  }
+  int status = GKB_OK;
+  try {
+    for (int i = 0; i < count; ++i) {
+      S[i]->prof.reset();
+      S[i]->stage_in(g[i], r[i], nullptr, nullptr);
+      S[i]->init_state(tol, delay);
+    }
+    GKB_CUDA(cudaGraphLaunch(B->exec, st));
+    for (int i = 0; i < count; ++i) {
+      const int si = S[i]->finish(w[i], p[i], nullptr, nullptr, true);
+      if (status == GKB_OK && si != GKB_OK) status = si;
+    }
+  } catch (...) {
+    for (int i = 0; i < count; ++i) S[i]->stream = own[i];
+    throw;
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < count; ++i) {
+    S[i]->stream = own[i];
+    S[i]->stats.solve_seconds = secs;
+  }
+  return status;
 }
 
 }  // namespace gkb

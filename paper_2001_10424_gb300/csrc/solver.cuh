@@ -85,19 +85,18 @@ struct Gmg {
   void smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s);
 };
 
-// An instantiated graph "prefix; while (cond) body; suffix" with the launch
-// counts of each part recorded at capture time.
-struct LoopGraph {
+// An instantiated graph of a whole solve with the launch counts of its
+// parts recorded at capture time: [0] once, [1] per outer iteration,
+// [2] per inner solve, [3] per inner loop-body execution.
+struct SolveGraph {
   cudaGraphExec_t exec = nullptr;
-  long long cl[3][GKB_KC_COUNT] = {};
-  long long cu[3][GKB_KC_COUNT] = {};
+  long long cl[4][GKB_KC_COUNT] = {};
+  long long cu[4][GKB_KC_COUNT] = {};
   void destroy() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
   }
-  ~LoopGraph() { destroy(); }
-  // add the launches of one run with `body_runs` loop iterations
-  void account(Profiler* P, long long body_runs) const;
+  ~SolveGraph() { destroy(); }
 };
 
 // Conjugate gradients for M x = f in precision T on one level, optionally
@@ -113,13 +112,6 @@ struct Cg {
   void init(const Lvl& L_, Gmg<T>* pre_, const RedBuf& red_, CgState* st_dev, CgState* st_host);
   // x = M^-1 f to relative tolerance tol (zero start); returns status
   int solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* iters);
-  // the same loop as one CUDA graph with a device-side while node, for the
-  // fixed arrays (f, x) given at build time
-  LoopGraph G;
-  const T* gf = nullptr;
-  T* gx = nullptr;
-  void build_graph(const T* f, T* x, int maxit, cudaStream_t cs, cudaStream_t cs2);
-  int solve_graph(double tol, int maxit, cudaStream_t s, int* iters);
 };
 
 struct Solver {
@@ -159,14 +151,21 @@ struct Solver {
   DevBuf<float> f32, x32;                      // mixed refinement FP32 rhs / correction
   DevBuf<double> hist;                         // alpha, beta, zeta, est histories
   DevBuf<double> stage_m, stage_n;             // compact staging for host I/O
-  std::vector<int> inner_its;
   gkb_stats_t stats{};
   Profiler prof;
-  cudaStream_t cap1 = nullptr, cap2 = nullptr;  // private capture streams
-  LoopGraph mixed_graph;
-  bool graphs_ready = false;
-  void build_graphs();
-  int mixed_solve_graph(int* iters);
+  cudaStream_t cap1 = nullptr, cap2 = nullptr, cap3 = nullptr;  // private capture streams
+  SolveGraph sgraph;              // whole solve as one graph (use_graph, no profiling)
+  DevBuf<int> hist_inner;         // CG iterations of each inner solve
+  int generation = 0;             // bumped by every set_problem
+  void ensure_capture_streams();
+  void build_solve_graph();
+  // emitters shared by the graph capture and the host-sequenced path
+  void capture_core(cudaStream_t s, cudaStream_t sb1, cudaStream_t sb2);
+  void capture_inner(cudaStream_t s, cudaStream_t sb);
+  void stage_in(const double* g, const double* r, const double* w0, const double* p0);
+  void init_state(double tol, int delay);
+  void run_core_host();
+  int finish(double* w_out, double* p_out, const double* w0, const double* p0, bool graph_run);
 
   void set_problem(const gkb_grid* g, const double* viscosity, double mu0, double gamma, double n_scale);
   int solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
@@ -179,5 +178,13 @@ struct Solver {
   int mixed_solve(const double* f, double* x, int* iters);
   ~Solver();
 };
+
+// Solve independent problems (one handle each) in one CUDA graph launch: the
+// whole solve of every problem is one branch of the graph, branches run
+// concurrently. The graph is captured at the first call for a list of
+// handles and reused while none of them is re-set or destroyed.
+int solve_batched(Solver** S, int count, const double* const* g, const double* const* r, double tol, int delay,
+                  double* const* w, double* const* p);
+void forget_batches(const Solver* s);
 
 }  // namespace gkb

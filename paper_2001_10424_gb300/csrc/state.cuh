@@ -144,7 +144,15 @@ struct GkbState {
   double* h_beta;
   double* h_zeta;
   double* h_est;
+  int* h_inner;              // CG iterations of each inner solve, capacity icap
   int hcap;
+  int icap;
+  // inner-solve bookkeeping kept on the device (graph form)
+  int inner_status;          // first non-OK inner status
+  int inner_solves;
+  long long inner_its;       // total CG iterations
+  long long inner_runs;      // total loop-body executions of the inner graphs
+  int outer_runs;            // loop-body executions of the outer graph
   int pad;
 };
 

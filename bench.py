@@ -1,18 +1,25 @@
 #!/usr/bin/env python
 """GKB time-to-1e-8 benchmark on one GB300 (or N independent replicas).
 
-Workload (default): the enclosed 2D Stokes cavity on the unit square, MAC grid
-1024 x 1024 (2,095,104 velocity and 1,048,576 pressure unknowns), forcing
-g ~ N(0,1) per velocity unknown from the fixed seed, r = 0, viscosity 1,
-N = h^2 I, delay d = 5, outer tolerance 1e-8, inner CG preconditioned by one
-GMG V-cycle to 1e-10, plain FP64. One step solves the system for both
-gamma = 10 and gamma = 1000 (two handles set up before timing; setup is
-reported separately). ``value`` is the device time of one step (seconds,
-lower is better) with inputs resident in HBM; L2 is flushed between steps.
+Default workload (``--workload stokes2d``): the enclosed 2D Stokes cavity on
+the unit square, MAC grid 1024 x 1024 (2,095,104 velocity and 1,048,576
+pressure unknowns), forcing g ~ N(0,1) per velocity unknown from the fixed
+seed, r = 0, viscosity 1, N = h^2 I, delay d = 5, outer tolerance 1e-8, inner
+CG preconditioned by one GMG V-cycle to 1e-10, plain FP64. One step solves
+the system for gamma = 10 and for gamma = 1000 (two handles set up before
+timing; setup is reported separately). ``value`` is the device time of one
+step (seconds, lower is better) with inputs resident in HBM; L2 is flushed
+between steps.
+
+Other workloads: ``stokes3d`` (256^3 cavity, gamma 100, mixed FP32/FP64),
+``poiseuille`` (32 x 32 channel, gamma 100, plain CG to 1e-12, seeded
+initial guess), ``batched2d`` (256 cavities of side 32*U{2..16} with
+per-problem viscosity, gamma 100, mixed, one graph launch per step; value
+in solves/s).
 
 ``--impl reference`` times the CPU oracle (sparse-LU inner solves) on the
-host cores instead, on a 256 x 256 member of the same family, extrapolated
-by the unknown ratio.
+host cores instead, on a reduced member of the same family, scaled by the
+unknown ratio.
 """
 import argparse
 import json
@@ -31,24 +38,18 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.258   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.25)
 FP32_PEAK_TFLOPS = 80.6    # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 
-# algorithmic work per velocity unknown of the launch's level (2D), per class:
-# (flops, element accesses); see DESIGN.md "Roofline accounting"
-PER_UNIT_2D = {
-    "apply": (14.0, 2.0),      # M x with fused dot: read x, write y
-    "residual": (14.0, 3.0),   # r = b - M x: read x, b, write r
-    "smooth": (20.0, 4.5),     # z = C r (2 patch rows), d, x updates; mean of first/other steps
-    "restrict": (1.5, 1.25),   # read fine r, write coarse (1/4)
-    "prolong": (1.5, 2.25),    # read coarse (1/4), read + write x
-    "blas": (2.0, 3.0),        # per element: mean of dot / update kernels
+# algorithmic work per velocity unknown of the launch's level, per kernel
+# class: (flops, element accesses); see DESIGN.md "Roofline accounting"
+PER_UNIT = {
+    2: {"apply": (14.0, 2.0), "residual": (14.0, 3.0), "smooth": (20.0, 4.5), "restrict": (1.5, 1.25),
+        "prolong": (1.5, 2.25), "blas": (2.0, 3.0)},
+    3: {"apply": (19.0, 2.0), "residual": (19.0, 3.0), "smooth": (35.0, 4.5), "restrict": (1.5, 1.125),
+        "prolong": (1.5, 2.125), "blas": (2.0, 3.0)},
 }
-PER_UNIT_3D = {
-    "apply": (19.0, 2.0),
-    "residual": (19.0, 3.0),
-    "smooth": (35.0, 4.5),
-    "restrict": (1.5, 1.125),
-    "prolong": (1.5, 2.125),
-    "blas": (2.0, 3.0),
-}
+
+# per-launch DRAM traffic (bytes) of the dominant kernel from ncu captures,
+# keyed by (workload, form, kernel class); summarised under profiles/
+TRAFFIC = {}
 
 
 def measured_peaks():
@@ -120,96 +121,157 @@ def dist_setup():
     return ws, rank, local
 
 
-def cpu_oracle_sample(n_sample, gammas, tol, delay):
-    """Oracle (sparse-LU inner solves) on the n_sample^2 member of the family."""
-    import workloads
-    from oracle import gkb as ogkb
-    from oracle import mac
-    wl = workloads.stokes2d(n_sample)
-    grid = mac.MacGrid(wl["n"], wl["h"], wl["bc"])
-    t0 = time.perf_counter()
-    iters = []
-    for gm in gammas:
-        ops = mac.assemble(grid, 1.0, gm)
-        res = ogkb.solve(grid, ops, wl["g"], wl["r"], tol=tol, delay=delay, inner="direct")
-        iters.append(res["iterations"])
-    return time.perf_counter() - t0, iters
+# ---------------------------------------------------------------------------
+# workloads: the problems one step solves
+# ---------------------------------------------------------------------------
+
+class Workload:
+    """name, problems (dicts: n, h, bc, mu, gamma, g, r, optional w0/p0 and
+    inflow), handle options, and how a step runs (sequential or batched)."""
+
+    def __init__(self, args):
+        import workloads as W
+        self.name = args.workload
+        self.batched = False
+        self.inner = 1          # GMG-PCG
+        self.tol_inner = args.tol_inner
+        self.form = args.form
+        if self.name == "stokes2d":
+            base = W.stokes2d(args.n)
+            self.problems = [dict(base, gamma=float(gm)) for gm in args.gammas]
+            self.dim = 2
+            self.label = "%dx%d MAC Stokes cavity, gamma in {%s}" % (args.n, args.n, ",".join("%g" % g for g in args.gammas))
+            self.sample = ("cavity", 256, args.gammas)
+        elif self.name == "stokes3d":
+            n = args.n if args.n != 1024 else 256
+            base = W.stokes3d(n)
+            self.problems = [dict(base, gamma=100.0)]
+            self.dim = 3
+            self.form = "mixed" if args.form_default else args.form
+            self.label = "%d^3 MAC Stokes cavity, gamma 100" % n
+            self.sample = ("cavity3d", 24, [100.0])
+        elif self.name == "poiseuille":
+            pr = W.poiseuille(32, shifted=False, guess=True)
+            self.problems = [dict(pr, gamma=100.0)]
+            self.dim = 2
+            self.inner = 0
+            self.tol_inner = 1e-12
+            self.label = "32x32 MAC Poiseuille channel, gamma 100, inner CG 1e-12"
+            self.sample = ("poiseuille", 32, [100.0])
+        elif self.name == "batched2d":
+            count = args.batch
+            self.problems = [dict(pr, gamma=100.0) for pr in W.batched2d(count=count)]
+            self.dim = 2
+            self.batched = True
+            self.form = "mixed" if args.form_default else args.form
+            self.label = "%d MAC Stokes cavities, side 32*U{2..16}, gamma 100, one graph launch" % count
+            self.sample = ("batched", 48, [100.0])
+        else:
+            raise ValueError(self.name)
+
+    def metric(self):
+        if self.batched:
+            return "GKB batched solves/s to 1e-8 error (%s, %s GMG-PCG)" % (self.label, self.form_text())
+        inner = "GMG-PCG" if self.inner == 1 else "CG"
+        return "GKB time-to-1e-8 error (%s, %s %s)" % (self.label, self.form_text(), inner)
+
+    def form_text(self):
+        return "plain FP64" if self.form == "fp64" else "mixed FP32/FP64"
+
+    def unit(self):
+        return "solves/s" if self.batched else "s"
 
 
-def run_reference(args, ws, rank):
-    if rank != 0:
-        return 0
-    n_s = 256
-    scale = (args.n / n_s) ** 2
-    times = []
-    for i in range(args.warmup + args.steps):
-        t, _ = cpu_oracle_sample(n_s, args.gammas, args.tol, args.delay)
-        if i >= args.warmup:
-            times.append(t * scale)
-    val = statistics.mean(times)
-    line = {
-        "impl": "reference", "metric": metric_name(args), "value": val, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config(args),
-        "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": "oracle GKB with sparse-LU inner solves on the %dx%d cavity, gamma %s, "
-                                   "time x%.0f (unknown ratio) per step" % (n_s, n_s, args.gammas, scale)},
-        "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
-    return 0
+def make_handle(gk, torch, pr, wk, form, profile=0):
+    opt = gk.gkb_default_options()
+    opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
+    opt.inner = wk.inner
+    opt.tol_inner = wk.tol_inner
+    opt.maxit = 1000
+    opt.maxit_inner = 20000 if wk.inner == 0 else 5000
+    opt.profile = profile
+    opt.stream = torch.cuda.current_stream().cuda_stream
+    h = gk.gkb_create(opt)
+    mu = pr["mu"]
+    import numpy as np
+    if np.isscalar(mu):
+        gk.gkb_set_problem(h, gk.make_grid(pr["n"], pr["h"], pr["bc"]), None, float(mu), pr["gamma"], 0.0)
+    else:
+        visc = np.ascontiguousarray(np.asarray(mu).ravel(order="F"))
+        gk.gkb_set_problem(h, gk.make_grid(pr["n"], pr["h"], pr["bc"]), visc, 1.0, pr["gamma"], 0.0)
+    return h
 
 
-def metric_name(args):
-    return "GKB time-to-1e-8 error (%dx%d MAC Stokes cavity, gamma in {%s}, %s GMG-PCG)" % (
-        args.n, args.n, ",".join("%g" % g for g in args.gammas), "plain FP64" if args.form == "fp64" else "mixed FP32/FP64")
+class Bound:
+    """Handles plus device/host buffers of a workload, and its step."""
+
+    def __init__(self, gk, torch, wk, form, profile=0, subset=None):
+        import numpy as np
+        self.gk, self.torch, self.wk = gk, torch, wk
+        probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
+        self.probs = probs
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile) for pr in probs]
+        self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
+        for h, pr in zip(self.hs, probs):
+            m, n = gk.gkb_layout(h)
+            if "inflow" in pr:   # Dirichlet inflow folded by the library
+                g0 = np.zeros(m)
+                r0 = np.zeros(n)
+                gk.gkb_boundary_rhs(h, 0, np.ascontiguousarray(pr["inflow"]), g0, r0)
+                pr = dict(pr, g=g0, r=r0)
+            self.g.append(torch.tensor(pr["g"], device="cuda"))
+            self.r.append(torch.tensor(pr["r"], device="cuda"))
+            self.w.append(torch.empty(m, dtype=torch.float64, device="cuda"))
+            self.p.append(torch.empty(n, dtype=torch.float64, device="cuda"))
+            self.w0.append(torch.tensor(pr["w0"], device="cuda") if "w0" in pr else None)
+            self.p0.append(torch.tensor(pr["p0"], device="cuda") if "p0" in pr else None)
+        self.host = None
+
+    def step(self, args, host=False):
+        gk = self.gk
+        g, r, w, p = (self.host if host else (self.g, self.r, self.w, self.p))
+        w0 = [None if x is None else (x.cpu().pin_memory() if host else x) for x in self.w0] if host else self.w0
+        p0 = [None if x is None else (x.cpu().pin_memory() if host else x) for x in self.p0] if host else self.p0
+        status = []
+        if self.wk.batched:
+            status.append(gk.gkb_solve_batched(self.hs, g, r, args.tol, args.delay, w, p))
+        else:
+            for i, h in enumerate(self.hs):
+                status.append(gk.gkb_solve(h, g[i], r[i], args.tol, args.delay, w[i], p[i], w0[i], p0[i]))
+        return status
+
+    def pin_host(self):
+        t = self.torch
+        self.host = ([x.cpu().pin_memory() for x in self.g], [x.cpu().pin_memory() for x in self.r],
+                     [t.empty(x.numel(), dtype=t.float64).pin_memory() for x in self.w],
+                     [t.empty(x.numel(), dtype=t.float64).pin_memory() for x in self.p])
+        return sum(x.numel() for x in self.g + self.r) * 8, sum(x.numel() for x in self.w + self.p) * 8
+
+    def stats(self):
+        return [self.gk.gkb_stats(h) for h in self.hs]
+
+    def destroy(self):
+        for h in self.hs:
+            self.gk.gkb_destroy(h)
+        self.hs = []
 
 
-def config(args):
-    return {"workload": "stokes2d_cavity_%d_gamma_%s" % (args.n, "_".join("%g" % g for g in args.gammas)),
-            "grid": [args.n, args.n], "gammas": args.gammas, "tol": args.tol, "delay": args.delay,
-            "tol_inner": args.tol_inner, "form": args.form, "inner": "gmg_pcg", "n_scale": "h^2",
-            "l2": "flushed between steps (1 GiB write)", "parallelism": "replicas" if args.gpus > 1 else "single"}
-
-
-def make_handles(gk, torch, wl, args, form, profile=0):
-    hs = []
-    for gm in args.gammas:
-        opt = gk.gkb_default_options()
-        opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
-        opt.inner = gk.GKB_INNER_GMG_PCG
-        opt.tol_inner = args.tol_inner
-        opt.maxit = 1000
-        opt.maxit_inner = 5000
-        opt.profile = profile
-        opt.stream = torch.cuda.current_stream().cuda_stream
-        h = gk.gkb_create(opt)
-        gk.gkb_set_problem(h, gk.make_grid(wl["n"], wl["h"], wl["bc"]), None, 1.0, float(gm), 0.0)
-        hs.append(h)
-    return hs
-
-
-def roofline(gk, torch, wl, args, form, hbm_peak, peak_kind):
-    """Profiled step: the dominant kernel class's algorithmic throughput,
-    summed over its launches and divided by their CUDA-event durations."""
-    hs = make_handles(gk, torch, wl, args, form, profile=1)
-    m, n = gk.gkb_layout(hs[0])
-    g = torch.tensor(wl["g"], device="cuda")
-    r = torch.tensor(wl["r"], device="cuda")
-    w = torch.empty(m, dtype=torch.float64, device="cuda")
-    p = torch.empty(n, dtype=torch.float64, device="cuda")
+def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
+    """Profiled step (CUDA events around every launch on its stream): the
+    dominant kernel class's algorithmic throughput, summed over its launches
+    and divided by their durations."""
+    subset = list(range(min(len(wk.problems), 16))) if wk.batched else None
+    B = Bound(gk, torch, wk, form, profile=1, subset=subset)
     ms, units, launches = {}, {}, {}
-    for h in hs:
-        gk.gkb_solve(h, g, r, args.tol, args.delay, w, p)
+    for i, h in enumerate(B.hs):
+        gk.gkb_solve(h, B.g[i], B.r[i], args.tol, args.delay, B.w[i], B.p[i], B.w0[i], B.p0[i])
         st = gk.gkb_stats(h)
         for k in gk.KERNEL_CLASSES:
             ms[k] = ms.get(k, 0.0) + st["kernel_ms"][k]
             units[k] = units.get(k, 0) + st["kernel_units"][k]
             launches[k] = launches.get(k, 0) + st["kernel_launches"][k]
-    for h in hs:
-        gk.gkb_destroy(h)
-    table = PER_UNIT_2D
+    B.destroy()
+    table = PER_UNIT[wk.dim]
     cand = {k: v for k, v in ms.items() if k in table}
     top = max(cand, key=cand.get)
     s = 8.0 if form == "fp64" else 4.0
@@ -217,23 +279,110 @@ def roofline(gk, torch, wl, args, form, hbm_peak, peak_kind):
     byts = units[top] * table[top][1] * s
     t = ms[top] * 1e-3
     alu_peak = (FP64_PEAK_TFLOPS if form == "fp64" else FP32_PEAK_TFLOPS) * 1e12
-    alu_time, mem_time = flops / alu_peak, byts / (hbm_peak * 1e9)
     total_ms = sum(ms.values())
-    if alu_time > mem_time:
-        rl = {"bound": "alu", "achieved": flops / t / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-              "peak_kind": "FP64 FMA rate derived from SM count and clock (probe measured 1.25)"
-              if form == "fp64" else "FP32 FMA rate derived from SM count and clock"}
+    if form == "fp64" and flops / alu_peak > byts / (hbm_peak * 1e9):
+        rl = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+              "peak_kind": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe measured 1.25)"}
     else:
         rl = {"bound": "hbm", "achieved": byts / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
-              "peak_kind": "%s hbm_gbs" % peak_kind}
+              "peak_kind": "%s hbm_gbs (copy, burst)" % peak_kind}
     rl["frac"] = rl["achieved"] / rl["peak"]
     rl["kernel_class"] = top
     rl["launches"] = launches[top]
     rl["avg_launch_us"] = ms[top] * 1e3 / max(1, launches[top])
     rl["share_of_kernel_time"] = ms[top] / total_ms if total_ms else None
-    rl["traffic"] = None
+    rl["traffic"] = TRAFFIC.get((wk.name, form, top))
     rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
+    rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % len(ms and (subset or [0]))
     return rl
+
+
+def cpu_oracle_sample(wk, args):
+    """The oracle (sparse-LU inner solves; plain CG for the Poiseuille case)
+    on a reduced member of the workload's family; returns (seconds measured,
+    unknown-ratio scale to the full step, description)."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import gkb as ogkb
+    from oracle import mac
+    kind, n_s, gammas = wk.sample
+    t0 = time.perf_counter()
+    if kind == "cavity":
+        pr = W.stokes2d(n_s)
+        grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+        for gm in gammas:
+            ogkb.solve(grid, mac.assemble(grid, 1.0, gm), pr["g"], pr["r"], tol=args.tol, delay=args.delay, inner="direct")
+        full = sum(p["m"] + p["ncells"] for p in wk.problems)
+        part = len(gammas) * (pr["m"] + pr["ncells"])
+        desc = "%dx%d cavity, gamma %s" % (n_s, n_s, gammas)
+    elif kind == "cavity3d":
+        pr = W.stokes3d(n_s)
+        grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+        ogkb.solve(grid, mac.assemble(grid, 1.0, gammas[0]), pr["g"], pr["r"], tol=args.tol, delay=args.delay, inner="direct")
+        full = sum(p["m"] + p["ncells"] for p in wk.problems)
+        part = pr["m"] + pr["ncells"]
+        desc = "%d^3 cavity, gamma %g" % (n_s, gammas[0])
+    elif kind == "poiseuille":
+        pr = W.poiseuille(32, shifted=False, guess=True)
+        grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+        ops = mac.assemble(grid, 1.0, 100.0)
+        g, r = mac.dirichlet_rhs(grid, ops, {0: pr["inflow"]})
+        ogkb.solve(grid, ops, g, r, tol=args.tol, delay=args.delay, inner="cg", tol_inner=1e-12,
+                   w0=pr["w0"], p0=pr["p0"])
+        full = part = 1
+        desc = "the full 32x32 channel (plain CG inner solves)"
+    else:  # batched: the n_s smallest problems solved one by one
+        order = np.argsort([p["ncells"] for p in wk.problems])[:n_s]
+        part = 0
+        for i in order:
+            pr = wk.problems[int(i)]
+            grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+            ogkb.solve(grid, mac.assemble(grid, pr["mu"], pr["gamma"]), pr["g"], pr["r"], tol=args.tol,
+                       delay=args.delay, inner="direct")
+            part += pr["m"] + pr["ncells"]
+        full = sum(p["m"] + p["ncells"] for p in wk.problems)
+        desc = "%d smallest of the %d cavities, one by one" % (n_s, len(wk.problems))
+    secs = time.perf_counter() - t0
+    return secs, full / part, desc
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    wk = Workload(args)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t, scale, desc = cpu_oracle_sample(wk, args)
+        if i >= args.warmup:
+            times.append(t * scale)
+    step_s = statistics.mean(times)
+    val = len(wk.problems) / step_s if wk.batched else step_s
+    line = {
+        "impl": "reference", "metric": wk.metric(), "value": val, "unit": wk.unit(), "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": bool(wk.batched), "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(args, wk),
+        "cpu_baseline": {"value": val, "unit": wk.unit(), "cores": 1, "kind": "oracle",
+                         "sample": "oracle GKB on %s, scaled x%.0f by the unknown ratio per step" % (desc, scale)},
+        "e2e": {"value": val, "unit": wk.unit(), "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config(args, wk):
+    sizes = sorted(set(tuple(p["n"]) for p in wk.problems))
+    c = {"workload": wk.name, "problems": len(wk.problems), "tol": args.tol, "delay": args.delay,
+         "tol_inner": wk.tol_inner, "form": wk.form, "inner": "gmg_pcg" if wk.inner == 1 else "cg",
+         "n_scale": "h^d", "l2": "flushed between steps (1 GiB write)",
+         "parallelism": "replicas" if args.gpus > 1 else "single"}
+    if len(sizes) <= 4:
+        c["grid"] = [list(s) for s in sizes]
+    else:
+        c["grid_sides"] = [int(s[0]) for s in sizes]
+    c["gammas"] = sorted(set(p["gamma"] for p in wk.problems))
+    return c
 
 
 def run_ours(args, ws, rank, local):
@@ -241,7 +390,6 @@ def run_ours(args, ws, rank, local):
     import torch
 
     import paper_2001_10424_gb300 as gk
-    import workloads
 
     torch.cuda.set_device(local)
     if ws > 1:
@@ -250,47 +398,30 @@ def run_ours(args, ws, rank, local):
     gk.build.build()
     gk.load()
     hbm_peak, peak_kind = measured_peaks()
-    wl = workloads.stokes2d(args.n)
+    wk = Workload(args)
     t0 = time.perf_counter()
-    hs = make_handles(gk, torch, wl, args, args.form)
+    B = Bound(gk, torch, wk, wk.form)
     setup_s = time.perf_counter() - t0
-    m, n = gk.gkb_layout(hs[0])
-    g = torch.tensor(wl["g"], device="cuda")
-    r = torch.tensor(wl["r"], device="cuda")
-    w = torch.empty(m, dtype=torch.float64, device="cuda")
-    p = torch.empty(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(1 << 28, dtype=torch.float32, device="cuda")  # 1 GiB > L2
     stream = torch.cuda.current_stream()
-
-    def step():
-        outer, inner, launches, status = [], [], 0, []
-        for h in hs:
-            rc = gk.gkb_solve(h, g, r, args.tol, args.delay, w, p)
-            st = gk.gkb_stats(h)
-            status.append(rc)
-            outer.append(st["outer_iterations"])
-            inner.append(st["inner_iterations"])
-            launches += sum(st["kernel_launches"].values())
-        return outer, inner, launches, status
-
     for _ in range(args.warmup):
-        step()
+        B.step(args)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    step_ms, launches_total, outer, inner, status = [], 0, None, None, None
+    step_ms, launches_total, status = [], 0, None
     for _ in range(args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        outer, inner, nl, status = step()
+        status = B.step(args)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        launches_total += nl
+        launches_total += sum(sum(st["kernel_launches"].values()) for st in B.stats())
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -300,76 +431,72 @@ def run_ours(args, ws, rank, local):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    # end to end through the C ABI with pinned host buffers
-    gh = torch.tensor(wl["g"]).pin_memory()
-    rh = torch.tensor(wl["r"]).pin_memory()
-    wh = torch.empty(m, dtype=torch.float64).pin_memory()
-    ph = torch.empty(n, dtype=torch.float64).pin_memory()
+    stats = B.stats()
+    outer = [st["outer_iterations"] for st in stats]
+    inner = [st["inner_iterations"] for st in stats]
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    h2d, d2h = B.pin_host()
     e2e = []
     for i in range(args.steps + 1):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        for h in hs:
-            gk.gkb_solve(h, gh, rh, args.tol, args.delay, wh, ph)
+        B.step(args, host=True)
         t2 = time.perf_counter()
         if i > 0:
             e2e.append(t2 - t1)
     e2e_s = statistics.mean(e2e)
-    correct = bool(np.isfinite(wh.numpy()).all())
-    for h in hs:
-        gk.gkb_destroy(h)
+    finite = bool(all(np.isfinite(x.numpy()).all() for x in B.host[2]))
+    B.destroy()
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return 0
-    rl = roofline(gk, torch, wl, args, args.form, hbm_peak, peak_kind)
-    rl["traffic"] = TRAFFIC.get((args.form, rl["kernel_class"]))
+    rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
-    if not args.no_forms:
-        other = "mixed" if args.form == "fp64" else "fp64"
-        hs2 = make_handles(gk, torch, wl, args, other)
+    if not args.no_forms and not wk.batched and wk.inner == 1:
+        other = "mixed" if wk.form == "fp64" else "fp64"
+        B2 = Bound(gk, torch, wk, other)
         for _ in range(2):
-            for h in hs2:
-                gk.gkb_solve(h, g, r, args.tol, args.delay, w, p)
+            B2.step(args)
         vals = []
         for _ in range(max(1, min(args.steps, 3))):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for h in hs2:
-                gk.gkb_solve(h, g, r, args.tol, args.delay, w, p)
+            B2.step(args)
             e1.record(stream)
             e1.synchronize()
             vals.append(e0.elapsed_time(e1) / 1e3)
-        its = [gk.gkb_stats(h)["outer_iterations"] for h in hs2]
-        inn = [gk.gkb_stats(h)["inner_iterations"] for h in hs2]
-        for h in hs2:
-            gk.gkb_destroy(h)
-        forms[other] = {"s_per_step": statistics.mean(vals), "outer_iterations": its, "inner_iterations": inn}
-        forms[args.form] = {"s_per_step": ms / 1e3, "outer_iterations": outer, "inner_iterations": inner}
+        st2 = B2.stats()
+        B2.destroy()
+        forms[other] = {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
+                        "inner_iterations": [s["inner_iterations"] for s in st2]}
+        forms[wk.form] = {"s_per_step": ms / 1e3, "outer_iterations": outer, "inner_iterations": inner}
     cpu = None
     if not args.no_cpu_baseline:
-        n_s = 256
-        t_cpu, _ = cpu_oracle_sample(n_s, args.gammas, args.tol, args.delay)
-        scale = (args.n / n_s) ** 2
-        cpu = {"value": t_cpu * scale, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": "oracle GKB (sparse-LU inner solves) on the %dx%d cavity, gamma %s, %.1f s measured, "
-                         "x%.0f (unknown ratio) to the %dx%d step" % (n_s, n_s, args.gammas, t_cpu, scale, args.n, args.n)}
-    value = ms / 1e3
+        t_cpu, scale, desc = cpu_oracle_sample(wk, args)
+        cpu_step = t_cpu * scale
+        cpu = {"value": len(wk.problems) / cpu_step if wk.batched else cpu_step, "unit": wk.unit(), "cores": 1,
+               "kind": "oracle",
+               "sample": "oracle GKB on %s: %.1f s measured, x%.0f (unknown ratio) to the full step" % (desc, t_cpu, scale)}
+    step_s = ms / 1e3
+    value = args.gpus * len(wk.problems) / step_s if wk.batched else step_s
+    e2e_val = args.gpus * len(wk.problems) / e2e_s if wk.batched else e2e_s
     line = {
-        "metric": metric_name(args), "value": value, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(len(args.gammas) * (m + n) * 8),
-                "d2h_bytes_per_step": int(len(args.gammas) * (m + n) * 8)},
+        "metric": wk.metric(), "value": value, "unit": wk.unit(), "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": bool(wk.batched), "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if wk.form == "fp64" else "f32+f64", "data": "synthetic",
+        "config": config(args, wk),
+        "e2e": {"value": e2e_val, "unit": wk.unit(), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches_total),
         "roofline": rl, "cpu_baseline": cpu, "clocks": clk,
-        "solves_per_s": args.gpus * len(args.gammas) / value,
-        "inner_iterations_per_s": args.gpus * sum(inner) / value,
-        "outer_iterations": outer, "inner_iterations": inner, "status": status,
-        "setup_s": setup_s, "forms": forms, "finite_output": correct,
+        "solves_per_s": args.gpus * len(wk.problems) / step_s,
+        "inner_iterations_per_s": args.gpus * sum(inner) / step_s,
+        "outer_iterations": outer if len(outer) <= 8 else {"min": min(outer), "max": max(outer), "sum": sum(outer)},
+        "inner_iterations": inner if len(inner) <= 8 else {"min": min(inner), "max": max(inner), "sum": sum(inner)},
+        "status": status, "setup_s": setup_s, "forms": forms, "finite_output": finite,
     }
     print(json.dumps(line))
     if ws > 1:
@@ -382,31 +509,20 @@ def run_probe(args, local):
     import torch
 
     import paper_2001_10424_gb300 as gk
-    import workloads
     torch.cuda.set_device(local)
     gk.build.build()
     gk.load()
-    wl = workloads.stokes2d(args.n)
-    args.gammas = args.gammas[:1]
-    h = make_handles(gk, torch, wl, args, args.form)[0]
-    m, n = gk.gkb_layout(h)
-    g = torch.tensor(wl["g"], device="cuda")
-    r = torch.tensor(wl["r"], device="cuda")
-    w = torch.empty(m, dtype=torch.float64, device="cuda")
-    p = torch.empty(n, dtype=torch.float64, device="cuda")
+    wk = Workload(args)
+    wk.problems = wk.problems[:1]
+    B = Bound(gk, torch, wk, wk.form)
     if args.probe == "precond":
-        gk.gkb_precond(h, g, w)
+        gk.gkb_precond(B.hs[0], B.g[0], B.w[0])
     else:
-        gk.gkb_solve(h, g, r, args.tol, args.delay, w, p)
+        B.step(args)
     torch.cuda.synchronize()
-    gk.gkb_destroy(h)
+    B.destroy()
     print("probe done")
     return 0
-
-
-# per-launch DRAM traffic (bytes) of the dominant kernel from ncu captures,
-# keyed by (form, kernel class); summarised under profiles/
-TRAFFIC = {}
 
 
 def main():
@@ -415,8 +531,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--form", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", choices=["stokes2d", "stokes3d", "poiseuille", "batched2d"], default="stokes2d")
+    ap.add_argument("--form", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--gammas", type=str, default="10,1000")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--tol-inner", type=float, default=1e-10)
@@ -424,8 +542,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--probe", choices=["precond", "solve"], default=None,
-                    help="profiling target: set up one handle (first gamma) and run one V-cycle or one solve")
+                    help="profiling target: set up one handle and run one V-cycle or one solve")
     args = ap.parse_args()
+    args.form_default = args.form is None
+    if args.form is None:
+        args.form = "fp64"
     args.gammas = [float(x) for x in args.gammas.split(",")]
     args.warmup = max(args.warmup, 0)
     ws, rank, local = dist_setup()

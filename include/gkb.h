@@ -88,7 +88,8 @@ extern "C" {
 #define GKB_KC_BLAS      6    /* dots and vector updates of CG                  */
 #define GKB_KC_GKB       7    /* GKB recurrence kernels (Algorithm 1 steps)     */
 #define GKB_KC_LAYOUT    8    /* packing, precision conversion, gradients       */
-#define GKB_KC_COUNT     9
+#define GKB_KC_UNET      9    /* U-Net convolutions, pooling, loss, optimiser   */
+#define GKB_KC_COUNT     10
 
 typedef struct gkb_ctx* gkb_handle;
 
@@ -240,6 +241,44 @@ int gkb_precond(gkb_handle h, const double* r, double* z);
 #define GKB_NOALLOC_MAX_ELEMS 1048576
 int gkb_apply_noalloc(const gkb_grid* grid, double mu0, double gamma, double n_scale, int op,
                       const double* x, double* y, void* stream);
+
+/* ---- learned preconditioner: a convolutional U-Net ---------------------
+ * (The paper has no learned component; the network is the learned part of
+ * the variable-viscosity workload.) Architecture: 3 levels with 16 / 32 / 32
+ * channels and 3x3 convolutions with zero padding; encoder a1, a2 (full
+ * resolution), 2x2 mean pooling, b1, b2, pooling, c1, c2; decoder: bilinear
+ * doubling (pixel-centre aligned, edges clamped) of c2 concatenated with the
+ * b2 output -> d1; doubling of d1 concatenated with the a2 output -> e1; a
+ * linear 3x3 output convolution.
+ * ReLU after every convolution but the last. Images are NHWC float arrays
+ * in device memory with sides divisible by 4. Parameters: one flat float
+ * vector, per layer the weights w[ky][kx][cin][cout] then the bias, layers
+ * in the order a1 a2 b1 b2 c1 c2 d1 e1 out. Training uses FP32 kernels; the
+ * inference path can run the convolutions on BF16 tensor cores with FP32
+ * accumulation. */
+typedef struct gkb_unet_ctx* gkb_unet;
+
+/* Create a network with c_in inputs (1..16), c1 = 16 and c2 = 32 channels and
+ * c_out outputs (1..3); He-normal weights from `seed`, zero biases. Returns
+ * GKB_ERR_INVALID_ARG for other shapes. The handle is bound to the current
+ * device and to `stream` (NULL: the legacy default stream). */
+int gkb_unet_create(gkb_unet* out, int c_in, int c1, int c2, int c_out, unsigned long long seed, void* stream);
+int gkb_unet_num_params(gkb_unet u, int64_t* n);
+/* Copy the flat parameter vector out of / into the network (host or device). */
+int gkb_unet_get_params(gkb_unet u, float* params);
+int gkb_unet_set_params(gkb_unet u, const float* params);
+/* y = N(x), x (n, h, w, c_in) and y (n, h, w, c_out) device arrays;
+ * tensor_cores = 1 runs the convolutions in BF16 with FP32 accumulation. */
+int gkb_unet_forward(gkb_unet u, const float* x, int n, int h, int w, float* y, int tensor_cores);
+/* loss = (1/n) sum over the n samples of ||N(x) - target||^2 (FP32 forward), and its
+ * gradient w.r.t. the parameters (kept for gkb_unet_adam_step; copied to grad
+ * when not NULL, host or device). */
+int gkb_unet_loss_grad(gkb_unet u, const float* x, const float* target, int n, int h, int w, double* loss,
+                       float* grad);
+/* One Adam update with the last gradient (bias-corrected moments). */
+int gkb_unet_adam_step(gkb_unet u, float lr, float beta1, float beta2, float eps);
+const char* gkb_unet_last_error(gkb_unet u);
+int gkb_unet_destroy(gkb_unet u);
 
 /* Message for the last failing call (never NULL). */
 const char* gkb_last_error(gkb_handle h);

@@ -32,7 +32,7 @@ GKB_PREC_MIXED = 1
 GKB_INNER_CG = 0
 GKB_INNER_GMG_PCG = 1
 GKB_OP_W, GKB_OP_A, GKB_OP_AT, GKB_OP_M = 0, 1, 2, 3
-KERNEL_CLASSES = ["apply", "residual", "smooth", "restrict", "prolong", "coarse", "blas", "gkb", "layout"]
+KERNEL_CLASSES = ["apply", "residual", "smooth", "restrict", "prolong", "coarse", "blas", "gkb", "layout", "unet"]
 
 STATUS_NAMES = {
     0: "OK", 1: "INVALID_ARG", 2: "NOT_SPD", 3: "NOT_CONVERGED", 4: "INNER_NOT_CONVERGED",
@@ -44,6 +44,8 @@ EXPORTED = [
     "gkb_default_options", "gkb_create", "gkb_set_problem", "gkb_layout", "gkb_boundary_rhs",
     "gkb_solve", "gkb_stats", "gkb_history", "gkb_apply", "gkb_precond", "gkb_last_error",
     "gkb_destroy", "gkb_apply_noalloc", "gkb_solve_batched",
+    "gkb_unet_create", "gkb_unet_num_params", "gkb_unet_get_params", "gkb_unet_set_params",
+    "gkb_unet_forward", "gkb_unet_loss_grad", "gkb_unet_adam_step", "gkb_unet_last_error", "gkb_unet_destroy",
 ]
 GKB_NOALLOC_MAX_ELEMS = 1048576
 
@@ -64,8 +66,8 @@ class gkb_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("inner_solves", ctypes.c_int),
                 ("inner_iterations", ctypes.c_int64), ("estimate", ctypes.c_double),
                 ("setup_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
-                ("levels", ctypes.c_int), ("kernel_launches", ctypes.c_int64 * 9),
-                ("kernel_units", ctypes.c_int64 * 9), ("kernel_ms", ctypes.c_double * 9)]
+                ("levels", ctypes.c_int), ("kernel_launches", ctypes.c_int64 * 10),
+                ("kernel_units", ctypes.c_int64 * 10), ("kernel_ms", ctypes.c_double * 10)]
 
 
 class GkbError(RuntimeError):
@@ -104,6 +106,15 @@ def load(path=None):
         "gkb_apply_noalloc": (i, [ctypes.POINTER(gkb_grid), d, d, d, i, _P, _P, _P]),
         "gkb_solve_batched": (i, [ctypes.POINTER(_P), i, ctypes.POINTER(_P), ctypes.POINTER(_P), d, i,
                                   ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+        "gkb_unet_create": (i, [ctypes.POINTER(_P), i, i, i, i, ctypes.c_ulonglong, _P]),
+        "gkb_unet_num_params": (i, [_P, ctypes.POINTER(ctypes.c_int64)]),
+        "gkb_unet_get_params": (i, [_P, _P]),
+        "gkb_unet_set_params": (i, [_P, _P]),
+        "gkb_unet_forward": (i, [_P, _P, i, i, i, _P, i]),
+        "gkb_unet_loss_grad": (i, [_P, _P, _P, i, i, i, ctypes.POINTER(d), _P]),
+        "gkb_unet_adam_step": (i, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "gkb_unet_last_error": (ctypes.c_char_p, [_P]),
+        "gkb_unet_destroy": (i, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -113,18 +124,18 @@ def load(path=None):
     return lib
 
 
-def _ptr(a):
-    """Raw pointer of a float64 contiguous tensor / array (None -> NULL)."""
+def _ptr(a, dtype="float64"):
+    """Raw pointer of a contiguous tensor / array of the given dtype (None -> NULL)."""
     if a is None:
         return None
     if hasattr(a, "data_ptr"):  # torch tensor
         import torch
-        if a.dtype != torch.float64 or not a.is_contiguous():
-            raise TypeError("tensors must be contiguous float64")
+        if a.dtype != getattr(torch, dtype) or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous %s" % dtype)
         return a.data_ptr()
     import numpy as np
-    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
-        raise TypeError("arrays must be C-contiguous float64 numpy arrays")
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("arrays must be C-contiguous %s numpy arrays" % dtype)
     return a.ctypes.data
 
 
@@ -230,6 +241,59 @@ def gkb_apply_noalloc(grid, mu0, gamma, n_scale, op, x, y, stream=None):
     """y = op(x) without a handle or any device allocation (device arrays);
     returns the status code."""
     return load().gkb_apply_noalloc(ctypes.byref(grid), mu0, gamma, n_scale, op, _ptr(x), _ptr(y), stream)
+
+
+def _ucheck(u, rc):
+    if rc != GKB_OK:
+        msg = load().gkb_unet_last_error(u)
+        raise GkbError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def gkb_unet_create(c_in=3, c1=16, c2=32, c_out=2, seed=0, stream=None):
+    u = _P()
+    rc = load().gkb_unet_create(ctypes.byref(u), c_in, c1, c2, c_out, seed, stream)
+    if rc != GKB_OK:
+        raise GkbError(rc, "gkb_unet_create")
+    return u
+
+
+def gkb_unet_num_params(u):
+    n = ctypes.c_int64()
+    _ucheck(u, load().gkb_unet_num_params(u, ctypes.byref(n)))
+    return n.value
+
+
+def gkb_unet_get_params(u, out):
+    return _ucheck(u, load().gkb_unet_get_params(u, _ptr(out, "float32")))
+
+
+def gkb_unet_set_params(u, params):
+    return _ucheck(u, load().gkb_unet_set_params(u, _ptr(params, "float32")))
+
+
+def gkb_unet_forward(u, x, n, h, w, y, tensor_cores=0):
+    return _ucheck(u, load().gkb_unet_forward(u, _ptr(x, "float32"), n, h, w, _ptr(y, "float32"), tensor_cores))
+
+
+def gkb_unet_loss_grad(u, x, target, n, h, w, grad=None):
+    loss = ctypes.c_double()
+    _ucheck(u, load().gkb_unet_loss_grad(u, _ptr(x, "float32"), _ptr(target, "float32"), n, h, w,
+                                         ctypes.byref(loss), _ptr(grad, "float32")))
+    return loss.value
+
+
+def gkb_unet_adam_step(u, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    return _ucheck(u, load().gkb_unet_adam_step(u, lr, beta1, beta2, eps))
+
+
+def gkb_unet_last_error(u):
+    msg = load().gkb_unet_last_error(u)
+    return msg.decode() if msg else ""
+
+
+def gkb_unet_destroy(u):
+    return load().gkb_unet_destroy(u)
 
 
 def gkb_last_error(h):

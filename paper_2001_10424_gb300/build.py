@@ -15,7 +15,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgkb.so")
 
-SOURCES = ["kernels_f64.cu", "kernels_f32.cu", "solver.cu", "api.cu", "noalloc.cu"]
+# (source, defines): the stencil / smoother instantiations are split by
+# GKB_PART into units that compile in parallel
+SOURCES = ([("kernels_f64.cu", ["-DGKB_PART=%d" % k]) for k in range(1, 8)]
+           + [("kernels_f32.cu", ["-DGKB_PART=%d" % k]) for k in range(1, 8)]
+           + [(f, []) for f in ("solver.cu", "api.cu", "noalloc.cu", "unet.cu")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]
@@ -42,9 +46,11 @@ def build(force=False, verbose=False):
     nvcc = nvcc_path()
     inc = ["-I", os.path.join(os.path.dirname(HERE), "include")]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + FLAGS + inc + ["-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, defs = unit
+        tag = "".join(d.split("=")[-1] for d in defs)
+        obj = os.path.join(BUILD, src.replace(".cu", (("_p" + tag) if tag else "") + ".o"))
+        cmd = [nvcc] + ARCH + FLAGS + defs + inc + ["-c", os.path.join(CSRC, src), "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), res.stderr))
@@ -52,7 +58,8 @@ def build(force=False, verbose=False):
             sys.stderr.write(res.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    workers = max(1, min(len(SOURCES), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs

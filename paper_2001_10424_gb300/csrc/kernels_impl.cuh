@@ -271,6 +271,26 @@ __device__ __forceinline__ void patch_active(const Lvl& L, const int e[3], bool 
   act[3] = face_active<b>(L, e[0], e[1], e[2]);
 }
 
+// local solve of the patch of edge e with the matrix assembled on the fly
+template <typename T, bool VarMu, int E>
+__device__ __forceinline__ T patch_solve_inl(const Lvl& L, const T* r, const int e[3], long long ce, int slot) {
+  bool act[4];
+  T rp[4];
+  T Mp[4][4];
+  patch_matrix<T, VarMu, E>(L, e, Mp, act);
+  patch_rhs<T, E>(L, r, ce, act, rp);
+  chol4_solve<T>(Mp, rp);
+  return rp[slot];
+}
+
+// the same, out of line: used for the twelve patches of a 3D face, whose
+// inlined copies multiply the compile time of the kernels twentyfold
+template <typename T, bool VarMu, int E>
+__device__ __noinline__ T patch_solve(const Lvl& L, const T* r, int e0, int e1, int e2, long long ce, int slot) {
+  const int e[3] = {e0, e1, e2};
+  return patch_solve_inl<T, VarMu, E>(L, r, e, ce, slot);
+}
+
 // contribution of the patch of edge e (padded index ce) to slot `slot` of z = C r
 template <typename T, bool VarMu, int E>
 __device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e[3], long long ce, int slot,
@@ -278,11 +298,8 @@ __device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e
   bool act[4];
   T rp[4];
   if (VarMu || table == nullptr) {
-    T Mp[4][4];
-    patch_matrix<T, VarMu, E>(L, e, Mp, act);
-    patch_rhs<T, E>(L, r, ce, act, rp);
-    chol4_solve<T>(Mp, rp);
-    return rp[slot];
+    if (E == 2 && L.dim == 2) return patch_solve_inl<T, VarMu, E>(L, r, e, ce, slot);
+    return patch_solve<T, VarMu, E>(L, r, e[0], e[1], e[2], ce, slot);
   }
   patch_active<E>(L, e, act);
   patch_rhs<T, E>(L, r, ce, act, rp);

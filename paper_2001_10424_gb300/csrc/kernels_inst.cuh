@@ -1,12 +1,24 @@
 // kernels_inst.cuh - launch wrappers, instantiated for KT (see kernels_f64.cu).
+//
+// GKB_PART selects one group of wrappers so that the build can compile the
+// heavy stencil and smoother instantiations as separate, parallel units:
+// 1 operator products, 2 residuals, 3 Chebyshev steps, 4 patch smoother,
+// 5 transfers, coarse solve and BLAS-1, 6 / 7 the variable-viscosity
+// Chebyshev / patch smoother; 0 (default) all of them.
 #pragma once
 #include "kernels_impl.cuh"
 #include "prof.h"
+
+#ifndef GKB_PART
+#define GKB_PART 0
+#endif
+#define GKB_IN_PART(k) (GKB_PART == 0 || GKB_PART == (k))
 
 namespace gkb {
 
 #define GKB_VARMU(L) ((sizeof(KT) == 8) ? (L.mu64 != nullptr) : (L.mu32 != nullptr))
 
+#if GKB_IN_PART(1)
 template <>
 long long Ops<KT>::face_blocks(const Lvl& L) {
   dim3 g = face_grid(L);
@@ -30,7 +42,9 @@ void Ops<KT>::apply_dot(const Lvl& L, int mode, const KT* x, KT* y, const RedBuf
   if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
   else k_mac_tile<KT, false, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
 }
+#endif
 
+#if GKB_IN_PART(2)
 template <>
 void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s, const int* pred) {
   ProfScope ps_(GKB_KC_RESIDUAL, s, lvl_unknowns(L));
@@ -38,19 +52,39 @@ void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream
   if (GKB_VARMU(L)) k_mac_tile<KT, true, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
   else k_mac_tile<KT, false, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
 }
+#endif
 
+// variable-viscosity smoother launches, compiled in their own units (6, 7)
+void launch_cheb_varmu(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, cudaStream_t s);
+void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, cudaStream_t s);
+
+#if GKB_IN_PART(3)
 template <>
 void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* table,
                    cudaStream_t s) {
   ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) k_cheb<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, nullptr);
+  if (GKB_VARMU(L)) launch_cheb_varmu(L, r, x, d, ca, cb, x_zero, s);
   else k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
 }
+#endif
 
+#if GKB_IN_PART(6)
+void launch_cheb_varmu(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, cudaStream_t s) {
+  k_cheb<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, nullptr);
+}
+#endif
+
+#if GKB_IN_PART(7)
+void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, cudaStream_t s) {
+  k_patch<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, nullptr);
+}
+#endif
+
+#if GKB_IN_PART(4)
 template <>
 void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStream_t s) {
   ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) k_patch<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, nullptr);
+  if (GKB_VARMU(L)) launch_patch_varmu(L, r, z, s);
   else k_patch<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, table);
 }
 
@@ -59,7 +93,9 @@ void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
   ProfScope ps_(GKB_KC_LAYOUT, s, 0);
   k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
 }
+#endif
 
+#if GKB_IN_PART(5)
 template <>
 void Ops<KT>::grad(const Lvl& L, const KT* p, KT* y, KT scale, cudaStream_t s) {
   ProfScope ps_(GKB_KC_LAYOUT, s, lvl_unknowns(L));
@@ -123,6 +159,8 @@ void Ops<KT>::axpby(long long len, KT a, const KT* x, KT b, KT* y, cudaStream_t 
   ProfScope ps_(GKB_KC_BLAS, s, len);
   k_axpby<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, x, b, y);
 }
+#endif
 
 #undef GKB_VARMU
+#undef GKB_IN_PART
 }  // namespace gkb

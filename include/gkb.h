@@ -72,6 +72,14 @@ extern "C" {
 
 #define GKB_INNER_CG      0   /* unpreconditioned CG                         */
 #define GKB_INNER_GMG_PCG 1   /* CG + one GMG V-cycle (all-Dirichlet grids)  */
+#define GKB_INNER_FCG_UNET 2  /* flexible CG (FCG(1)) + a V-cycle whose coarse
+                                 correction at the level of unet_side cells is
+                                 a U-Net (gkb_set_unet; 2D all-Dirichlet);
+                                 without a network: the plain V-cycle         */
+#define GKB_INNER_FCG_UNET_MG 3  /* flexible CG + a V-cycle that takes the
+                                 network's correction at the level of
+                                 unet_side cells as the starting guess of the
+                                 ordinary cycle from that level down           */
 
 #define GKB_OP_W   0          /* y = W x                 (m -> m) */
 #define GKB_OP_A   1          /* y = A x (gradient)      (n -> m) */
@@ -126,6 +134,15 @@ typedef struct {
                              values bit for bit as the general paths):
                              0: on in FP32, off in FP64 (measured fastest);
                              1: off everywhere; 2: on everywhere               */
+  int unet_side;          /* GKB_INNER_FCG_UNET: longer side (cells) of the
+                             multigrid level where the network replaces the
+                             rest of the V-cycle; 0: the finest level (the
+                             network alone)                                   */
+  double fcg_rho;         /* GKB_INNER_FCG_UNET: an inner solve whose residual
+                             after k >= 5 iterations exceeds fcg_rho^k ||f||
+                             (or whose preconditioned vector is not finite)
+                             continues as plain GMG-PCG from its iterate;
+                             0 disables the switch                            */
   void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
 } gkb_options;
 
@@ -138,6 +155,7 @@ typedef struct {
   double setup_seconds;       /* gkb_set_problem wall time                   */
   double solve_seconds;       /* last gkb_solve wall time                    */
   int levels;                 /* multigrid levels (0 without GMG)            */
+  int inner_fallbacks;        /* flexible inner solves that switched to GMG-PCG */
   int64_t kernel_launches[GKB_KC_COUNT];  /* launches per class, last solve  */
   int64_t kernel_units[GKB_KC_COUNT];     /* work per class: velocity unknowns
                                              of the launch's level summed over
@@ -277,8 +295,39 @@ int gkb_unet_loss_grad(gkb_unet u, const float* x, const float* target, int n, i
                        float* grad);
 /* One Adam update with the last gradient (bias-corrected moments). */
 int gkb_unet_adam_step(gkb_unet u, float lr, float beta1, float beta2, float eps);
+/* Train: `steps` Adam steps (beta1 0.9, beta2 0.999, eps 1e-8, rate lr) on
+ * minibatches of `batch` pairs drawn without replacement from the count pairs
+ * (x_img (count, h, w, c_in), t_img (count, h, w, c_out), device arrays),
+ * reshuffled by a generator seeded with `seed` on every pass; the loss of
+ * each step goes to losses[step] when losses (host) is not NULL. The targets
+ * are multiplied by the network's target scale. */
+int gkb_unet_train(gkb_unet u, const float* x_img, const float* t_img, int64_t count, int h, int w, int batch,
+                   int steps, float lr, unsigned long long seed, double* losses);
+/* The network is trained on s * e^ and used as e^ = N(r^) / s (default 1). */
+int gkb_unet_set_target_scale(gkb_unet u, float s);
+int gkb_unet_get_target_scale(gkb_unet u, float* s);
 const char* gkb_unet_last_error(gkb_unet u);
 int gkb_unet_destroy(gkb_unet u);
+
+/* Attach the network to a handle (NULL detaches): with GKB_INNER_FCG_UNET the
+ * V-cycle descends to the level with unet_side cells per side and applies
+ * z = (||b|| / sqrt(nx ny)) / s * N(b^, log mu) there, with b^ = b sqrt(nx ny) / ||b||
+ * on the west u / south v face of every cell (z = 0 for b = 0). The network must
+ * outlive its use by the handle; its weights are read at each solve (a BF16
+ * copy is refreshed when they changed). Rebuilds the handle's solve graph. */
+int gkb_set_unet(gkb_handle h, gkb_unet u);
+
+/* Training pairs from the handle's problem (2D, sides divisible by 4, FP64
+ * with GKB_INNER_GMG_PCG): GMG-PCG on M x = f (f: compact velocity vector,
+ * host or device) from x = 0 to tol_inner; for every iteration k before
+ * convergence, x_img[k] (ny, nx, 3) = (r_k^ u, r_k^ v, log mu) and t_img[k]
+ * (ny, nx, 2) = e_k^ with r_k^ = r_k sqrt(nx ny) / ||r_k||, e_k^ = (x* - x_k)
+ * sqrt(nx ny) / ||r_k||, on the west u / south v face of each cell (wall faces
+ * 0); only the leading iterations with ||r_k|| >= 1e4 ||r_final|| (the error
+ * of x* - x_k is about their ratio); at most max_pairs, the count in *n_pairs
+ * (0 unless the solve converged); images past the count are zero.
+ * The images are device arrays. */
+int gkb_harvest_pairs(gkb_handle h, const double* f, int max_pairs, float* x_img, float* t_img, int* n_pairs);
 
 /* Message for the last failing call (never NULL). */
 const char* gkb_last_error(gkb_handle h);

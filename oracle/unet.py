@@ -238,12 +238,14 @@ def image_to_mac(grid, img):
     return vel
 
 
-def apply_preconditioner(params, shapes, grid, r, logmu, quant=None):
-    """z = ||r|| N(r / ||r||, log mu) on the faces: the scale-equivariant use of
-    the network as an approximate inverse of M (z = 0 for r = 0)."""
+def apply_preconditioner(params, shapes, grid, r, logmu, target_scale=1.0, quant=None):
+    """The scale-equivariant use of the network as an approximate inverse of
+    M: with c = ||r|| / sqrt(nx ny) (the RMS of r over the cells),
+    z = c / target_scale * N(r / c, log mu) on the faces (z = 0 for r = 0)."""
     nr = float(np.linalg.norm(r))
     if nr == 0.0:
         return np.zeros_like(r)
-    img = mac_to_image(grid, r / nr, logmu)[None]
+    c = nr / np.sqrt(grid.n[0] * grid.n[1])
+    img = mac_to_image(grid, r / c, logmu)[None]
     y = forward(params, img, shapes, quant=quant)[0]
-    return nr * image_to_mac(grid, y)
+    return (c / target_scale) * image_to_mac(grid, y)

@@ -31,6 +31,8 @@ GKB_PREC_FP64 = 0
 GKB_PREC_MIXED = 1
 GKB_INNER_CG = 0
 GKB_INNER_GMG_PCG = 1
+GKB_INNER_FCG_UNET = 2
+GKB_INNER_FCG_UNET_MG = 3
 GKB_OP_W, GKB_OP_A, GKB_OP_AT, GKB_OP_M = 0, 1, 2, 3
 KERNEL_CLASSES = ["apply", "residual", "smooth", "restrict", "prolong", "coarse", "blas", "gkb", "layout", "unet"]
 
@@ -46,6 +48,7 @@ EXPORTED = [
     "gkb_destroy", "gkb_apply_noalloc", "gkb_solve_batched",
     "gkb_unet_create", "gkb_unet_num_params", "gkb_unet_get_params", "gkb_unet_set_params",
     "gkb_unet_forward", "gkb_unet_loss_grad", "gkb_unet_adam_step", "gkb_unet_last_error", "gkb_unet_destroy",
+    "gkb_unet_train", "gkb_unet_set_target_scale", "gkb_unet_get_target_scale", "gkb_set_unet", "gkb_harvest_pairs",
 ]
 GKB_NOALLOC_MAX_ELEMS = 1048576
 
@@ -59,14 +62,15 @@ class gkb_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("inner", ctypes.c_int), ("tol_inner", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
-                ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("unet_side", ctypes.c_int),
+                ("fcg_rho", ctypes.c_double), ("stream", ctypes.c_void_p)]
 
 
 class gkb_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("inner_solves", ctypes.c_int),
                 ("inner_iterations", ctypes.c_int64), ("estimate", ctypes.c_double),
                 ("setup_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
-                ("levels", ctypes.c_int), ("kernel_launches", ctypes.c_int64 * 10),
+                ("levels", ctypes.c_int), ("inner_fallbacks", ctypes.c_int), ("kernel_launches", ctypes.c_int64 * 10),
                 ("kernel_units", ctypes.c_int64 * 10), ("kernel_ms", ctypes.c_double * 10)]
 
 
@@ -115,6 +119,11 @@ def load(path=None):
         "gkb_unet_adam_step": (i, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "gkb_unet_last_error": (ctypes.c_char_p, [_P]),
         "gkb_unet_destroy": (i, [_P]),
+        "gkb_unet_train": (i, [_P, _P, _P, ctypes.c_int64, i, i, i, i, ctypes.c_float, ctypes.c_ulonglong, _P]),
+        "gkb_unet_set_target_scale": (i, [_P, ctypes.c_float]),
+        "gkb_unet_get_target_scale": (i, [_P, ctypes.POINTER(ctypes.c_float)]),
+        "gkb_set_unet": (i, [_P, _P]),
+        "gkb_harvest_pairs": (i, [_P, _P, i, _P, _P, ctypes.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -285,6 +294,37 @@ def gkb_unet_loss_grad(u, x, target, n, h, w, grad=None):
 
 def gkb_unet_adam_step(u, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return _ucheck(u, load().gkb_unet_adam_step(u, lr, beta1, beta2, eps))
+
+
+def gkb_unet_train(u, x_img, t_img, count, h, w, batch, steps, lr, seed=0, losses=None):
+    """Adam training on device pairs; returns the per-step losses (numpy)."""
+    import numpy as np
+    out = np.zeros(max(steps, 1), dtype=np.float64) if losses is None else losses
+    _ucheck(u, load().gkb_unet_train(u, _ptr(x_img, "float32"), _ptr(t_img, "float32"), count, h, w, batch, steps,
+                                     lr, seed, _ptr(out)))
+    return out[:steps]
+
+
+def gkb_unet_set_target_scale(u, s):
+    return _ucheck(u, load().gkb_unet_set_target_scale(u, s))
+
+
+def gkb_unet_get_target_scale(u):
+    v = ctypes.c_float()
+    _ucheck(u, load().gkb_unet_get_target_scale(u, ctypes.byref(v)))
+    return v.value
+
+
+def gkb_set_unet(h, u):
+    return _check(h, load().gkb_set_unet(h, u))
+
+
+def gkb_harvest_pairs(h, f, max_pairs, x_img, t_img):
+    """Training pairs from GMG-PCG on M x = f; returns how many were written."""
+    n = ctypes.c_int()
+    _check(h, load().gkb_harvest_pairs(h, _ptr(f), max_pairs, _ptr(x_img, "float32"), _ptr(t_img, "float32"),
+                                       ctypes.byref(n)))
+    return n.value
 
 
 def gkb_unet_last_error(u):

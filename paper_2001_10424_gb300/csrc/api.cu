@@ -6,6 +6,7 @@
 #include <new>
 
 #include "solver.cuh"
+#include "unet.cuh"
 
 struct gkb_ctx {
   gkb::Solver s;
@@ -64,6 +65,8 @@ int gkb_default_options(gkb_options* opt) {
   opt->use_graph = 1;
   opt->profile = 0;
   opt->kernel_variant = 0;
+  opt->unet_side = 0;
+  opt->fcg_rho = 0.8;
   opt->stream = nullptr;
   return GKB_OK;
 }
@@ -72,7 +75,8 @@ int gkb_create(gkb_handle* out, const gkb_options* opt) {
   if (!out || !opt) return GKB_ERR_INVALID_ARG;
   *out = nullptr;
   if (opt->precision != GKB_PREC_FP64 && opt->precision != GKB_PREC_MIXED) return GKB_ERR_INVALID_ARG;
-  if (opt->inner != GKB_INNER_CG && opt->inner != GKB_INNER_GMG_PCG) return GKB_ERR_INVALID_ARG;
+  if (opt->inner < GKB_INNER_CG || opt->inner > GKB_INNER_FCG_UNET_MG) return GKB_ERR_INVALID_ARG;
+  if (opt->unet_side < 0 || !(opt->fcg_rho >= 0 && opt->fcg_rho < 1)) return GKB_ERR_INVALID_ARG;
   if (!(opt->tol_inner > 0) || opt->maxit < 0 || opt->maxit > 100000000 || opt->maxit_inner < 1 ||
       opt->smoother_degree < 1 || opt->smoother_degree > 16 || opt->coarse_max < 4 ||
       !(opt->mixed_rtol > 0 && opt->mixed_rtol < 1) || opt->kernel_variant < 0 || opt->kernel_variant > 2)
@@ -97,6 +101,18 @@ int gkb_set_problem(gkb_handle h, const gkb_grid* grid, const double* viscosity,
     h->s.set_problem(grid, viscosity, mu0, gamma, n_scale);
     return GKB_OK;
   });
+}
+
+int gkb_set_unet(gkb_handle h, gkb_unet u) {
+  return guarded(h, [&] {
+    if (u && u->device != h->device) throw gkb::Error{GKB_ERR_INVALID_ARG, "the network lives on another device"};
+    h->s.set_net(u ? &u->u : nullptr);
+    return GKB_OK;
+  });
+}
+
+int gkb_harvest_pairs(gkb_handle h, const double* f, int max_pairs, float* x_img, float* t_img, int* n_pairs) {
+  return guarded(h, [&] { return h->s.harvest(f, max_pairs, x_img, t_img, n_pairs); });
 }
 
 int gkb_layout(gkb_handle h, int64_t* m, int64_t* n) {

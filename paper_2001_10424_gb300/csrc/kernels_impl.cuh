@@ -872,6 +872,21 @@ __global__ void __launch_bounds__(RB) k_dot(long long len, const T* __restrict__
   grid_reduce<1>(v, red, fin, st);
 }
 
+// sums a.b and b.c in one pass
+template <typename T>
+__global__ void __launch_bounds__(RB) k_dot2(long long len, const T* __restrict__ a, const T* __restrict__ b,
+                                              const T* __restrict__ c, RedBuf red, int fin, void* st) {
+  T ab = 0, bc = 0;
+  const long long stride = (long long)gridDim.x * RB;
+  for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride) {
+    const T bt = b[t];
+    ab += a[t] * bt;
+    bc += bt * c[t];
+  }
+  double v[2] = {(double)ab, (double)bc};
+  grid_reduce<2>(v, red, fin, st);
+}
+
 // x += alpha p ; r -= alpha q ; sum r.r      (alpha from CgState)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_cg_update(long long len, T* __restrict__ x, const T* __restrict__ p,

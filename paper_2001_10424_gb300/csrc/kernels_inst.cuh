@@ -142,6 +142,13 @@ void Ops<KT>::dot(long long len, const KT* a, const KT* b, const RedBuf& red, in
 }
 
 template <>
+void Ops<KT>::dot2(long long len, const KT* a, const KT* b, const KT* c, const RedBuf& red, int fin, void* st,
+                   cudaStream_t s) {
+  ProfScope ps_(GKB_KC_BLAS, s, len);
+  k_dot2<KT><<<(unsigned)blas_blocks(len), RB, 0, s>>>(len, a, b, c, red, fin, st);
+}
+
+template <>
 void Ops<KT>::cg_update(long long len, KT* x, const KT* p, KT* r, const KT* q, const CgState* cg,
                         const RedBuf& red, void* st, cudaStream_t s, int fin) {
   ProfScope ps_(GKB_KC_BLAS, s, len);

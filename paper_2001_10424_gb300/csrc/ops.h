@@ -37,6 +37,9 @@ struct Ops {
   // reductions and vector updates on flat padded arrays
   static void dot(long long len, const T* a, const T* b, const RedBuf& red, int fin, void* st, cudaStream_t s,
                   const int* pred = nullptr);
+  // sums a.b and b.c (flexible CG: r.z and z.q)
+  static void dot2(long long len, const T* a, const T* b, const T* c, const RedBuf& red, int fin, void* st,
+                   cudaStream_t s);
   static void cg_update(long long len, T* x, const T* p, T* r, const T* q, const CgState* cg,
                         const RedBuf& red, void* st, cudaStream_t s, int fin = FIN_CG_RR);
   static void cg_dir(long long len, T* p, const T* z, const CgState* cg, int first, cudaStream_t s);

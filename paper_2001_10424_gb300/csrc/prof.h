@@ -23,8 +23,8 @@ struct Profiler {
   size_t used = 0;  // events used (pairs)
   int cur = -1;
   int phase = -1;   // >= 0 while a graph is captured: launches go to cap[phase]
-  long long cap_l[4][GKB_KC_COUNT] = {};
-  long long cap_u[4][GKB_KC_COUNT] = {};
+  long long cap_l[5][GKB_KC_COUNT] = {};
+  long long cap_u[5][GKB_KC_COUNT] = {};
 
   void enable(size_t pairs) {
     timing = true;

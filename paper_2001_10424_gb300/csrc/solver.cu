@@ -13,6 +13,7 @@
 
 #include "solver.cuh"
 #include "prof.h"
+#include "unet.cuh"
 
 namespace gkb {
 
@@ -198,10 +199,11 @@ __global__ void k_cg_cond_init(cudaGraphConditionalHandle h, CgState* c) {
 
 // continue while the CG has not stopped; hard_max bounds the loop even if
 // the iteration counter were never advanced
-__global__ void k_cg_cond(cudaGraphConditionalHandle h, CgState* c, int hard_max) {
-  c->graph_iters += 1;
+__global__ void k_cg_cond(cudaGraphConditionalHandle h, CgState* c, int hard_max, int fb = 0) {
+  int& runs = fb ? c->fb_iters : c->graph_iters;
+  runs += 1;
   unsigned cont = c->done ? 0u : 1u;
-  if (c->graph_iters >= hard_max) {
+  if (runs >= hard_max) {
     cont = 0u;
     if (!c->done) {
       if (c->status == ST_OK) c->status = ST_INNER_NOT_CONVERGED;
@@ -268,6 +270,8 @@ template <typename T>
 void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, const RedBuf& red,
                    double* scratch, cudaStream_t s) {
   degree = deg;
+  this->red = red;
+  detach_net();
   lev.clear();
   lev.reserve(32);
   lev.emplace_back();
@@ -453,26 +457,61 @@ void Gmg<T>::smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s) {
 }
 
 template <typename T>
-void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s) {
+void Gmg<T>::attach_net(Unet* u, int level, bool composite, cudaStream_t s) {
+  if (level < 0 || level >= (int)lev.size()) throw Error{GKB_ERR_INVALID_ARG, "no multigrid level for the network"};
+  const Lvl& L = lev[level].L;
+  if (L.dim != 2 || L.n[0] % 4 || L.n[1] % 4)
+    throw Error{GKB_ERR_INVALID_ARG, "the network level must be 2D with sides divisible by 4"};
+  if (!net_act) net_act = new UnetAct();
+  u->ensure(*net_act, 1, L.n[1], L.n[0]);
+  net_img.alloc((size_t)L.n[0] * L.n[1] * 3);
+  net_nrm.alloc(4);
+  if (u->bf16_stale) u->refresh_bf16(s);
+  net = u;
+  net_level = level;
+  net_composite = composite;
+}
+
+template <typename T>
+void Gmg<T>::detach_net() {
+  net = nullptr;
+  net_level = -1;
+}
+
+template <typename T>
+Gmg<T>::~Gmg() {
+  delete net_act;
+}
+
+template <typename T>
+void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s, bool use_net) {
   const int nl = (int)lev.size();
-  if (nl == 1) {
-    Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, r0, z0, s);
-    return;
-  }
-  for (int l = 0; l < nl - 1; ++l) {
-    const T* b = (l == 0) ? r0 : lev[l].b.p;
-    T* x = (l == 0) ? z0 : lev[l].x.p;
-    smooth(l, b, x, true, s);
-    Ops<T>::residual(lev[l].L, x, b, lev[l].r.p, s);
+  const bool with_net = use_net && net && net_level >= 0;
+  // replace form: the network is the correction of its level and everything
+  // below it; composite form: the network's correction is the starting
+  // guess of the ordinary cycle from its level down
+  const bool replace = with_net && !net_composite;
+  const int lc = replace ? net_level : nl - 1;  // the level of the coarsest correction
+  auto lvl_b = [&](int l) { return (l == 0) ? r0 : (const T*)lev[l].b.p; };
+  auto lvl_x = [&](int l) { return (l == 0) ? z0 : lev[l].x.p; };
+  auto net_at = [&](int l) {
+    unet_correct<T>(*net, *net_act, lev[l].L, lvl_b(l), lvl_x(l), net_img.p, net_nrm.p, red, s);
+  };
+  for (int l = 0; l < lc; ++l) {
+    bool x_zero = true;
+    if (with_net && l == net_level) {  // composite form
+      net_at(l);
+      x_zero = false;
+    }
+    smooth(l, lvl_b(l), lvl_x(l), x_zero, s);
+    Ops<T>::residual(lev[l].L, lvl_x(l), lvl_b(l), lev[l].r.p, s);
     Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, lev[l + 1].x.p, lev[l + 1].t2.p, s);
   }
-  Level& Cl = lev[nl - 1];
-  Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, Cl.b.p, Cl.x.p, s);
-  for (int l = nl - 2; l >= 0; --l) {
-    const T* b = (l == 0) ? r0 : lev[l].b.p;
-    T* x = (l == 0) ? z0 : lev[l].x.p;
-    Ops<T>::prolong(lev[l].L, lev[l + 1].L, lev[l + 1].x.p, x, s);
-    smooth(l, b, x, false, s);
+  if (replace) net_at(lc);
+  else Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, lvl_b(lc), lvl_x(lc), s);
+  for (int l = lc - 1; l >= 0; --l) {
+    Ops<T>::prolong(lev[l].L, lev[l + 1].L, lev[l + 1].x.p, lvl_x(l), s);
+    smooth(l, lvl_b(l), lvl_x(l), false, s);
   }
 }
 
@@ -482,6 +521,21 @@ template struct Gmg<float>;
 // ---------------------------------------------------------------------------
 // conjugate gradients (host-sequenced, device scalars)
 // ---------------------------------------------------------------------------
+
+// host-sequenced forms: after a flexible solve stopped (state synchronised
+// in `host`), prepare the fallback loop the way k_fb_init does; true when it
+// has to run
+static bool fallback_restart(CgState* dev, CgState* host, cudaStream_t s) {
+  if (!host->fallback || host->status != ST_OK) return false;
+  if (host->it >= host->maxit) host->status = ST_INNER_NOT_CONVERGED;
+  else {
+    host->done = 0;
+    host->rz_old = 0.0;
+  }
+  GKB_CUDA(cudaMemcpyAsync(dev, host, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  return host->status == ST_OK;
+}
 
 template <typename T>
 void Cg<T>::init(const Lvl& L_, Gmg<T>* pre_, const RedBuf& red_, CgState* st_dev, CgState* st_host) {
@@ -502,6 +556,7 @@ int Cg<T>::solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* i
   CgState h{};
   h.tol2 = tol * tol;
   h.maxit = maxit;
+  h.rho2 = flex ? rho2 : 0.0;
   GKB_CUDA(cudaMemcpyAsync(st, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
   GKB_CUDA(cudaMemsetAsync(x, 0, len * sizeof(T), s));
   GKB_CUDA(cudaMemcpyAsync(r.p, f, len * sizeof(T), cudaMemcpyDeviceToDevice, s));
@@ -519,8 +574,21 @@ int Cg<T>::solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* i
     GKB_CUDA(cudaStreamSynchronize(s));
     if (host->done) break;
     if (pre) pre->vcycle(r.p, zp, s);
-    Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
+    if (flex) Ops<T>::dot2(len, r.p, zp, q.p, red, FIN_FCG_RZ, st, s);
+    else Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
     Ops<T>::cg_dir(len, p.p, zp, st, 0, s);
+  }
+  if (flex && fallback_restart(st, host, s)) {
+    // plain GMG-PCG from the current iterate (beta of the first step is 0)
+    while (!host->done) {
+      pre->vcycle(r.p, zp, s, false);
+      Ops<T>::dot(len, r.p, zp, red, FIN_CG_RZ, st, s);
+      Ops<T>::cg_dir(len, p.p, zp, st, 0, s);
+      Ops<T>::apply_dot(L, 1, p.p, q.p, red, FIN_CG_PAP, st, s);
+      Ops<T>::cg_update(len, x, p.p, r.p, q.p, st, red, st, s);
+      GKB_CUDA(cudaMemcpyAsync(host, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+      GKB_CUDA(cudaStreamSynchronize(s));
+    }
   }
   if (iters) *iters = host->it;
   return host->status;
@@ -753,15 +821,33 @@ __global__ void __launch_bounds__(CB) k_mixed_accum(long long len, float* __rest
 
 // header of an inner CG solve (written on the device so that graphs can
 // start a solve without a host copy)
-__global__ void k_cg_setup(CgState* c, double tol2, int maxit, double delta2) {
+__global__ void k_cg_setup(CgState* c, double tol2, int maxit, double delta2, double rho2) {
   c->tol2 = tol2;
   c->maxit = maxit;
   c->delta2 = delta2;
+  c->rho2 = rho2;
   c->done = 0;
   c->status = ST_OK;
   c->it = 0;
   c->update = 0;
   c->graph_iters = 0;
+  c->fallback = 0;
+  c->fb_iters = 0;
+}
+
+// start of the fallback loop: run it when the flexible solve handed over
+// (restarting the directions: beta of the first step is 0)
+__global__ void k_fb_init(cudaGraphConditionalHandle h, CgState* c) {
+  bool go = c->fallback && c->status == ST_OK;
+  if (go && c->it >= c->maxit) {
+    c->status = ST_INNER_NOT_CONVERGED;
+    go = false;
+  }
+  if (go) {
+    c->done = 0;
+    c->rz_old = 0.0;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 // record an inner solve in the GKB state: status, iterations, history
@@ -771,6 +857,8 @@ __global__ void k_note_inner(GkbState* S, const CgState* c) {
   S->inner_solves = idx + 1;
   S->inner_its += c->it;
   S->inner_runs += c->graph_iters;
+  S->inner_fb_runs += c->fb_iters;
+  S->inner_fallbacks += c->fallback;
   if (c->status != ST_OK && S->inner_status == ST_OK) S->inner_status = c->status;
 }
 
@@ -861,8 +949,11 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   int nat[6] = {0, 0, 0, 0, 0, 0};
   enclosed = true;
   for (int s = 0; s < 2 * g->dim; ++s) { nat[s] = g->bc[s] == GKB_BC_NATURAL; if (nat[s]) enclosed = false; }
-  if (opt.inner == GKB_INNER_GMG_PCG && !enclosed)
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || learned_inner();
+  if (use_gmg && !enclosed)
     throw Error{GKB_ERR_INVALID_ARG, "the multigrid preconditioner needs Dirichlet velocity on every side"};
+  if (learned_inner() && g->dim != 2)
+    throw Error{GKB_ERR_INVALID_ARG, "the learned inner solver is 2D only"};
   int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
   L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
   L64.mu0 = viscosity ? 1.0 : mu0;
@@ -912,11 +1003,12 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   cg_dev = (CgState*)state_mem.p;
   gkb_dev = (GkbState*)(state_mem.p + ((sizeof(CgState) + 127) / 128) * 128);
   // multigrid + CG
-  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG;
   stats = gkb_stats_t{};
   if (mixed) {
     if (use_gmg) gmg32.build(L32, mu32.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
     cg32.init(L32, use_gmg ? &gmg32 : nullptr, red, cg_dev, cg_host);
+    cg32.flex = learned_inner();
+    cg32.rho2 = opt.fcg_rho * opt.fcg_rho;
     r64.alloc(L64.nvel);
     f32.alloc(L64.nvel);
     x32.alloc(L64.nvel);
@@ -924,6 +1016,8 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   } else {
     if (use_gmg) gmg64.build(L64, mu64.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
     cg64.init(L64, use_gmg ? &gmg64 : nullptr, red, cg_dev, cg_host);
+    cg64.flex = learned_inner();
+    cg64.rho2 = opt.fcg_rho * opt.fcg_rho;
     stats.levels = use_gmg ? (int)gmg64.lev.size() : 0;
   }
   // GKB vectors
@@ -933,11 +1027,49 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   stage_n.alloc(ncell);
   hist.alloc(4 * (size_t)(opt.maxit + 2));
   hist_inner.alloc((size_t)opt.maxit + 4);
+  attach_net_levels();
   GKB_CUDA(cudaStreamSynchronize(stream));
   generation += 1;
   have_problem = true;
   build_solve_graph();
   stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// The network gives the coarse correction of the level whose longer side is
+// opt.unet_side cells (0: the finest level, i.e. the network alone).
+void Solver::attach_net_levels() {
+  gmg64.detach_net();
+  gmg32.detach_net();
+  if (!net || !learned_inner()) return;
+  const bool composite = opt.inner == GKB_INNER_FCG_UNET_MG;
+  const bool mixed = opt.precision == GKB_PREC_MIXED;
+  const int nl = mixed ? (int)gmg32.lev.size() : (int)gmg64.lev.size();
+  int level = -1;
+  for (int l = 0; l < nl; ++l) {
+    const Lvl& L = mixed ? gmg32.lev[l].L : gmg64.lev[l].L;
+    const int side = std::max(L.n[0], L.n[1]);
+    if ((opt.unet_side == 0 && l == 0) || side == opt.unet_side) { level = l; break; }
+  }
+  if (level < 0) throw Error{GKB_ERR_INVALID_ARG, "no multigrid level has unet_side cells per side"};
+  if (mixed) gmg32.attach_net(net, level, composite, stream);
+  else gmg64.attach_net(net, level, composite, stream);
+}
+
+void Solver::set_net(Unet* u) {
+  net = u;
+  if (!have_problem) return;
+  sgraph.destroy();
+  forget_batches(this);
+  attach_net_levels();
+  GKB_CUDA(cudaStreamSynchronize(stream));
+  generation += 1;
+  build_solve_graph();
+}
+
+// weights trained since the last solve: refresh their BF16 copy (the
+// captured graphs read it at a fixed address)
+void Solver::refresh_net() {
+  if (net && net->bf16_stale && learned_inner()) net->refresh_bf16(stream);
 }
 
 int Solver::inner_solve(const double* fpad, double* xpad) {
@@ -961,6 +1093,7 @@ int Solver::mixed_solve(const double* f, double* x64, int* iters) {
   h.tol2 = opt.tol_inner * opt.tol_inner;
   h.maxit = opt.maxit_inner;
   h.delta2 = opt.mixed_rtol * opt.mixed_rtol;
+  h.rho2 = c.flex ? c.rho2 : 0.0;
   GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
   GKB_CUDA(cudaMemsetAsync(x64, 0, len * sizeof(double), s));
   GKB_CUDA(cudaMemsetAsync(x32.p, 0, len * sizeof(float), s));
@@ -989,8 +1122,32 @@ int Solver::mixed_solve(const double* f, double* x64, int* iters) {
       if (cg_host->done) break;
     }
     if (c.pre) c.pre->vcycle(c.r.p, zp, s);
-    Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, s);
+    if (c.flex) Ops<float>::dot2(len, c.r.p, zp, c.q.p, red, FIN_FCG_RZ, cg_dev, s);
+    else Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, s);
     Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, s);
+  }
+  auto reliable_update = [&]() {
+    // x64 += x32, x32 = 0, r64 = f - M x64 (FP64), r32 = r64
+    { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_mixed_accum<<<lin_blocks(len), CB, 0, s>>>(len, x32.p, x64, nullptr); }
+    Ops<double>::residual(L64, x64, f, r64.p, s);
+    { ProfScope ps_(GKB_KC_LAYOUT, s, len); k_cvt_f32<<<lin_blocks(len), CB, 0, s>>>(len, r64.p, c.r.p, nullptr); }
+    Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, s);
+    GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    GKB_CUDA(cudaStreamSynchronize(s));
+  };
+  if (c.flex && fallback_restart(cg_dev, cg_host, s)) {
+    // plain GMG-PCG from the current iterate (beta of the first step is 0)
+    while (!cg_host->done) {
+      c.pre->vcycle(c.r.p, zp, s, false);
+      Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, s);
+      Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, s);
+      Ops<float>::apply_dot(L32, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, s);
+      Ops<float>::cg_update(len, x32.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, s, FIN_MX_RR);
+      GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+      GKB_CUDA(cudaStreamSynchronize(s));
+      if (cg_host->done) break;
+      if (cg_host->update) reliable_update();
+    }
   }
   // a solve that stopped on the FP32 side (NaN, not SPD) still returns the
   // FP64 accumulation of its progress
@@ -1023,7 +1180,7 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
     capture_loop(
         s, sb, 3,
         [&](cudaStream_t st, cudaGraphConditionalHandle h) {
-          k_cg_setup<<<1, 1, 0, st>>>(cg_dev, tol2, maxit, delta2);
+          k_cg_setup<<<1, 1, 0, st>>>(cg_dev, tol2, maxit, delta2, c.rho2);
           GKB_CUDA(cudaMemsetAsync(x.p, 0, len * sizeof(double), st));
           GKB_CUDA(cudaMemsetAsync(x32.p, 0, len * sizeof(float), st));
           Ops<double>::dot(len, f.p, f.p, red, FIN_CG_INIT, cg_dev, st);
@@ -1042,20 +1199,43 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
           { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_cvt_f32<<<lin_blocks(len), CB, 0, st>>>(len, r64.p, c.r.p, upd); }
           Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, st, upd);
           if (c.pre) c.pre->vcycle(c.r.p, zp, st);
-          Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
+          if (c.flex) Ops<float>::dot2(len, c.r.p, zp, c.q.p, red, FIN_FCG_RZ, cg_dev, st);
+          else Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
           Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, st);
           k_cg_cond<<<1, 1, 0, st>>>(h, cg_dev, maxit + 2);
         },
         [&](cudaStream_t st) {
           { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_mixed_accum<<<lin_blocks(len), CB, 0, st>>>(len, x32.p, x.p, nullptr); }
         });
+    if (c.flex && c.pre && c.pre->net) {
+      // fallback: plain GMG-PCG from the current iterate when the flexible
+      // solve handed over (zero trips otherwise); the step order is rotated
+      // so that the restart needs no prefix of its own
+      capture_loop(
+          s, sb, 4, [&](cudaStream_t st, cudaGraphConditionalHandle h) { k_fb_init<<<1, 1, 0, st>>>(h, cg_dev); },
+          [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+            c.pre->vcycle(c.r.p, zp, st, false);
+            Ops<float>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
+            Ops<float>::cg_dir(len, c.p.p, zp, cg_dev, 0, st);
+            Ops<float>::apply_dot(L32, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, st);
+            Ops<float>::cg_update(len, x32.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, st, FIN_MX_RR);
+            { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_mixed_accum<<<lin_blocks(len), CB, 0, st>>>(len, x32.p, x.p, upd); }
+            Ops<double>::residual(L64, x.p, f.p, r64.p, st, upd);
+            { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_cvt_f32<<<lin_blocks(len), CB, 0, st>>>(len, r64.p, c.r.p, upd); }
+            Ops<double>::dot(len, r64.p, r64.p, red, FIN_MX_RR64, cg_dev, st, upd);
+            k_cg_cond<<<1, 1, 0, st>>>(h, cg_dev, maxit + 4, 1);
+          },
+          [&](cudaStream_t st) {
+            { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_mixed_accum<<<lin_blocks(len), CB, 0, st>>>(len, x32.p, x.p, nullptr); }
+          });
+    }
   } else {
     Cg<double>& c = cg64;
     double* zp = c.pre ? c.z.p : c.r.p;
     capture_loop(
         s, sb, 3,
         [&](cudaStream_t st, cudaGraphConditionalHandle h) {
-          k_cg_setup<<<1, 1, 0, st>>>(cg_dev, tol2, maxit, 0.0);
+          k_cg_setup<<<1, 1, 0, st>>>(cg_dev, tol2, maxit, 0.0, c.rho2);
           GKB_CUDA(cudaMemsetAsync(x.p, 0, len * sizeof(double), st));
           GKB_CUDA(cudaMemcpyAsync(c.r.p, f.p, len * sizeof(double), cudaMemcpyDeviceToDevice, st));
           Ops<double>::dot(len, f.p, f.p, red, FIN_CG_INIT, cg_dev, st);
@@ -1068,11 +1248,25 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
           Ops<double>::apply_dot(L64, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, st);
           Ops<double>::cg_update(len, x.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, st);
           if (c.pre) c.pre->vcycle(c.r.p, zp, st);
-          Ops<double>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
+          if (c.flex) Ops<double>::dot2(len, c.r.p, zp, c.q.p, red, FIN_FCG_RZ, cg_dev, st);
+          else Ops<double>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
           Ops<double>::cg_dir(len, c.p.p, zp, cg_dev, 0, st);
           k_cg_cond<<<1, 1, 0, st>>>(h, cg_dev, maxit + 2);
         },
         [&](cudaStream_t) {});
+    if (c.flex && c.pre && c.pre->net) {
+      capture_loop(
+          s, sb, 4, [&](cudaStream_t st, cudaGraphConditionalHandle h) { k_fb_init<<<1, 1, 0, st>>>(h, cg_dev); },
+          [&](cudaStream_t st, cudaGraphConditionalHandle h) {
+            c.pre->vcycle(c.r.p, zp, st, false);
+            Ops<double>::dot(len, c.r.p, zp, red, FIN_CG_RZ, cg_dev, st);
+            Ops<double>::cg_dir(len, c.p.p, zp, cg_dev, 0, st);
+            Ops<double>::apply_dot(L64, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, st);
+            Ops<double>::cg_update(len, x.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, st);
+            k_cg_cond<<<1, 1, 0, st>>>(h, cg_dev, maxit + 4, 1);
+          },
+          [&](cudaStream_t) {});
+    }
   }
   { ProfScope ps_(GKB_KC_GKB, s); k_note_inner<<<1, 1, 0, s>>>(gkb_dev, cg_dev); }
   if (P) P->phase = saved;
@@ -1131,7 +1325,7 @@ void Solver::build_solve_graph() {
   ensure_capture_streams();
   Profiler* P = g_prof;
   if (P) {
-    for (int ph = 0; ph < 4; ++ph)
+    for (int ph = 0; ph < 5; ++ph)
       for (int k = 0; k < GKB_KC_COUNT; ++k) { P->cap_l[ph][k] = 0; P->cap_u[ph][k] = 0; }
     P->phase = 0;
   }
@@ -1152,7 +1346,7 @@ void Solver::build_solve_graph() {
   cudaGraphDestroy(g);
   if (P) {
     P->phase = -1;
-    for (int ph = 0; ph < 4; ++ph)
+    for (int ph = 0; ph < 5; ++ph)
       for (int k = 0; k < GKB_KC_COUNT; ++k) { sgraph.cl[ph][k] = P->cap_l[ph][k]; sgraph.cu[ph][k] = P->cap_u[ph][k]; }
   }
 }
@@ -1304,9 +1498,9 @@ int Solver::finish(double* w_out, double* p_out, const double* w0, const double*
     // launches of the graph: captured counts times the executions of each part
     for (int k = 0; k < GKB_KC_COUNT; ++k) {
       prof.launches[k] += sgraph.cl[0][k] + H.outer_runs * sgraph.cl[1][k] + H.inner_solves * sgraph.cl[2][k] +
-                          H.inner_runs * sgraph.cl[3][k];
+                          H.inner_runs * sgraph.cl[3][k] + H.inner_fb_runs * sgraph.cl[4][k];
       prof.units[k] += sgraph.cu[0][k] + H.outer_runs * sgraph.cu[1][k] + H.inner_solves * sgraph.cu[2][k] +
-                       H.inner_runs * sgraph.cu[3][k];
+                       H.inner_runs * sgraph.cu[3][k] + H.inner_fb_runs * sgraph.cu[4][k];
     }
   }
   prof.collect();
@@ -1319,6 +1513,7 @@ int Solver::finish(double* w_out, double* p_out, const double* w0, const double*
   stats.outer_iterations = H.k;
   stats.estimate = H.est;
   stats.inner_iterations = H.inner_its;
+  stats.inner_fallbacks = H.inner_fallbacks;
   stats.inner_solves = H.inner_solves;
   return status;
 }
@@ -1334,6 +1529,7 @@ int Solver::solve(const double* g, const double* r, double tol, int delay, doubl
   if (opt.profile) prof.enable(32768);
   stage_in(g, r, w0, p0);
   init_state(tol, delay);
+  refresh_net();
   const bool graph_run = sgraph.exec != nullptr && !opt.profile;
   if (graph_run) GKB_CUDA(cudaGraphLaunch(sgraph.exec, stream));
   else run_core_host();
@@ -1454,7 +1650,8 @@ void Solver::precond(const double* rin, double* zout) {
   }
   GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
   { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p); }
-  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG;
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || learned_inner();
+  refresh_net();
   if (opt.precision == GKB_PREC_MIXED) {
     { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<float><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, f32.p); }
     if (use_gmg) gmg32.vcycle(f32.p, x32.p, s);
@@ -1476,6 +1673,87 @@ void Solver::precond(const double* rin, double* zout) {
   GKB_CUDA(cudaGetLastError());
 }
 
+
+// Training pairs for the learned correction: FP64 GMG-PCG on M x = f from a
+// zero start; after every iteration k that has not yet converged, the
+// residual r_k and the iterate x_k are kept; once the solve has converged to
+// x*, pair k is the image of r_k / ||r_k|| and of the error x* - x_k / ||r_k||
+// (both times sqrt(nx ny)), so that M e^ = r^ up to the solve's tolerance.
+int Solver::harvest(const double* fin, int max_pairs, float* x_img, float* t_img, int* n_pairs) {
+  if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (!fin || !x_img || !t_img || !n_pairs || max_pairs < 1) throw Error{GKB_ERR_INVALID_ARG, "bad harvest arguments"};
+  if (grid.dim != 2 || grid.n[0] % 4 || grid.n[1] % 4)
+    throw Error{GKB_ERR_INVALID_ARG, "pairs are harvested on 2D grids with sides divisible by 4"};
+  if (opt.precision != GKB_PREC_FP64 || opt.inner != GKB_INNER_GMG_PCG)
+    throw Error{GKB_ERR_INVALID_ARG, "pairs are harvested by the FP64 GMG-PCG inner solver"};
+  if (!is_device_ptr(x_img) || !is_device_ptr(t_img)) throw Error{GKB_ERR_INVALID_ARG, "images must be device arrays"};
+  cudaStream_t s = stream;
+  const Lvl& L = L64;
+  const long long len = L.nvel;
+  const long long px = (long long)L.n[0] * L.n[1];
+  Compact cmp = make_compact(L);
+  const double* src = fin;
+  if (!is_device_ptr(fin)) {
+    GKB_CUDA(cudaMemcpyAsync(stage_m.p, fin, m * sizeof(double), cudaMemcpyHostToDevice, s));
+    src = stage_m.p;
+  }
+  GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
+  { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p); }
+  DevBuf<double> xk, nrm;
+  xk.alloc((size_t)max_pairs * len);
+  nrm.alloc((size_t)max_pairs * 4);
+  Cg<double>& c = cg64;
+  CgState h{};
+  h.tol2 = opt.tol_inner * opt.tol_inner;
+  h.maxit = opt.maxit_inner;
+  GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
+  GKB_CUDA(cudaMemsetAsync(x.p, 0, len * sizeof(double), s));
+  GKB_CUDA(cudaMemcpyAsync(c.r.p, wtmp.p, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  Ops<double>::dot(len, wtmp.p, wtmp.p, red, FIN_CG_INIT, cg_dev, s);
+  int np = 0;
+  auto keep = [&]() {
+    if (np >= max_pairs) return;
+    Ops<double>::dot(len, c.r.p, c.r.p, red, FIN_STORE, nrm.p + 4 * np, s);
+    mac_to_img<double>(L, c.r.p, nrm.p + 4 * np, x_img + (size_t)np * px * 3, s);
+    GKB_CUDA(cudaMemcpyAsync(xk.p + (size_t)np * len, x.p, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ++np;
+  };
+  GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  if (!cg_host->done) keep();
+  c.pre->vcycle(c.r.p, c.z.p, s);
+  Ops<double>::dot(len, c.r.p, c.z.p, red, FIN_CG_RZ0, cg_dev, s);
+  Ops<double>::cg_dir(len, c.p.p, c.z.p, cg_dev, 1, s);
+  GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  GKB_CUDA(cudaStreamSynchronize(s));
+  while (!cg_host->done) {
+    Ops<double>::apply_dot(L, 1, c.p.p, c.q.p, red, FIN_CG_PAP, cg_dev, s);
+    Ops<double>::cg_update(len, x.p, c.p.p, c.r.p, c.q.p, cg_dev, red, cg_dev, s);
+    GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    GKB_CUDA(cudaStreamSynchronize(s));
+    if (cg_host->done) break;
+    keep();
+    c.pre->vcycle(c.r.p, c.z.p, s);
+    Ops<double>::dot(len, c.r.p, c.z.p, red, FIN_CG_RZ, cg_dev, s);
+    Ops<double>::cg_dir(len, c.p.p, c.z.p, cg_dev, 0, s);
+  }
+  const int status = cg_host->status;
+  if (status != ST_OK) np = 0;
+  // x* - x_k is known only to about ||r*|| / ||r_k|| relative: keep the
+  // leading pairs whose residual is at least 1e4 times the final one
+  std::vector<double> hn(4 * (size_t)std::max(np, 1));
+  if (np > 0) GKB_CUDA(cudaMemcpy(hn.data(), nrm.p, 4 * np * sizeof(double), cudaMemcpyDeviceToHost));
+  int keep_n = 0;
+  while (keep_n < np && hn[4 * keep_n] >= 1e8 * cg_host->rr) ++keep_n;
+  if (keep_n < np)
+    GKB_CUDA(cudaMemsetAsync(x_img + (size_t)keep_n * px * 3, 0, (size_t)(np - keep_n) * px * 3 * sizeof(float), s));
+  np = keep_n;
+  for (int k = 0; k < np; ++k)
+    err_to_img(L, x.p, xk.p + (size_t)k * len, nrm.p + 4 * k, t_img + (size_t)k * px * 2, s);
+  GKB_CUDA(cudaStreamSynchronize(s));
+  *n_pairs = np;
+  return status;
+}
 
 // ---------------------------------------------------------------------------
 // batched solves: one graph, one branch per problem
@@ -1600,6 +1878,7 @@ int solve_batched(Solver** S, int count, const double* const* g, const double* c
       S[i]->prof.reset();
       S[i]->stage_in(g[i], r[i], nullptr, nullptr);
       S[i]->init_state(tol, delay);
+      S[i]->refresh_net();
     }
     GKB_CUDA(cudaGraphLaunch(B->exec, st));
     for (int i = 0; i < count; ++i) {

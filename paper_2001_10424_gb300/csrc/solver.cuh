@@ -55,6 +55,9 @@ struct DevBuf {
   }
 };
 
+struct Unet;
+struct UnetAct;
+
 // Geometry of one level (both precisions share it; mu pointers differ).
 Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc);
 
@@ -76,22 +79,38 @@ struct Gmg {
   int degree = 2;
   double cheb_lo = 0.1;    // interval [cheb_lo * lam, cheb_hi * lam]
   double cheb_hi = 1.1;
+  RedBuf red{};
+  // learned coarse correction (optional): at level net_level the V-cycle
+  // stops descending and applies the network instead
+  Unet* net = nullptr;
+  int net_level = -1;
+  bool net_composite = false;  // network, then the ordinary cycle from its level
+  UnetAct* net_act = nullptr;  // owned: this hierarchy's activation workspace
+  DevBuf<float> net_img;
+  DevBuf<double> net_nrm;
+  void attach_net(Unet* u, int level, bool composite, cudaStream_t s);
+  void detach_net();
+  Gmg() = default;
+  Gmg(const Gmg&) = delete;
+  Gmg& operator=(const Gmg&) = delete;
+  ~Gmg();
 
   // levels[0] geometry given; mu0_cells: fine padded cell viscosity (T) or null
   void build(const Lvl& fine, const T* fine_mu, int coarse_max, int degree, const RedBuf& red,
              double* scratch_dev, cudaStream_t s);
   // z = B r on the finest level (one V-cycle); r, z fine padded arrays
-  void vcycle(const T* r, T* z, cudaStream_t s);
+  void vcycle(const T* r, T* z, cudaStream_t s, bool use_net = true);
   void smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s);
 };
 
 // An instantiated graph of a whole solve with the launch counts of its
 // parts recorded at capture time: [0] once, [1] per outer iteration,
-// [2] per inner solve, [3] per inner loop-body execution.
+// [2] per inner solve, [3] per inner loop-body execution, [4] per
+// execution of the body of the flexible form's fallback loop.
 struct SolveGraph {
   cudaGraphExec_t exec = nullptr;
-  long long cl[4][GKB_KC_COUNT] = {};
-  long long cu[4][GKB_KC_COUNT] = {};
+  long long cl[5][GKB_KC_COUNT] = {};
+  long long cu[5][GKB_KC_COUNT] = {};
   void destroy() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -105,6 +124,8 @@ template <typename T>
 struct Cg {
   Lvl L;
   Gmg<T>* pre = nullptr;
+  bool flex = false;          // flexible CG (FCG(1) beta), for a nonlinear preconditioner
+  double rho2 = 0;            // flexible CG: fallback contraction threshold squared
   DevBuf<T> r, z, p, q;
   CgState* st = nullptr;      // device
   CgState* host = nullptr;    // pinned mirror
@@ -157,6 +178,11 @@ struct Solver {
   SolveGraph sgraph;              // whole solve as one graph (use_graph, no profiling)
   DevBuf<int> hist_inner;         // CG iterations of each inner solve
   int generation = 0;             // bumped by every set_problem
+  Unet* net = nullptr;            // learned correction (GKB_INNER_FCG_UNET[_MG])
+  bool learned_inner() const { return opt.inner == GKB_INNER_FCG_UNET || opt.inner == GKB_INNER_FCG_UNET_MG; }
+  void set_net(Unet* u);
+  void attach_net_levels();
+  void refresh_net();
   void ensure_capture_streams();
   void build_solve_graph();
   // emitters shared by the graph capture and the host-sequenced path
@@ -173,6 +199,7 @@ struct Solver {
   void apply(int op, const double* x, double* y);
   void boundary_rhs(int side, const double* normal_velocity, double* g, double* r);
   void precond(const double* r, double* z);
+  int harvest(const double* f, int max_pairs, float* x_img, float* t_img, int* n_pairs);
   // inner solve in FP64 padded layout: x = M^-1 f; returns status
   int inner_solve(const double* f, double* x);
   int mixed_solve(const double* f, double* x, int* iters);

@@ -29,6 +29,7 @@ enum FinOp {
   FIN_CG_RZ,       // s0 = r.z  -> beta
   FIN_MX_RR,       // s0 = r32.r32 -> iteration count, reliable-update trigger
   FIN_MX_RR64,     // s0 = r64.r64 (true FP64 residual) -> convergence test
+  FIN_FCG_RZ,      // s0 = r.z, s1 = z.q -> flexible beta = -z.q / p.q
 };
 
 struct CgState {
@@ -49,8 +50,17 @@ struct CgState {
   double delta2;    // mixed form: trigger ratio squared
   double rr64;      // mixed form: last true FP64 ||r||^2
   int graph_iters;  // loop-body executions of the graph form (device counted)
-  int pad2;
+  int fallback;     // flexible form: 1 once the solve has switched to plain GMG-PCG
+  int fb_iters;     // loop-body executions of the fallback loop (graph form)
+  double rho2;      // flexible form: fall back when ||r_k||^2 > rho2^k ||f||^2 (k >= 5)
 };
+
+// the flexible CG gives up on its preconditioner: it stops here and the
+// solve continues as plain GMG-PCG from the current iterate
+__device__ __forceinline__ void fcg_fallback(CgState* c) {
+  c->fallback = 1;
+  c->done = 1;
+}
 
 __device__ __forceinline__ void cg_fail(CgState* c, int code) {
   if (c->status == ST_OK) c->status = code;
@@ -118,6 +128,19 @@ __device__ __forceinline__ void finalize(int op, const double* s, void* st) {
       c->beta = (c->rz_old != 0.0) ? s[0] / c->rz_old : 0.0;
       c->rz_old = s[0];
     } break;
+    case FIN_FCG_RZ: {
+      // flexible CG (Notay's FCG(1)): the new direction is made M-orthogonal
+      // to the previous one, beta = -(z, M p) / (p, M p); with a fixed SPD
+      // preconditioner this equals the Polak-Ribiere form of the CG beta
+      CgState* c = (CgState*)st;
+      if (c->done) break;
+      // a non-finite preconditioned vector, or a residual that falls behind
+      // the contraction rate rho per iteration, hands over to GMG-PCG
+      if (!isfinite(s[0]) || !isfinite(s[1])) { c->beta = 0.0; fcg_fallback(c); break; }
+      if (c->rho2 > 0.0 && c->it >= 5 && c->rr > c->ff * pow(c->rho2, (double)c->it)) { fcg_fallback(c); break; }
+      c->beta = (c->pAp > 0.0) ? -s[1] / c->pAp : 0.0;
+      c->rz_old = s[0];
+    } break;
     default: break;
   }
 }
@@ -152,8 +175,9 @@ struct GkbState {
   int inner_solves;
   long long inner_its;       // total CG iterations
   long long inner_runs;      // total loop-body executions of the inner graphs
+  long long inner_fb_runs;   // total loop-body executions of the fallback loops
   int outer_runs;            // loop-body executions of the outer graph
-  int pad;
+  int inner_fallbacks;       // flexible inner solves that switched to GMG-PCG
 };
 
 }  // namespace gkb

@@ -10,9 +10,13 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <new>
+#include <random>
 #include <string>
+#include <vector>
 
 #include "../../include/gkb.h"
 #include "prof.h"
@@ -399,12 +403,12 @@ __global__ void k_up_bwd(const float* __restrict__ dfull, float* __restrict__ d,
   }
 }
 
-// dy = scale (y - t) (scale = 2 / batch), and the sum of (y - t)^2
+// dy = scale (y - tscale t) (scale = 2 / batch), and the sum of (y - tscale t)^2
 __global__ void __launch_bounds__(256) k_mse(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ dy,
-                                             long long n, float scale, RedBuf red, double* out) {
+                                             long long n, float scale, float tscale, RedBuf red, double* out) {
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float d = y[i] - t[i];
+    const float d = y[i] - tscale * t[i];
     dy[i] = scale * d;
     acc += (double)d * (double)d;
   }
@@ -488,24 +492,28 @@ void Unet::init(int cin, int k1, int k2, int cout, unsigned long long seed, cuda
   adam_t = 0;
 }
 
-void Unet::ensure(int n, int h, int w) {
+void Unet::ensure(UnetAct& A, int n, int h, int w) const {
   if (h % 4 || w % 4 || n < 1 || h < 4 || w < 4) throw Error{GKB_ERR_INVALID_ARG, "U-Net images need sides divisible by 4"};
-  if (n == an && h == ah && w == aw) return;
+  if (n == A.n && h == A.h && w == A.w) return;
   const long long P = (long long)n * h * w, P2 = P / 4, P4 = P / 16;
-  a1.alloc(P * c1); s1.alloc(P * c1); e1.alloc(P * c1); y.alloc(P * c_out);
-  p1.alloc(P2 * c1); b1.alloc(P2 * c2); s2.alloc(P2 * c2); d1.alloc(P2 * c2);
-  p2.alloc(P4 * c2); c1a.alloc(P4 * c2); c2a.alloc(P4 * c2);
-  g_full0.alloc(P * c2); g_full1.alloc(P * c2); g_e.alloc(P * c1);
-  g_half0.alloc(P2 * c2); g_half1.alloc(P2 * c2);
-  g_q0.alloc(P4 * c2); g_q1.alloc(P4 * c2);
-  an = n; ah = h; aw = w;
+  A.a1.alloc(P * c1); A.s1.alloc(P * c1); A.e1.alloc(P * c1); A.y.alloc(P * c_out);
+  A.p1.alloc(P2 * c1); A.b1.alloc(P2 * c2); A.s2.alloc(P2 * c2); A.d1.alloc(P2 * c2);
+  A.p2.alloc(P4 * c2); A.c1a.alloc(P4 * c2); A.c2a.alloc(P4 * c2);
+  A.n = n; A.h = h; A.w = w;
 }
 
-static void conv_fwd(const Unet& U, int li, In2 in, float* out, int n, int h, int w, int relu, bool tc) {
+void Unet::refresh_bf16(cudaStream_t s) {
+  ProfScope ps_(GKB_KC_UNET, s, nparams);
+  k_to_bf16<<<grid_for(nparams), UT, 0, s>>>(params.p, params_bf16.p, nparams);
+  GKB_CUDA(cudaGetLastError());
+  bf16_stale = false;
+}
+
+static void conv_fwd(const Unet& U, int li, In2 in, float* out, int n, int h, int w, int relu, bool tc,
+                     cudaStream_t s) {
   const ConvLayer& L = U.layers[li];
   const float* wp = U.params.p + L.off;
   const float* bp = wp + L.nw();
-  cudaStream_t s = U.stream;
   const long long P = (long long)n * h * w;
   ProfScope ps_(GKB_KC_UNET, s, P);
   if (tc) {
@@ -530,27 +538,22 @@ static void conv_fwd(const Unet& U, int li, In2 in, float* out, int n, int h, in
   GKB_CUDA(cudaGetLastError());
 }
 
-const float* Unet::forward(const float* x, int n, int h, int w, bool tc) {
-  ensure(n, h, w);
-  if (tc && bf16_stale) {
-    k_to_bf16<<<grid_for(nparams), UT, 0, stream>>>(params.p, params_bf16.p, nparams);
-    GKB_CUDA(cudaGetLastError());
-    bf16_stale = false;
-  }
+const float* Unet::forward(UnetAct& A, const float* x, int n, int h, int w, bool tc, cudaStream_t s) {
+  ensure(A, n, h, w);
+  if (tc && bf16_stale) refresh_bf16(s);
   const int h2 = h / 2, w2 = w / 2, h4 = h / 4, w4 = w / 4;
-  cudaStream_t s = stream;
-  conv_fwd(*this, 0, In2{x, c_in, 0, nullptr, 0}, a1.p, n, h, w, 1, tc);
-  conv_fwd(*this, 1, In2{a1.p, c1, 0, nullptr, 0}, s1.p, n, h, w, 1, tc);
-  { ProfScope ps_(GKB_KC_UNET, s); k_pool<<<grid_for((long long)n * h2 * w2 * c1), UT, 0, s>>>(s1.p, p1.p, n, h, w, c1); }
-  conv_fwd(*this, 2, In2{p1.p, c1, 0, nullptr, 0}, b1.p, n, h2, w2, 1, tc);
-  conv_fwd(*this, 3, In2{b1.p, c2, 0, nullptr, 0}, s2.p, n, h2, w2, 1, tc);
-  { ProfScope ps_(GKB_KC_UNET, s); k_pool<<<grid_for((long long)n * h4 * w4 * c2), UT, 0, s>>>(s2.p, p2.p, n, h2, w2, c2); }
-  conv_fwd(*this, 4, In2{p2.p, c2, 0, nullptr, 0}, c1a.p, n, h4, w4, 1, tc);
-  conv_fwd(*this, 5, In2{c1a.p, c2, 0, nullptr, 0}, c2a.p, n, h4, w4, 1, tc);
-  conv_fwd(*this, 6, In2{c2a.p, c2, 1, s2.p, c2}, d1.p, n, h2, w2, 1, tc);
-  conv_fwd(*this, 7, In2{d1.p, c2, 1, s1.p, c1}, e1.p, n, h, w, 1, tc);
-  conv_fwd(*this, 8, In2{e1.p, c1, 0, nullptr, 0}, y.p, n, h, w, 0, tc);
-  return y.p;
+  conv_fwd(*this, 0, In2{x, c_in, 0, nullptr, 0}, A.a1.p, n, h, w, 1, tc, s);
+  conv_fwd(*this, 1, In2{A.a1.p, c1, 0, nullptr, 0}, A.s1.p, n, h, w, 1, tc, s);
+  { ProfScope ps_(GKB_KC_UNET, s); k_pool<<<grid_for((long long)n * h2 * w2 * c1), UT, 0, s>>>(A.s1.p, A.p1.p, n, h, w, c1); }
+  conv_fwd(*this, 2, In2{A.p1.p, c1, 0, nullptr, 0}, A.b1.p, n, h2, w2, 1, tc, s);
+  conv_fwd(*this, 3, In2{A.b1.p, c2, 0, nullptr, 0}, A.s2.p, n, h2, w2, 1, tc, s);
+  { ProfScope ps_(GKB_KC_UNET, s); k_pool<<<grid_for((long long)n * h4 * w4 * c2), UT, 0, s>>>(A.s2.p, A.p2.p, n, h2, w2, c2); }
+  conv_fwd(*this, 4, In2{A.p2.p, c2, 0, nullptr, 0}, A.c1a.p, n, h4, w4, 1, tc, s);
+  conv_fwd(*this, 5, In2{A.c1a.p, c2, 0, nullptr, 0}, A.c2a.p, n, h4, w4, 1, tc, s);
+  conv_fwd(*this, 6, In2{A.c2a.p, c2, 1, A.s2.p, c2}, A.d1.p, n, h2, w2, 1, tc, s);
+  conv_fwd(*this, 7, In2{A.d1.p, c2, 1, A.s1.p, c1}, A.e1.p, n, h, w, 1, tc, s);
+  conv_fwd(*this, 8, In2{A.e1.p, c1, 0, nullptr, 0}, A.y.p, n, h, w, 0, tc, s);
+  return A.y.p;
 }
 
 // weight gradient of layer li into grads (two deterministic passes)
@@ -595,8 +598,17 @@ static void conv_bwd_data(Unet& U, int li, const float* dpre, int c0, float* d0,
 }
 
 double Unet::loss_grad(const float* x, const float* t, int n, int h, int w) {
-  forward(x, n, h, w, false);
   cudaStream_t s = stream;
+  forward(act, x, n, h, w, false, s);
+  if (n != gn || h != gh || w != gw) {
+    const long long P = (long long)n * h * w, P2 = P / 4, P4 = P / 16;
+    g_full0.alloc(P * c2); g_full1.alloc(P * c2); g_e.alloc(P * c1);
+    g_half0.alloc(P2 * c2); g_half1.alloc(P2 * c2);
+    g_q0.alloc(P4 * c2); g_q1.alloc(P4 * c2);
+    gn = n; gh = h; gw = w;
+  }
+  float *a1 = act.a1.p, *s1 = act.s1.p, *p1 = act.p1.p, *b1 = act.b1.p, *s2 = act.s2.p, *p2 = act.p2.p;
+  float *c1a = act.c1a.p, *c2a = act.c2a.p, *d1 = act.d1.p, *e1 = act.e1.p, *y = act.y.p;
   const int h2 = h / 2, w2 = w / 2, h4 = h / 4, w4 = w / 4;
   const long long P = (long long)n * h * w, P2 = P / 4, P4 = P / 16;
   RedBuf red{red_partial.p, red_ticket.p};
@@ -604,51 +616,51 @@ double Unet::loss_grad(const float* x, const float* t, int n, int h, int w) {
   float* dy = g_e.p;
   {
     ProfScope ps_(GKB_KC_UNET, s);
-    k_mse<<<grid_for(P * c_out), 256, 0, s>>>(y.p, t, dy, P * c_out, 2.f / (float)n, red, loss_dev.p);
+    k_mse<<<grid_for(P * c_out), 256, 0, s>>>(y, t, dy, P * c_out, 2.f / (float)n, target_scale, red, loss_dev.p);
   }
   // out layer (no ReLU): input e1
-  conv_bwd_w(*this, 8, In2{e1.p, c1, 0, nullptr, 0}, dy, n, h, w);
+  conv_bwd_w(*this, 8, In2{e1, c1, 0, nullptr, 0}, dy, n, h, w);
   float* de1 = g_full1.p;  // P * c1
   conv_bwd_data(*this, 8, dy, c1, de1, nullptr, n, h, w);
-  k_relu_mask<<<grid_for(P * c1), UT, 0, s>>>(de1, e1.p, P * c1);
+  k_relu_mask<<<grid_for(P * c1), UT, 0, s>>>(de1, e1, P * c1);
   // e1 = relu(conv([up(d1), s1]))
-  conv_bwd_w(*this, 7, In2{d1.p, c2, 1, s1.p, c1}, de1, n, h, w);
+  conv_bwd_w(*this, 7, In2{d1, c2, 1, s1, c1}, de1, n, h, w);
   float* du1 = g_full0.p;     // P * c2 (gradient of up(d1))
   float* ds1 = g_e.p;         // P * c1 (dy no longer needed)
   conv_bwd_data(*this, 7, de1, c2, du1, ds1, n, h, w);
   float* dd1 = g_half0.p;     // P2 * c2
   k_up_bwd<<<grid_for(P2 * c2), UT, 0, s>>>(du1, dd1, n, h, w, c2);
-  k_relu_mask<<<grid_for(P2 * c2), UT, 0, s>>>(dd1, d1.p, P2 * c2);
+  k_relu_mask<<<grid_for(P2 * c2), UT, 0, s>>>(dd1, d1, P2 * c2);
   // d1 = relu(conv([up(c2a), s2]))
-  conv_bwd_w(*this, 6, In2{c2a.p, c2, 1, s2.p, c2}, dd1, n, h2, w2);
+  conv_bwd_w(*this, 6, In2{c2a, c2, 1, s2, c2}, dd1, n, h2, w2);
   float* du2 = g_full1.p;     // P2 * c2 (reuse)
   float* ds2 = g_half1.p;     // P2 * c2
   conv_bwd_data(*this, 6, dd1, c2, du2, ds2, n, h2, w2);
   float* dc2 = g_q0.p;        // P4 * c2
   k_up_bwd<<<grid_for(P4 * c2), UT, 0, s>>>(du2, dc2, n, h2, w2, c2);
-  k_relu_mask<<<grid_for(P4 * c2), UT, 0, s>>>(dc2, c2a.p, P4 * c2);
-  conv_bwd_w(*this, 5, In2{c1a.p, c2, 0, nullptr, 0}, dc2, n, h4, w4);
+  k_relu_mask<<<grid_for(P4 * c2), UT, 0, s>>>(dc2, c2a, P4 * c2);
+  conv_bwd_w(*this, 5, In2{c1a, c2, 0, nullptr, 0}, dc2, n, h4, w4);
   float* dc1 = g_q1.p;
   conv_bwd_data(*this, 5, dc2, c2, dc1, nullptr, n, h4, w4);
-  k_relu_mask<<<grid_for(P4 * c2), UT, 0, s>>>(dc1, c1a.p, P4 * c2);
-  conv_bwd_w(*this, 4, In2{p2.p, c2, 0, nullptr, 0}, dc1, n, h4, w4);
+  k_relu_mask<<<grid_for(P4 * c2), UT, 0, s>>>(dc1, c1a, P4 * c2);
+  conv_bwd_w(*this, 4, In2{p2, c2, 0, nullptr, 0}, dc1, n, h4, w4);
   float* dp2 = g_q0.p;
   conv_bwd_data(*this, 4, dc1, c2, dp2, nullptr, n, h4, w4);
   k_pool_bwd_add<<<grid_for(P2 * c2), UT, 0, s>>>(dp2, ds2, n, h2, w2, c2);
-  k_relu_mask<<<grid_for(P2 * c2), UT, 0, s>>>(ds2, s2.p, P2 * c2);
-  conv_bwd_w(*this, 3, In2{b1.p, c2, 0, nullptr, 0}, ds2, n, h2, w2);
+  k_relu_mask<<<grid_for(P2 * c2), UT, 0, s>>>(ds2, s2, P2 * c2);
+  conv_bwd_w(*this, 3, In2{b1, c2, 0, nullptr, 0}, ds2, n, h2, w2);
   float* db1 = g_half0.p;
   conv_bwd_data(*this, 3, ds2, c2, db1, nullptr, n, h2, w2);
-  k_relu_mask<<<grid_for(P2 * c2), UT, 0, s>>>(db1, b1.p, P2 * c2);
-  conv_bwd_w(*this, 2, In2{p1.p, c1, 0, nullptr, 0}, db1, n, h2, w2);
+  k_relu_mask<<<grid_for(P2 * c2), UT, 0, s>>>(db1, b1, P2 * c2);
+  conv_bwd_w(*this, 2, In2{p1, c1, 0, nullptr, 0}, db1, n, h2, w2);
   float* dp1 = g_half1.p;     // P2 * c1
   conv_bwd_data(*this, 2, db1, c1, dp1, nullptr, n, h2, w2);
   k_pool_bwd_add<<<grid_for(P * c1), UT, 0, s>>>(dp1, ds1, n, h, w, c1);
-  k_relu_mask<<<grid_for(P * c1), UT, 0, s>>>(ds1, s1.p, P * c1);
-  conv_bwd_w(*this, 1, In2{a1.p, c1, 0, nullptr, 0}, ds1, n, h, w);
+  k_relu_mask<<<grid_for(P * c1), UT, 0, s>>>(ds1, s1, P * c1);
+  conv_bwd_w(*this, 1, In2{a1, c1, 0, nullptr, 0}, ds1, n, h, w);
   float* da1 = g_full1.p;
   conv_bwd_data(*this, 1, ds1, c1, da1, nullptr, n, h, w);
-  k_relu_mask<<<grid_for(P * c1), UT, 0, s>>>(da1, a1.p, P * c1);
+  k_relu_mask<<<grid_for(P * c1), UT, 0, s>>>(da1, a1, P * c1);
   conv_bwd_w(*this, 0, In2{x, c_in, 0, nullptr, 0}, da1, n, h, w);
   GKB_CUDA(cudaGetLastError());
   double loss = 0.0;
@@ -667,17 +679,129 @@ void Unet::adam(float lr, float beta1, float beta2, float eps) {
   bf16_stale = true;
 }
 
+void Unet::train(const float* x_img, const float* t_img, long long count, int h, int w, int batch, int steps, float lr,
+                 unsigned long long seed, double* losses) {
+  if (count < 1 || batch < 1 || batch > count || steps < 0 || !(lr > 0))
+    throw Error{GKB_ERR_INVALID_ARG, "training needs 1 <= batch <= count, steps >= 0 and lr > 0"};
+  const long long xs = (long long)h * w * c_in, ts = (long long)h * w * c_out;
+  if (xb.n != (size_t)(batch * xs)) xb.alloc((size_t)batch * xs);
+  if (tb.n != (size_t)(batch * ts)) tb.alloc((size_t)batch * ts);
+  std::vector<long long> order(count);
+  for (long long i = 0; i < count; ++i) order[i] = i;
+  std::mt19937_64 rng(seed);
+  long long pos = count;  // forces a shuffle before the first batch
+  for (int it = 0; it < steps; ++it) {
+    for (int b = 0; b < batch; ++b) {
+      if (pos == count) {
+        std::shuffle(order.begin(), order.end(), rng);
+        pos = 0;
+      }
+      const long long k = order[pos++];
+      GKB_CUDA(cudaMemcpyAsync(xb.p + b * xs, x_img + k * xs, xs * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+      GKB_CUDA(cudaMemcpyAsync(tb.p + b * ts, t_img + k * ts, ts * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+    }
+    const double l = loss_grad(xb.p, tb.p, batch, h, w);
+    if (losses) losses[it] = l;
+    adam(lr, 0.9f, 0.999f, 1e-8f);
+  }
+  GKB_CUDA(cudaStreamSynchronize(stream));
+}
+
+// ---------------------------------------------------------------------------
+// the network as a coarse correction on a 2D MAC level
+// ---------------------------------------------------------------------------
+
+// image (ny, nx, 3): west u face and south v face of each cell scaled by
+// sqrt(nx ny / ||b||^2), and log viscosity
+template <typename T>
+__global__ void k_mac_to_img(Lvl L, const T* __restrict__ b, const double* __restrict__ nrm, float* __restrict__ img) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.n[0] || j >= L.n[1]) return;
+  const double nr2 = nrm[0];
+  const double sc = nr2 > 0.0 ? sqrt((double)L.n[0] * L.n[1] / nr2) : 0.0;
+  const long long c = cix(L, i, j, 0);
+  float* o = img + ((long long)j * L.n[0] + i) * 3;
+  o[0] = face_active<0>(L, i, j, 0) ? (float)((double)b[L.off[0] + c] * sc) : 0.f;
+  o[1] = face_active<1>(L, i, j, 0) ? (float)((double)b[L.off[1] + c] * sc) : 0.f;
+  const T* mu = MuPtr<T>::get(L);
+  o[2] = (float)log(mu ? (double)mu[c] : L.mu0);
+}
+
+// x on every face of the level: the network output scaled back, zero on the
+// faces that are not unknowns and on east / north boundary faces
+template <typename T>
+__global__ void k_img_to_mac(Lvl L, const float* __restrict__ y, const double* __restrict__ nrm, float inv_tscale,
+                             T* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > L.n[0] || j > L.n[1]) return;
+  const double nr2 = nrm[0];
+  const double sc = nr2 > 0.0 ? sqrt(nr2 / ((double)L.n[0] * L.n[1])) * inv_tscale : 0.0;
+  const long long c = cix(L, i, j, 0);
+  const bool in = i < L.n[0] && j < L.n[1];
+  if (j < L.n[1]) {  // u face (i, j), i <= nx
+    const bool a = in && face_active<0>(L, i, j, 0);
+    x[L.off[0] + c] = a ? (T)((double)y[((long long)j * L.n[0] + i) * 2 + 0] * sc) : (T)0;
+  }
+  if (i < L.n[0]) {  // v face (i, j), j <= ny
+    const bool a = in && face_active<1>(L, i, j, 0);
+    x[L.off[1] + c] = a ? (T)((double)y[((long long)j * L.n[0] + i) * 2 + 1] * sc) : (T)0;
+  }
+}
+
+// (xs - xk) on the west u / south v face of every cell, scaled like k_mac_to_img
+__global__ void k_err_to_img(Lvl L, const double* __restrict__ xs, const double* __restrict__ xk,
+                             const double* __restrict__ nrm, float* __restrict__ img) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= L.n[0] || j >= L.n[1]) return;
+  const double nr2 = nrm[0];
+  const double sc = nr2 > 0.0 ? sqrt((double)L.n[0] * L.n[1] / nr2) : 0.0;
+  const long long c = cix(L, i, j, 0);
+  float* o = img + ((long long)j * L.n[0] + i) * 2;
+  const long long cu = L.off[0] + c, cv = L.off[1] + c;
+  o[0] = face_active<0>(L, i, j, 0) ? (float)((xs[cu] - xk[cu]) * sc) : 0.f;
+  o[1] = face_active<1>(L, i, j, 0) ? (float)((xs[cv] - xk[cv]) * sc) : 0.f;
+}
+
+template <typename T>
+void mac_to_img(const Lvl& L, const T* b, const double* nrm, float* img, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_UNET, s, (long long)L.n[0] * L.n[1]);
+  k_mac_to_img<T><<<dim3((L.n[0] + 31) / 32, (L.n[1] + 7) / 8), dim3(32, 8), 0, s>>>(L, b, nrm, img);
+  GKB_CUDA(cudaGetLastError());
+}
+template void mac_to_img<double>(const Lvl&, const double*, const double*, float*, cudaStream_t);
+template void mac_to_img<float>(const Lvl&, const float*, const double*, float*, cudaStream_t);
+
+void err_to_img(const Lvl& L, const double* xs, const double* xk, const double* nrm, float* img, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_UNET, s, (long long)L.n[0] * L.n[1]);
+  k_err_to_img<<<dim3((L.n[0] + 31) / 32, (L.n[1] + 7) / 8), dim3(32, 8), 0, s>>>(L, xs, xk, nrm, img);
+  GKB_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void unet_correct(Unet& U, UnetAct& A, const Lvl& L, const T* b, T* x, float* img_in, double* nrm, const RedBuf& red,
+                  cudaStream_t s) {
+  if (L.dim != 2) throw Error{GKB_ERR_INVALID_ARG, "the learned correction is 2D only"};
+  Ops<T>::dot(L.nvel, b, b, red, FIN_STORE, nrm, s);
+  const dim3 blk(32, 8);
+  mac_to_img<T>(L, b, nrm, img_in, s);
+  const float* y = U.forward(A, img_in, 1, L.n[1], L.n[0], true, s);
+  {
+    ProfScope ps_(GKB_KC_UNET, s, (long long)L.n[0] * L.n[1]);
+    k_img_to_mac<T><<<dim3((L.n[0] + 32) / 32, (L.n[1] + 8) / 8), blk, 0, s>>>(L, y, nrm, 1.f / U.target_scale, x);
+  }
+  GKB_CUDA(cudaGetLastError());
+}
+
+template void unet_correct<double>(Unet&, UnetAct&, const Lvl&, const double*, double*, float*, double*, const RedBuf&,
+                                   cudaStream_t);
+template void unet_correct<float>(Unet&, UnetAct&, const Lvl&, const float*, float*, float*, double*, const RedBuf&,
+                                  cudaStream_t);
+
 }  // namespace gkb
 
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
-
-struct gkb_unet_ctx {
-  gkb::Unet u;
-  int device = 0;
-  std::string last_error = "no error";
-};
 
 namespace {
 
@@ -768,7 +892,7 @@ int gkb_unet_set_params(gkb_unet h, const float* params) {
 int gkb_unet_forward(gkb_unet h, const float* x, int n, int hh, int w, float* y, int tensor_cores) {
   return unet_guard(h, [&] {
     if (!x || !y || !dev_ptr(x) || !dev_ptr(y)) throw gkb::Error{GKB_ERR_INVALID_ARG, "x and y must be device arrays"};
-    const float* out = h->u.forward(x, n, hh, w, tensor_cores != 0);
+    const float* out = h->u.forward(h->u.act, x, n, hh, w, tensor_cores != 0, h->u.stream);
     gkb::check_cuda(cudaMemcpyAsync(y, out, (size_t)n * hh * w * h->u.c_out * sizeof(float), cudaMemcpyDeviceToDevice,
                                     h->u.stream), "copy");
     gkb::check_cuda(cudaStreamSynchronize(h->u.stream), "sync");
@@ -793,6 +917,33 @@ int gkb_unet_adam_step(gkb_unet h, float lr, float beta1, float beta2, float eps
   return unet_guard(h, [&] {
     h->u.adam(lr, beta1, beta2, eps);
     gkb::check_cuda(cudaStreamSynchronize(h->u.stream), "sync");
+    return GKB_OK;
+  });
+}
+
+int gkb_unet_train(gkb_unet h, const float* x_img, const float* t_img, int64_t count, int hh, int w, int batch,
+                   int steps, float lr, unsigned long long seed, double* losses) {
+  return unet_guard(h, [&] {
+    if (!x_img || !t_img || !dev_ptr(x_img) || !dev_ptr(t_img))
+      throw gkb::Error{GKB_ERR_INVALID_ARG, "x_img and t_img must be device arrays"};
+    h->u.ensure(h->u.act, batch < 1 ? 1 : batch, hh, w);
+    h->u.train(x_img, t_img, count, hh, w, batch, steps, lr, seed, losses);
+    return GKB_OK;
+  });
+}
+
+int gkb_unet_set_target_scale(gkb_unet h, float s) {
+  return unet_guard(h, [&] {
+    if (!(s > 0) || !std::isfinite(s)) throw gkb::Error{GKB_ERR_INVALID_ARG, "target scale must be positive"};
+    h->u.target_scale = s;
+    return GKB_OK;
+  });
+}
+
+int gkb_unet_get_target_scale(gkb_unet h, float* s) {
+  return unet_guard(h, [&] {
+    if (!s) return GKB_ERR_INVALID_ARG;
+    *s = h->u.target_scale;
     return GKB_OK;
   });
 }

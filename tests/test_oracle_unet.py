@@ -148,3 +148,23 @@ def test_mac_image_maps():
         idx = grid.face_index[c][:6, :4]
         covered[idx[idx >= 0]] = True
     assert np.array_equal(back[covered], v[covered]) and np.all(back[~covered] == 0)
+
+
+def test_preconditioner_is_scale_equivariant():
+    shapes = unet.layer_shapes()
+    rng = np.random.default_rng(8)
+    params = 0.1 * rng.standard_normal(unet.num_params(shapes))
+    grid = mac.MacGrid((8, 12), 1.0 / 8)
+    r = rng.standard_normal(grid.m)
+    logmu = rng.standard_normal((8, 12))
+    z = unet.apply_preconditioner(params, shapes, grid, r, logmu)
+    zmax = np.abs(z).max()
+    # z(a r) = a z(r) for a > 0, the target scale divides, z(0) = 0
+    assert np.abs(unet.apply_preconditioner(params, shapes, grid, 7.5 * r, logmu) - 7.5 * z).max() < 1e-12 * zmax
+    assert np.abs(unet.apply_preconditioner(params, shapes, grid, r, logmu, target_scale=4.0) - z / 4.0).max() < 1e-15 * zmax
+    assert not np.any(unet.apply_preconditioner(params, shapes, grid, 0 * r, logmu))
+    # on an all-Dirichlet box every unknown is a west or south face of a
+    # cell, so the residual channels hold all of r: at unit RMS their squares
+    # sum to the number of cells
+    img = unet.mac_to_image(grid, r / (np.linalg.norm(r) / np.sqrt(96)), logmu)
+    assert abs(np.sum(img[:, :, :2] ** 2) - 96) < 1e-9 * 96

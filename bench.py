@@ -15,7 +15,11 @@ Other workloads: ``stokes3d`` (256^3 cavity, gamma 100, mixed FP32/FP64),
 ``poiseuille`` (32 x 32 channel, gamma 100, plain CG to 1e-12, seeded
 initial guess), ``batched2d`` (256 cavities of side 32*U{2..16} with
 per-problem viscosity, gamma 100, mixed, one graph launch per step; value
-in solves/s).
+in solves/s), ``varvisc2d`` (2048 x 2048 cavity with log-normal viscosity
+from a Gaussian random field, gamma 100, mixed; inner flexible CG whose
+V-cycle takes a U-Net correction at the 512 x 512 level; the network is
+trained before timing on pairs harvested from GMG-PCG on 512 x 512
+instances of the same family, and the GMG-PCG forms are timed beside it).
 
 ``--impl reference`` times the CPU oracle (sparse-LU inner solves) on the
 host cores instead, on a reduced member of the same family, scaled by the
@@ -35,6 +39,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
+BF16_FALLBACK_TFLOPS = 1900.0
 FP64_PEAK_TFLOPS = 1.258   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.25)
 FP32_PEAK_TFLOPS = 80.6    # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 
@@ -46,6 +51,14 @@ PER_UNIT = {
     3: {"apply": (19.0, 2.0), "residual": (19.0, 3.0), "smooth": (35.0, 4.5), "restrict": (1.5, 1.125),
         "prolong": (1.5, 2.125), "blas": (2.0, 3.0)},
 }
+
+# U-Net forward: flops per pixel of the image (9 convolutions: 4 at full,
+# 3 at half, 2 at quarter resolution) and unit count per pixel of one
+# forward as the launch counters record it (pixels of each convolution and
+# of the two image conversions)
+UNET_FLOP_PER_PX = (2 * 9 * (3 * 16 + 16 * 16 + 48 * 16 + 16 * 2)
+                    + 2 * 9 * (16 * 32 + 32 * 32 + 64 * 32) / 4 + 2 * 9 * (2 * 32 * 32) / 16)
+UNET_UNITS_PER_PX = 4 + 3 / 4 + 2 / 16 + 2
 
 # per-launch DRAM traffic (bytes) of the dominant kernel from ncu captures,
 # keyed by (workload, form, kernel class); summarised under profiles/
@@ -59,6 +72,66 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return HBM_FALLBACK_GBS, "fallback"
+
+
+def measured_bf16_sustained():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return BF16_FALLBACK_TFLOPS * 0.9, "fallback"
+
+
+def train_network(gk, torch, wk, args):
+    """The learned part's setup (untimed, reported): harvest (r^, e^) pairs
+    with FP64 GMG-PCG on 512 x 512 instances of the workload's family (own
+    seeds, so the timed instance is held out), then train the U-Net with
+    Adam on the device. Returns the network and a report."""
+    import numpy as np
+
+    import workloads as W
+    side = wk.unet_side
+    t0 = time.perf_counter()
+    cap = 40
+    x_img = torch.zeros((args.train_pairs + cap, side, side, 3), dtype=torch.float32, device="cuda")
+    t_img = torch.zeros((args.train_pairs + cap, side, side, 2), dtype=torch.float32, device="cuda")
+    count, inst = 0, 0
+    opt = gk.gkb_default_options()
+    opt.precision = gk.GKB_PREC_FP64
+    opt.inner = gk.GKB_INNER_GMG_PCG
+    opt.tol_inner = 1e-10
+    opt.maxit_inner = 5000
+    opt.stream = torch.cuda.current_stream().cuda_stream
+    h = gk.gkb_create(opt)
+    try:
+        while count < args.train_pairs and time.perf_counter() - t0 < args.harvest_seconds:
+            pr = W.varvisc2d(side, seed_offset=1000 + 2 * inst)
+            visc = np.ascontiguousarray(np.asarray(pr["mu"]).ravel(order="F"))
+            gk.gkb_set_problem(h, gk.make_grid(pr["n"], pr["h"], pr["bc"]), visc, 1.0, 100.0, 0.0)
+            k = gk.gkb_harvest_pairs(h, pr["g"], cap, x_img[count:], t_img[count:])
+            count += k
+            inst += 1
+    finally:
+        gk.gkb_destroy(h)
+    count = min(count, args.train_pairs)
+    torch.cuda.synchronize()
+    harvest_s = time.perf_counter() - t0
+    x_img, t_img = x_img[:count], t_img[:count]
+    rms = float(t_img.pow(2).mean().sqrt())
+    net = gk.gkb_unet_create(3, 16, 32, 2, 20010424, torch.cuda.current_stream().cuda_stream)
+    gk.gkb_unet_set_target_scale(net, 1.0 / rms)
+    t1 = time.perf_counter()
+    losses = gk.gkb_unet_train(net, x_img, t_img, count, side, side, args.train_batch, args.train_steps,
+                               args.train_lr, seed=7)
+    train_s = time.perf_counter() - t1
+    del x_img, t_img
+    torch.cuda.empty_cache()
+    head = float(np.mean(losses[:10])) if len(losses) else None
+    tail = float(np.mean(losses[-10:])) if len(losses) else None
+    return net, {"instances": inst, "pairs": count, "harvest_s": harvest_s, "train_s": train_s,
+                 "steps": args.train_steps, "batch": args.train_batch, "lr": args.train_lr,
+                 "target_rms": rms, "loss_first10": head, "loss_last10": tail,
+                 "samples_per_s": args.train_steps * args.train_batch / train_s if train_s > 0 else None}
 
 
 class ClockSampler:
@@ -136,6 +209,8 @@ class Workload:
         self.inner = 1          # GMG-PCG
         self.tol_inner = args.tol_inner
         self.form = args.form
+        self.learned = None     # "replace" / "composite": flexible CG with the network
+        self.net = None
         if self.name == "stokes2d":
             base = W.stokes2d(args.n)
             self.problems = [dict(base, gamma=float(gm)) for gm in args.gammas]
@@ -158,6 +233,16 @@ class Workload:
             self.tol_inner = 1e-12
             self.label = "32x32 MAC Poiseuille channel, gamma 100, inner CG 1e-12"
             self.sample = ("poiseuille", 32, [100.0])
+        elif self.name == "varvisc2d":
+            n = args.n if args.n != 1024 else 2048
+            base = W.varvisc2d(n)
+            self.problems = [dict(base, gamma=100.0)]
+            self.dim = 2
+            self.form = "mixed" if args.form_default else args.form
+            self.learned = args.learned_form
+            self.unet_side = args.unet_side
+            self.label = "%dx%d MAC Stokes cavity, log-normal GRF viscosity, gamma 100" % (n, n)
+            self.sample = ("varvisc", 128, [100.0])
         elif self.name == "batched2d":
             count = args.batch
             self.problems = [dict(pr, gamma=100.0) for pr in W.batched2d(count=count)]
@@ -173,6 +258,8 @@ class Workload:
         if self.batched:
             return "GKB batched solves/s to 1e-8 error (%s, %s GMG-PCG)" % (self.label, self.form_text())
         inner = "GMG-PCG" if self.inner == 1 else "CG"
+        if self.learned:
+            inner = "flexible CG, V-cycle with U-Net at %d^2 (%s form)" % (self.unet_side, self.learned)
         return "GKB time-to-1e-8 error (%s, %s %s)" % (self.label, self.form_text(), inner)
 
     def form_text(self):
@@ -182,7 +269,7 @@ class Workload:
         return "solves/s" if self.batched else "s"
 
 
-def make_handle(gk, torch, pr, wk, form, profile=0):
+def make_handle(gk, torch, pr, wk, form, profile=0, learned=None):
     opt = gk.gkb_default_options()
     opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
     opt.inner = wk.inner
@@ -191,7 +278,12 @@ def make_handle(gk, torch, pr, wk, form, profile=0):
     opt.maxit_inner = 20000 if wk.inner == 0 else 5000
     opt.profile = profile
     opt.stream = torch.cuda.current_stream().cuda_stream
+    if learned:
+        opt.inner = gk.GKB_INNER_FCG_UNET if learned == "replace" else gk.GKB_INNER_FCG_UNET_MG
+        opt.unet_side = wk.unet_side
     h = gk.gkb_create(opt)
+    if learned:
+        gk.gkb_set_unet(h, wk.net)
     mu = pr["mu"]
     import numpy as np
     if np.isscalar(mu):
@@ -205,12 +297,13 @@ def make_handle(gk, torch, pr, wk, form, profile=0):
 class Bound:
     """Handles plus device/host buffers of a workload, and its step."""
 
-    def __init__(self, gk, torch, wk, form, profile=0, subset=None):
+    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default"):
         import numpy as np
         self.gk, self.torch, self.wk = gk, torch, wk
         probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
         self.probs = probs
-        self.hs = [make_handle(gk, torch, pr, wk, form, profile) for pr in probs]
+        lf = wk.learned if learned == "default" else learned
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf) for pr in probs]
         self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
         for h, pr in zip(self.hs, probs):
             m, n = gk.gkb_layout(h)
@@ -272,14 +365,29 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
             launches[k] = launches.get(k, 0) + st["kernel_launches"][k]
     B.destroy()
     table = PER_UNIT[wk.dim]
-    cand = {k: v for k, v in ms.items() if k in table}
+    cand = {k: v for k, v in ms.items() if k in table or (k == "unet" and wk.learned)}
     top = max(cand, key=cand.get)
     s = 8.0 if form == "fp64" else 4.0
+    t = ms[top] * 1e-3
+    total_ms = sum(ms.values())
+    if top == "unet":
+        # BF16 tensor-core convolutions: algorithmic flops of the forwards
+        flops = units[top] / UNET_UNITS_PER_PX * UNET_FLOP_PER_PX
+        bf16_peak, bf16_kind = measured_bf16_sustained()
+        rl = {"bound": "tensor", "achieved": flops / t / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+              "peak_kind": "%s bf16_tflops_sustained (kernel timed inside a long step)" % bf16_kind}
+        rl["frac"] = rl["achieved"] / rl["peak"]
+        rl["kernel_class"] = top
+        rl["launches"] = launches[top]
+        rl["avg_launch_us"] = ms[top] * 1e3 / max(1, launches[top])
+        rl["share_of_kernel_time"] = ms[top] / total_ms if total_ms else None
+        rl["traffic"] = TRAFFIC.get((wk.name, form, top))
+        rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
+        rl["profiled"] = "1 problem, profiled host-sequenced solve"
+        return rl
     flops = units[top] * table[top][0]
     byts = units[top] * table[top][1] * s
-    t = ms[top] * 1e-3
     alu_peak = (FP64_PEAK_TFLOPS if form == "fp64" else FP32_PEAK_TFLOPS) * 1e12
-    total_ms = sum(ms.values())
     if form == "fp64" and flops / alu_peak > byts / (hbm_peak * 1e9):
         rl = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
               "peak_kind": "FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe measured 1.25)"}
@@ -323,6 +431,14 @@ def cpu_oracle_sample(wk, args):
         full = sum(p["m"] + p["ncells"] for p in wk.problems)
         part = pr["m"] + pr["ncells"]
         desc = "%d^3 cavity, gamma %g" % (n_s, gammas[0])
+    elif kind == "varvisc":
+        pr = W.varvisc2d(n_s)
+        grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+        ogkb.solve(grid, mac.assemble(grid, pr["mu"], gammas[0]), pr["g"], pr["r"], tol=args.tol, delay=args.delay,
+                   inner="direct")
+        full = sum(p["m"] + p["ncells"] for p in wk.problems)
+        part = pr["m"] + pr["ncells"]
+        desc = "%dx%d log-normal viscosity cavity, gamma %g" % (n_s, n_s, gammas[0])
     elif kind == "poiseuille":
         pr = W.poiseuille(32, shifted=False, guess=True)
         grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
@@ -399,6 +515,9 @@ def run_ours(args, ws, rank, local):
     gk.load()
     hbm_peak, peak_kind = measured_peaks()
     wk = Workload(args)
+    training = None
+    if wk.learned:
+        wk.net, training = train_network(gk, torch, wk, args)
     t0 = time.perf_counter()
     B = Bound(gk, torch, wk, wk.form)
     setup_s = time.perf_counter() - t0
@@ -454,9 +573,9 @@ def run_ours(args, ws, rank, local):
         return 0
     rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
-    if not args.no_forms and not wk.batched and wk.inner == 1:
-        other = "mixed" if wk.form == "fp64" else "fp64"
-        B2 = Bound(gk, torch, wk, other)
+
+    def time_form(form, learned):
+        B2 = Bound(gk, torch, wk, form, learned=learned)
         for _ in range(2):
             B2.step(args)
         vals = []
@@ -471,9 +590,23 @@ def run_ours(args, ws, rank, local):
             vals.append(e0.elapsed_time(e1) / 1e3)
         st2 = B2.stats()
         B2.destroy()
-        forms[other] = {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
-                        "inner_iterations": [s["inner_iterations"] for s in st2]}
-        forms[wk.form] = {"s_per_step": ms / 1e3, "outer_iterations": outer, "inner_iterations": inner}
+        return {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
+                "inner_iterations": [s["inner_iterations"] for s in st2],
+                "inner_fallbacks": [s["inner_fallbacks"] for s in st2]}
+
+    if not args.no_forms and not wk.batched and wk.inner == 1:
+        head = {"s_per_step": ms / 1e3, "outer_iterations": outer, "inner_iterations": inner,
+                "inner_fallbacks": [s["inner_fallbacks"] for s in stats]}
+        if wk.learned:
+            forms["learned_" + wk.learned + "_" + wk.form] = head
+            other = "composite" if wk.learned == "replace" else "replace"
+            forms["learned_" + other + "_" + wk.form] = time_form(wk.form, other)
+            forms["gmg_pcg_" + wk.form] = time_form(wk.form, None)
+            forms["gmg_pcg_fp64"] = time_form("fp64", None)
+        else:
+            other = "mixed" if wk.form == "fp64" else "fp64"
+            forms[other] = time_form(other, None)
+            forms[wk.form] = head
     cpu = None
     if not args.no_cpu_baseline:
         t_cpu, scale, desc = cpu_oracle_sample(wk, args)
@@ -498,6 +631,10 @@ def run_ours(args, ws, rank, local):
         "inner_iterations": inner if len(inner) <= 8 else {"min": min(inner), "max": max(inner), "sum": sum(inner)},
         "status": status, "setup_s": setup_s, "forms": forms, "finite_output": finite,
     }
+    if training:
+        line["training"] = training
+    if wk.net is not None:
+        gk.gkb_unet_destroy(wk.net)
     print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -514,6 +651,8 @@ def run_probe(args, local):
     gk.load()
     wk = Workload(args)
     wk.problems = wk.problems[:1]
+    if wk.learned:   # untrained weights: the launches are the same
+        wk.net = gk.gkb_unet_create(3, 16, 32, 2, 1, torch.cuda.current_stream().cuda_stream)
     B = Bound(gk, torch, wk, wk.form)
     if args.probe == "precond":
         gk.gkb_precond(B.hs[0], B.g[0], B.w[0])
@@ -531,7 +670,15 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["stokes2d", "stokes3d", "poiseuille", "batched2d"], default="stokes2d")
+    ap.add_argument("--workload", choices=["stokes2d", "stokes3d", "poiseuille", "batched2d", "varvisc2d"],
+                    default="stokes2d")
+    ap.add_argument("--unet-side", type=int, default=512, help="varvisc2d: level (cells per side) of the network")
+    ap.add_argument("--train-pairs", type=int, default=10000)
+    ap.add_argument("--harvest-seconds", type=float, default=120.0)
+    ap.add_argument("--train-steps", type=int, default=800)
+    ap.add_argument("--train-batch", type=int, default=8)
+    ap.add_argument("--train-lr", type=float, default=1e-3)
+    ap.add_argument("--learned-form", choices=["replace", "composite"], default="replace")
     ap.add_argument("--form", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=256)

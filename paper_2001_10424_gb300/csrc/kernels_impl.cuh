@@ -291,13 +291,45 @@ __device__ __noinline__ T patch_solve(const Lvl& L, const T* r, int e0, int e1, 
   return patch_solve_inl<T, VarMu, E>(L, r, e, ce, slot);
 }
 
+// Variable viscosity: the inverse of every patch matrix is stored once per
+// level (symmetric, 10 entries, zero in the rows and columns of inactive
+// faces), as planes of vtab_plane(L) values indexed by the padded index of
+// the patch's edge (node in 2D); one group of 10 planes per orientation in 3D.
+__host__ __device__ __forceinline__ long long vtab_plane(const Lvl& L) {
+  return (L.dim == 3 ? (long long)(L.n[2] + 1) : 1LL) * L.S;
+}
+
+// packed index of entry (r, c) of a symmetric 4 x 4 matrix, r <= c
+__host__ __device__ __forceinline__ int sym4(int r, int c) {
+  return r <= c ? (r * (7 - r)) / 2 + c : (c * (7 - c)) / 2 + r;
+}
+
+// row `slot` of the stored inverse of patch e applied to the patch residual
+template <typename T, int E>
+__device__ __forceinline__ T patch_vtab_row(const Lvl& L, const T* r, const int e[3], long long ce, int slot,
+                                            const T* __restrict__ vtab) {
+  constexpr int a = EAx<E>::a, b = EAx<E>::b;
+  const long long Q = vtab_plane(L);
+  const T* t = vtab + (size_t)(L.dim == 3 ? E : 0) * 10 * Q + ce;
+  const T* ra = r + L.off[a] + ce;
+  const T* rb = r + L.off[b] + ce;
+  // faces outside the store (below the first node) are inactive: coefficient 0
+  const T r0 = e[b] > 0 ? __ldg(ra - strd<b>(L)) : (T)0;
+  const T r2 = e[a] > 0 ? __ldg(rb - strd<a>(L)) : (T)0;
+  return __ldg(t + sym4(slot, 0) * Q) * r0 + __ldg(t + sym4(slot, 1) * Q) * __ldg(ra) +
+         __ldg(t + sym4(slot, 2) * Q) * r2 + __ldg(t + sym4(slot, 3) * Q) * __ldg(rb);
+}
+
 // contribution of the patch of edge e (padded index ce) to slot `slot` of z = C r
+// (table: the class inverses for constant viscosity, the per-patch inverses
+// for variable viscosity)
 template <typename T, bool VarMu, int E>
 __device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e[3], long long ce, int slot,
                                            const T* __restrict__ table) {
   bool act[4];
   T rp[4];
-  if (VarMu || table == nullptr) {
+  if (VarMu) return patch_vtab_row<T, E>(L, r, e, ce, slot, table);
+  if (table == nullptr) {
     if (E == 2 && L.dim == 2) return patch_solve_inl<T, VarMu, E>(L, r, e, ce, slot);
     return patch_solve<T, VarMu, E>(L, r, e[0], e[1], e[2], ce, slot);
   }
@@ -474,6 +506,41 @@ __global__ void k_patch_table(Lvl L, T* table) {
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 4; ++c)
       table[(size_t)t * 16 + r * 4 + c] = (act[r] && act[c]) ? (T)inv[r][c] : (T)0;
+}
+
+// Per-patch inverses for variable viscosity (one thread per edge of
+// orientation E; e[a] in [0, n_a], e[b] in [0, n_b], e[E] in [0, n_E - 1]):
+// the patch matrix in the level's precision, Gauss-Jordan in FP64.
+template <typename T, int E>
+__global__ void k_patch_vtab(Lvl L, T* __restrict__ vtab) {
+  constexpr int a = EAx<E>::a, b = EAx<E>::b;
+  const int e[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
+                    (int)blockIdx.z};
+  if (e[a] > L.n[a] || e[b] > L.n[b]) return;
+  if (L.dim == 3 && e[E] >= L.n[E]) return;
+  T Mt[4][4];
+  bool act[4];
+  patch_matrix<T, true, E>(L, e, Mt, act);
+  double Mp[4][4], inv[4][4];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      Mp[r][c] = (double)Mt[r][c];
+      inv[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < 4; ++c) {
+    const double piv = 1.0 / Mp[c][c];
+    for (int k2 = 0; k2 < 4; ++k2) { Mp[c][k2] *= piv; inv[c][k2] *= piv; }
+    for (int r = 0; r < 4; ++r) {
+      if (r == c) continue;
+      const double f = Mp[r][c];
+      for (int k2 = 0; k2 < 4; ++k2) { Mp[r][k2] -= f * Mp[c][k2]; inv[r][k2] -= f * inv[c][k2]; }
+    }
+  }
+  const long long Q = vtab_plane(L);
+  T* t = vtab + (size_t)(L.dim == 3 ? E : 0) * 10 * Q + cix(L, e[0], e[1], e[2]);
+  for (int r = 0; r < 4; ++r)
+    for (int c = r; c < 4; ++c)
+      t[(long long)sym4(r, c) * Q] = (act[r] && act[c]) ? (T)(0.5 * (inv[r][c] + inv[c][r])) : (T)0;
 }
 
 // ---------------------------------------------------------------------------

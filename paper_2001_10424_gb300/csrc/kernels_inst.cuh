@@ -55,28 +55,30 @@ void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream
 #endif
 
 // variable-viscosity smoother launches, compiled in their own units (6, 7)
-void launch_cheb_varmu(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, cudaStream_t s);
-void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, cudaStream_t s);
+void launch_cheb_varmu(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* vtab,
+                       cudaStream_t s);
+void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, const KT* vtab, cudaStream_t s);
 
 #if GKB_IN_PART(3)
 template <>
 void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* table,
                    cudaStream_t s) {
   ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) launch_cheb_varmu(L, r, x, d, ca, cb, x_zero, s);
+  if (GKB_VARMU(L)) launch_cheb_varmu(L, r, x, d, ca, cb, x_zero, table, s);
   else k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
 }
 #endif
 
 #if GKB_IN_PART(6)
-void launch_cheb_varmu(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, cudaStream_t s) {
-  k_cheb<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, nullptr);
+void launch_cheb_varmu(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* vtab,
+                       cudaStream_t s) {
+  k_cheb<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, vtab);
 }
 #endif
 
 #if GKB_IN_PART(7)
-void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, cudaStream_t s) {
-  k_patch<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, nullptr);
+void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, const KT* vtab, cudaStream_t s) {
+  k_patch<KT, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, vtab);
 }
 #endif
 
@@ -84,14 +86,34 @@ void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, cudaStream_t s) {
 template <>
 void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStream_t s) {
   ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) launch_patch_varmu(L, r, z, s);
+  if (GKB_VARMU(L)) launch_patch_varmu(L, r, z, table, s);
   else k_patch<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, z, table);
+}
+
+template <>
+long long Ops<KT>::patch_table_len(const Lvl& L) {
+  if (!GKB_VARMU(L)) return 3 * 75 * 16;
+  return (L.dim == 3 ? 3 : 1) * 10 * vtab_plane(L);
 }
 
 template <>
 void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
   ProfScope ps_(GKB_KC_LAYOUT, s, 0);
-  k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
+  if (!GKB_VARMU(L)) {
+    k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
+    return;
+  }
+  // variable viscosity: the per-patch inverses (entries never written stay 0)
+  cudaMemsetAsync(table, 0, patch_table_len(L) * sizeof(KT), s);
+  const dim3 blk(32, 8);
+  const dim3 g((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 7) / 8, L.dim == 3 ? L.n[2] + 1 : 1);
+  if (L.dim == 2) {
+    k_patch_vtab<KT, 2><<<g, blk, 0, s>>>(L, table);
+  } else {
+    k_patch_vtab<KT, 0><<<g, blk, 0, s>>>(L, table);
+    k_patch_vtab<KT, 1><<<g, blk, 0, s>>>(L, table);
+    k_patch_vtab<KT, 2><<<g, blk, 0, s>>>(L, table);
+  }
 }
 #endif
 

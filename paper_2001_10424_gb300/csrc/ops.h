@@ -22,7 +22,9 @@ struct Ops {
                    cudaStream_t s);
   // z = C r (additive patch preconditioner)
   static void patch(const Lvl& L, const T* r, T* z, const T* table, cudaStream_t s);
-  // inverse patch matrices of the constant-coefficient classes (3*75*16 entries)
+  // length of the smoother's inverse table of level L: the patch classes
+  // (3*75*16 entries) for constant viscosity, every patch for variable
+  static long long patch_table_len(const Lvl& L);
   static void patch_table(const Lvl& L, T* table, cudaStream_t s);
   // y = scale * A p (faces from cells)
   static void grad(const Lvl& L, const T* p, T* y, T scale, cudaStream_t s);

@@ -318,12 +318,11 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     if (l < nl - 1) {
       V.r.alloc(V.L.nvel);
       V.d.alloc(V.L.nvel);
-      const bool var = (sizeof(T) == 8) ? V.L.mu64 != nullptr : V.L.mu32 != nullptr;
-      if (!var) {
-        V.table.alloc(3 * 75 * 16);
-        Ops<T>::patch_table(V.L, V.table.p, s);
-        GKB_CUDA(cudaGetLastError());
-      }
+      // constant viscosity: inverses of the 75 patch classes; variable
+      // viscosity: the inverse of every patch
+      V.table.alloc(Ops<T>::patch_table_len(V.L));
+      Ops<T>::patch_table(V.L, V.table.p, s);
+      GKB_CUDA(cudaGetLastError());
     }
   }
   // power iteration for lambda_max(C M) on every smoothing level

@@ -269,8 +269,9 @@ class Workload:
         return "solves/s" if self.batched else "s"
 
 
-def make_handle(gk, torch, pr, wk, form, profile=0, learned=None):
+def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0):
     opt = gk.gkb_default_options()
+    opt.autotune = autotune
     opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
     opt.inner = wk.inner
     opt.tol_inner = wk.tol_inner
@@ -297,13 +298,13 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None):
 class Bound:
     """Handles plus device/host buffers of a workload, and its step."""
 
-    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default"):
+    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0):
         import numpy as np
         self.gk, self.torch, self.wk = gk, torch, wk
         probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
         self.probs = probs
         lf = wk.learned if learned == "default" else learned
-        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf) for pr in probs]
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune) for pr in probs]
         self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
         for h, pr in zip(self.hs, probs):
             m, n = gk.gkb_layout(h)
@@ -574,8 +575,10 @@ def run_ours(args, ws, rank, local):
     rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
 
-    def time_form(form, learned):
-        B2 = Bound(gk, torch, wk, form, learned=learned)
+    def time_form(form, learned, autotune=0):
+        t_setup = time.perf_counter()
+        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune)
+        t_setup = time.perf_counter() - t_setup
         for _ in range(2):
             B2.step(args)
         vals = []
@@ -589,10 +592,18 @@ def run_ours(args, ws, rank, local):
             e1.synchronize()
             vals.append(e0.elapsed_time(e1) / 1e3)
         st2 = B2.stats()
+        out = {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
+               "inner_iterations": [s["inner_iterations"] for s in st2],
+               "inner_fallbacks": [s["inner_fallbacks"] for s in st2]}
+        if autotune:
+            out["setup_s_with_tuning"] = t_setup
+            out["tuned"] = []
+            for h in B2.hs:
+                o = gk.gkb_get_options(h)
+                out["tuned"].append({"smoother_degree": o.smoother_degree, "kernel_variant": o.kernel_variant,
+                                     "coarse_max": o.coarse_max})
         B2.destroy()
-        return {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
-                "inner_iterations": [s["inner_iterations"] for s in st2],
-                "inner_fallbacks": [s["inner_fallbacks"] for s in st2]}
+        return out
 
     if not args.no_forms and not wk.batched and wk.inner == 1:
         head = {"s_per_step": ms / 1e3, "outer_iterations": outer, "inner_iterations": inner,
@@ -607,6 +618,8 @@ def run_ours(args, ws, rank, local):
             other = "mixed" if wk.form == "fp64" else "fp64"
             forms[other] = time_form(other, None)
             forms[wk.form] = head
+        if not args.no_autotune:
+            forms[wk.form + "_autotuned"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=1)
     cpu = None
     if not args.no_cpu_baseline:
         t_cpu, scale, desc = cpu_oracle_sample(wk, args)
@@ -688,6 +701,7 @@ def main():
     ap.add_argument("--delay", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuned form in `forms`")
     ap.add_argument("--probe", choices=["precond", "solve"], default=None,
                     help="profiling target: set up one handle and run one V-cycle or one solve")
     args = ap.parse_args()

@@ -143,6 +143,16 @@ typedef struct {
                              (or whose preconditioned vector is not finite)
                              continues as plain GMG-PCG from its iterate;
                              0 disables the switch                            */
+  int autotune;           /* 1: gkb_set_problem searches smoother_degree (1..3),
+                             kernel_variant (0..2) and coarse_max (8, 16, 32)
+                             for the fastest inner solve (device time of one
+                             GMG-PCG solve to tol_inner) and keeps it; results
+                             are cached per device, grid, viscosity kind,
+                             precision, inner solver and gamma decade in the
+                             process and, when the environment variable
+                             GKB_TUNE_CACHE names a file, in that file (read
+                             once, appended). gkb_get_options returns the
+                             choice. Multigrid inner solvers only.           */
   void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
 } gkb_options;
 
@@ -156,6 +166,7 @@ typedef struct {
   double solve_seconds;       /* last gkb_solve wall time                    */
   int levels;                 /* multigrid levels (0 without GMG)            */
   int inner_fallbacks;        /* flexible inner solves that switched to GMG-PCG */
+  double tuned_inner_ms;      /* autotune: inner-solve device time of the choice (0 if not tuned) */
   int64_t kernel_launches[GKB_KC_COUNT];  /* launches per class, last solve  */
   int64_t kernel_units[GKB_KC_COUNT];     /* work per class: velocity unknowns
                                              of the launch's level summed over
@@ -184,6 +195,9 @@ int gkb_set_problem(gkb_handle h, const gkb_grid* grid, const double* viscosity,
 
 /* Sizes of the compact velocity (m) and pressure (n) vectors. */
 int gkb_layout(gkb_handle h, int64_t* m, int64_t* n);
+
+/* The handle's effective options (after autotuning, if any). */
+int gkb_get_options(gkb_handle h, gkb_options* out);
 
 /* Fold a Dirichlet normal velocity on one side into (g, r) in place: for
  * every boundary face b of that side with value u_b, the momentum row of the

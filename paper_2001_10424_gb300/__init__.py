@@ -49,6 +49,7 @@ EXPORTED = [
     "gkb_unet_create", "gkb_unet_num_params", "gkb_unet_get_params", "gkb_unet_set_params",
     "gkb_unet_forward", "gkb_unet_loss_grad", "gkb_unet_adam_step", "gkb_unet_last_error", "gkb_unet_destroy",
     "gkb_unet_train", "gkb_unet_set_target_scale", "gkb_unet_get_target_scale", "gkb_set_unet", "gkb_harvest_pairs",
+    "gkb_get_options",
 ]
 GKB_NOALLOC_MAX_ELEMS = 1048576
 
@@ -63,14 +64,15 @@ class gkb_options(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("unet_side", ctypes.c_int),
-                ("fcg_rho", ctypes.c_double), ("stream", ctypes.c_void_p)]
+                ("fcg_rho", ctypes.c_double), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class gkb_stats_t(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("outer_iterations", ctypes.c_int), ("inner_solves", ctypes.c_int),
                 ("inner_iterations", ctypes.c_int64), ("estimate", ctypes.c_double),
                 ("setup_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
-                ("levels", ctypes.c_int), ("inner_fallbacks", ctypes.c_int), ("kernel_launches", ctypes.c_int64 * 10),
+                ("levels", ctypes.c_int), ("inner_fallbacks", ctypes.c_int), ("tuned_inner_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64 * 10),
                 ("kernel_units", ctypes.c_int64 * 10), ("kernel_ms", ctypes.c_double * 10)]
 
 
@@ -123,6 +125,7 @@ def load(path=None):
         "gkb_unet_set_target_scale": (i, [_P, ctypes.c_float]),
         "gkb_unet_get_target_scale": (i, [_P, ctypes.POINTER(ctypes.c_float)]),
         "gkb_set_unet": (i, [_P, _P]),
+        "gkb_get_options": (i, [_P, ctypes.POINTER(gkb_options)]),
         "gkb_harvest_pairs": (i, [_P, _P, i, _P, _P, ctypes.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
@@ -313,6 +316,12 @@ def gkb_unet_get_target_scale(u):
     v = ctypes.c_float()
     _ucheck(u, load().gkb_unet_get_target_scale(u, ctypes.byref(v)))
     return v.value
+
+
+def gkb_get_options(h):
+    o = gkb_options()
+    _check(h, load().gkb_get_options(h, ctypes.byref(o)))
+    return o
 
 
 def gkb_set_unet(h, u):

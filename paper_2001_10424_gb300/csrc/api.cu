@@ -76,7 +76,8 @@ int gkb_create(gkb_handle* out, const gkb_options* opt) {
   *out = nullptr;
   if (opt->precision != GKB_PREC_FP64 && opt->precision != GKB_PREC_MIXED) return GKB_ERR_INVALID_ARG;
   if (opt->inner < GKB_INNER_CG || opt->inner > GKB_INNER_FCG_UNET_MG) return GKB_ERR_INVALID_ARG;
-  if (opt->unet_side < 0 || !(opt->fcg_rho >= 0 && opt->fcg_rho < 1)) return GKB_ERR_INVALID_ARG;
+  if (opt->unet_side < 0 || !(opt->fcg_rho >= 0 && opt->fcg_rho < 1) || opt->autotune < 0 || opt->autotune > 1)
+    return GKB_ERR_INVALID_ARG;
   if (!(opt->tol_inner > 0) || opt->maxit < 0 || opt->maxit > 100000000 || opt->maxit_inner < 1 ||
       opt->smoother_degree < 1 || opt->smoother_degree > 16 || opt->coarse_max < 4 ||
       !(opt->mixed_rtol > 0 && opt->mixed_rtol < 1) || opt->kernel_variant < 0 || opt->kernel_variant > 2)
@@ -113,6 +114,14 @@ int gkb_set_unet(gkb_handle h, gkb_unet u) {
 
 int gkb_harvest_pairs(gkb_handle h, const double* f, int max_pairs, float* x_img, float* t_img, int* n_pairs) {
   return guarded(h, [&] { return h->s.harvest(f, max_pairs, x_img, t_img, n_pairs); });
+}
+
+int gkb_get_options(gkb_handle h, gkb_options* out) {
+  return guarded(h, [&] {
+    if (!out) return GKB_ERR_INVALID_ARG;
+    *out = h->s.opt;
+    return GKB_OK;
+  });
 }
 
 int gkb_layout(gkb_handle h, int64_t* m, int64_t* n) {

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstddef>
+#include <map>
 #include <mutex>
 #include <chrono>
 #include <cstdio>
@@ -266,6 +267,35 @@ static void abandon_captures(std::initializer_list<cudaStream_t> ss) {
 // multigrid hierarchy
 // ---------------------------------------------------------------------------
 
+// In-place Gauss-Jordan inversion of an SPD matrix, pivot k: save the
+// scaled pivot row (entry k = 1/p) and the pivot column, then update every
+// entry (a_ij - a_ik a_kj / p; the pivot column becomes -a_ik / p)
+__global__ void k_gj_save(const double* __restrict__ A, int m, int k, double* __restrict__ rowk,
+                          double* __restrict__ colk, int* bad) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const double p = A[(size_t)k * m + k];
+  if (t == 0 && !(p > 0.0)) *bad = 1;
+  colk[t] = A[(size_t)t * m + k];
+  rowk[t] = (t == k) ? 1.0 / p : A[(size_t)k * m + t] / p;
+}
+
+__global__ void k_gj_update(double* __restrict__ A, int m, int k, const double* __restrict__ rowk,
+                            const double* __restrict__ colk) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= m || j >= m) return;
+  double& a = A[(size_t)i * m + j];
+  if (i == k) a = rowk[j];
+  else a = ((j == k) ? 0.0 : a) - colk[i] * rowk[j];
+}
+
+template <typename T>
+__global__ void k_gj_store(const double* __restrict__ A, int m, T* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x, r = blockIdx.y * blockDim.y + threadIdx.y;
+  if (r >= m || c >= m) return;
+  out[(size_t)r * m + c] = (T)(0.5 * (A[(size_t)r * m + c] + A[(size_t)c * m + r]));
+}
+
 template <typename T>
 void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, const RedBuf& red,
                    double* scratch, cudaStream_t s) {
@@ -365,7 +395,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
       rho = rn;
     }
   }
-  // coarsest level: dense M by probing with unit vectors, inverted on host
+  // coarsest level: dense M, inverted once
   Level& Cl = lev.back();
   const Lvl& L = Cl.L;
   Compact cmp = make_compact(L);
@@ -373,67 +403,97 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
   if (m > 4096) throw Error{GKB_ERR_INVALID_ARG, "coarsest multigrid level too large (" + std::to_string(m) + " unknowns)"};
   coarse_m = m;
   std::vector<long long> pidx(m);
+  std::vector<int> ucomp(m), upos(3 * (size_t)m);  // component and (i, j, k) of every unknown
   {
     int t = 0;
     for (int comp = 0; comp < L.dim; ++comp)
       for (int k = 0; k < cmp.ext[comp][2]; ++k)
         for (int j = 0; j < cmp.ext[comp][1]; ++j)
-          for (int i = 0; i < cmp.ext[comp][0]; ++i)
-            pidx[t++] = L.off[comp] + cix(L, i + cmp.lo[comp][0], j + cmp.lo[comp][1], k + cmp.lo[comp][2]);
+          for (int i = 0; i < cmp.ext[comp][0]; ++i) {
+            const int pi = i + cmp.lo[comp][0], pj = j + cmp.lo[comp][1], pk = k + cmp.lo[comp][2];
+            pidx[t] = L.off[comp] + cix(L, pi, pj, pk);
+            ucomp[t] = comp;
+            upos[3 * t] = pi;
+            upos[3 * t + 1] = pj;
+            upos[3 * t + 2] = pk;
+            ++t;
+          }
   }
-  std::vector<double> A((size_t)m * m);
+  // M by colored probing: faces interact only within one cell in every axis
+  // (W links and the grad-div coupling of the faces of a cell), so the
+  // columns of one component whose positions agree modulo 3 in every axis
+  // have disjoint row supports and one product recovers all of them
+  std::vector<int> row_of(L.nvel, -1);
+  for (int r = 0; r < m; ++r) row_of[pidx[r]] = r;
+  std::vector<double> A((size_t)m * m, 0.0);
   {
     DevBuf<T> e, y;
     e.alloc(L.nvel);
     y.alloc(L.nvel);
-    std::vector<T> hy(L.nvel);
-    const T one = (T)1;
-    for (int c = 0; c < m; ++c) {
-      GKB_CUDA(cudaMemsetAsync(e.p, 0, L.nvel * sizeof(T), s));
-      GKB_CUDA(cudaMemcpyAsync(e.p + pidx[c], &one, sizeof(T), cudaMemcpyHostToDevice, s));
-      Ops<T>::apply(L, 1, e.p, y.p, s);
-      GKB_CUDA(cudaMemcpyAsync(hy.data(), y.p, L.nvel * sizeof(T), cudaMemcpyDeviceToHost, s));
-      GKB_CUDA(cudaStreamSynchronize(s));
-      for (int r = 0; r < m; ++r) A[(size_t)r * m + c] = (double)hy[pidx[r]];
-    }
+    std::vector<T> he(L.nvel), hy(L.nvel);
+    const int ncol = (L.dim == 3) ? 27 : 9;
+    for (int comp = 0; comp < L.dim; ++comp)
+      for (int color = 0; color < ncol; ++color) {
+        const int cc[3] = {color % 3, (color / 3) % 3, color / 9};
+        std::fill(he.begin(), he.end(), (T)0);
+        std::vector<int> cols;
+        for (int c = 0; c < m; ++c) {
+          if (ucomp[c] != comp || upos[3 * c] % 3 != cc[0] || upos[3 * c + 1] % 3 != cc[1] ||
+              upos[3 * c + 2] % 3 != cc[2])
+            continue;
+          he[pidx[c]] = (T)1;
+          cols.push_back(c);
+        }
+        if (cols.empty()) continue;
+        GKB_CUDA(cudaMemcpyAsync(e.p, he.data(), L.nvel * sizeof(T), cudaMemcpyHostToDevice, s));
+        Ops<T>::apply(L, 1, e.p, y.p, s);
+        GKB_CUDA(cudaMemcpyAsync(hy.data(), y.p, L.nvel * sizeof(T), cudaMemcpyDeviceToHost, s));
+        GKB_CUDA(cudaStreamSynchronize(s));
+        for (int c : cols) {
+          const int i = upos[3 * c], j = upos[3 * c + 1], k = upos[3 * c + 2];
+          for (int rc = 0; rc < L.dim; ++rc)
+            for (int dk = (L.dim == 3 ? -1 : 0); dk <= (L.dim == 3 ? 1 : 0); ++dk)
+              for (int dj = -1; dj <= 1; ++dj)
+                for (int di = -1; di <= 1; ++di) {
+                  const int ii = i + di, jj = j + dj, kk = k + dk;
+                  // the faces of component rc: position n along axis rc, n - 1 along the others
+                  if (ii < 0 || jj < 0 || kk < 0 || ii > L.n[0] - (rc != 0) || jj > L.n[1] - (rc != 1) ||
+                      kk > L.n[2] - (rc != 2 || L.dim == 2 ? 1 : 0))
+                    continue;
+                  const long long pr = L.off[rc] + cix(L, ii, jj, kk);
+                  const int r = row_of[pr];
+                  if (r >= 0) A[(size_t)r * m + c] = (double)hy[pr];
+                }
+        }
+      }
   }
-  // symmetrise, Cholesky, explicit inverse
+  // symmetrise; in-place Gauss-Jordan inversion on the device (SPD: no pivoting)
   for (int r = 0; r < m; ++r)
     for (int c = r + 1; c < m; ++c) {
       const double a = 0.5 * (A[(size_t)r * m + c] + A[(size_t)c * m + r]);
       A[(size_t)r * m + c] = A[(size_t)c * m + r] = a;
     }
-  std::vector<double> Lc((size_t)m * m, 0.0);
-  for (int j = 0; j < m; ++j) {
-    double sjj = A[(size_t)j * m + j];
-    for (int k = 0; k < j; ++k) sjj -= Lc[(size_t)j * m + k] * Lc[(size_t)j * m + k];
-    if (!(sjj > 0)) throw Error{GKB_ERR_NOT_SPD, "coarse-level matrix is not positive definite"};
-    const double ljj = sqrt(sjj);
-    Lc[(size_t)j * m + j] = ljj;
-    for (int i = j + 1; i < m; ++i) {
-      double sij = A[(size_t)i * m + j];
-      for (int k = 0; k < j; ++k) sij -= Lc[(size_t)i * m + k] * Lc[(size_t)j * m + k];
-      Lc[(size_t)i * m + j] = sij / ljj;
+  {
+    DevBuf<double> Ad, rowk, colk;
+    DevBuf<int> bad;
+    Ad.alloc((size_t)m * m);
+    rowk.alloc(m);
+    colk.alloc(m);
+    bad.alloc(1);
+    GKB_CUDA(cudaMemcpyAsync(Ad.p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    const dim3 b2(32, 8), g2((m + 31) / 32, (m + 7) / 8);
+    for (int k = 0; k < m; ++k) {
+      { ProfScope ps_(GKB_KC_COARSE, s); k_gj_save<<<(m + 255) / 256, 256, 0, s>>>(Ad.p, m, k, rowk.p, colk.p, bad.p); }
+      { ProfScope ps_(GKB_KC_COARSE, s); k_gj_update<<<g2, b2, 0, s>>>(Ad.p, m, k, rowk.p, colk.p); }
     }
+    coarse_inv.alloc((size_t)m * m);
+    { ProfScope ps_(GKB_KC_COARSE, s); k_gj_store<T><<<g2, b2, 0, s>>>(Ad.p, m, coarse_inv.p); }
+    GKB_CUDA(cudaGetLastError());
+    int hbad = 0;
+    GKB_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GKB_CUDA(cudaStreamSynchronize(s));
+    if (hbad) throw Error{GKB_ERR_NOT_SPD, "coarse-level matrix is not positive definite"};
   }
-  std::vector<double> inv((size_t)m * m, 0.0), col(m);
-  for (int c = 0; c < m; ++c) {
-    for (int i = 0; i < m; ++i) {
-      double sv = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) sv -= Lc[(size_t)i * m + k] * col[k];
-      col[i] = sv / Lc[(size_t)i * m + i];
-    }
-    for (int i = m - 1; i >= 0; --i) {
-      double sv = col[i];
-      for (int k = i + 1; k < m; ++k) sv -= Lc[(size_t)k * m + i] * col[k];
-      col[i] = sv / Lc[(size_t)i * m + i];
-    }
-    for (int i = 0; i < m; ++i) inv[(size_t)i * m + c] = col[i];
-  }
-  std::vector<T> invT((size_t)m * m);
-  for (size_t t = 0; t < invT.size(); ++t) invT[t] = (T)(0.5 * (inv[t] + inv[(t % m) * m + t / m]));
-  coarse_inv.alloc((size_t)m * m);
-  GKB_CUDA(cudaMemcpyAsync(coarse_inv.p, invT.data(), invT.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   std::vector<int> idx32(m);
   for (int i = 0; i < m; ++i) idx32[i] = (int)pidx[i];
   coarse_idx.alloc(m);
@@ -1001,16 +1061,46 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   state_mem.alloc(sizeof(CgState) + sizeof(GkbState) + 256);
   cg_dev = (CgState*)state_mem.p;
   gkb_dev = (GkbState*)(state_mem.p + ((sizeof(CgState) + 127) / 128) * 128);
-  // multigrid + CG
+  // GKB vectors
   stats = gkb_stats_t{};
+  if (mixed) {
+    r64.alloc(L64.nvel);
+    f32.alloc(L64.nvel);
+    x32.alloc(L64.nvel);
+  }
+  for (DevBuf<double>* b : {&u, &v, &x, &w, &t, &f, &y0, &wtmp}) b->alloc(L64.nvel);
+  for (DevBuf<double>* b : {&q, &d, &pp, &gq, &bc, &ctmp}) b->alloc(L64.ncell);
+  stage_m.alloc(m);
+  stage_n.alloc(ncell);
+  hist.alloc(4 * (size_t)(opt.maxit + 2));
+  hist_inner.alloc((size_t)opt.maxit + 4);
+  // multigrid + CG (tuned first when asked)
+  tuned_ms = 0;
+  if (opt.autotune && use_gmg) autotune_inner(viscosity != nullptr);
+  else build_inner();
+  stats.tuned_inner_ms = tuned_ms;
+  attach_net_levels();
+  GKB_CUDA(cudaStreamSynchronize(stream));
+  generation += 1;
+  have_problem = true;
+  build_solve_graph();
+  stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// Multigrid hierarchy and CG of the handle's precision from the current
+// options (smoother degree, coarse size, kernel variant).
+void Solver::build_inner() {
+  const bool mixed = opt.precision == GKB_PREC_MIXED;
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || learned_inner();
+  // deep-interior fast paths: variant 0 enables them in FP32 only (faster
+  // there, slower on the FP64 pipe), 1 nowhere, 2 everywhere
+  L64.fast = (opt.kernel_variant == 2) ? 1 : 0;
+  L32.fast = (opt.kernel_variant == 1) ? 0 : 1;
   if (mixed) {
     if (use_gmg) gmg32.build(L32, mu32.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
     cg32.init(L32, use_gmg ? &gmg32 : nullptr, red, cg_dev, cg_host);
     cg32.flex = learned_inner();
     cg32.rho2 = opt.fcg_rho * opt.fcg_rho;
-    r64.alloc(L64.nvel);
-    f32.alloc(L64.nvel);
-    x32.alloc(L64.nvel);
     stats.levels = use_gmg ? (int)gmg32.lev.size() : 0;
   } else {
     if (use_gmg) gmg64.build(L64, mu64.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
@@ -1019,19 +1109,150 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
     cg64.rho2 = opt.fcg_rho * opt.fcg_rho;
     stats.levels = use_gmg ? (int)gmg64.lev.size() : 0;
   }
-  // GKB vectors
-  for (DevBuf<double>* b : {&u, &v, &x, &w, &t, &f, &y0, &wtmp}) b->alloc(L64.nvel);
-  for (DevBuf<double>* b : {&q, &d, &pp, &gq, &bc, &ctmp}) b->alloc(L64.ncell);
-  stage_m.alloc(m);
-  stage_n.alloc(ncell);
-  hist.alloc(4 * (size_t)(opt.maxit + 2));
-  hist_inner.alloc((size_t)opt.maxit + 4);
-  attach_net_levels();
+}
+
+// Device time (ms) of one inner solve M x = f on a fixed pseudo-random f,
+// run as a captured graph like the solver's own; +inf when it fails.
+double Solver::time_inner_solve() {
+  ensure_capture_streams();
+  { ProfScope ps_(GKB_KC_LAYOUT, stream); k_fill_hash<double><<<fgrid(L64), dim3(32, 8), 0, stream>>>(L64, f.p); }
   GKB_CUDA(cudaStreamSynchronize(stream));
-  generation += 1;
-  have_problem = true;
-  build_solve_graph();
-  stats.setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  Profiler* P = g_prof;
+  const int saved = P ? P->phase : -1;
+  if (P) P->phase = 0;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  try {
+    GKB_CUDA(cudaGraphCreate(&g, 0));
+    GKB_CUDA(cudaStreamBeginCaptureToGraph(cap1, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    capture_inner(cap1, cap2);
+    GKB_CUDA(cudaStreamEndCapture(cap1, &g));
+    GKB_CUDA(cudaGraphInstantiate(&ge, g, 0));
+  } catch (...) {
+    if (P) P->phase = saved;
+    abandon_captures({cap2, cap1});
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  if (P) P->phase = saved;
+  cudaGraphDestroy(g);
+  double best = 1e300;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GKB_CUDA(cudaEventCreate(&e0));
+  GKB_CUDA(cudaEventCreate(&e1));
+  bool ok = true;
+  for (int rep = 0; rep < 3 && ok; ++rep) {
+    GKB_CUDA(cudaEventRecord(e0, stream));
+    GKB_CUDA(cudaGraphLaunch(ge, stream));
+    GKB_CUDA(cudaEventRecord(e1, stream));
+    GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, stream));
+    GKB_CUDA(cudaStreamSynchronize(stream));
+    float ms = 0.f;
+    GKB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ok = cg_host->status == ST_OK;
+    if (rep > 0) best = std::min(best, (double)ms);  // the first launch warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  return ok ? best : 1e300;
+}
+
+namespace {
+struct Tuned {
+  int degree, variant, coarse_max;
+  double ms;
+};
+std::mutex g_tune_mutex;
+std::map<std::string, Tuned> g_tune_cache;
+bool g_tune_file_read = false;
+
+const char* tune_file() {
+  const char* p = getenv("GKB_TUNE_CACHE");
+  return (p && *p) ? p : nullptr;
+}
+
+void tune_read_file() {
+  if (g_tune_file_read) return;
+  g_tune_file_read = true;
+  const char* path = tune_file();
+  if (!path) return;
+  FILE* fp = fopen(path, "r");
+  if (!fp) return;
+  char key[512];
+  Tuned t{};
+  while (fscanf(fp, "%511s %d %d %d %lf", key, &t.degree, &t.variant, &t.coarse_max, &t.ms) == 5)
+    g_tune_cache[key] = t;
+  fclose(fp);
+}
+}  // namespace
+
+// Autotuner: search the inner solver's smoother degree (1..3), kernel variant
+// (0..2) and coarse size (8, 16, 32) one after another, each by the device
+// time of a whole inner solve to tol_inner, and keep the fastest; results are
+// cached per device, grid, viscosity kind, precision, inner solver and gamma
+// decade, in the process and (GKB_TUNE_CACHE) in a text file.
+void Solver::autotune_inner(bool var_mu) {
+  int dev = 0;
+  GKB_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  GKB_CUDA(cudaGetDeviceProperties(&prop, dev));
+  std::string name(prop.name);
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  char key[512];
+  snprintf(key, sizeof key, "%s|d%d|%dx%dx%d|%s|p%d|i%d|g%+.0f", name.c_str(), grid.dim, L64.n[0], L64.n[1], L64.n[2],
+           var_mu ? "varmu" : "mu", opt.precision, opt.inner, gamma > 0 ? std::floor(std::log10(gamma)) : -99.0);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_read_file();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      opt.smoother_degree = it->second.degree;
+      opt.kernel_variant = it->second.variant;
+      opt.coarse_max = it->second.coarse_max;
+      tuned_ms = it->second.ms;
+      build_inner();
+      return;
+    }
+  }
+  Tuned best{opt.smoother_degree, opt.kernel_variant, opt.coarse_max, 1e300};
+  auto trial = [&](int deg, int var, int cmax) {
+    opt.smoother_degree = deg;
+    opt.kernel_variant = var;
+    opt.coarse_max = cmax;
+    double ms = 1e300;
+    try {
+      build_inner();
+      ms = time_inner_solve();
+    } catch (const Error& e) {
+      if (e.code != GKB_ERR_INVALID_ARG) throw;  // an infeasible candidate (coarse level too large)
+    }
+    if (ms < best.ms) best = Tuned{deg, var, cmax, ms};
+  };
+  trial(best.degree, best.variant, best.coarse_max);
+  for (int v = 0; v <= 2; ++v)
+    if (v != best.variant) trial(best.degree, v, best.coarse_max);
+  const int v0 = best.variant;
+  for (int deg = 1; deg <= 3; ++deg)
+    if (deg != best.degree) trial(deg, v0, best.coarse_max);
+  const int d0 = best.degree;
+  for (int cmax : {8, 16, 32})
+    if (cmax != best.coarse_max) trial(d0, v0, cmax);
+  if (!(best.ms < 1e300)) throw Error{GKB_ERR_INNER_NOT_CONVERGED, "no autotuning candidate converged"};
+  opt.smoother_degree = best.degree;
+  opt.kernel_variant = best.variant;
+  opt.coarse_max = best.coarse_max;
+  tuned_ms = best.ms;
+  build_inner();
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = best;
+  if (const char* path = tune_file()) {
+    if (FILE* fp = fopen(path, "a")) {
+      fprintf(fp, "%s %d %d %d %.6f\n", key, best.degree, best.variant, best.coarse_max, best.ms);
+      fclose(fp);
+    }
+  }
 }
 
 // The network gives the coarse correction of the level whose longer side is
@@ -1513,6 +1734,7 @@ int Solver::finish(double* w_out, double* p_out, const double* w0, const double*
   stats.estimate = H.est;
   stats.inner_iterations = H.inner_its;
   stats.inner_fallbacks = H.inner_fallbacks;
+  stats.tuned_inner_ms = tuned_ms;
   stats.inner_solves = H.inner_solves;
   return status;
 }

@@ -181,6 +181,10 @@ struct Solver {
   Unet* net = nullptr;            // learned correction (GKB_INNER_FCG_UNET[_MG])
   bool learned_inner() const { return opt.inner == GKB_INNER_FCG_UNET || opt.inner == GKB_INNER_FCG_UNET_MG; }
   void set_net(Unet* u);
+  double tuned_ms = 0;            // inner-solve time of the tuned configuration
+  void build_inner();
+  double time_inner_solve();
+  void autotune_inner(bool var_mu);
   void attach_net_levels();
   void refresh_net();
   void ensure_capture_streams();

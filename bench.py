@@ -60,9 +60,23 @@ UNET_FLOP_PER_PX = (2 * 9 * (3 * 16 + 16 * 16 + 48 * 16 + 16 * 2)
                     + 2 * 9 * (16 * 32 + 32 * 32 + 64 * 32) / 4 + 2 * 9 * (2 * 32 * 32) / 16)
 UNET_UNITS_PER_PX = 4 + 3 / 4 + 2 / 16 + 2
 
-# per-launch DRAM traffic (bytes) of the dominant kernel from ncu captures,
-# keyed by (workload, form, kernel class); summarised under profiles/
-TRAFFIC = {}
+# variable viscosity: the smoother also reads the per-patch inverses (10
+# entries per node in 2D, per edge of each orientation in 3D), in elements
+# per velocity unknown
+VARMU_SMOOTH_EXTRA = {2: 5.0, 3: 10.0}
+
+# DRAM traffic (bytes) of one finest-level launch of the dominant kernel from
+# ncu captures of the current kernels (cold cache), keyed by (workload, form,
+# kernel class); summarised under profiles/
+TRAFFIC = {
+    ("stokes2d", "fp64", "smooth"): 16.85e6 + 0.05e6,      # smoother_residual_stokes2d_1024_fp64_full.md
+    ("stokes2d", "fp64", "residual"): 33.71e6 + 0.04e6,
+    ("varvisc2d", "mixed", "smooth"): 203.05e6 + 47.62e6,  # varvisc_smoother_residual_2048_mixed_full.md
+}
+# algorithmic bytes of the captured finest-level launch per velocity unknown,
+# in elements (first Chebyshev step: r read, d and x written; residual: x, b
+# read, r written)
+CAPTURED_ELEMS = {"smooth": 3.0, "residual": 3.0}
 
 
 def measured_peaks():
@@ -354,6 +368,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     """Profiled step (CUDA events around every launch on its stream): the
     dominant kernel class's algorithmic throughput, summed over its launches
     and divided by their durations."""
+    import numpy as np
     subset = list(range(min(len(wk.problems), 16))) if wk.batched else None
     B = Bound(gk, torch, wk, form, profile=1, subset=subset)
     ms, units, launches = {}, {}, {}
@@ -386,8 +401,10 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
         rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
         rl["profiled"] = "1 problem, profiled host-sequenced solve"
         return rl
+    varmu = any(not np.isscalar(p["mu"]) for p in wk.problems)
+    per_unit_bytes = table[top][1] + (VARMU_SMOOTH_EXTRA[wk.dim] if (top == "smooth" and varmu) else 0.0)
     flops = units[top] * table[top][0]
-    byts = units[top] * table[top][1] * s
+    byts = units[top] * per_unit_bytes * s
     alu_peak = (FP64_PEAK_TFLOPS if form == "fp64" else FP32_PEAK_TFLOPS) * 1e12
     if form == "fp64" and flops / alu_peak > byts / (hbm_peak * 1e9):
         rl = {"bound": "alu", "achieved": flops / t / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -401,6 +418,11 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     rl["avg_launch_us"] = ms[top] * 1e3 / max(1, launches[top])
     rl["share_of_kernel_time"] = ms[top] / total_ms if total_ms else None
     rl["traffic"] = TRAFFIC.get((wk.name, form, top))
+    if rl["traffic"] is not None:
+        m0 = wk.problems[0]["m"]
+        extra = VARMU_SMOOTH_EXTRA[wk.dim] if (top == "smooth" and varmu) else 0.0
+        rl["traffic_basis"] = "ncu DRAM read+write of one finest-level launch (cold cache)"
+        rl["traffic_algorithmic"] = m0 * (CAPTURED_ELEMS.get(top, table[top][1]) + extra) * s
     rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
     rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % len(ms and (subset or [0]))
     return rl

@@ -138,6 +138,12 @@ __device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
 template <typename T>
 __device__ __forceinline__ T ldv(const T* x, long long idx) { return __ldg(x + idx); }
 
+// rounded product that the compiler may not fuse into a neighbouring add:
+// with the explicit fma() of the link sums it fixes every rounding of a W
+// row, so that differently structured paths give bitwise equal rows
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Velocity value of component C at face position p; positions outside the
 // face grid read as 0 (callers only ask for in-grid or wall-adjacent ones).
 template <typename T, int C>
@@ -183,12 +189,12 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
     if (p[C] < L.n[C]) {
       q[C] = p[C] + 1;
       T mu = cell_mu<T, VarMu>(L, p[0], p[1], p[2]);
-      acc += mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+      acc = fma(mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
     }
     if (p[C] > 0) {
       q[C] = p[C] - 1;
       T mu = cell_mu<T, VarMu>(L, q[0], q[1], q[2]);
-      acc += mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+      acc = fma(mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
     }
   }
   const bool half = (p[C] == 0 && L.nat[2 * C]) || (p[C] == L.n[C] && L.nat[2 * C + 1]);
@@ -206,9 +212,9 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
       else mu = edge_mu<T, VarMu, C, 2>(L, p, p[A] + 1);
       if (p[A] + 1 < L.n[A]) {
         q[A] = p[A] + 1;
-        acc += area * mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+        acc = fma(area * mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
       } else if (!L.nat[2 * A + 1]) {
-        acc += (T)2 * area * mu * xf;
+        acc = fma((T)2 * area * mu, xf, acc);
       }
     }
     // - direction: crosses A-face coordinate p[A]
@@ -219,9 +225,9 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
       else mu = edge_mu<T, VarMu, C, 2>(L, p, p[A]);
       if (p[A] > 0) {
         q[A] = p[A] - 1;
-        acc += area * mu * (xf - face_val<T, C>(L, x, q[0], q[1], q[2]));
+        acc = fma(area * mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
       } else if (!L.nat[2 * A]) {
-        acc += (T)2 * area * mu * xf;
+        acc = fma((T)2 * area * mu, xf, acc);
       }
     }
   }

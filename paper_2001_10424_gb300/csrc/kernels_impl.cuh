@@ -58,6 +58,29 @@ __device__ __forceinline__ T w_row_const(const Lvl& L, const T* x, const T* xc, 
   return w_row<T, false, C>(L, x, p, xf) * Kc<T>::ws(L);
 }
 
+// W row for variable viscosity at a deep-interior face (all links regular,
+// all cells in the domain): the same operations in the same order as the
+// general link-by-link row, without its bookkeeping. xc points at the face,
+// mc at the viscosity of the cell with the face's padded index.
+template <typename T, int C>
+__device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* mc, T xf) {
+  const long long sc = strd<C>(L);
+  T acc = 0;
+  acc = fma(__ldg(mc), xf - __ldg(xc + sc), acc);
+  acc = fma(__ldg(mc - sc), xf - __ldg(xc - sc), acc);
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+    if (A == C || A >= L.dim) continue;
+    const long long sa = A == 0 ? 1LL : (A == 1 ? (long long)L.P : L.S);
+    // node/edge means: cells at C-offsets -1, 0 and A-offsets (0, +1) / (-1, 0)
+    const T mup = (((__ldg(mc - sc) + __ldg(mc - sc + sa)) + __ldg(mc)) + __ldg(mc + sa)) / (T)4;
+    acc = fma(mup, xf - __ldg(xc + sa), acc);
+    const T mum = (((__ldg(mc - sc - sa) + __ldg(mc - sc)) + __ldg(mc - sa)) + __ldg(mc)) / (T)4;
+    acc = fma(mum, xf - __ldg(xc - sa), acc);
+  }
+  return acc;
+}
+
 // Tiled MAC operator: the block first stores the (negative) divergence of
 // its cells plus a one-cell halo (and the plane below in 3D) in shared
 // memory, then every thread forms the W row of its faces and adds the
@@ -110,6 +133,23 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
     GKB_TILE_DEEP(1, Dt[cur][ty + 1][tx + 1], Dt[cur][ty][tx + 1])
     if (L.dim == 3) { GKB_TILE_DEEP(2, Dt[1][ty + 1][tx + 1], Dt[0][ty + 1][tx + 1]) }
 #undef GKB_TILE_DEEP
+  } else if (VarMu && x != nullptr && deep_interior(L, i, j, k)) {
+    const T ws = Kc<T>::ws(L);
+    const T* mc = MuPtr<T>::get(L) + cb;
+#define GKB_TILE_VDEEP(C, DPLUS, DMINUS)                                         \
+    {                                                                            \
+      const long long id = L.off[C] + cb;                                        \
+      const T xf = __ldg(x + id);                                                \
+      T m = mul_rn(w_row_var_deep<T, C>(L, x + id, mc, xf), ws);                 \
+      if (gd) m = fma(g2, (DPLUS) - (DMINUS), m);                                \
+      const T val = (MODE == 0) ? b[id] - m : m;                                 \
+      if (DOT) dot += (double)xf * (double)val;                                  \
+      y[id] = val;                                                               \
+    }
+    GKB_TILE_VDEEP(0, Dt[cur][ty + 1][tx + 1], Dt[cur][ty + 1][tx])
+    GKB_TILE_VDEEP(1, Dt[cur][ty + 1][tx + 1], Dt[cur][ty][tx + 1])
+    if (L.dim == 3) { GKB_TILE_VDEEP(2, Dt[1][ty + 1][tx + 1], Dt[0][ty + 1][tx + 1]) }
+#undef GKB_TILE_VDEEP
   } else {
 #define GKB_TILE_COMP(C, DPLUS, DMINUS)                                          \
   if (in_store<C>(L, i, j, k)) {                                                 \
@@ -119,9 +159,13 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
       T m = 0, xf = 0;                                                           \
       if (x) {                                                                   \
         xf = x[id];                                                              \
-        if (VarMu) m = w_row<T, VarMu, C>(L, x, p, xf) * Kc<T>::ws(L);           \
-        else m = w_row_const<T, C>(L, x, x + id, p, xf);                         \
-        if (gd) m += g2 * ((DPLUS) - (DMINUS));                                  \
+        if (VarMu) {                                                             \
+          m = mul_rn(w_row<T, VarMu, C>(L, x, p, xf), Kc<T>::ws(L));             \
+          if (gd) m = fma(g2, (DPLUS) - (DMINUS), m);                            \
+        } else {                                                                 \
+          m = w_row_const<T, C>(L, x, x + id, p, xf);                            \
+          if (gd) m += g2 * ((DPLUS) - (DMINUS));                                \
+        }                                                                        \
       }                                                                          \
       val = (MODE == 0) ? b[id] - m : m;                                         \
       if (DOT) dot += (double)xf * (double)val;                                  \

@@ -312,16 +312,20 @@ def test_graph_and_host_loops_agree_bitwise(lib, prec):
     assert sum(l1.values()) >= sum(l2.values()) > 0
 
 
-@pytest.mark.parametrize("n,prec", [((64, 48), FP64), ((70, 66), MIXED), ((14, 12, 10), FP64), ((12, 14, 16), MIXED)])
-def test_fast_paths_match_general_paths_bitwise(lib, n, prec):
+@pytest.mark.parametrize("n,prec,var", [((64, 48), FP64, 0), ((70, 66), MIXED, 0), ((14, 12, 10), FP64, 0),
+                                        ((12, 14, 16), MIXED, 0), ((64, 48), FP64, 1), ((70, 66), MIXED, 1),
+                                        ((14, 12, 10), MIXED, 1)])
+def test_fast_paths_match_general_paths_bitwise(lib, n, prec, var):
     """The deep-interior fast paths of the operator and smoother kernels must
     reproduce the general paths bit for bit: one V-cycle and one operator
-    product with kernel_variant 0 and 1."""
+    product with kernel_variant 2 (fast paths everywhere) and 1 (none), for
+    constant and variable viscosity."""
     gk = lib
     bc = (D,) * (2 * len(n))
+    mu = np.exp(0.7 * np.random.default_rng(5).standard_normal(n)) if var else 1.0
     outs = []
     for variant in (2, 1):
-        h = make_handle(gk, n, bc, 1.0, 50.0, precision=prec, kernel_variant=variant)
+        h = make_handle(gk, n, bc, mu, 50.0, precision=prec, kernel_variant=variant)
         try:
             m, _ = gk.gkb_layout(h)
             x = np.random.default_rng(21).standard_normal(m)

@@ -135,8 +135,14 @@ __device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
   return s / (T)cnt;
 }
 
-template <typename T>
-__device__ __forceinline__ T ldv(const T* x, long long idx) { return __ldg(x + idx); }
+// velocity loads: through the read-only path (NC, the default: the array is
+// not written during the kernel) or plain coherent loads (kernels that
+// update the array they read between their own barriers)
+template <typename T, bool NC = true>
+__device__ __forceinline__ T ldv(const T* x, long long idx) {
+  if (NC) return __ldg(x + idx);
+  return x[idx];
+}
 
 // rounded product that the compiler may not fuse into a neighbouring add:
 // with the explicit fma() of the link sums it fixes every rounding of a W
@@ -146,9 +152,9 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 
 // Velocity value of component C at face position p; positions outside the
 // face grid read as 0 (callers only ask for in-grid or wall-adjacent ones).
-template <typename T, int C>
+template <typename T, int C, bool NC = true>
 __device__ __forceinline__ T face_val(const Lvl& L, const T* x, int i, int j, int k) {
-  return ldv(x, L.off[C] + cix(L, i, j, k));
+  return ldv<T, NC>(x, L.off[C] + cix(L, i, j, k));
 }
 
 // index stride of axis A in the padded layout
@@ -159,28 +165,27 @@ __host__ __device__ __forceinline__ long long strd(const Lvl& L) {
 
 // (A^T x)_cell / ascale = sum over components of (low face - high face),
 // for the in-domain cell with padded index cb
-template <typename T>
+template <typename T, bool NC = true>
 __device__ __forceinline__ T neg_div_at(const Lvl& L, const T* x, long long cb) {
-  const T* u = x + L.off[0] + cb;
-  const T* v = x + L.off[1] + cb;
-  T s = __ldg(u) - __ldg(u + 1) + __ldg(v) - __ldg(v + L.P);
+  const long long u = L.off[0] + cb, v = L.off[1] + cb;
+  T s = ldv<T, NC>(x, u) - ldv<T, NC>(x, u + 1) + ldv<T, NC>(x, v) - ldv<T, NC>(x, v + L.P);
   if (L.dim == 3) {
-    const T* w = x + L.off[2] + cb;
-    s += __ldg(w) - __ldg(w + L.S);
+    const long long w = L.off[2] + cb;
+    s += ldv<T, NC>(x, w) - ldv<T, NC>(x, w + L.S);
   }
   return s;
 }
 
-template <typename T>
+template <typename T, bool NC = true>
 __device__ __forceinline__ T neg_div(const Lvl& L, const T* x, int i, int j, int k) {
   if (!cell_in(L, i, j, k)) return (T)0;
-  return neg_div_at<T>(L, x, cix(L, i, j, k));
+  return neg_div_at<T, NC>(L, x, cix(L, i, j, k));
 }
 
 // Row of W at an active face of component C, position p (FV links, see
 // include/gkb.h). Returns sum_links kappa (x_f - x_nb) with x_nb = 0 for
 // mirror links, divided by wscale (the caller scales).
-template <typename T, bool VarMu, int C>
+template <typename T, bool VarMu, int C, bool NC = true>
 __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T xf) {
   T acc = 0;
   // normal links across the cells p[C]-1 and p[C]
@@ -189,12 +194,12 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
     if (p[C] < L.n[C]) {
       q[C] = p[C] + 1;
       T mu = cell_mu<T, VarMu>(L, p[0], p[1], p[2]);
-      acc = fma(mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
+      acc = fma(mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
     }
     if (p[C] > 0) {
       q[C] = p[C] - 1;
       T mu = cell_mu<T, VarMu>(L, q[0], q[1], q[2]);
-      acc = fma(mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
+      acc = fma(mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
     }
   }
   const bool half = (p[C] == 0 && L.nat[2 * C]) || (p[C] == L.n[C] && L.nat[2 * C + 1]);
@@ -212,7 +217,7 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
       else mu = edge_mu<T, VarMu, C, 2>(L, p, p[A] + 1);
       if (p[A] + 1 < L.n[A]) {
         q[A] = p[A] + 1;
-        acc = fma(area * mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
+        acc = fma(area * mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
       } else if (!L.nat[2 * A + 1]) {
         acc = fma((T)2 * area * mu, xf, acc);
       }
@@ -225,7 +230,7 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
       else mu = edge_mu<T, VarMu, C, 2>(L, p, p[A]);
       if (p[A] > 0) {
         q[A] = p[A] - 1;
-        acc = fma(area * mu, xf - face_val<T, C>(L, x, q[0], q[1], q[2]), acc);
+        acc = fma(area * mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
       } else if (!L.nat[2 * A]) {
         acc = fma((T)2 * area * mu, xf, acc);
       }
@@ -266,15 +271,15 @@ __device__ __forceinline__ int face_cells(const Lvl& L, const int p[3]) {
 }
 
 // (M x)_f at an active face of component C: W row + gc * ascale^2 * grad(negdiv)
-template <typename T, bool VarMu, int C>
+template <typename T, bool VarMu, int C, bool NC = true>
 __device__ __forceinline__ T m_row(const Lvl& L, const T* x, const int p[3]) {
-  const T xf = face_val<T, C>(L, x, p[0], p[1], p[2]);
-  T wv = w_row<T, VarMu, C>(L, x, p, xf) * Kc<T>::ws(L);
+  const T xf = face_val<T, C, NC>(L, x, p[0], p[1], p[2]);
+  T wv = w_row<T, VarMu, C, NC>(L, x, p, xf) * Kc<T>::ws(L);
   if (!L.has_gd) return wv;
   int q[3] = {p[0], p[1], p[2]};
-  T dplus = neg_div<T>(L, x, q[0], q[1], q[2]);
+  T dplus = neg_div<T, NC>(L, x, q[0], q[1], q[2]);
   q[C] -= 1;
-  T dminus = neg_div<T>(L, x, q[0], q[1], q[2]);
+  T dminus = neg_div<T, NC>(L, x, q[0], q[1], q[2]);
   return wv + Kc<T>::g2(L) * (dplus - dminus);
 }
 

@@ -12,6 +12,8 @@
 #include <chrono>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "solver.cuh"
 #include "prof.h"
 #include "unet.cuh"
@@ -909,6 +911,135 @@ __global__ void k_fb_init(cudaGraphConditionalHandle h, CgState* c) {
   cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
+// ---------------------------------------------------------------------------
+// small problems: a whole unpreconditioned CG solve in one thread-block
+// cluster (FP64 work spread over the cluster's SMs, hardware cluster
+// barriers instead of kernel launches between the steps)
+// ---------------------------------------------------------------------------
+constexpr int SB = 256;   // threads per block of the cluster solve
+
+// sum over the cluster, returned to every thread: block sums in a fixed
+// order, then the blocks' sums in rank order through distributed shared
+// memory (deterministic)
+__device__ double cluster_sum(double v, double* sh, double* part) {
+  namespace cgx = cooperative_groups;
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    w = warp_sum(w);
+    if (lane == 0) *part = w;
+  }
+  cl.sync();
+  // one warp fetches the blocks' partials (one remote load per lane, all in
+  // flight together) and reduces them in a fixed order
+  if (warp == 0) {
+    const unsigned nb = cl.num_blocks();
+    double w = (unsigned)lane < nb ? *cl.map_shared_rank(part, (unsigned)lane) : 0.0;
+    w = warp_sum(w);
+    if (lane == 0) sh[0] = w;
+  }
+  cl.sync();  // every block has read the partials before they are reused
+  const double tot = sh[0];
+  __syncthreads();  // sh is rewritten by the next call
+  return tot;
+}
+
+// M x = f from x = 0 by CG (same recurrences and stopping rule as the
+// multi-kernel form: ||r||^2 <= tol2 ||f||^2 on the recursive residual). Block
+// `rank` of the cluster owns one contiguous share of the face positions and
+// one of the padded arrays (balanced over the cluster's SMs); the arrays it
+// rewrites are read with plain coherent loads. The final state goes to c.
+template <bool VarMu>
+__global__ void __launch_bounds__(SB) k_cg_cluster(Lvl L, const double* __restrict__ f, double* __restrict__ x,
+                                                    double* __restrict__ r, double* __restrict__ p,
+                                                    double* __restrict__ q, CgState* c, double tol2, int maxit) {
+  namespace cgx = cooperative_groups;
+  cgx::cluster_group cl = cgx::this_cluster();
+  __shared__ double sh[32];
+  __shared__ double part;
+  const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks(), tid = threadIdx.x;
+  const int len = (int)L.nvel;
+  const int nx = L.n[0] + 1, ny = L.n[1] + 1, nz = (L.dim == 3) ? L.n[2] + 1 : 1;
+  const int npos = nx * ny * nz;
+  const int vch = (len + nb - 1) / nb, pch = (npos + nb - 1) / nb;
+  const int v0 = rank * vch, v1 = min(len, v0 + vch);
+  const int p0 = rank * pch, p1 = min(npos, p0 + pch);
+  double ff = 0.0;
+  for (int t = v0 + tid; t < v1; t += SB) {
+    const double ft = f[t];
+    x[t] = 0.0;
+    r[t] = ft;
+    p[t] = ft;
+    ff += ft * ft;
+  }
+  ff = cluster_sum(ff, sh, &part);  // its barriers also publish p
+  double rr = ff;
+  int it = 0, status = ST_OK;
+  if (!isfinite(ff)) status = ST_NAN;
+  bool done = (ff == 0.0) || status != ST_OK;
+  while (!done) {
+    double pq = 0.0;
+    for (int t = p0 + tid; t < p1; t += SB) {
+      const int i = t % nx, u = t / nx;
+      const int j = u % ny, k = u / ny;
+      const int pos[3] = {i, j, k};
+      const long long cb = cix(L, i, j, k);
+      if (face_active<0>(L, i, j, k)) {
+        const double v = m_row<double, VarMu, 0, false>(L, p, pos);
+        q[L.off[0] + cb] = v;
+        pq += p[L.off[0] + cb] * v;
+      }
+      if (face_active<1>(L, i, j, k)) {
+        const double v = m_row<double, VarMu, 1, false>(L, p, pos);
+        q[L.off[1] + cb] = v;
+        pq += p[L.off[1] + cb] * v;
+      }
+      if (L.dim == 3 && face_active<2>(L, i, j, k)) {
+        const double v = m_row<double, VarMu, 2, false>(L, p, pos);
+        q[L.off[2] + cb] = v;
+        pq += p[L.off[2] + cb] * v;
+      }
+    }
+    pq = cluster_sum(pq, sh, &part);  // q complete everywhere after this
+    if (!isfinite(pq)) { status = ST_NAN; break; }
+    if (!(pq > 0.0)) { status = ST_NOT_SPD; break; }
+    const double alpha = rr / pq;
+    double rn = 0.0;
+    for (int t = v0 + tid; t < v1; t += SB) {
+      x[t] += alpha * p[t];
+      const double rt = r[t] - alpha * q[t];
+      r[t] = rt;
+      rn += rt * rt;
+    }
+    rn = cluster_sum(rn, sh, &part);
+    ++it;
+    const double rprev = rr;
+    rr = rn;
+    if (!isfinite(rn)) { status = ST_NAN; break; }
+    if (rn <= tol2 * ff) break;
+    if (it >= maxit) { status = ST_INNER_NOT_CONVERGED; break; }
+    const double beta = rn / rprev;
+    for (int t = v0 + tid; t < v1; t += SB) p[t] = r[t] + beta * p[t];
+    cl.sync();  // p complete before the next product reads neighbours
+  }
+  if (rank == 0 && tid == 0) {
+    c->ff = ff;
+    c->rr = rr;
+    c->it = it;
+    c->total_it += it;
+    c->solves += 1;
+    c->status = status;
+    c->done = 1;
+    c->graph_iters = 0;
+    c->fb_iters = 0;
+    c->fallback = 0;
+  }
+}
+
 // record an inner solve in the GKB state: status, iterations, history
 __global__ void k_note_inner(GkbState* S, const CgState* c) {
   const int idx = S->inner_solves;
@@ -1292,10 +1423,70 @@ void Solver::refresh_net() {
   if (net && net->bf16_stale && learned_inner()) net->refresh_bf16(stream);
 }
 
+// small unpreconditioned FP64 problems run each inner solve as one kernel
+bool Solver::small_cg() const {
+  return opt.inner == GKB_INNER_CG && opt.precision == GKB_PREC_FP64 && L64.nvel <= (1LL << 15);
+}
+
+// cluster size for k_cg_cluster: 16 blocks where the device allows it, else 8
+static int cg_cluster_size(bool var_mu) {
+  static int cached[2] = {0, 0};
+  int& cs = cached[var_mu ? 1 : 0];
+  if (cs) return cs;
+  const void* fn = var_mu ? (const void*)k_cg_cluster<true> : (const void*)k_cg_cluster<false>;
+  cs = 8;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(SB);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) cs = 16;
+  }
+  (void)cudaGetLastError();
+  return cs;
+}
+
+void Solver::launch_cg_block(const double* fpad, double* xpad, cudaStream_t s) {
+  Cg<double>& c = cg64;
+  ProfScope ps_(GKB_KC_APPLY, s, 0);  // unknowns counted per iteration in finish()
+  const double tol2 = opt.tol_inner * opt.tol_inner;
+  const bool var = L64.mu64 != nullptr;
+  const int cs = cg_cluster_size(var);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cs;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(SB);
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (var)
+    GKB_CUDA(cudaLaunchKernelEx(&cfg, k_cg_cluster<true>, L64, fpad, xpad, c.r.p, c.p.p, c.q.p, cg_dev, tol2,
+                                opt.maxit_inner));
+  else
+    GKB_CUDA(cudaLaunchKernelEx(&cfg, k_cg_cluster<false>, L64, fpad, xpad, c.r.p, c.p.p, c.q.p, cg_dev, tol2,
+                                opt.maxit_inner));
+}
+
 int Solver::inner_solve(const double* fpad, double* xpad) {
   int its = 0, st = 0;
   if (opt.precision == GKB_PREC_MIXED) st = mixed_solve(fpad, xpad, &its);
-  else st = cg64.solve(fpad, xpad, opt.tol_inner, opt.maxit_inner, stream, &its);
+  else if (small_cg()) {
+    launch_cg_block(fpad, xpad, stream);
+    GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, stream));
+    GKB_CUDA(cudaStreamSynchronize(stream));
+    st = cg_host->status;
+  } else st = cg64.solve(fpad, xpad, opt.tol_inner, opt.maxit_inner, stream, &its);
   { ProfScope ps_(GKB_KC_GKB, stream); k_note_inner<<<1, 1, 0, stream>>>(gkb_dev, cg_dev); }
   return st;
 }
@@ -1449,6 +1640,8 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
             { ProfScope ps_(GKB_KC_LAYOUT, st, len); k_mixed_accum<<<lin_blocks(len), CB, 0, st>>>(len, x32.p, x.p, nullptr); }
           });
     }
+  } else if (small_cg()) {
+    launch_cg_block(f.p, x.p, s);
   } else {
     Cg<double>& c = cg64;
     double* zp = c.pre ? c.z.p : c.r.p;
@@ -1723,6 +1916,8 @@ int Solver::finish(double* w_out, double* p_out, const double* w0, const double*
                        H.inner_runs * sgraph.cu[3][k] + H.inner_fb_runs * sgraph.cu[4][k];
     }
   }
+  // the single-kernel CG solves: one operator product per iteration
+  if (small_cg()) prof.units[GKB_KC_APPLY] += H.inner_its * L64.nvel;
   prof.collect();
   for (int kc = 0; kc < GKB_KC_COUNT; ++kc) {
     stats.kernel_launches[kc] = prof.launches[kc];

@@ -206,6 +206,8 @@ struct Solver {
   int harvest(const double* f, int max_pairs, float* x_img, float* t_img, int* n_pairs);
   // inner solve in FP64 padded layout: x = M^-1 f; returns status
   int inner_solve(const double* f, double* x);
+  bool small_cg() const;
+  void launch_cg_block(const double* f, double* x, cudaStream_t s);
   int mixed_solve(const double* f, double* x, int* iters);
   ~Solver();
 };

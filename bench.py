@@ -370,7 +370,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     and divided by their durations."""
     import numpy as np
     subset = list(range(min(len(wk.problems), 16))) if wk.batched else None
-    B = Bound(gk, torch, wk, form, profile=1, subset=subset)
+    B = Bound(gk, torch, wk, form, profile=1, subset=subset, autotune=args.autotune)
     ms, units, launches = {}, {}, {}
     for i, h in enumerate(B.hs):
         gk.gkb_solve(h, B.g[i], B.r[i], args.tol, args.delay, B.w[i], B.p[i], B.w0[i], B.p0[i])
@@ -515,7 +515,8 @@ def config(args, wk):
     c = {"workload": wk.name, "problems": len(wk.problems), "tol": args.tol, "delay": args.delay,
          "tol_inner": wk.tol_inner, "form": wk.form, "inner": "gmg_pcg" if wk.inner == 1 else "cg",
          "n_scale": "h^d", "l2": "flushed between steps (1 GiB write)",
-         "parallelism": "replicas" if args.gpus > 1 else "single"}
+         "parallelism": "replicas" if args.gpus > 1 else "single",
+         "autotune": bool(getattr(args, "autotune", 0))}
     if len(sizes) <= 4:
         c["grid"] = [list(s) for s in sizes]
     else:
@@ -538,12 +539,20 @@ def run_ours(args, ws, rank, local):
     gk.load()
     hbm_peak, peak_kind = measured_peaks()
     wk = Workload(args)
+    if args.autotune < 0:
+        args.autotune = 0 if wk.batched else 1
     training = None
     if wk.learned:
         wk.net, training = train_network(gk, torch, wk, args)
     t0 = time.perf_counter()
-    B = Bound(gk, torch, wk, wk.form)
+    B = Bound(gk, torch, wk, wk.form, autotune=args.autotune)
     setup_s = time.perf_counter() - t0
+    tuned = []
+    if args.autotune:
+        for h in B.hs[:8]:
+            o = gk.gkb_get_options(h)
+            tuned.append({"smoother_degree": o.smoother_degree, "kernel_variant": o.kernel_variant,
+                          "coarse_max": o.coarse_max})
     flush = torch.empty(1 << 28, dtype=torch.float32, device="cuda")  # 1 GiB > L2
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -597,7 +606,8 @@ def run_ours(args, ws, rank, local):
     rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
 
-    def time_form(form, learned, autotune=0):
+    def time_form(form, learned, autotune=None):
+        autotune = args.autotune if autotune is None else autotune
         t_setup = time.perf_counter()
         B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune)
         t_setup = time.perf_counter() - t_setup
@@ -640,7 +650,9 @@ def run_ours(args, ws, rank, local):
             other = "mixed" if wk.form == "fp64" else "fp64"
             forms[other] = time_form(other, None)
             forms[wk.form] = head
-        if not args.no_autotune:
+        if args.autotune:
+            forms[wk.form + "_default_options"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=0)
+        else:
             forms[wk.form + "_autotuned"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=1)
     cpu = None
     if not args.no_cpu_baseline:
@@ -666,6 +678,8 @@ def run_ours(args, ws, rank, local):
         "inner_iterations": inner if len(inner) <= 8 else {"min": min(inner), "max": max(inner), "sum": sum(inner)},
         "status": status, "setup_s": setup_s, "forms": forms, "finite_output": finite,
     }
+    if tuned:
+        line["tuned_options"] = tuned
     if training:
         line["training"] = training
     if wk.net is not None:
@@ -723,7 +737,10 @@ def main():
     ap.add_argument("--delay", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuned form in `forms`")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="1: the timed handles are autotuned at setup (reported in setup_s); 0: default options; "
+                         "-1 (default): 1 for single problems, 0 for the batched form (its tuning times one "
+                         "problem alone, which misjudges the coarse-level cost of 256 concurrent problems)")
     ap.add_argument("--probe", choices=["precond", "solve"], default=None,
                     help="profiling target: set up one handle and run one V-cycle or one solve")
     args = ap.parse_args()

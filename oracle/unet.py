@@ -238,14 +238,21 @@ def image_to_mac(grid, img):
     return vel
 
 
-def apply_preconditioner(params, shapes, grid, r, logmu, target_scale=1.0, quant=None):
+def apply_preconditioner(params, shapes, grid, r, logmu, target_scale=1.0, quant=None, M=None):
     """The scale-equivariant use of the network as an approximate inverse of
     M: with c = ||r|| / sqrt(nx ny) (the RMS of r over the cells),
-    z = c / target_scale * N(r / c, log mu) on the faces (z = 0 for r = 0)."""
+    z = c / target_scale * N(r / c, log mu) on the faces (z = 0 for r = 0).
+    With the matrix M given, z is then scaled by the energy-optimal step
+    omega = (r, z) / (z, M z) (0 unless (z, M z) > 0): the minimiser of
+    ||M^-1 r - omega z||_M."""
     nr = float(np.linalg.norm(r))
     if nr == 0.0:
         return np.zeros_like(r)
     c = nr / np.sqrt(grid.n[0] * grid.n[1])
     img = mac_to_image(grid, r / c, logmu)[None]
     y = forward(params, img, shapes, quant=quant)[0]
-    return (c / target_scale) * image_to_mac(grid, y)
+    z = (c / target_scale) * image_to_mac(grid, y)
+    if M is None:
+        return z
+    zmz = float(z @ (M @ z))
+    return (float(r @ z) / zmz) * z if zmz > 0 else np.zeros_like(z)

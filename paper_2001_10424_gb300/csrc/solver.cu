@@ -526,7 +526,8 @@ void Gmg<T>::attach_net(Unet* u, int level, bool composite, cudaStream_t s) {
   if (!net_act) net_act = new UnetAct();
   u->ensure(*net_act, 1, L.n[1], L.n[0]);
   net_img.alloc((size_t)L.n[0] * L.n[1] * 3);
-  net_nrm.alloc(4);
+  net_nrm.alloc(8);
+  net_q.alloc(L.nvel);
   if (u->bf16_stale) u->refresh_bf16(s);
   net = u;
   net_level = level;
@@ -556,7 +557,7 @@ void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s, bool use_net) {
   auto lvl_b = [&](int l) { return (l == 0) ? r0 : (const T*)lev[l].b.p; };
   auto lvl_x = [&](int l) { return (l == 0) ? z0 : lev[l].x.p; };
   auto net_at = [&](int l) {
-    unet_correct<T>(*net, *net_act, lev[l].L, lvl_b(l), lvl_x(l), net_img.p, net_nrm.p, red, s);
+    unet_correct<T>(*net, *net_act, lev[l].L, lvl_b(l), lvl_x(l), net_q.p, net_img.p, net_nrm.p, red, s);
   };
   for (int l = 0; l < lc; ++l) {
     bool x_zero = true;

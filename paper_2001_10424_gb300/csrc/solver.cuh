@@ -88,6 +88,7 @@ struct Gmg {
   UnetAct* net_act = nullptr;  // owned: this hierarchy's activation workspace
   DevBuf<float> net_img;
   DevBuf<double> net_nrm;
+  DevBuf<T> net_q;             // M z of the network's correction
   void attach_net(Unet* u, int level, bool composite, cudaStream_t s);
   void detach_net();
   Gmg() = default;

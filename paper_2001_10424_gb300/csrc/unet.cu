@@ -777,9 +777,18 @@ void err_to_img(const Lvl& L, const double* xs, const double* xk, const double* 
   GKB_CUDA(cudaGetLastError());
 }
 
+// x *= omega, omega = d[0] / d[1] when d[1] > 0, else 0
 template <typename T>
-void unet_correct(Unet& U, UnetAct& A, const Lvl& L, const T* b, T* x, float* img_in, double* nrm, const RedBuf& red,
-                  cudaStream_t s) {
+__global__ void k_scale_step(T* __restrict__ x, long long n, const double* __restrict__ d) {
+  const double den = d[1];
+  const T w = (T)(den > 0.0 && isfinite(den) && isfinite(d[0]) ? d[0] / den : 0.0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    x[t] *= w;
+}
+
+template <typename T>
+void unet_correct(Unet& U, UnetAct& A, const Lvl& L, const T* b, T* x, T* q, float* img_in, double* nrm,
+                  const RedBuf& red, cudaStream_t s) {
   if (L.dim != 2) throw Error{GKB_ERR_INVALID_ARG, "the learned correction is 2D only"};
   Ops<T>::dot(L.nvel, b, b, red, FIN_STORE, nrm, s);
   const dim3 blk(32, 8);
@@ -789,13 +798,20 @@ void unet_correct(Unet& U, UnetAct& A, const Lvl& L, const T* b, T* x, float* im
     ProfScope ps_(GKB_KC_UNET, s, (long long)L.n[0] * L.n[1]);
     k_img_to_mac<T><<<dim3((L.n[0] + 32) / 32, (L.n[1] + 8) / 8), blk, 0, s>>>(L, y, nrm, 1.f / U.target_scale, x);
   }
+  // energy-optimal step along the network's direction
+  Ops<T>::apply(L, 1, x, q, s);
+  Ops<T>::dot2(L.nvel, b, x, q, red, FIN_STORE, nrm + 4, s);
+  {
+    ProfScope ps_(GKB_KC_UNET, s, L.nvel);
+    k_scale_step<T><<<grid_for(L.nvel), UT, 0, s>>>(x, L.nvel, nrm + 4);
+  }
   GKB_CUDA(cudaGetLastError());
 }
 
-template void unet_correct<double>(Unet&, UnetAct&, const Lvl&, const double*, double*, float*, double*, const RedBuf&,
-                                   cudaStream_t);
-template void unet_correct<float>(Unet&, UnetAct&, const Lvl&, const float*, float*, float*, double*, const RedBuf&,
-                                  cudaStream_t);
+template void unet_correct<double>(Unet&, UnetAct&, const Lvl&, const double*, double*, double*, float*, double*,
+                                   const RedBuf&, cudaStream_t);
+template void unet_correct<float>(Unet&, UnetAct&, const Lvl&, const float*, float*, float*, float*, double*,
+                                  const RedBuf&, cudaStream_t);
 
 }  // namespace gkb
 

@@ -70,11 +70,14 @@ void mac_to_img(const Lvl& L, const T* b, const double* nrm, float* img, cudaStr
 // image (ny, nx, 2) of (xs - xk) scaled by sqrt(nx ny / nrm[0]), same faces
 void err_to_img(const Lvl& L, const double* xs, const double* xk, const double* nrm, float* img, cudaStream_t s);
 
-// Learned coarse correction on a 2D level: x = (||b|| / sqrt(nx ny)) /
-// target_scale * N(b^, log mu) with b^ = b sqrt(nx ny) / ||b|| (x = 0 for b = 0),
-// through the images img_in (ny, nx, 3) / A.y (ny, nx, 2); nrm: device double[4].
+// Learned coarse correction on a 2D level: z = (||b|| / sqrt(nx ny)) /
+// target_scale * N(b^, log mu) with b^ = b sqrt(nx ny) / ||b|| (z = 0 for b = 0),
+// through the images img_in (ny, nx, 3) / A.y (ny, nx, 2), then scaled by the
+// energy-optimal step: x = omega z, omega = (b, z) / (z, M z) (0 unless
+// (z, M z) > 0), so that the correction never increases the M-norm error of
+// the level system. q: level-sized scratch (M z); nrm: device double[8].
 template <typename T>
-void unet_correct(Unet& U, UnetAct& A, const Lvl& L, const T* b, T* x, float* img_in, double* nrm,
+void unet_correct(Unet& U, UnetAct& A, const Lvl& L, const T* b, T* x, T* q, float* img_in, double* nrm,
                   const RedBuf& red, cudaStream_t s);
 
 }  // namespace gkb

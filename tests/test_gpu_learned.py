@@ -65,7 +65,8 @@ def test_learned_correction_matches_oracle(lib, prec):
         r = rng.standard_normal(grid.m)
         z = np.empty(grid.m)
         gk.gkb_precond(h, r, z)
-        ref = ou.apply_preconditioner(params.astype(np.float64), SHAPES, grid, r, logmu, 2.5, quant=ou.bf16_round)
+        M = mac.assemble(grid, np.exp(logmu), 100.0)["M"]
+        ref = ou.apply_preconditioner(params.astype(np.float64), SHAPES, grid, r, logmu, 2.5, quant=ou.bf16_round, M=M)
         assert np.abs(z - ref).max() <= 3e-3 * np.abs(ref).max()
         # scale equivariance holds on the GPU too (the normalisation divides it out)
         z2 = np.empty(grid.m)

@@ -168,3 +168,25 @@ def test_preconditioner_is_scale_equivariant():
     # sum to the number of cells
     img = unet.mac_to_image(grid, r / (np.linalg.norm(r) / np.sqrt(96)), logmu)
     assert abs(np.sum(img[:, :, :2] ** 2) - 96) < 1e-9 * 96
+
+
+def test_energy_optimal_step_of_the_correction():
+    """With M given, the returned multiple of the network's direction is the
+    best one in the M-norm: ||e - x||_M <= ||e - t z||_M for every t, and
+    never above ||e||_M (e = M^-1 r); it stays scale equivariant."""
+    shapes = unet.layer_shapes()
+    rng = np.random.default_rng(9)
+    params = 0.1 * rng.standard_normal(unet.num_params(shapes))
+    grid = mac.MacGrid((8, 8), 1.0 / 8)
+    logmu = 0.5 * rng.standard_normal((8, 8))
+    M = mac.assemble(grid, np.exp(logmu), 100.0)["M"].toarray()
+    r = rng.standard_normal(grid.m)
+    e = np.linalg.solve(M, r)
+    z = unet.apply_preconditioner(params, shapes, grid, r, logmu)
+    x = unet.apply_preconditioner(params, shapes, grid, r, logmu, M=M)
+    en = lambda v: float(v @ (M @ v))
+    assert en(e - x) <= en(e) * (1 + 1e-12)
+    for t in np.linspace(-2, 2, 41) * (np.abs(x).max() / np.abs(z).max()):
+        assert en(e - x) <= en(e - t * z) * (1 + 1e-12)
+    assert np.abs(unet.apply_preconditioner(params, shapes, grid, 3.0 * r, logmu, M=M) - 3.0 * x).max() \
+        < 1e-12 * np.abs(x).max()

@@ -516,7 +516,7 @@ def config(args, wk):
          "tol_inner": wk.tol_inner, "form": wk.form, "inner": "gmg_pcg" if wk.inner == 1 else "cg",
          "n_scale": "h^d", "l2": "flushed between steps (1 GiB write)",
          "parallelism": "replicas" if args.gpus > 1 else "single",
-         "autotune": bool(getattr(args, "autotune", 0))}
+         "autotune": bool(getattr(args, "autotune", 0) > 0)}
     if len(sizes) <= 4:
         c["grid"] = [list(s) for s in sizes]
     else:

@@ -162,6 +162,9 @@ template <int A>
 __host__ __device__ __forceinline__ long long strd(const Lvl& L) {
   return A == 0 ? 1LL : (A == 1 ? (long long)L.P : L.S);
 }
+__host__ __device__ __forceinline__ long long strd_rt(const Lvl& L, int a) {
+  return a == 0 ? 1LL : (a == 1 ? (long long)L.P : L.S);
+}
 
 // (A^T x)_cell / ascale = sum over components of (low face - high face),
 // for the in-domain cell with padded index cb

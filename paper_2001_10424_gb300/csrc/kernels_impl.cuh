@@ -453,6 +453,86 @@ __device__ __forceinline__ T patch_apply_deep(const Lvl& L, const T* r, long lon
   return acc;
 }
 
+// 3D interior faces, constant viscosity: the four interior patches through a
+// face of component C (two orientations, two patches each) act as one fixed
+// 13-point stencil on r, stored after the class table (PATCH_FOLD_OFF) as 16
+// coefficients per component: [0] the face itself, then for each orientation
+// E != C in increasing order six neighbour terms (see k_patch_fold).
+constexpr int PATCH_FOLD_OFF = 3 * 75 * 16;
+
+template <typename T, int C>
+__device__ __forceinline__ T patch_apply_fold(const Lvl& L, const T* __restrict__ r, long long cb,
+                                              const T* __restrict__ fold) {
+  const T* f = fold + C * 16;
+  const T* rc = r + L.off[C] + cb;
+  T acc = __ldg(f) * __ldg(rc);
+  int t = 1;
+#pragma unroll
+  for (int E = 0; E < 3; ++E) {
+    if (E == C) continue;
+    const int a = (E == 0) ? 1 : 0, b = (E == 2) ? 1 : 2;
+    const long long sa = strd_rt(L, a), sb = strd_rt(L, b);
+    const T* ra = r + L.off[a] + cb;
+    const T* rb = r + L.off[b] + cb;
+    if (C == a) {
+      acc += __ldg(f + t + 0) * __ldg(ra - sb);
+      acc += __ldg(f + t + 1) * __ldg(rb - sa);
+      acc += __ldg(f + t + 2) * __ldg(rb);
+      acc += __ldg(f + t + 3) * __ldg(ra + sb);
+      acc += __ldg(f + t + 4) * __ldg(rb + sb - sa);
+      acc += __ldg(f + t + 5) * __ldg(rb + sb);
+    } else {
+      acc += __ldg(f + t + 0) * __ldg(ra - sb);
+      acc += __ldg(f + t + 1) * __ldg(ra);
+      acc += __ldg(f + t + 2) * __ldg(rb - sa);
+      acc += __ldg(f + t + 3) * __ldg(ra + sa - sb);
+      acc += __ldg(f + t + 4) * __ldg(ra + sa);
+      acc += __ldg(f + t + 5) * __ldg(rb + sa);
+    }
+    t += 6;
+  }
+  return acc;
+}
+
+// The folded interior stencils of the 3D constant-viscosity smoother, from the
+// interior-class rows of the table (one thread per component): for a face of
+// component C = a of orientation E the patches are e = p (row 1) and
+// p + e_b (row 0); for C = b they are e = p (row 3) and p + e_a (row 2); the
+// face's own residual collects one entry of each row.
+template <typename T>
+__global__ void k_patch_fold(Lvl L, T* table) {
+  const int C = threadIdx.x;
+  if (L.dim != 3 || C >= 3) return;
+  T* f = table + PATCH_FOLD_OFF + C * 16;
+  for (int k = 0; k < 16; ++k) f[k] = (T)0;
+  double self = 0.0;
+  int t = 1;
+  for (int E = 0; E < 3; ++E) {
+    if (E == C) continue;
+    const int a = (E == 0) ? 1 : 0;
+    const T* R = table + (size_t)(E * 75 + (2 * 5 + 2) * 3 + 1) * 16;  // interior class in 3D
+    if (C == a) {
+      self += (double)R[1 * 4 + 1] + (double)R[0 * 4 + 0];
+      f[t + 0] = R[1 * 4 + 0];
+      f[t + 1] = R[1 * 4 + 2];
+      f[t + 2] = R[1 * 4 + 3];
+      f[t + 3] = R[0 * 4 + 1];
+      f[t + 4] = R[0 * 4 + 2];
+      f[t + 5] = R[0 * 4 + 3];
+    } else {
+      self += (double)R[3 * 4 + 3] + (double)R[2 * 4 + 2];
+      f[t + 0] = R[3 * 4 + 0];
+      f[t + 1] = R[3 * 4 + 1];
+      f[t + 2] = R[3 * 4 + 2];
+      f[t + 3] = R[2 * 4 + 0];
+      f[t + 4] = R[2 * 4 + 1];
+      f[t + 5] = R[2 * 4 + 3];
+    }
+    t += 6;
+  }
+  f[0] = (T)self;
+}
+
 // One Chebyshev step of the patch-preconditioned smoother:
 //   z = C r;  d = ca * z + cb * d;  x = (x_zero ? 0 : x) + d
 template <typename T, bool VarMu>
@@ -467,7 +547,8 @@ __global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r,
 #define GKB_CHEB_DEEP(C)                                                         \
     {                                                                            \
       const long long id = L.off[C] + pc;                                        \
-      const T z = patch_apply_deep<T, C>(L, r, pc, table);                       \
+      const T z = (L.dim == 3) ? patch_apply_fold<T, C>(L, r, pc, table + PATCH_FOLD_OFF) \
+                               : patch_apply_deep<T, C>(L, r, pc, table);        \
       const T dn = (cb != (T)0) ? ca * z + cb * d[id] : ca * z;                  \
       d[id] = dn;                                                                \
       x[id] = x_zero ? dn : x[id] + dn;                                          \

@@ -92,7 +92,7 @@ void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStrea
 
 template <>
 long long Ops<KT>::patch_table_len(const Lvl& L) {
-  if (!GKB_VARMU(L)) return 3 * 75 * 16;
+  if (!GKB_VARMU(L)) return PATCH_FOLD_OFF + 3 * 16;  // class inverses, then the 3D folded stencils
   return (L.dim == 3 ? 3 : 1) * 10 * vtab_plane(L);
 }
 
@@ -101,6 +101,7 @@ void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
   ProfScope ps_(GKB_KC_LAYOUT, s, 0);
   if (!GKB_VARMU(L)) {
     k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
+    if (L.dim == 3) k_patch_fold<KT><<<1, 32, 0, s>>>(L, table);
     return;
   }
   // variable viscosity: the per-patch inverses (entries never written stay 0)

@@ -319,7 +319,9 @@ def test_fast_paths_match_general_paths_bitwise(lib, n, prec, var):
     """The deep-interior fast paths of the operator and smoother kernels must
     reproduce the general paths bit for bit: one V-cycle and one operator
     product with kernel_variant 2 (fast paths everywhere) and 1 (none), for
-    constant and variable viscosity."""
+    constant and variable viscosity. Exception: the 3D constant-viscosity
+    smoother folds its four interior patches into one 13-point stencil, which
+    sums in another order, so the 3D V-cycle agrees to rounding."""
     gk = lib
     bc = (D,) * (2 * len(n))
     mu = np.exp(0.7 * np.random.default_rng(5).standard_normal(n)) if var else 1.0
@@ -335,5 +337,9 @@ def test_fast_paths_match_general_paths_bitwise(lib, n, prec, var):
             outs.append((z, y))
         finally:
             gk.gkb_destroy(h)
-    assert np.array_equal(outs[0][0], outs[1][0])
+    if len(n) == 3 and not var:
+        tol = 1e-12 if prec == FP64 else 1e-5
+        assert np.abs(outs[0][0] - outs[1][0]).max() <= tol * np.abs(outs[1][0]).max()
+    else:
+        assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])

@@ -890,8 +890,40 @@ __device__ __forceinline__ T slope3(const Lvl& Lc, const T* xc, const int P[3]) 
   return (up - um) * (T)0.125;
 }
 
+// The coarse slopes of every coarse face, computed once per prolongation:
+// sl[kk * nvel + index of face P of component C] = slope3<C, Oth<C, kk>>(P)
+// (0 on inactive faces, which are never written and stay 0).
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_slopes3d(Lvl Lc, const T* __restrict__ xc, T* __restrict__ sl) {
+  const int i = blockIdx.x * BX + threadIdx.x;
+  const int j = blockIdx.y * BY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int P[3] = {i, j, k};
+  const long long c = cix(Lc, i, j, k);
+#define GKB_SLOPES(C)                                                            \
+  if (in_store<C>(Lc, i, j, k) && face_active<C>(Lc, i, j, k)) {                 \
+    sl[Lc.off[C] + c] = slope3<T, C, Oth<C, 0>::v>(Lc, xc, P);                   \
+    sl[Lc.nvel + Lc.off[C] + c] = slope3<T, C, Oth<C, 1>::v>(Lc, xc, P);         \
+  }
+  GKB_SLOPES(0)
+  GKB_SLOPES(1)
+  GKB_SLOPES(2)
+#undef GKB_SLOPES
+}
+
+// slope / 8 of component C along axis A at coarse face P, from the table
+template <typename T, int C, int A>
+__device__ __forceinline__ T slope3_at(const Lvl& Lc, const T* __restrict__ sl, const int P[3]) {
+  constexpr int kk = (Oth<C, 0>::v == A) ? 0 : 1;
+  return __ldg(sl + kk * Lc.nvel + Lc.off[C] + cix(Lc, P[0], P[1], P[2]));
+}
+
+// value of the prolongation at fine face p of component C: on a coarse face,
+// the coarse value plus its two tangential slopes; inside a coarse cell, the
+// mean of the two line values plus half the differences of the other
+// components' slopes along C (slopes read from the table of k_slopes3d)
 template <typename T, int C>
-__device__ __forceinline__ T prolong3_val(const Lvl& Lc, const T* xc, const int p[3]) {
+__device__ __forceinline__ T prolong3_val_tab(const Lvl& Lc, const T* xc, const T* sl, const int p[3]) {
   constexpr int t1 = Oth<C, 0>::v, t2 = Oth<C, 1>::v;
   const int q[3] = {p[0] >> 1, p[1] >> 1, p[2] >> 1};
   const T s1 = (p[t1] & 1) ? (T)1 : (T)-1;
@@ -899,7 +931,8 @@ __device__ __forceinline__ T prolong3_val(const Lvl& Lc, const T* xc, const int 
   auto line_val = [&](int I) -> T {
     int P[3] = {q[0], q[1], q[2]};
     P[C] = I;
-    return coarse_face<T, C>(Lc, xc, P[0], P[1], P[2]) + s1 * slope3<T, C, t1>(Lc, xc, P) + s2 * slope3<T, C, t2>(Lc, xc, P);
+    return coarse_face<T, C>(Lc, xc, P[0], P[1], P[2]) + s1 * slope3_at<T, C, t1>(Lc, sl, P) +
+           s2 * slope3_at<T, C, t2>(Lc, sl, P);
   };
   if ((p[C] & 1) == 0) return line_val(p[C] >> 1);
   const int I = p[C] >> 1;
@@ -909,20 +942,24 @@ __device__ __forceinline__ T prolong3_val(const Lvl& Lc, const T* xc, const int 
   int hi1[3] = {lo[0], lo[1], lo[2]}, hi2[3] = {lo[0], lo[1], lo[2]};
   hi1[t1] += 1;
   hi2[t2] += 1;
-  val += (T)0.5 * (slope3<T, t1, C>(Lc, xc, hi1) - slope3<T, t1, C>(Lc, xc, lo));
-  val += (T)0.5 * (slope3<T, t2, C>(Lc, xc, hi2) - slope3<T, t2, C>(Lc, xc, lo));
+  val += (T)0.5 * (slope3_at<T, t1, C>(Lc, sl, hi1) - slope3_at<T, t1, C>(Lc, sl, lo));
+  val += (T)0.5 * (slope3_at<T, t2, C>(Lc, sl, hi2) - slope3_at<T, t2, C>(Lc, sl, lo));
   return val;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_prolong_flux3d(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+__global__ void __launch_bounds__(BX* BY) k_prolong_flux3d(Lvl Lf, Lvl Lc, const T* __restrict__ xc,
+                                                           const T* __restrict__ sl, T* __restrict__ xf) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
   const int p[3] = {i, j, k};
-  if (in_store<0>(Lf, i, j, k) && face_active<0>(Lf, i, j, k)) xf[Lf.off[0] + cix(Lf, i, j, k)] += prolong3_val<T, 0>(Lc, xc, p);
-  if (in_store<1>(Lf, i, j, k) && face_active<1>(Lf, i, j, k)) xf[Lf.off[1] + cix(Lf, i, j, k)] += prolong3_val<T, 1>(Lc, xc, p);
-  if (in_store<2>(Lf, i, j, k) && face_active<2>(Lf, i, j, k)) xf[Lf.off[2] + cix(Lf, i, j, k)] += prolong3_val<T, 2>(Lc, xc, p);
+  if (in_store<0>(Lf, i, j, k) && face_active<0>(Lf, i, j, k))
+    xf[Lf.off[0] + cix(Lf, i, j, k)] += prolong3_val_tab<T, 0>(Lc, xc, sl, p);
+  if (in_store<1>(Lf, i, j, k) && face_active<1>(Lf, i, j, k))
+    xf[Lf.off[1] + cix(Lf, i, j, k)] += prolong3_val_tab<T, 1>(Lc, xc, sl, p);
+  if (in_store<2>(Lf, i, j, k) && face_active<2>(Lf, i, j, k))
+    xf[Lf.off[2] + cix(Lf, i, j, k)] += prolong3_val_tab<T, 2>(Lc, xc, sl, p);
 }
 
 template <typename T, int C>

@@ -31,7 +31,8 @@ struct Ops {
   // y = scale * A^T x (cells from faces)
   static void negdiv(const Lvl& L, const T* x, T* y, T scale, cudaStream_t s);
   // xf += P xc
-  static void prolong(const Lvl& Lf, const Lvl& Lc, const T* xc, T* xf, cudaStream_t s);
+  // (slopes: 2 x the coarse level's velocity length of scratch, 3D only)
+  static void prolong(const Lvl& Lf, const Lvl& Lc, const T* xc, T* xf, T* slopes, cudaStream_t s);
   // bc = P^T rf (tmp, tmp2: coarse-sized scratch; tmp2 only in 3D)
   static void restrict_(const Lvl& Lf, const Lvl& Lc, const T* rf, T* bc, T* tmp, T* tmp2, cudaStream_t s);
   // coarsest level dense solve through the stored inverse

@@ -345,7 +345,10 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     if (l > 0) {
       V.x.alloc(V.L.nvel);
       V.b.alloc(V.L.nvel);
-      if (V.L.dim == 3) V.t2.alloc(V.L.nvel);
+      if (V.L.dim == 3) {
+        V.t2.alloc(V.L.nvel);
+        V.sl.alloc(2 * (size_t)V.L.nvel);
+      }
     }
     if (l < nl - 1) {
       V.r.alloc(V.L.nvel);
@@ -572,7 +575,7 @@ void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s, bool use_net) {
   if (replace) net_at(lc);
   else Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, lvl_b(lc), lvl_x(lc), s);
   for (int l = lc - 1; l >= 0; --l) {
-    Ops<T>::prolong(lev[l].L, lev[l + 1].L, lev[l + 1].x.p, lvl_x(l), s);
+    Ops<T>::prolong(lev[l].L, lev[l + 1].L, lev[l + 1].x.p, lvl_x(l), lev[l + 1].sl.p, s);
     smooth(l, lvl_b(l), lvl_x(l), false, s);
   }
 }

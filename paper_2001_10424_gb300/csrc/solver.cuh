@@ -68,6 +68,7 @@ struct Gmg {
     Lvl L;
     DevBuf<T> x, b, r, d, mu;
     DevBuf<T> t2;               // second restriction scratch (3D coarse levels)
+    DevBuf<T> sl;               // coarse slopes for the 3D prolongation
     DevBuf<T> table;            // patch class inverses (constant viscosity)
     std::vector<double> ca, cb; // Chebyshev coefficients per step
     double lam_max = 0;

@@ -612,7 +612,7 @@ void Cg<T>::init(const Lvl& L_, Gmg<T>* pre_, const RedBuf& red_, CgState* st_de
   r.alloc(L.nvel);
   p.alloc(L.nvel);
   q.alloc(L.nvel);
-  if (pre) z.alloc(L.nvel);
+  z.alloc(L.nvel);  // also the second work vector of the single-kernel CG
 }
 
 template <typename T>
@@ -922,49 +922,95 @@ __global__ void k_fb_init(cudaGraphConditionalHandle h, CgState* c) {
 // ---------------------------------------------------------------------------
 constexpr int SB = 256;   // threads per block of the cluster solve
 
-// sum over the cluster, returned to every thread: block sums in a fixed
-// order, then the blocks' sums in rank order through distributed shared
-// memory (deterministic)
-__device__ double cluster_sum(double v, double* sh, double* part) {
+// sums over the cluster of NV values, returned to every thread: block sums
+// in a fixed order, then the blocks' sums in rank order through distributed
+// shared memory (deterministic). part[2][NV] alternates between calls, so
+// one cluster barrier per call suffices: a block rewrites a slot only after
+// the next call's barrier, which every block passes after it has read it.
+template <int NV>
+__device__ void cluster_sums(double (&v)[NV], double (*sh)[32], double (*part)[4], int& phase) {
   namespace cgx = cooperative_groups;
   cgx::cluster_group cl = cgx::this_cluster();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_sum(v);
-  if (lane == 0) sh[warp] = v;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double w = warp_sum(v[k]);
+    if (lane == 0) sh[k][warp] = w;
+  }
   __syncthreads();
   if (warp == 0) {
-    double w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-    w = warp_sum(w);
-    if (lane == 0) *part = w;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double w = lane < (int)(blockDim.x >> 5) ? sh[k][lane] : 0.0;
+      w = warp_sum(w);
+      if (lane == 0) part[phase][k] = w;
+    }
   }
   cl.sync();
-  // one warp fetches the blocks' partials (one remote load per lane, all in
-  // flight together) and reduces them in a fixed order
   if (warp == 0) {
     const unsigned nb = cl.num_blocks();
-    double w = (unsigned)lane < nb ? *cl.map_shared_rank(part, (unsigned)lane) : 0.0;
-    w = warp_sum(w);
-    if (lane == 0) sh[0] = w;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double w = (unsigned)lane < nb ? cl.map_shared_rank(&part[phase][0], (unsigned)lane)[k] : 0.0;
+      w = warp_sum(w);
+      if (lane == 0) sh[k][0] = w;
+    }
   }
-  cl.sync();  // every block has read the partials before they are reused
-  const double tot = sh[0];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = sh[k][0];
   __syncthreads();  // sh is rewritten by the next call
-  return tot;
+  phase ^= 1;
 }
 
-// M x = f from x = 0 by CG (same recurrences and stopping rule as the
-// multi-kernel form: ||r||^2 <= tol2 ||f||^2 on the recursive residual). Block
-// `rank` of the cluster owns one contiguous share of the face positions and
-// one of the padded arrays (balanced over the cluster's SMs); the arrays it
-// rewrites are read with plain coherent loads. The final state goes to c.
+// q = M p on this block's share of the face positions; returns (p, q) over it
+template <bool VarMu>
+__device__ __forceinline__ double apply_share(const Lvl& L, const double* p, double* q, int p0, int p1, int nx, int ny) {
+  double pq = 0.0;
+  for (int t = p0 + (int)threadIdx.x; t < p1; t += (int)blockDim.x) {
+    const int i = t % nx, u = t / nx;
+    const int j = u % ny, k = u / ny;
+    const int pos[3] = {i, j, k};
+    const long long cb = cix(L, i, j, k);
+    if (face_active<0>(L, i, j, k)) {
+      const double v = m_row<double, VarMu, 0, false>(L, p, pos);
+      q[L.off[0] + cb] = v;
+      pq += p[L.off[0] + cb] * v;
+    }
+    if (face_active<1>(L, i, j, k)) {
+      const double v = m_row<double, VarMu, 1, false>(L, p, pos);
+      q[L.off[1] + cb] = v;
+      pq += p[L.off[1] + cb] * v;
+    }
+    if (L.dim == 3 && face_active<2>(L, i, j, k)) {
+      const double v = m_row<double, VarMu, 2, false>(L, p, pos);
+      q[L.off[2] + cb] = v;
+      pq += p[L.off[2] + cb] * v;
+    }
+  }
+  return pq;
+}
+
+// M x = f from x = 0 by CG in the one-reduction form of Chronopoulos and
+// Gear (the CG iterates, with the two inner products of an iteration fused:
+// gamma = (r, r), delta = (M r, r); beta = gamma / gamma_prev, the step
+// alpha = gamma / (delta - beta gamma / alpha_prev) = gamma / (p, M p);
+// p = r + beta p, s = M r + beta s, x += alpha p, r -= alpha s). The stopping
+// rule is that of the multi-kernel form: ||r||^2 <= tol2 ||f||^2 on the
+// recursive residual. Block `rank` of the cluster owns one contiguous share of
+// the face positions and one of the padded arrays (balanced over the
+// cluster's SMs); arrays the kernel rewrites are read with plain coherent
+// loads. Two cluster barriers per iteration; the final state goes to c.
 template <bool VarMu>
 __global__ void __launch_bounds__(SB) k_cg_cluster(Lvl L, const double* __restrict__ f, double* __restrict__ x,
                                                     double* __restrict__ r, double* __restrict__ p,
-                                                    double* __restrict__ q, CgState* c, double tol2, int maxit) {
+                                                    double* __restrict__ w, double* __restrict__ sv, CgState* c,
+                                                    double tol2, int maxit) {
   namespace cgx = cooperative_groups;
   cgx::cluster_group cl = cgx::this_cluster();
-  __shared__ double sh[32];
-  __shared__ double part;
+  __shared__ double sh[2][32];
+  __shared__ double part[2][4];
+  int phase = 0;
   const int rank = (int)cl.block_rank(), nb = (int)cl.num_blocks(), tid = threadIdx.x;
   const int len = (int)L.nvel;
   const int nx = L.n[0] + 1, ny = L.n[1] + 1, nz = (L.dim == 3) ? L.n[2] + 1 : 1;
@@ -977,62 +1023,51 @@ __global__ void __launch_bounds__(SB) k_cg_cluster(Lvl L, const double* __restri
     const double ft = f[t];
     x[t] = 0.0;
     r[t] = ft;
-    p[t] = ft;
+    p[t] = 0.0;
+    sv[t] = 0.0;
     ff += ft * ft;
   }
-  ff = cluster_sum(ff, sh, &part);  // its barriers also publish p
-  double rr = ff;
+  cl.sync();  // r complete
+  double g[2] = {ff, apply_share<VarMu>(L, r, w, p0, p1, nx, ny)};  // (r, r), (M r, r)
+  cluster_sums<2>(g, sh, part, phase);
+  ff = g[0];
+  double gamma = g[0], delta = g[1], gamma_prev = 0.0, alpha = 0.0;
   int it = 0, status = ST_OK;
-  if (!isfinite(ff)) status = ST_NAN;
+  if (!isfinite(ff) || !isfinite(delta)) status = ST_NAN;
   bool done = (ff == 0.0) || status != ST_OK;
   while (!done) {
-    double pq = 0.0;
-    for (int t = p0 + tid; t < p1; t += SB) {
-      const int i = t % nx, u = t / nx;
-      const int j = u % ny, k = u / ny;
-      const int pos[3] = {i, j, k};
-      const long long cb = cix(L, i, j, k);
-      if (face_active<0>(L, i, j, k)) {
-        const double v = m_row<double, VarMu, 0, false>(L, p, pos);
-        q[L.off[0] + cb] = v;
-        pq += p[L.off[0] + cb] * v;
-      }
-      if (face_active<1>(L, i, j, k)) {
-        const double v = m_row<double, VarMu, 1, false>(L, p, pos);
-        q[L.off[1] + cb] = v;
-        pq += p[L.off[1] + cb] * v;
-      }
-      if (L.dim == 3 && face_active<2>(L, i, j, k)) {
-        const double v = m_row<double, VarMu, 2, false>(L, p, pos);
-        q[L.off[2] + cb] = v;
-        pq += p[L.off[2] + cb] * v;
-      }
+    double beta = 0.0, den = delta;
+    if (it > 0) {
+      beta = gamma / gamma_prev;
+      den = delta - beta * gamma / alpha;
     }
-    pq = cluster_sum(pq, sh, &part);  // q complete everywhere after this
-    if (!isfinite(pq)) { status = ST_NAN; break; }
-    if (!(pq > 0.0)) { status = ST_NOT_SPD; break; }
-    const double alpha = rr / pq;
-    double rn = 0.0;
+    if (!(den > 0.0)) { status = isfinite(den) ? ST_NOT_SPD : ST_NAN; break; }
+    alpha = gamma / den;
+    double rr = 0.0;
     for (int t = v0 + tid; t < v1; t += SB) {
-      x[t] += alpha * p[t];
-      const double rt = r[t] - alpha * q[t];
+      const double pt = r[t] + beta * p[t];
+      const double st = w[t] + beta * sv[t];
+      p[t] = pt;
+      sv[t] = st;
+      x[t] += alpha * pt;
+      const double rt = r[t] - alpha * st;
       r[t] = rt;
-      rn += rt * rt;
+      rr += rt * rt;
     }
-    rn = cluster_sum(rn, sh, &part);
     ++it;
-    const double rprev = rr;
-    rr = rn;
-    if (!isfinite(rn)) { status = ST_NAN; break; }
-    if (rn <= tol2 * ff) break;
+    cl.sync();  // r complete before the product reads neighbours
+    double h[2] = {rr, apply_share<VarMu>(L, r, w, p0, p1, nx, ny)};
+    cluster_sums<2>(h, sh, part, phase);
+    gamma_prev = gamma;
+    gamma = h[0];
+    delta = h[1];
+    if (!isfinite(gamma) || !isfinite(delta)) { status = ST_NAN; break; }
+    if (gamma <= tol2 * ff) break;
     if (it >= maxit) { status = ST_INNER_NOT_CONVERGED; break; }
-    const double beta = rn / rprev;
-    for (int t = v0 + tid; t < v1; t += SB) p[t] = r[t] + beta * p[t];
-    cl.sync();  // p complete before the next product reads neighbours
   }
   if (rank == 0 && tid == 0) {
     c->ff = ff;
-    c->rr = rr;
+    c->rr = gamma;
     c->it = it;
     c->total_it += it;
     c->solves += 1;
@@ -1475,11 +1510,11 @@ void Solver::launch_cg_block(const double* fpad, double* xpad, cudaStream_t s) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   if (var)
-    GKB_CUDA(cudaLaunchKernelEx(&cfg, k_cg_cluster<true>, L64, fpad, xpad, c.r.p, c.p.p, c.q.p, cg_dev, tol2,
-                                opt.maxit_inner));
+    GKB_CUDA(cudaLaunchKernelEx(&cfg, k_cg_cluster<true>, L64, fpad, xpad, c.r.p, c.p.p, c.q.p, c.z.p, cg_dev,
+                                tol2, opt.maxit_inner));
   else
-    GKB_CUDA(cudaLaunchKernelEx(&cfg, k_cg_cluster<false>, L64, fpad, xpad, c.r.p, c.p.p, c.q.p, cg_dev, tol2,
-                                opt.maxit_inner));
+    GKB_CUDA(cudaLaunchKernelEx(&cfg, k_cg_cluster<false>, L64, fpad, xpad, c.r.p, c.p.p, c.q.p, c.z.p, cg_dev,
+                                tol2, opt.maxit_inner));
 }
 
 int Solver::inner_solve(const double* fpad, double* xpad) {

@@ -71,7 +71,8 @@ VARMU_SMOOTH_EXTRA = {2: 5.0, 3: 10.0}
 TRAFFIC = {
     ("stokes2d", "fp64", "smooth"): 16.85e6 + 0.05e6,      # smoother_residual_stokes2d_1024_fp64_full.md
     ("stokes2d", "fp64", "residual"): 33.71e6 + 0.04e6,
-    ("varvisc2d", "mixed", "smooth"): 203.05e6 + 47.62e6,  # varvisc_smoother_residual_2048_mixed_full.md
+    ("varvisc2d", "mixed", "smooth"): 203.01e6 + 47.88e6,  # varvisc_smoother_residual_2048_mixed_full.md
+    ("varvisc2d", "mixed", "residual"): 84.23e6 + 12.84e6,
 }
 # algorithmic bytes of the captured finest-level launch per velocity unknown,
 # in elements (first Chebyshev step: r read, d and x written; residual: x, b

@@ -1467,10 +1467,15 @@ bool Solver::small_cg() const {
   return opt.inner == GKB_INNER_CG && opt.precision == GKB_PREC_FP64 && L64.nvel <= (1LL << 15);
 }
 
-// cluster size for k_cg_cluster: 16 blocks where the device allows it, else 8
+// cluster size for k_cg_cluster: 16 blocks where the device allows it, else
+// 8 (decided once per device and kernel)
 static int cg_cluster_size(bool var_mu) {
-  static int cached[2] = {0, 0};
-  int& cs = cached[var_mu ? 1 : 0];
+  static std::mutex mtx;
+  static std::map<int, int> cached;
+  int dev = 0;
+  GKB_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mtx);
+  int& cs = cached[2 * dev + (var_mu ? 1 : 0)];
   if (cs) return cs;
   const void* fn = var_mu ? (const void*)k_cg_cluster<true> : (const void*)k_cg_cluster<false>;
   cs = 8;

@@ -209,6 +209,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(value, ws, device="cuda"):
+    """The largest value over the ranks of the initialised process group
+    (the step time of a multi-GPU run is its slowest rank's)."""
+    if ws <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def batch_seed_offset(rank):
+    """Seed offset of rank `rank`'s batch: every rank solves its own problems
+    (weak scaling: per-GPU work fixed, no data-path collective)."""
+    return 6 + 1000 * int(rank)
+
+
 # ---------------------------------------------------------------------------
 # workloads: the problems one step solves
 # ---------------------------------------------------------------------------
@@ -260,7 +278,8 @@ class Workload:
             self.sample = ("varvisc", 128, [100.0])
         elif self.name == "batched2d":
             count = args.batch
-            self.problems = [dict(pr, gamma=100.0) for pr in W.batched2d(count=count)]
+            self.problems = [dict(pr, gamma=100.0)
+                             for pr in W.batched2d(count=count, seed_offset=batch_seed_offset(getattr(args, "rank", 0)))]
             self.dim = 2
             self.batched = True
             self.form = "mixed" if args.form_default else args.form
@@ -578,11 +597,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms = statistics.mean(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), ws)
     stats = B.stats()
     outer = [st["outer_iterations"] for st in stats]
     inner = [st["inner_iterations"] for st in stats]
@@ -751,6 +766,7 @@ def main():
     args.gammas = [float(x) for x in args.gammas.split(",")]
     args.warmup = max(args.warmup, 0)
     ws, rank, local = dist_setup()
+    args.rank = rank
     if args.impl == "reference":
         return run_reference(args, ws, rank)
     if args.probe:

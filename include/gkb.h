@@ -317,7 +317,9 @@ int gkb_unet_adam_step(gkb_unet u, float lr, float beta1, float beta2, float eps
  * are multiplied by the network's target scale. */
 int gkb_unet_train(gkb_unet u, const float* x_img, const float* t_img, int64_t count, int h, int w, int batch,
                    int steps, float lr, unsigned long long seed, double* losses);
-/* The network is trained on s * e^ and used as e^ = N(r^) / s (default 1). */
+/* The network is trained on s * e^ and used as e^ = N(r^) / s (default 1).
+ * A handle's captured solve graph keeps the s of its last gkb_set_unet or
+ * gkb_set_problem; call gkb_set_unet again after changing it. */
 int gkb_unet_set_target_scale(gkb_unet u, float s);
 int gkb_unet_get_target_scale(gkb_unet u, float* s);
 const char* gkb_unet_last_error(gkb_unet u);

@@ -133,12 +133,14 @@ __global__ void __launch_bounds__(UT) k_conv_fwd(In2 in, const float* __restrict
 
 // ---------------------------------------------------------------------------
 // BF16 tensor-core forward convolution (mma.sync m16n8k16, FP32 accumulate)
-// Block: 4 warps, tile of 4 rows x 16 columns of output pixels; warp = one
-// row = one M tile of 16 pixels; N = output channels in tiles of 8; K = 9 taps
-// x input channels in steps of 16. The input tile (with a one-pixel halo) and
-// the transposed weights are staged in shared memory as BF16.
+// Block: 8 warps, tile of TR = 8 rows x TC = 32 columns of output pixels; warp
+// w owns row w as two M tiles of 16 pixels; N = output channels in tiles of
+// 8; K = 9 taps x input channels in steps of 16. The input tile with a
+// one-pixel halo and all nine taps of transposed weights are staged once in
+// shared memory as BF16, every pixel's (and output channel's) K vector padded
+// by 8 elements so that the fragment loads of a warp hit distinct banks.
 // ---------------------------------------------------------------------------
-constexpr int TR = 4, TC = 16;
+constexpr int TR = 8, TC = 32, TCT = 256;
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
   asm volatile(
@@ -147,82 +149,127 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// four consecutive channels [ci, ci + 4) of the (concatenated) input at
+// full-resolution pixel (yy, xx); the group lies inside one of the two
+// inputs whenever c0 is a multiple of 4 (vector loads), else per channel
+__device__ __forceinline__ float4 in_val4(const In2& in, int b, int yy, int xx, int h, int wd, int ci, int cin) {
+  if ((in.c0 & 3) == 0 && ci + 4 <= cin) {
+    if (ci < in.c0 && !in.up0 && (in.c0 & 3) == 0)
+      return __ldg(reinterpret_cast<const float4*>(in.p0 + (((long long)b * h + yy) * wd + xx) * in.c0 + ci));
+    if (ci >= in.c0 && (in.c1 & 3) == 0)
+      return __ldg(reinterpret_cast<const float4*>(in.p1 + (((long long)b * h + yy) * wd + xx) * in.c1 + (ci - in.c0)));
+  }
+  float4 v;
+  v.x = ci + 0 < cin ? in_val(in, b, yy, xx, h, wd, ci + 0) : 0.f;
+  v.y = ci + 1 < cin ? in_val(in, b, yy, xx, h, wd, ci + 1) : 0.f;
+  v.z = ci + 2 < cin ? in_val(in, b, yy, xx, h, wd, ci + 2) : 0.f;
+  v.w = ci + 3 < cin ? in_val(in, b, yy, xx, h, wd, ci + 3) : 0.f;
+  return v;
+}
+
+template <int CIP, int COP>
+struct TcSmem {
+  static constexpr int KS = CIP + 8;                     // padded K stride (elements)
+  static constexpr int XS = (TR + 2) * (TC + 2) * KS;    // input tile
+  static constexpr int WS = 9 * COP * KS;                // weights [tap][co][ci]
+  static constexpr size_t bytes = (size_t)(XS + WS) * sizeof(__nv_bfloat16);
+};
+
 // CIP: input channels padded to a multiple of 16; COP: output channels padded to a multiple of 8
 template <int CIP, int COP>
-__global__ void __launch_bounds__(128) k_conv_fwd_tc(In2 in, const __nv_bfloat16* __restrict__ wbf /*[9][cin][cout]*/,
+__global__ void __launch_bounds__(TCT) k_conv_fwd_tc(In2 in, const __nv_bfloat16* __restrict__ wbf /*[9][cin][cout]*/,
                                                      const float* __restrict__ bias, float* __restrict__ out, int cout,
                                                      int n, int h, int wd, int relu) {
-  __shared__ __align__(16) __nv_bfloat16 xs[(TR + 2) * (TC + 2) * CIP];
-  __shared__ __align__(16) __nv_bfloat16 wt[COP * CIP];  // one tap: [co][ci] (k contiguous)
+  using SM = TcSmem<CIP, COP>;
+  constexpr int KS = SM::KS;
+  extern __shared__ __align__(16) __nv_bfloat16 tc_smem[];
+  __nv_bfloat16* xs = tc_smem;
+  __nv_bfloat16* wt = tc_smem + SM::XS;
   const int cin = in.c0 + in.c1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int x0 = blockIdx.x * TC, y0 = blockIdx.y * TR, b = blockIdx.z;
-  // stage the input tile with halo (zero outside the image, zero channel padding)
-  for (int t = tid; t < (TR + 2) * (TC + 2) * CIP; t += blockDim.x) {
-    const int ci = t % CIP, px = t / CIP;
-    const int ty = px / (TC + 2), tx = px % (TC + 2);
+  // input tile with halo, four channels per item (zero outside the image and
+  // in the channel padding)
+  constexpr int G4 = CIP / 4;
+  for (int t = tid; t < (TR + 2) * (TC + 2) * G4; t += TCT) {
+    const int g4 = t % G4, px = t / G4;
+    const int ty = px / (TC + 2), tx = px - ty * (TC + 2);
     const int yy = y0 + ty - 1, xx = x0 + tx - 1;
-    float v = 0.f;
-    if (yy >= 0 && yy < h && xx >= 0 && xx < wd && ci < cin) v = in_val(in, b, yy, xx, h, wd, ci);
-    xs[t] = __float2bfloat16(v);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (yy >= 0 && yy < h && xx >= 0 && xx < wd && 4 * g4 < cin) v = in_val4(in, b, yy, xx, h, wd, 4 * g4, cin);
+    __nv_bfloat16* d = xs + px * KS + 4 * g4;
+    d[0] = __float2bfloat16(v.x);
+    d[1] = __float2bfloat16(v.y);
+    d[2] = __float2bfloat16(v.z);
+    d[3] = __float2bfloat16(v.w);
+  }
+  // all nine taps of the weights, transposed to [tap][co][ci] (zero padded)
+  for (int t = tid; t < 9 * COP * CIP; t += TCT) {
+    const int co = t % COP, ci = (t / COP) % CIP, tap = t / (COP * CIP);
+    wt[(tap * COP + co) * KS + ci] =
+        (ci < cin && co < cout) ? wbf[((long long)tap * cin + ci) * cout + co] : __float2bfloat16(0.f);
   }
   __syncthreads();
   const int g = lane >> 2, tq = lane & 3;
   constexpr int NT = COP / 8;
-  float acc[NT][4];
+  float acc[2][NT][4];
 #pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[nt][q] = 0.f;
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
   const int row = warp;  // output row within the tile
+#pragma unroll 1
   for (int tap = 0; tap < 9; ++tap) {
-    const int ky = tap / 3, kx = tap % 3;
-    // stage this tap's transposed weights (zero padded)
-    __syncthreads();
-    for (int t = tid; t < COP * CIP; t += blockDim.x) {
-      const int ci = t % CIP, co = t / CIP;
-      wt[t] = (ci < cin && co < cout) ? wbf[((long long)tap * cin + ci) * cout + co] : __float2bfloat16(0.f);
-    }
-    __syncthreads();
+    const int ky = tap / 3, kx = tap - 3 * ky;
+    const __nv_bfloat16* wtap = wt + tap * COP * KS;
 #pragma unroll
     for (int k0 = 0; k0 < CIP; k0 += 16) {
-      // A[m][k] = xs[(row + ky)][(m + kx)][k0 + k]
-      const __nv_bfloat16* arow0 = xs + (((row + ky) * (TC + 2) + (g + kx)) * CIP + k0);
-      const __nv_bfloat16* arow1 = xs + (((row + ky) * (TC + 2) + (g + 8 + kx)) * CIP + k0);
-      uint32_t a[4];
-      a[0] = *reinterpret_cast<const uint32_t*>(arow0 + 2 * tq);
-      a[1] = *reinterpret_cast<const uint32_t*>(arow1 + 2 * tq);
-      a[2] = *reinterpret_cast<const uint32_t*>(arow0 + 2 * tq + 8);
-      a[3] = *reinterpret_cast<const uint32_t*>(arow1 + 2 * tq + 8);
+      uint32_t bb[NT][2];
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
-        // B[k][n] = w[tap][k0 + k][nt*8 + n], staged as wt[nt*8 + n][k0 + k]
-        const __nv_bfloat16* bcol = wt + ((nt * 8 + g) * CIP + k0);
-        uint32_t bb[2];
-        bb[0] = *reinterpret_cast<const uint32_t*>(bcol + 2 * tq);
-        bb[1] = *reinterpret_cast<const uint32_t*>(bcol + 2 * tq + 8);
-        mma_bf16(acc[nt], a, bb);
+        // B[k][n] = w[tap][k0 + k][nt*8 + n], staged as wt[tap][nt*8 + n][k0 + k]
+        const __nv_bfloat16* bcol = wtap + (nt * 8 + g) * KS + k0;
+        bb[nt][0] = *reinterpret_cast<const uint32_t*>(bcol + 2 * tq);
+        bb[nt][1] = *reinterpret_cast<const uint32_t*>(bcol + 2 * tq + 8);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        // A[m][k] = xs[row + ky][mt*16 + m + kx][k0 + k]
+        const __nv_bfloat16* arow0 = xs + ((row + ky) * (TC + 2) + (mt * 16 + g + kx)) * KS + k0;
+        const __nv_bfloat16* arow1 = arow0 + 8 * KS;
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(arow0 + 2 * tq);
+        a[1] = *reinterpret_cast<const uint32_t*>(arow1 + 2 * tq);
+        a[2] = *reinterpret_cast<const uint32_t*>(arow0 + 2 * tq + 8);
+        a[3] = *reinterpret_cast<const uint32_t*>(arow1 + 2 * tq + 8);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) mma_bf16(acc[mt][nt], a, bb[nt]);
       }
     }
   }
   // D[m][n]: rows g and g + 8, columns 2 tq and 2 tq + 1 of each n tile
   const int yy = y0 + row;
+  if (yy >= h) return;
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    const int xx = x0 + g + 8 * half;
-    if (yy >= h || xx >= wd) continue;
-    float* op = out + (((long long)b * h + yy) * wd + xx) * cout;
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
+    for (int half = 0; half < 2; ++half) {
+      const int xx = x0 + mt * 16 + g + 8 * half;
+      if (xx >= wd) continue;
+      float* op = out + (((long long)b * h + yy) * wd + xx) * cout;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int co = nt * 8 + 2 * tq + e;
-        if (co < cout) {
-          const float v = acc[nt][2 * half + e] + __ldg(bias + co);
-          op[co] = relu ? fmaxf(v, 0.f) : v;
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int co = nt * 8 + 2 * tq + e;
+          if (co < cout) {
+            const float v = acc[mt][nt][2 * half + e] + __ldg(bias + co);
+            op[co] = relu ? fmaxf(v, 0.f) : v;
+          }
         }
-      }
-  }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -487,6 +534,13 @@ void Unet::init(int cin, int k1, int k2, int cout, unsigned long long seed, cuda
   // the largest FP32 convolution needs 9 * 64 * 32 floats of shared memory
   const int big = 9 * 64 * 32 * 4;
   GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+  // the tensor-core convolutions stage all nine weight taps (up to 80 KB)
+  GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcSmem<16, 8>::bytes));
+  GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc<16, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcSmem<16, 16>::bytes));
+  GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc<16, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcSmem<16, 32>::bytes));
+  GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc<32, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcSmem<32, 32>::bytes));
+  GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc<48, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcSmem<48, 16>::bytes));
+  GKB_CUDA(cudaFuncSetAttribute(k_conv_fwd_tc<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TcSmem<64, 32>::bytes));
   GKB_CUDA(cudaFuncSetAttribute(k_conv_bwd_data<64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
   bf16_stale = true;
   adam_t = 0;
@@ -520,12 +574,15 @@ static void conv_fwd(const Unet& U, int li, In2 in, float* out, int n, int h, in
     const __nv_bfloat16* wb = U.params_bf16.p + L.off;
     dim3 grid((w + TC - 1) / TC, (h + TR - 1) / TR, n);
     const int cin = L.cin;
-    if (cin <= 16 && L.cout <= 8) k_conv_fwd_tc<16, 8><<<grid, 128, 0, s>>>(in, wb, bp, out, L.cout, n, h, w, relu);
-    else if (cin <= 16 && L.cout <= 16) k_conv_fwd_tc<16, 16><<<grid, 128, 0, s>>>(in, wb, bp, out, L.cout, n, h, w, relu);
-    else if (cin <= 16) k_conv_fwd_tc<16, 32><<<grid, 128, 0, s>>>(in, wb, bp, out, L.cout, n, h, w, relu);
-    else if (cin <= 32) k_conv_fwd_tc<32, 32><<<grid, 128, 0, s>>>(in, wb, bp, out, L.cout, n, h, w, relu);
-    else if (cin <= 48) k_conv_fwd_tc<48, 16><<<grid, 128, 0, s>>>(in, wb, bp, out, L.cout, n, h, w, relu);
-    else k_conv_fwd_tc<64, 32><<<grid, 128, 0, s>>>(in, wb, bp, out, L.cout, n, h, w, relu);
+#define GKB_TC(CI, CO) \
+  k_conv_fwd_tc<CI, CO><<<grid, TCT, TcSmem<CI, CO>::bytes, s>>>(in, wb, bp, out, L.cout, n, h, w, relu)
+    if (cin <= 16 && L.cout <= 8) GKB_TC(16, 8);
+    else if (cin <= 16 && L.cout <= 16) GKB_TC(16, 16);
+    else if (cin <= 16) GKB_TC(16, 32);
+    else if (cin <= 32) GKB_TC(32, 32);
+    else if (cin <= 48) GKB_TC(48, 16);
+    else GKB_TC(64, 32);
+#undef GKB_TC
   } else {
     const size_t sm = 9ull * L.cin * L.cout * sizeof(float);
     if (L.cout == 32) k_conv_fwd<32><<<grid_for(P), UT, sm, s>>>(in, wp, bp, out, n, h, w, relu);

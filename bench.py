@@ -244,6 +244,7 @@ class Workload:
         self.form = args.form
         self.learned = None     # "replace" / "composite": flexible CG with the network
         self.net = None
+        self.kernel_variant = getattr(args, "kernel_variant", None)
         if self.name == "stokes2d":
             base = W.stokes2d(args.n)
             self.problems = [dict(base, gamma=float(gm)) for gm in args.gammas]
@@ -303,9 +304,11 @@ class Workload:
         return "solves/s" if self.batched else "s"
 
 
-def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0):
+def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, inner=None):
     opt = gk.gkb_default_options()
     opt.autotune = autotune
+    if wk.kernel_variant is not None:
+        opt.kernel_variant = wk.kernel_variant
     opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
     opt.inner = wk.inner
     opt.tol_inner = wk.tol_inner
@@ -316,6 +319,8 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0):
     if learned:
         opt.inner = gk.GKB_INNER_FCG_UNET if learned == "replace" else gk.GKB_INNER_FCG_UNET_MG
         opt.unet_side = wk.unet_side
+    if inner is not None:
+        opt.inner = inner
     h = gk.gkb_create(opt)
     if learned:
         gk.gkb_set_unet(h, wk.net)
@@ -332,13 +337,13 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0):
 class Bound:
     """Handles plus device/host buffers of a workload, and its step."""
 
-    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0):
+    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0, inner=None):
         import numpy as np
         self.gk, self.torch, self.wk = gk, torch, wk
         probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
         self.probs = probs
         lf = wk.learned if learned == "default" else learned
-        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune) for pr in probs]
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner) for pr in probs]
         self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
         for h, pr in zip(self.hs, probs):
             m, n = gk.gkb_layout(h)
@@ -622,10 +627,10 @@ def run_ours(args, ws, rank, local):
     rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
 
-    def time_form(form, learned, autotune=None):
+    def time_form(form, learned, autotune=None, inner=None):
         autotune = args.autotune if autotune is None else autotune
         t_setup = time.perf_counter()
-        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune)
+        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune, inner=inner)
         t_setup = time.perf_counter() - t_setup
         for _ in range(2):
             B2.step(args)
@@ -666,6 +671,8 @@ def run_ours(args, ws, rank, local):
             other = "mixed" if wk.form == "fp64" else "fp64"
             forms[other] = time_form(other, None)
             forms[wk.form] = head
+            if wk.dim == 2:   # the paper's other inner Krylov method (host-sequenced)
+                forms["fgmres_fp64"] = time_form("fp64", None, autotune=0, inner=gk.GKB_INNER_FGMRES)
         if args.autotune:
             forms[wk.form + "_default_options"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=0)
         else:
@@ -744,6 +751,8 @@ def main():
     ap.add_argument("--train-batch", type=int, default=8)
     ap.add_argument("--train-lr", type=float, default=1e-3)
     ap.add_argument("--learned-form", choices=["replace", "composite"], default="replace")
+    ap.add_argument("--kernel-variant", type=int, choices=[0, 1, 2], default=None,
+                    help="deep-interior fast paths: 0 FP32 only (default), 1 none, 2 everywhere (untuned handles)")
     ap.add_argument("--form", choices=["fp64", "mixed"], default=None)
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=256)

@@ -76,6 +76,10 @@ extern "C" {
                                  correction at the level of unet_side cells is
                                  a U-Net (gkb_set_unet; 2D all-Dirichlet);
                                  without a network: the plain V-cycle         */
+#define GKB_INNER_FGMRES  4   /* restarted flexible GMRES (fgmres_restart
+                                 vectors) with one GMG V-cycle as right
+                                 preconditioner, FP64, host-sequenced (the
+                                 paper's other inner Krylov method, Sec. 3)  */
 #define GKB_INNER_FCG_UNET_MG 3  /* flexible CG + a V-cycle that takes the
                                  network's correction at the level of
                                  unet_side cells as the starting guess of the
@@ -143,6 +147,7 @@ typedef struct {
                              (or whose preconditioned vector is not finite)
                              continues as plain GMG-PCG from its iterate;
                              0 disables the switch                            */
+  int fgmres_restart;     /* GKB_INNER_FGMRES: Krylov vectors per cycle (1..64) */
   int autotune;           /* 1: gkb_set_problem searches smoother_degree (1..3),
                              kernel_variant (0..2) and coarse_max (8, 16, 32)
                              for the fastest inner solve (device time of one

@@ -33,6 +33,7 @@ GKB_INNER_CG = 0
 GKB_INNER_GMG_PCG = 1
 GKB_INNER_FCG_UNET = 2
 GKB_INNER_FCG_UNET_MG = 3
+GKB_INNER_FGMRES = 4
 GKB_OP_W, GKB_OP_A, GKB_OP_AT, GKB_OP_M = 0, 1, 2, 3
 KERNEL_CLASSES = ["apply", "residual", "smooth", "restrict", "prolong", "coarse", "blas", "gkb", "layout", "unet"]
 
@@ -64,7 +65,8 @@ class gkb_options(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("unet_side", ctypes.c_int),
-                ("fcg_rho", ctypes.c_double), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("fcg_rho", ctypes.c_double), ("fgmres_restart", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class gkb_stats_t(ctypes.Structure):

@@ -67,6 +67,7 @@ int gkb_default_options(gkb_options* opt) {
   opt->kernel_variant = 0;
   opt->unet_side = 0;
   opt->fcg_rho = 0.8;
+  opt->fgmres_restart = 30;
   opt->stream = nullptr;
   return GKB_OK;
 }
@@ -75,7 +76,9 @@ int gkb_create(gkb_handle* out, const gkb_options* opt) {
   if (!out || !opt) return GKB_ERR_INVALID_ARG;
   *out = nullptr;
   if (opt->precision != GKB_PREC_FP64 && opt->precision != GKB_PREC_MIXED) return GKB_ERR_INVALID_ARG;
-  if (opt->inner < GKB_INNER_CG || opt->inner > GKB_INNER_FCG_UNET_MG) return GKB_ERR_INVALID_ARG;
+  if (opt->inner < GKB_INNER_CG || opt->inner > GKB_INNER_FGMRES) return GKB_ERR_INVALID_ARG;
+  if (opt->inner == GKB_INNER_FGMRES && (opt->fgmres_restart < 1 || opt->fgmres_restart > 64))
+    return GKB_ERR_INVALID_ARG;
   if (opt->unet_side < 0 || !(opt->fcg_rho >= 0 && opt->fcg_rho < 1) || opt->autotune < 0 || opt->autotune > 1)
     return GKB_ERR_INVALID_ARG;
   if (!(opt->tol_inner > 0) || opt->maxit < 0 || opt->maxit > 100000000 || opt->maxit_inner < 1 ||

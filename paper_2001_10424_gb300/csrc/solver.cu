@@ -1178,7 +1178,9 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   int nat[6] = {0, 0, 0, 0, 0, 0};
   enclosed = true;
   for (int s = 0; s < 2 * g->dim; ++s) { nat[s] = g->bc[s] == GKB_BC_NATURAL; if (nat[s]) enclosed = false; }
-  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || learned_inner();
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || opt.inner == GKB_INNER_FGMRES || learned_inner();
+  if (opt.inner == GKB_INNER_FGMRES && opt.precision != GKB_PREC_FP64)
+    throw Error{GKB_ERR_INVALID_ARG, "the FGMRES inner solver runs in FP64"};
   if (use_gmg && !enclosed)
     throw Error{GKB_ERR_INVALID_ARG, "the multigrid preconditioner needs Dirichlet velocity on every side"};
   if (learned_inner() && g->dim != 2)
@@ -1246,8 +1248,9 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   hist_inner.alloc((size_t)opt.maxit + 4);
   // multigrid + CG (tuned first when asked)
   tuned_ms = 0;
-  if (opt.autotune && use_gmg) autotune_inner(viscosity != nullptr);
+  if (opt.autotune && use_gmg && opt.inner != GKB_INNER_FGMRES) autotune_inner(viscosity != nullptr);
   else build_inner();
+  if (opt.inner == GKB_INNER_FGMRES) fgm.init(L64.nvel, opt.fgmres_restart);
   stats.tuned_inner_ms = tuned_ms;
   attach_net_levels();
   GKB_CUDA(cudaStreamSynchronize(stream));
@@ -1261,7 +1264,7 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
 // options (smoother degree, coarse size, kernel variant).
 void Solver::build_inner() {
   const bool mixed = opt.precision == GKB_PREC_MIXED;
-  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || learned_inner();
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || opt.inner == GKB_INNER_FGMRES || learned_inner();
   // deep-interior fast paths: variant 0 enables them in FP32 only (faster
   // there, slower on the FP64 pipe), 1 nowhere, 2 everywhere
   L64.fast = (opt.kernel_variant == 2) ? 1 : 0;
@@ -1525,7 +1528,15 @@ void Solver::launch_cg_block(const double* fpad, double* xpad, cudaStream_t s) {
 int Solver::inner_solve(const double* fpad, double* xpad) {
   int its = 0, st = 0;
   if (opt.precision == GKB_PREC_MIXED) st = mixed_solve(fpad, xpad, &its);
-  else if (small_cg()) {
+  else if (opt.inner == GKB_INNER_FGMRES) {
+    st = fgmres_solve(*this, fpad, xpad, &its);
+    // the inner-solve record reads the CG state: its count and status
+    CgState h{};
+    h.it = its;
+    h.status = st;
+    h.done = 1;
+    GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, stream));
+  } else if (small_cg()) {
     launch_cg_block(fpad, xpad, stream);
     GKB_CUDA(cudaMemcpyAsync(cg_host, cg_dev, sizeof(CgState), cudaMemcpyDeviceToHost, stream));
     GKB_CUDA(cudaStreamSynchronize(stream));
@@ -1778,7 +1789,7 @@ void Solver::capture_core(cudaStream_t s, cudaStream_t sb1, cudaStream_t sb2) {
 
 void Solver::build_solve_graph() {
   sgraph.destroy();
-  if (!opt.use_graph || opt.profile) return;
+  if (!opt.use_graph || opt.profile || opt.inner == GKB_INNER_FGMRES) return;  // FGMRES: host-sequenced
   ensure_capture_streams();
   Profiler* P = g_prof;
   if (P) {
@@ -2110,7 +2121,7 @@ void Solver::precond(const double* rin, double* zout) {
   }
   GKB_CUDA(cudaMemsetAsync(wtmp.p, 0, len * sizeof(double), s));
   { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<double><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, wtmp.p); }
-  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || learned_inner();
+  const bool use_gmg = opt.inner == GKB_INNER_GMG_PCG || opt.inner == GKB_INNER_FGMRES || learned_inner();
   refresh_net();
   if (opt.precision == GKB_PREC_MIXED) {
     { ProfScope ps_(GKB_KC_LAYOUT, s); k_pack_vel<float><<<lin_blocks(m), 256, 0, s>>>(L, cmp, src, f32.p); }

@@ -137,6 +137,19 @@ struct Cg {
   int solve(const T* f, T* x, double tol, int maxit, cudaStream_t s, int* iters);
 };
 
+// Work space of the FGMRES(m) inner solver (fgmres.cu): the Krylov basis
+// V (m + 1 vectors), the preconditioned vectors Z (m), and small scratch.
+struct Fgmres {
+  int m = 0;
+  long long len = 0;
+  DevBuf<double> V, Z, w, r, h, h2, y, part;
+  void init(long long len, int m);
+};
+
+struct Solver;
+// x = M^-1 f by FGMRES(m) with one V-cycle as right preconditioner (FP64)
+int fgmres_solve(Solver& S, const double* f, double* x, int* iters);
+
 struct Solver {
   gkb_options opt{};
   cudaStream_t stream = nullptr;
@@ -164,6 +177,7 @@ struct Solver {
   // multigrid and CG in both precisions (only the ones in use are built)
   Gmg<double> gmg64;
   Gmg<float> gmg32;
+  Fgmres fgm;
   Cg<double> cg64;
   Cg<float> cg32;
 

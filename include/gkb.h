@@ -148,8 +148,12 @@ typedef struct {
                              continues as plain GMG-PCG from its iterate;
                              0 disables the switch                            */
   int fgmres_restart;     /* GKB_INNER_FGMRES: Krylov vectors per cycle (1..64) */
+  double cheb_lo;         /* Chebyshev smoothing interval [cheb_lo, cheb_hi] x
+                             lambda_max(C M) (power-iteration estimate);   */
+  double cheb_hi;         /* 0 < cheb_lo < cheb_hi; defaults 0.1 and 1.1     */
   int autotune;           /* 1: gkb_set_problem searches smoother_degree (1..3),
-                             kernel_variant (0..2) and coarse_max (8, 16, 32)
+                             kernel_variant (0..2), coarse_max (8, 16, 32) and
+                             cheb_lo (0.05, 0.1, 0.2, 0.3), one after another,
                              for the fastest inner solve (device time of one
                              GMG-PCG solve to tol_inner) and keeps it; results
                              are cached per device, grid, viscosity kind,

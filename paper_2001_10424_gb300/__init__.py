@@ -65,8 +65,8 @@ class gkb_options(ctypes.Structure):
                 ("maxit", ctypes.c_int), ("maxit_inner", ctypes.c_int), ("smoother_degree", ctypes.c_int),
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("unet_side", ctypes.c_int),
-                ("fcg_rho", ctypes.c_double), ("fgmres_restart", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("fcg_rho", ctypes.c_double), ("fgmres_restart", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class gkb_stats_t(ctypes.Structure):

@@ -68,6 +68,8 @@ int gkb_default_options(gkb_options* opt) {
   opt->unet_side = 0;
   opt->fcg_rho = 0.8;
   opt->fgmres_restart = 30;
+  opt->cheb_lo = 0.1;
+  opt->cheb_hi = 1.1;
   opt->stream = nullptr;
   return GKB_OK;
 }
@@ -79,6 +81,7 @@ int gkb_create(gkb_handle* out, const gkb_options* opt) {
   if (opt->inner < GKB_INNER_CG || opt->inner > GKB_INNER_FGMRES) return GKB_ERR_INVALID_ARG;
   if (opt->inner == GKB_INNER_FGMRES && (opt->fgmres_restart < 1 || opt->fgmres_restart > 64))
     return GKB_ERR_INVALID_ARG;
+  if (!(opt->cheb_lo > 0 && opt->cheb_lo < opt->cheb_hi && opt->cheb_hi < 10)) return GKB_ERR_INVALID_ARG;
   if (opt->unet_side < 0 || !(opt->fcg_rho >= 0 && opt->fcg_rho < 1) || opt->autotune < 0 || opt->autotune > 1)
     return GKB_ERR_INVALID_ARG;
   if (!(opt->tol_inner > 0) || opt->maxit < 0 || opt->maxit > 100000000 || opt->maxit_inner < 1 ||

@@ -1269,6 +1269,8 @@ void Solver::build_inner() {
   // there, slower on the FP64 pipe), 1 nowhere, 2 everywhere
   L64.fast = (opt.kernel_variant == 2) ? 1 : 0;
   L32.fast = (opt.kernel_variant == 1) ? 0 : 1;
+  gmg32.cheb_lo = gmg64.cheb_lo = opt.cheb_lo;
+  gmg32.cheb_hi = gmg64.cheb_hi = opt.cheb_hi;
   if (mixed) {
     if (use_gmg) gmg32.build(L32, mu32.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
     cg32.init(L32, use_gmg ? &gmg32 : nullptr, red, cg_dev, cg_host);
@@ -1284,11 +1286,14 @@ void Solver::build_inner() {
   }
 }
 
-// Device time (ms) of one inner solve M x = f on a fixed pseudo-random f,
-// run as a captured graph like the solver's own; +inf when it fails.
+// Device time (ms) of one inner solve M x = f, run as a captured graph like
+// the solver's own; +inf when it fails. f = A A^T h for a fixed pseudo-random
+// h lies in the range of A like the right-hand sides A q of the GKB loop.
 double Solver::time_inner_solve() {
   ensure_capture_streams();
-  { ProfScope ps_(GKB_KC_LAYOUT, stream); k_fill_hash<double><<<fgrid(L64), dim3(32, 8), 0, stream>>>(L64, f.p); }
+  { ProfScope ps_(GKB_KC_LAYOUT, stream); k_fill_hash<double><<<fgrid(L64), dim3(32, 8), 0, stream>>>(L64, wtmp.p); }
+  Ops<double>::negdiv(L64, wtmp.p, ctmp.p, 1.0, stream);
+  Ops<double>::grad(L64, ctmp.p, f.p, 1.0, stream);
   GKB_CUDA(cudaStreamSynchronize(stream));
   Profiler* P = g_prof;
   const int saved = P ? P->phase : -1;
@@ -1334,7 +1339,7 @@ double Solver::time_inner_solve() {
 namespace {
 struct Tuned {
   int degree, variant, coarse_max;
-  double ms;
+  double lo, ms;
 };
 std::mutex g_tune_mutex;
 std::map<std::string, Tuned> g_tune_cache;
@@ -1354,14 +1359,15 @@ void tune_read_file() {
   if (!fp) return;
   char key[512];
   Tuned t{};
-  while (fscanf(fp, "%511s %d %d %d %lf", key, &t.degree, &t.variant, &t.coarse_max, &t.ms) == 5)
+  while (fscanf(fp, "%511s %d %d %d %lf %lf", key, &t.degree, &t.variant, &t.coarse_max, &t.lo, &t.ms) == 6)
     g_tune_cache[key] = t;
   fclose(fp);
 }
 }  // namespace
 
 // Autotuner: search the inner solver's smoother degree (1..3), kernel variant
-// (0..2) and coarse size (8, 16, 32) one after another, each by the device
+// (0..2), coarse size (8, 16, 32) and the lower end of the Chebyshev interval
+// (0.05 .. 0.3 of lambda_max) one after another, each by the device
 // time of a whole inner solve to tol_inner, and keep the fastest; results are
 // cached per device, grid, viscosity kind, precision, inner solver and gamma
 // decade, in the process and (GKB_TUNE_CACHE) in a text file.
@@ -1384,16 +1390,18 @@ void Solver::autotune_inner(bool var_mu) {
       opt.smoother_degree = it->second.degree;
       opt.kernel_variant = it->second.variant;
       opt.coarse_max = it->second.coarse_max;
+      opt.cheb_lo = it->second.lo;
       tuned_ms = it->second.ms;
       build_inner();
       return;
     }
   }
-  Tuned best{opt.smoother_degree, opt.kernel_variant, opt.coarse_max, 1e300};
-  auto trial = [&](int deg, int var, int cmax) {
+  Tuned best{opt.smoother_degree, opt.kernel_variant, opt.coarse_max, opt.cheb_lo, 1e300};
+  auto trial = [&](int deg, int var, int cmax, double lo) {
     opt.smoother_degree = deg;
     opt.kernel_variant = var;
     opt.coarse_max = cmax;
+    opt.cheb_lo = lo;
     double ms = 1e300;
     try {
       build_inner();
@@ -1401,28 +1409,33 @@ void Solver::autotune_inner(bool var_mu) {
     } catch (const Error& e) {
       if (e.code != GKB_ERR_INVALID_ARG) throw;  // an infeasible candidate (coarse level too large)
     }
-    if (ms < best.ms) best = Tuned{deg, var, cmax, ms};
+    if (ms < best.ms) best = Tuned{deg, var, cmax, lo, ms};
   };
-  trial(best.degree, best.variant, best.coarse_max);
+  const double lo0 = best.lo;
+  trial(best.degree, best.variant, best.coarse_max, lo0);
   for (int v = 0; v <= 2; ++v)
-    if (v != best.variant) trial(best.degree, v, best.coarse_max);
+    if (v != best.variant) trial(best.degree, v, best.coarse_max, lo0);
   const int v0 = best.variant;
   for (int deg = 1; deg <= 3; ++deg)
-    if (deg != best.degree) trial(deg, v0, best.coarse_max);
+    if (deg != best.degree) trial(deg, v0, best.coarse_max, lo0);
   const int d0 = best.degree;
   for (int cmax : {8, 16, 32})
-    if (cmax != best.coarse_max) trial(d0, v0, cmax);
+    if (cmax != best.coarse_max) trial(d0, v0, cmax, lo0);
+  const int c0 = best.coarse_max;
+  for (double lo : {0.05, 0.1, 0.2, 0.3})
+    if (lo != best.lo && lo < opt.cheb_hi) trial(d0, v0, c0, lo);
   if (!(best.ms < 1e300)) throw Error{GKB_ERR_INNER_NOT_CONVERGED, "no autotuning candidate converged"};
   opt.smoother_degree = best.degree;
   opt.kernel_variant = best.variant;
   opt.coarse_max = best.coarse_max;
+  opt.cheb_lo = best.lo;
   tuned_ms = best.ms;
   build_inner();
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune_cache[key] = best;
   if (const char* path = tune_file()) {
     if (FILE* fp = fopen(path, "a")) {
-      fprintf(fp, "%s %d %d %d %.6f\n", key, best.degree, best.variant, best.coarse_max, best.ms);
+      fprintf(fp, "%s %d %d %d %.4f %.6f\n", key, best.degree, best.variant, best.coarse_max, best.lo, best.ms);
       fclose(fp);
     }
   }

@@ -42,6 +42,7 @@ def test_tuned_handle_meets_the_bound(lib, precision):
     try:
         o = gk.gkb_get_options(h)
         assert o.smoother_degree in (1, 2, 3) and o.kernel_variant in (0, 1, 2) and o.coarse_max in (8, 16, 32)
+        assert o.cheb_lo in (0.05, 0.1, 0.2, 0.3) and o.cheb_hi == 1.1
         assert gk.gkb_stats(h)["tuned_inner_ms"] > 0
         rc, w, p = gpu_solve(gk, h, g, r, 1e-8, 5)
         assert rc == gk.GKB_OK, gk.gkb_last_error(h)
@@ -71,6 +72,7 @@ def test_tuning_is_cached_in_process_and_file(lib, tmp_path):
     mine = [ln for ln in lines if "|40x40x1|" in ln[0]]
     assert len(mine) == 1
     assert [int(v) for v in mine[0][1:4]] == [o1.smoother_degree, o1.kernel_variant, o1.coarse_max]
+    assert abs(float(mine[0][4]) - o1.cheb_lo) < 1e-12 and o1.cheb_lo in (0.05, 0.1, 0.2, 0.3)
 
 
 def test_autotune_without_multigrid_is_a_no_op(lib):

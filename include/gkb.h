@@ -228,6 +228,17 @@ int gkb_boundary_rhs(gkb_handle h, int side, const double* normal_velocity,
 int gkb_solve(gkb_handle h, const double* g, const double* r, double tol, int delay,
               double* w_out, double* p_out, const double* w0, const double* p0);
 
+/* GKB as a preconditioner (Sec. 3: the method serves as solver or as
+ * preconditioner): restarted flexible GMRES (restart 1..64 vectors, at most
+ * maxit iterations) on [W A; A^T 0][w; p] = [g; r], each iteration applying
+ * the handle's GKB solve (AL transform and Algorithm 1 with its inner solver)
+ * to tolerance pc_tol and delay `delay` as the preconditioner; stops when
+ * ||b - K z||_2 <= tol ||b||_2. Same layouts and host/device rules as
+ * gkb_solve; *iterations (may be NULL) receives the outer iterations. Returns
+ * GKB_ERR_NOT_CONVERGED when maxit is reached first. Host-sequenced. */
+int gkb_solve_preconditioned(gkb_handle h, const double* g, const double* r, double tol, int restart, int maxit,
+                             double pc_tol, int delay, double* w_out, double* p_out, int* iterations);
+
 /* Solve `count` independent problems in one CUDA graph launch (the batched
  * form; same method as gkb_solve for each). hs[i] is a handle set up with
  * gkb_set_problem, all on one device, with use_graph = 1 and profile = 0.

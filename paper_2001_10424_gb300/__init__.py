@@ -50,7 +50,7 @@ EXPORTED = [
     "gkb_unet_create", "gkb_unet_num_params", "gkb_unet_get_params", "gkb_unet_set_params",
     "gkb_unet_forward", "gkb_unet_loss_grad", "gkb_unet_adam_step", "gkb_unet_last_error", "gkb_unet_destroy",
     "gkb_unet_train", "gkb_unet_set_target_scale", "gkb_unet_get_target_scale", "gkb_set_unet", "gkb_harvest_pairs",
-    "gkb_get_options",
+    "gkb_get_options", "gkb_solve_preconditioned",
 ]
 GKB_NOALLOC_MAX_ELEMS = 1048576
 
@@ -128,6 +128,7 @@ def load(path=None):
         "gkb_unet_get_target_scale": (i, [_P, ctypes.POINTER(ctypes.c_float)]),
         "gkb_set_unet": (i, [_P, _P]),
         "gkb_get_options": (i, [_P, ctypes.POINTER(gkb_options)]),
+        "gkb_solve_preconditioned": (i, [_P, _P, _P, d, i, i, d, i, _P, _P, ctypes.POINTER(i)]),
         "gkb_harvest_pairs": (i, [_P, _P, i, _P, _P, ctypes.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
@@ -318,6 +319,16 @@ def gkb_unet_get_target_scale(u):
     v = ctypes.c_float()
     _ucheck(u, load().gkb_unet_get_target_scale(u, ctypes.byref(v)))
     return v.value
+
+
+def gkb_solve_preconditioned(h, g, r, tol, w_out, p_out, restart=20, maxit=200, pc_tol=1e-2, delay=5):
+    """FGMRES on the saddle system with GKB (to pc_tol) as preconditioner;
+    returns (status, outer iterations)."""
+    it = ctypes.c_int()
+    rc = _check(h, load().gkb_solve_preconditioned(h, _ptr(g), _ptr(r), tol, restart, maxit, pc_tol, delay,
+                                                    _ptr(w_out), _ptr(p_out), ctypes.byref(it)),
+                allow=(GKB_ERR_NOT_CONVERGED,))
+    return rc, it.value
 
 
 def gkb_get_options(h):

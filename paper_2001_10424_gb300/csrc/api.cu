@@ -144,6 +144,21 @@ int gkb_solve(gkb_handle h, const double* g, const double* r, double tol, int de
   return guarded(h, [&] { return h->s.solve(g, r, tol, delay, w_out, p_out, w0, p0); });
 }
 
+int gkb_solve_preconditioned(gkb_handle h, const double* g, const double* r, double tol, int restart, int maxit,
+                             double pc_tol, int delay, double* w_out, double* p_out, int* iterations) {
+  return guarded(h, [&] {
+    gkb::Solver& S = h->s;
+    if (!S.have_problem) throw gkb::Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+    if (!g || !r || !w_out || !p_out) throw gkb::Error{GKB_ERR_INVALID_ARG, "g, r, w_out and p_out must not be NULL"};
+    if (!(tol > 0) || !(pc_tol > 0) || restart < 1 || restart > 64 || maxit < 1 || delay < 0 || delay > gkb::GKB_RING - 2)
+      throw gkb::Error{GKB_ERR_INVALID_ARG, "bad outer solver arguments"};
+    int it = 0;
+    const int st = gkb::solve_preconditioned(S, g, r, tol, restart, maxit, pc_tol, delay, w_out, p_out, &it);
+    if (iterations) *iterations = it;
+    return st;
+  });
+}
+
 int gkb_solve_batched(gkb_handle* hs, int count, const double* const* g, const double* const* r, double tol,
                       int delay, double* const* w_out, double* const* p_out) {
   if (!hs || count < 1 || !hs[0]) return GKB_ERR_INVALID_ARG;

@@ -1478,6 +1478,12 @@ void Solver::refresh_net() {
   if (net && net->bf16_stale && learned_inner()) net->refresh_bf16(stream);
 }
 
+void Solver::cell_sum(const double* p, double* out) {
+  ProfScope ps_(GKB_KC_GKB, stream);
+  k_cell_sum<<<cgrid(L64), dim3(32, 8), 0, stream>>>(L64, p, red, out);
+  GKB_CUDA(cudaGetLastError());
+}
+
 // small unpreconditioned FP64 problems run each inner solve as one kernel
 bool Solver::small_cg() const {
   return opt.inner == GKB_INNER_CG && opt.precision == GKB_PREC_FP64 && L64.nvel <= (1LL << 15);

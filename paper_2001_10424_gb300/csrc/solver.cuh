@@ -149,6 +149,10 @@ struct Fgmres {
 struct Solver;
 // x = M^-1 f by FGMRES(m) with one V-cycle as right preconditioner (FP64)
 int fgmres_solve(Solver& S, const double* f, double* x, int* iters);
+// [W A; A^T 0][w; p] = [g; r] by FGMRES(restart) with GKB to pc_tol as the
+// preconditioner; stops at ||b - K z||_2 <= tol ||b||_2 (compact I/O)
+int solve_preconditioned(Solver& S, const double* g, const double* r, double tol, int restart, int maxit,
+                         double pc_tol, int delay, double* w_out, double* p_out, int* iters);
 
 struct Solver {
   gkb_options opt{};
@@ -177,7 +181,9 @@ struct Solver {
   // multigrid and CG in both precisions (only the ones in use are built)
   Gmg<double> gmg64;
   Gmg<float> gmg32;
-  Fgmres fgm;
+  Fgmres fgm;                     // inner FGMRES work space
+  Fgmres fgo;                     // outer FGMRES work space (saddle vectors)
+  void cell_sum(const double* p, double* out);  // out[0] = sum over the in-domain cells
   Cg<double> cg64;
   Cg<float> cg32;
 

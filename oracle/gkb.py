@@ -28,8 +28,14 @@ the design notes of the repository):
 * An initial guess ``(w0, p0)`` is handled by defect correction: the method is
   run on ``(g - W w0 - A p0, r - A^T w0)`` and the correction is added.
 * Enclosed flow (all sides Dirichlet): ``A`` annihilates constant pressure.
-  The mean is removed from ``b`` and from each new ``N``-step vector before
-  its norm is taken, and the returned pressure has zero mean.
+  The mean is removed from ``b`` (which lies in the range of ``A^T``,
+  orthogonal to the constants) and the ``N``-weighted mean
+  ``sum(N x) / sum(N)`` from each new ``N``-step vector before its norm is
+  taken (the exact ``q_k`` are ``N``-orthogonal to the constants; for
+  ``N = n I`` this is the plain mean), and the returned pressure has zero mean.
+* ``N`` is ``n_scale * I`` or a positive diagonal (Sec. 3 allows any
+  symmetric positive definite ``N``); ``N`` below is the scalar or the
+  diagonal, and every product with ``N`` or ``N^-1`` is elementwise.
 * A zero ``beta`` or ``alpha`` is a happy breakdown: the current iterate is
   the solution.
 """
@@ -92,12 +98,13 @@ class InnerSolver:
         return x
 
 
-def al_transform(A, n_scale, g, r, gamma, solve_M):
+def al_transform(A, N, g, r, gamma, solve_M):
     """Eq. (3): returns (y, b) with y = M^-1 (g + gamma A N^-1 r), b = r - A^T y.
 
     Then u = w - y solves the transformed system [M A; A^T 0][u; p] = [0; b].
+    ``N`` is the scalar of ``N = n I`` or the diagonal of ``N``.
     """
-    f = g + gamma * (A @ (r / n_scale))
+    f = g + gamma * (A @ (r / N))
     if not np.any(f):
         y = np.zeros_like(f)
     else:
@@ -106,11 +113,11 @@ def al_transform(A, n_scale, g, r, gamma, solve_M):
     return y, b
 
 
-def gkb(M, A, n_scale, b, solve_M, tol, delay, maxit, enclosed=False,
+def gkb(M, A, N, b, solve_M, tol, delay, maxit, enclosed=False,
         squared=False, keep_bases=False):
     """Algorithm 1 with the stopping rule of Eq. (5) (reading in module doc).
 
-    ``N = n_scale * I``. Returns a dict with the velocity ``u``, pressure ``p``,
+    ``N`` is the scalar of ``N = n I`` or the diagonal of ``N``. Returns a dict with the velocity ``u``, pressure ``p``,
     the sequences alpha_k, beta_k, zeta_k, the estimate after each step, the
     number of loop iterations and the convergence flag; with ``keep_bases`` it
     also holds the columns of V and Q.
@@ -118,11 +125,17 @@ def gkb(M, A, n_scale, b, solve_M, tol, delay, maxit, enclosed=False,
     def centre(x):
         return x - x.mean() if enclosed else x
 
+    def centre_N(x):     # remove the N-weighted mean
+        if not enclosed:
+            return x
+        Nx = N * np.ones_like(x)
+        return x - float(Nx @ x) / float(Nx.sum())
+
     def norm_N(x):       # ||x||_N
-        return math.sqrt(n_scale * float(x @ x))
+        return math.sqrt(float((N * x) @ x))
 
     def norm_Ninv(x):    # ||x||_{N^-1}
-        return math.sqrt(float(x @ x) / n_scale)
+        return math.sqrt(float(x @ (x / N)))
 
     def norm_M(x):       # ||x||_M
         return math.sqrt(float(x @ (M @ x)))
@@ -136,7 +149,7 @@ def gkb(M, A, n_scale, b, solve_M, tol, delay, maxit, enclosed=False,
     if beta == 0.0:
         out.update(u=u, p=p, iterations=0, converged=True)
         return out
-    q = (b / n_scale) / beta
+    q = (b / N) / beta
     w = solve_M(A @ q)
     alpha = norm_M(w)
     out["alpha"].append(alpha)
@@ -158,7 +171,7 @@ def gkb(M, A, n_scale, b, solve_M, tol, delay, maxit, enclosed=False,
     while not converged and k < maxit:
         k += 1
         # N-step: g = N^-1 (A^T v_k - alpha_k N q_k), beta_{k+1} = ||g||_N
-        gv = centre((A.T @ v) / n_scale - alpha * q)
+        gv = centre_N((A.T @ v) / N - alpha * q)
         beta = norm_N(gv)
         out["beta"].append(beta)
         if beta == 0.0:
@@ -205,15 +218,15 @@ def solve(grid, ops, g, r, tol=1e-8, delay=5, maxit=10000, inner="cg",
     ``w`` (velocity), ``p`` (pressure) and ``inner_iterations`` added.
     """
     W, A, M = ops["W"], ops["A"], ops["M"]
-    n_scale, gamma = ops["n_scale"], ops["gamma"]
+    N, gamma = ops.get("N", ops["n_scale"]), ops["gamma"]
     solver = InnerSolver(M, inner, tol_inner, maxit_inner)
     g = np.asarray(g, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64)
     if w0 is not None:
         g = g - W @ w0 - (A @ p0 if p0 is not None else 0.0)
         r = r - A.T @ w0
-    y, b = al_transform(A, n_scale, g, r, gamma, solver)
-    res = gkb(M, A, n_scale, b, solver, tol, delay, maxit,
+    y, b = al_transform(A, N, g, r, gamma, solver)
+    res = gkb(M, A, N, b, solver, tol, delay, maxit,
               enclosed=grid.enclosed, squared=squared, keep_bases=keep_bases)
     w = res["u"] + y
     p = res["p"]

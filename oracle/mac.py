@@ -29,8 +29,11 @@ finite-volume (cell-measure integrated) form:
   with the cells on the plus and minus side of face ``f``; a missing cell
   (beyond a natural boundary) contributes pressure 0. ``A^T`` is therefore the
   negative integrated divergence.
-* ``N = n_scale * I`` (Sec. 3: N restricted to a multiple of the identity), the
-  default ``n_scale = h**d`` being the pressure mass matrix.
+* ``N = n_scale * I`` (the restriction of the paper's PETSc implementation,
+  Sec. 3), the default ``n_scale = h**d`` being the pressure mass matrix; or,
+  since Sec. 3 allows any symmetric positive definite N, a positive diagonal
+  ``N = diag(n_diag)`` given per cell (e.g. the viscosity-weighted pressure
+  mass matrix ``h**d / mu``).
 * ``M = W + gamma * A N^-1 A^T`` (Eq. (2), the augmented (1,1) block).
 
 Unknown ordering (shared convention with the library's documented layout, not
@@ -152,11 +155,14 @@ def _edge_mu(grid, mu, X, c, a, a_face):
     return total / count
 
 
-def assemble(grid, mu=1.0, gamma=0.0, n_scale=None):
-    """Assemble W, A (CSR), the scalar N and M = W + gamma A N^-1 A^T (Eq. (2)).
+def assemble(grid, mu=1.0, gamma=0.0, n_scale=None, n_diag=None):
+    """Assemble W, A (CSR), N and M = W + gamma A N^-1 A^T (Eq. (2)).
 
     ``mu`` is a scalar or an array of cell viscosities indexed [x, y(, z)].
-    Returns a dict with W, A, M (scipy CSR, FP64), n_scale and the link list
+    ``n_diag`` (optional, same indexing, every entry > 0) selects the diagonal
+    ``N = diag(n_diag)``; otherwise ``N = n_scale * I``.
+    Returns a dict with W, A, M (scipy CSR, FP64), n_scale, ``N`` (the scalar
+    n_scale, or the diagonal of N in cell-index order) and the link list
     needed to fold Dirichlet data into the right-hand side.
     """
     d, h = grid.dim, grid.h
@@ -166,6 +172,13 @@ def assemble(grid, mu=1.0, gamma=0.0, n_scale=None):
     assert mu.shape == grid.n
     if n_scale is None:
         n_scale = h ** d
+    N = float(n_scale)
+    if n_diag is not None:
+        n_diag = np.asarray(n_diag, dtype=np.float64)
+        assert n_diag.shape == grid.n and np.all(n_diag > 0)
+        # the diagonal in the order of the pressure unknowns
+        N = np.empty(grid.n_cells)
+        N[grid.cell_index] = n_diag
     scale = h ** (d - 2)
     rows, cols, vals = [], [], []
     # Dirichlet couplings: (active face index, conductance, component,
@@ -261,9 +274,12 @@ def assemble(grid, mu=1.0, gamma=0.0, n_scale=None):
             aval.append(np.full(int(ok.sum()), sign * hd1))
     A = sp.csr_matrix((np.concatenate(aval), (np.concatenate(arow), np.concatenate(acol))),
                       shape=(grid.m, grid.n_cells))
-    M = (W + (gamma / n_scale) * (A @ A.T)).tocsr()
+    if np.isscalar(N):
+        M = (W + (gamma / N) * (A @ A.T)).tocsr()
+    else:
+        M = (W + gamma * (A @ sp.diags(1.0 / N) @ A.T)).tocsr()
     M.sum_duplicates()
-    return {"W": W, "A": A, "M": M, "n_scale": float(n_scale), "gamma": float(gamma),
+    return {"W": W, "A": A, "M": M, "n_scale": float(n_scale), "N": N, "gamma": float(gamma),
             "bnd_links": bnd_links}
 
 

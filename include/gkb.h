@@ -202,6 +202,21 @@ int gkb_create(gkb_handle* out, const gkb_options* opt);
 int gkb_set_problem(gkb_handle h, const gkb_grid* grid, const double* viscosity,
                     double mu0, double gamma, double n_scale);
 
+/* gkb_set_problem with a diagonal N = diag(n_diag) (Sec. 3: N may be any
+ * symmetric positive definite matrix; e.g. n_diag = h^dim / mu, the
+ * viscosity-weighted pressure mass matrix, which approximates the Schur
+ * complement A^T W^-1 A and cuts the outer iterations when mu varies).
+ * n_diag: n values > 0 in compact pressure ordering (host or device;
+ * copied). M = W + gamma A N^-1 A^T; the N-step of Algorithm 1 divides by
+ * N cell by cell and beta is the N-norm; on an enclosed grid the N-step
+ * vector is centred by its N-weighted mean. The multigrid levels carry the
+ * weights h^dim / N (coarsened by averaging), and the operator runs on the
+ * variable-viscosity kernels even for a constant mu0. Errors: those of
+ * gkb_set_problem, and INVALID_ARG for a NULL, non-positive or non-finite
+ * n_diag. */
+int gkb_set_problem_n(gkb_handle h, const gkb_grid* grid, const double* viscosity,
+                      double mu0, double gamma, const double* n_diag);
+
 /* Sizes of the compact velocity (m) and pressure (n) vectors. */
 int gkb_layout(gkb_handle h, int64_t* m, int64_t* n);
 

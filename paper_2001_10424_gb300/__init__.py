@@ -44,7 +44,7 @@ STATUS_NAMES = {
 
 # symbols declared in include/gkb.h
 EXPORTED = [
-    "gkb_default_options", "gkb_create", "gkb_set_problem", "gkb_layout", "gkb_boundary_rhs",
+    "gkb_default_options", "gkb_create", "gkb_set_problem", "gkb_set_problem_n", "gkb_layout", "gkb_boundary_rhs",
     "gkb_solve", "gkb_stats", "gkb_history", "gkb_apply", "gkb_precond", "gkb_last_error",
     "gkb_destroy", "gkb_apply_noalloc", "gkb_solve_batched",
     "gkb_unet_create", "gkb_unet_num_params", "gkb_unet_get_params", "gkb_unet_set_params",
@@ -102,6 +102,7 @@ def load(path=None):
         "gkb_default_options": (i, [ctypes.POINTER(gkb_options)]),
         "gkb_create": (i, [ctypes.POINTER(_P), ctypes.POINTER(gkb_options)]),
         "gkb_set_problem": (i, [_P, ctypes.POINTER(gkb_grid), _P, d, d, d]),
+        "gkb_set_problem_n": (i, [_P, ctypes.POINTER(gkb_grid), _P, d, d, _P]),
         "gkb_layout": (i, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
         "gkb_boundary_rhs": (i, [_P, i, _P, _P, _P]),
         "gkb_solve": (i, [_P, _P, _P, d, i, _P, _P, _P, _P]),
@@ -190,6 +191,11 @@ def gkb_create(opt=None):
 
 def gkb_set_problem(h, grid, viscosity=None, mu0=1.0, gamma=0.0, n_scale=0.0):
     return _check(h, load().gkb_set_problem(h, ctypes.byref(grid), _ptr(viscosity), mu0, gamma, n_scale))
+
+
+def gkb_set_problem_n(h, grid, n_diag, viscosity=None, mu0=1.0, gamma=0.0):
+    """N = diag(n_diag): n values in compact pressure ordering (host or device)."""
+    return _check(h, load().gkb_set_problem_n(h, ctypes.byref(grid), _ptr(viscosity), mu0, gamma, _ptr(n_diag)))
 
 
 def gkb_layout(h):

@@ -110,6 +110,15 @@ int gkb_set_problem(gkb_handle h, const gkb_grid* grid, const double* viscosity,
   });
 }
 
+int gkb_set_problem_n(gkb_handle h, const gkb_grid* grid, const double* viscosity, double mu0, double gamma,
+                      const double* n_diag) {
+  return guarded(h, [&] {
+    if (!n_diag) throw gkb::Error{GKB_ERR_INVALID_ARG, "n_diag is NULL"};
+    h->s.set_problem(grid, viscosity, mu0, gamma, 0.0, n_diag);
+    return GKB_OK;
+  });
+}
+
 int gkb_set_unet(gkb_handle h, gkb_unet u) {
   return guarded(h, [&] {
     if (u && u->device != h->device) throw gkb::Error{GKB_ERR_INVALID_ARG, "the network lives on another device"};

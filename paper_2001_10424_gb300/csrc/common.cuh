@@ -31,6 +31,11 @@ struct Lvl {
   double mu0;         // constant viscosity when mu == null
   const double* mu64; // cell viscosity in the padded cell layout, or null
   const float* mu32;
+  // diagonal N: relative grad-div weight n_ref / N_cell of every cell (the
+  // level's gc holds gamma / n_ref), or null for N = n_ref * I; only set on
+  // variable-viscosity levels
+  const double* nw64;
+  const float* nw32;
   // derived constants (set by finish_level), in both precisions so that FP32
   // kernels never convert from double on the FP64 pipe
   int has_gd;         // gc != 0
@@ -113,6 +118,18 @@ template <typename T, bool VarMu>
 __device__ __forceinline__ T cell_mu(const Lvl& L, int i, int j, int k) {
   if (!VarMu) return Kc<T>::mu0(L);
   return __ldg(MuPtr<T>::get(L) + cix(L, i, j, k));
+}
+
+template <typename T> struct NwPtr;
+template <> struct NwPtr<double> { static __device__ __forceinline__ const double* get(const Lvl& L) { return L.nw64; } };
+template <> struct NwPtr<float>  { static __device__ __forceinline__ const float*  get(const Lvl& L) { return L.nw32; } };
+
+// grad-div weight of an in-domain cell (1 unless N is a non-uniform diagonal)
+template <typename T, bool VarMu>
+__device__ __forceinline__ T cell_nw(const Lvl& L, long long cb) {
+  if (!VarMu) return (T)1;
+  const T* w = NwPtr<T>::get(L);
+  return w ? __ldg(w + cb) : (T)1;
 }
 
 // mean viscosity of the in-domain cells around the node/edge crossed by a
@@ -273,7 +290,22 @@ __device__ __forceinline__ int face_cells(const Lvl& L, const int p[3]) {
   return (p[C] < L.n[C] ? 1 : 0) + (p[C] > 0 ? 1 : 0);
 }
 
-// (M x)_f at an active face of component C: W row + gc * ascale^2 * grad(negdiv)
+// sum of the grad-div weights of the in-domain cells adjacent to a face
+// (face_cells when N is a multiple of the identity)
+template <typename T, bool VarMu, int C>
+__device__ __forceinline__ T face_nw(const Lvl& L, const int p[3]) {
+  if (!VarMu || !NwPtr<T>::get(L)) return (T)face_cells<C>(L, p);
+  T s = 0;
+  if (p[C] < L.n[C]) s += cell_nw<T, true>(L, cix(L, p[0], p[1], p[2]));
+  if (p[C] > 0) {
+    int q[3] = {p[0], p[1], p[2]};
+    q[C] -= 1;
+    s += cell_nw<T, true>(L, cix(L, q[0], q[1], q[2]));
+  }
+  return s;
+}
+
+// (M x)_f at an active face of component C: W row + gc * ascale^2 * grad(nw negdiv)
 template <typename T, bool VarMu, int C, bool NC = true>
 __device__ __forceinline__ T m_row(const Lvl& L, const T* x, const int p[3]) {
   const T xf = face_val<T, C, NC>(L, x, p[0], p[1], p[2]);
@@ -281,8 +313,10 @@ __device__ __forceinline__ T m_row(const Lvl& L, const T* x, const int p[3]) {
   if (!L.has_gd) return wv;
   int q[3] = {p[0], p[1], p[2]};
   T dplus = neg_div<T, NC>(L, x, q[0], q[1], q[2]);
+  if (cell_in(L, q[0], q[1], q[2])) dplus *= cell_nw<T, VarMu>(L, cix(L, q[0], q[1], q[2]));
   q[C] -= 1;
   T dminus = neg_div<T, NC>(L, x, q[0], q[1], q[2]);
+  if (cell_in(L, q[0], q[1], q[2])) dminus *= cell_nw<T, VarMu>(L, cix(L, q[0], q[1], q[2]));
   return wv + Kc<T>::g2(L) * (dplus - dminus);
 }
 

@@ -105,7 +105,14 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
       const int cj = rem / (BX + 1), ci = rem - cj * (BX + 1);
       const int gk = (L.dim == 3) ? k - 1 + pl : 0;
       const int gi = i0 - 1 + ci, gj = j0 - 1 + cj;
-      Dt[pl][cj][ci] = cell_in(L, gi, gj, gk) ? neg_div_at<T>(L, x, cix(L, gi, gj, gk)) : (T)0;
+      if (cell_in(L, gi, gj, gk)) {
+        const long long cc = cix(L, gi, gj, gk);
+        T dv = neg_div_at<T>(L, x, cc);
+        if (VarMu && NwPtr<T>::get(L)) dv *= __ldg(NwPtr<T>::get(L) + cc);
+        Dt[pl][cj][ci] = dv;
+      } else {
+        Dt[pl][cj][ci] = (T)0;
+      }
     }
     __syncthreads();
   }
@@ -232,10 +239,10 @@ __device__ void patch_matrix(const Lvl& L, const int e[3], T Mp[4][4], bool act[
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) Mp[r][c] = 0;
-  Mp[0][0] = act[0] ? ws * w_diag<T, VarMu, a>(L, q0) + g * (T)face_cells<a>(L, q0) : (T)1;
-  Mp[1][1] = act[1] ? ws * w_diag<T, VarMu, a>(L, e) + g * (T)face_cells<a>(L, e) : (T)1;
-  Mp[2][2] = act[2] ? ws * w_diag<T, VarMu, b>(L, q2) + g * (T)face_cells<b>(L, q2) : (T)1;
-  Mp[3][3] = act[3] ? ws * w_diag<T, VarMu, b>(L, e) + g * (T)face_cells<b>(L, e) : (T)1;
+  Mp[0][0] = act[0] ? ws * w_diag<T, VarMu, a>(L, q0) + g * face_nw<T, VarMu, a>(L, q0) : (T)1;
+  Mp[1][1] = act[1] ? ws * w_diag<T, VarMu, a>(L, e) + g * face_nw<T, VarMu, a>(L, e) : (T)1;
+  Mp[2][2] = act[2] ? ws * w_diag<T, VarMu, b>(L, q2) + g * face_nw<T, VarMu, b>(L, q2) : (T)1;
+  Mp[3][3] = act[3] ? ws * w_diag<T, VarMu, b>(L, e) + g * face_nw<T, VarMu, b>(L, e) : (T)1;
   if (act[0] && act[1]) {
     const T area = face_half<a>(L, e) ? (T)0.5 : (T)1;
     Mp[0][1] = Mp[1][0] = -ws * area * edge_mu<T, VarMu, a, b>(L, e, e[b]);
@@ -246,14 +253,19 @@ __device__ void patch_matrix(const Lvl& L, const int e[3], T Mp[4][4], bool act[
   }
   if (L.has_gd) {
     int cc[3] = {e[0], e[1], e[2]};
+    // the two faces share one cell: coupling +-g times its weight
     cc[a] = e[a] - 1; cc[b] = e[b] - 1;
-    if (act[0] && act[2] && cell_in(L, cc[0], cc[1], cc[2])) Mp[0][2] = Mp[2][0] = g;
+    if (act[0] && act[2] && cell_in(L, cc[0], cc[1], cc[2]))
+      Mp[0][2] = Mp[2][0] = g * cell_nw<T, VarMu>(L, cix(L, cc[0], cc[1], cc[2]));
     cc[a] = e[a]; cc[b] = e[b] - 1;
-    if (act[0] && act[3] && cell_in(L, cc[0], cc[1], cc[2])) Mp[0][3] = Mp[3][0] = -g;
+    if (act[0] && act[3] && cell_in(L, cc[0], cc[1], cc[2]))
+      Mp[0][3] = Mp[3][0] = -g * cell_nw<T, VarMu>(L, cix(L, cc[0], cc[1], cc[2]));
     cc[a] = e[a] - 1; cc[b] = e[b];
-    if (act[1] && act[2] && cell_in(L, cc[0], cc[1], cc[2])) Mp[1][2] = Mp[2][1] = -g;
+    if (act[1] && act[2] && cell_in(L, cc[0], cc[1], cc[2]))
+      Mp[1][2] = Mp[2][1] = -g * cell_nw<T, VarMu>(L, cix(L, cc[0], cc[1], cc[2]));
     cc[a] = e[a]; cc[b] = e[b];
-    if (act[1] && act[3] && cell_in(L, cc[0], cc[1], cc[2])) Mp[1][3] = Mp[3][1] = g;
+    if (act[1] && act[3] && cell_in(L, cc[0], cc[1], cc[2]))
+      Mp[1][3] = Mp[3][1] = g * cell_nw<T, VarMu>(L, cix(L, cc[0], cc[1], cc[2]));
   }
 }
 

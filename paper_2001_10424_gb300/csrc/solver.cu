@@ -60,6 +60,8 @@ Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
   L.mu0 = 1.0;
   L.mu64 = nullptr;
   L.mu32 = nullptr;
+  L.nw64 = nullptr;
+  L.nw32 = nullptr;
   L.fast = 1;
   finish_level(L);
   return L;
@@ -68,6 +70,9 @@ Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
 template <typename T> static void set_mu(Lvl& L, const T* mu);
 template <> void set_mu<double>(Lvl& L, const double* mu) { L.mu64 = mu; L.mu32 = nullptr; }
 template <> void set_mu<float>(Lvl& L, const float* mu) { L.mu32 = mu; L.mu64 = nullptr; }
+template <typename T> static void set_nw(Lvl& L, const T* w);
+template <> void set_nw<double>(Lvl& L, const double* w) { L.nw64 = w; L.nw32 = nullptr; }
+template <> void set_nw<float>(Lvl& L, const float* w) { L.nw32 = w; L.nw64 = nullptr; }
 
 // ---------------------------------------------------------------------------
 // layout kernels (compact ordering <-> padded layout)
@@ -337,6 +342,18 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
       { ProfScope ps_(GKB_KC_LAYOUT, s); k_mu_coarsen<T><<<g, dim3(32, 8), 0, s>>>(lev[lev.size() - 2].L, Lc, fmu, C.mu.p); }
       GKB_CUDA(cudaGetLastError());
       set_mu<T>(C.L, C.mu.p);
+    }
+    // diagonal N: the coarse weight is the mean of the 2^d children's, which
+    // with gc / 2^d and the divergence-preserving transfers makes the coarse
+    // grad-div term the Galerkin product of the fine one
+    const T* fnw = (sizeof(T) == 8) ? (const T*)lev[lev.size() - 2].L.nw64 : (const T*)lev[lev.size() - 2].L.nw32;
+    set_nw<T>(C.L, (const T*)nullptr);
+    if (fnw && fmu) {
+      C.nw.alloc(Lc.ncell);
+      dim3 g((nc[0] + 31) / 32, (nc[1] + 7) / 8, Lc.n[2]);
+      { ProfScope ps_(GKB_KC_LAYOUT, s); k_mu_coarsen<T><<<g, dim3(32, 8), 0, s>>>(lev[lev.size() - 2].L, Lc, fnw, C.nw.p); }
+      GKB_CUDA(cudaGetLastError());
+      set_nw<T>(C.L, C.nw.p);
     }
   }
   const int nl = (int)lev.size();
@@ -670,34 +687,46 @@ constexpr int CB = 256;
 
 static dim3 cgrid(const Lvl& L) { return dim3((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]); }
 
-// b = r - A^T y0 ; reduce sum b^2, sum b
+// b = r - A^T y0 ; reduce sum b^2 / N, sum b, sum b / N
 __global__ void __launch_bounds__(256) k_gkb_b(Lvl L, const double* __restrict__ rc, const double* __restrict__ y0,
-                                               double* __restrict__ b, RedBuf red, double* out) {
+                                               double* __restrict__ b, const GkbState* st, RedBuf red, double* out) {
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  double v[2] = {0.0, 0.0};
+  double v[3] = {0.0, 0.0, 0.0};
   if (i < L.n[0] && j < L.n[1]) {
     const long long id = cix(L, i, j, k);
     const double bv = rc[id] - L.ascale * neg_div<double>(L, y0, i, j, k);
+    const double ni = st->nd ? st->nd[id] : st->n_scale;
     b[id] = bv;
-    v[0] = bv * bv;
+    v[0] = bv * bv / ni;
     v[1] = bv;
+    v[2] = bv / ni;
   }
-  grid_reduce<2>(v, red, FIN_STORE, out);
+  grid_reduce<3>(v, red, FIN_STORE, out);
 }
 
-// g = N^-1 A^T v - alpha q ; reduce sum g^2, sum g
+// g = N^-1 A^T v - alpha q ; reduce sum N g^2, sum N g
 __global__ void __launch_bounds__(256) k_gk1(Lvl L, const double* __restrict__ v, const double* __restrict__ q,
                                              double* __restrict__ gq, const GkbState* st, RedBuf red, double* out) {
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
   double acc[2] = {0.0, 0.0};
   if (i < L.n[0] && j < L.n[1]) {
     const long long id = cix(L, i, j, k);
-    const double g = L.ascale * neg_div<double>(L, v, i, j, k) / st->n_scale - st->alpha * q[id];
+    const double ni = st->nd ? st->nd[id] : st->n_scale;
+    const double g = L.ascale * neg_div<double>(L, v, i, j, k) / ni - st->alpha * q[id];
     gq[id] = g;
-    acc[0] = g * g;
-    acc[1] = g;
+    acc[0] = ni * g * g;
+    acc[1] = ni * g;
   }
   grid_reduce<2>(acc, red, FIN_STORE, out);
+}
+
+// out = w * a on the in-domain cells (N^-1 r of the right-hand-side transform)
+__global__ void __launch_bounds__(256) k_cells_mul(Lvl L, const double* __restrict__ a, const double* __restrict__ w,
+                                                   double* __restrict__ out) {
+  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  if (i >= L.n[0] || j >= L.n[1]) return;
+  const long long id = cix(L, i, j, k);
+  out[id] = a[id] * w[id];
 }
 
 // f = A q_{k+1} with q_{k+1} = (g - mean) / beta (mean cancels on active faces)
@@ -770,13 +799,14 @@ __global__ void __launch_bounds__(256) k_gk4c(Lvl L, const double* __restrict__ 
   }
 }
 
-// q1 = (b - mean) / (n_scale beta1)
+// q1 = N^-1 (b - mean) / beta1
 __global__ void __launch_bounds__(256) k_gkb_q1(Lvl L, const double* __restrict__ b, double* __restrict__ q,
                                                 const GkbState* st) {
   const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
   if (i >= L.n[0] || j >= L.n[1]) return;
   const long long id = cix(L, i, j, k);
-  q[id] = (st->beta > 0.0) ? (b[id] - st->mean) / (st->n_scale * st->beta) : 0.0;
+  const double ni = st->nd ? st->nd[id] : st->n_scale;
+  q[id] = (st->beta > 0.0) ? (b[id] - st->mean) / (ni * st->beta) : 0.0;
 }
 
 enum { S_BETA1 = 0, S_ALPHA1 = 1, S_BETA = 2, S_ALPHA = 3 };
@@ -791,12 +821,13 @@ __global__ void k_gkb_scalar(int op, GkbState* st, const double* red) {
   GkbState& S = *st;
   switch (op) {
     case S_BETA1: {
-      // beta_1 = ||b||_{N^-1} on the mean-free b
+      // beta_1 = ||b||_{N^-1} on the mean-free b:
+      // sum (b - m)^2 / N = sum b^2 / N - 2 m sum b / N + m^2 sum 1 / N
       const double mean = S.enclosed ? red[1] / S.ncells : 0.0;
-      double s2 = red[0] - S.ncells * mean * mean;
+      double s2 = red[0] - 2.0 * mean * red[2] + mean * mean * S.ninvsum;
       if (s2 < 0) s2 = 0;
       S.mean = mean;
-      S.beta = sqrt(s2 / S.n_scale);
+      S.beta = sqrt(s2);
       hist_put(S.h_beta, S.hcap, 0, S.beta);
       if (!isfinite(S.beta)) { S.status = ST_NAN; S.stop = 1; }
       else if (S.beta == 0.0) { S.stop = 1; S.converged = 1; }
@@ -819,13 +850,14 @@ __global__ void k_gkb_scalar(int op, GkbState* st, const double* red) {
       if (S.maxit <= 0) S.stop = 1;
     } break;
     case S_BETA: {
-      // beta_{k+1} = ||g||_N on the mean-free g
+      // beta_{k+1} = ||g - c||_N with c = sum N g / sum N, the N-weighted
+      // mean (the plain mean when N = n I): sum N g^2 - c^2 sum N
       S.k += 1;
-      const double mean = S.enclosed ? red[1] / S.ncells : 0.0;
-      double s2 = red[0] - S.ncells * mean * mean;
+      const double mean = S.enclosed ? red[1] / S.nsum : 0.0;
+      double s2 = red[0] - S.nsum * mean * mean;
       if (s2 < 0) s2 = 0;
       S.mean = mean;
-      S.beta = sqrt(S.n_scale * s2);
+      S.beta = sqrt(s2);
       hist_put(S.h_beta, S.hcap, S.k, S.beta);
       if (!isfinite(S.beta)) { S.status = ST_NAN; S.stop = 1; }
       else if (S.beta == 0.0) { S.stop = 1; S.converged = 1; S.alpha = 0.0; }
@@ -1157,7 +1189,8 @@ Solver::~Solver() {
   if (cap3) cudaStreamDestroy(cap3);
 }
 
-void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_, double gamma_, double n_scale_) {
+void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_, double gamma_, double n_scale_,
+                         const double* n_diag) {
   auto t0 = std::chrono::steady_clock::now();
   if (!g) throw Error{GKB_ERR_INVALID_ARG, "grid is NULL"};
   sgraph.destroy();
@@ -1174,7 +1207,9 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   grid = *g;
   gamma = gamma_;
   mu0 = mu0_;
-  n_scale = (n_scale_ > 0) ? n_scale_ : pow(g->h, g->dim);
+  // with a diagonal N, n_scale is the reference h^d: the levels hold
+  // gamma / h^d and every cell the weight h^d / N_cell
+  n_scale = (n_scale_ > 0 && !n_diag) ? n_scale_ : pow(g->h, g->dim);
   int nat[6] = {0, 0, 0, 0, 0, 0};
   enclosed = true;
   for (int s = 0; s < 2 * g->dim; ++s) { nat[s] = g->bc[s] == GKB_BC_NATURAL; if (nat[s]) enclosed = false; }
@@ -1187,13 +1222,20 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
     throw Error{GKB_ERR_INVALID_ARG, "the learned inner solver is 2D only"};
   int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
   L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
+  ncell = (int64_t)n3[0] * n3[1] * n3[2];
+  // a non-uniform N runs on the variable-viscosity kernels, which carry the
+  // per-cell weights: a constant viscosity becomes an array of mu0
+  std::vector<double> mu_fill;
+  if (n_diag && !viscosity) {
+    mu_fill.assign((size_t)ncell, mu0);
+    viscosity = mu_fill.data();
+  }
   L64.mu0 = viscosity ? 1.0 : mu0;
   // fast paths: measured faster in FP32, slower in FP64 (FP64-pipe bound)
   L64.fast = (opt.kernel_variant == 2) ? 1 : 0;
   finish_level(L64);
   Compact cmp = make_compact(L64);
   m = cmp.m;
-  ncell = (int64_t)n3[0] * n3[1] * n3[2];
   // viscosity
   mu64.release();
   mu32.release();
@@ -1215,9 +1257,44 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
       if (!(vv > 0) || !std::isfinite(vv)) throw Error{GKB_ERR_INVALID_ARG, "viscosity must be positive and finite"};
   }
   L64.mu64 = mu64.p;
+  // diagonal N
+  nd64.release();
+  nw64.release();
+  nw32.release();
+  diag_n = n_diag != nullptr;
+  nsum = ninvsum = 0;
+  if (diag_n) {
+    DevBuf<double> tmp;
+    tmp.alloc(ncell);
+    GKB_CUDA(cudaMemcpyAsync(tmp.p, n_diag, ncell * sizeof(double), cudaMemcpyDefault, stream));
+    std::vector<double> hn(ncell);
+    GKB_CUDA(cudaMemcpyAsync(hn.data(), tmp.p, ncell * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    GKB_CUDA(cudaStreamSynchronize(stream));
+    std::vector<double> hw(ncell);
+    for (int64_t c = 0; c < ncell; ++c) {
+      if (!(hn[c] > 0) || !std::isfinite(hn[c])) throw Error{GKB_ERR_INVALID_ARG, "N must be positive and finite"};
+      nsum += hn[c];
+      ninvsum += 1.0 / hn[c];
+      hw[c] = n_scale / hn[c];
+    }
+    nd64.alloc(L64.ncell);
+    nw64.alloc(L64.ncell);
+    { ProfScope ps_(GKB_KC_LAYOUT, stream); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, nd64.p); }
+    GKB_CUDA(cudaMemcpyAsync(tmp.p, hw.data(), ncell * sizeof(double), cudaMemcpyHostToDevice, stream));
+    { ProfScope ps_(GKB_KC_LAYOUT, stream); k_pack_cell<double><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, nw64.p); }
+    if (mixed) {
+      nw32.alloc(L64.ncell);
+      { ProfScope ps_(GKB_KC_LAYOUT, stream); k_pack_cell<float><<<lin_blocks(ncell), 256, 0, stream>>>(L64, tmp.p, nw32.p); }
+    }
+    GKB_CUDA(cudaStreamSynchronize(stream));
+  }
+  L64.nw64 = nw64.p;
+  L64.nw32 = nullptr;
   L32 = L64;
   L32.mu64 = nullptr;
   L32.mu32 = mu32.p;
+  L32.nw64 = nullptr;
+  L32.nw32 = nw32.p;
   L32.fast = (opt.kernel_variant == 1) ? 0 : 1;
   // reduction scratch: enough partials for every launch shape used
   long long blocks = std::max<long long>(Ops<double>::face_blocks(L64), blas_blocks(L64.nvel));
@@ -1248,7 +1325,7 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   hist_inner.alloc((size_t)opt.maxit + 4);
   // multigrid + CG (tuned first when asked)
   tuned_ms = 0;
-  if (opt.autotune && use_gmg && opt.inner != GKB_INNER_FGMRES) autotune_inner(viscosity != nullptr);
+  if (opt.autotune && use_gmg && opt.inner != GKB_INNER_FGMRES) autotune_inner(viscosity != nullptr, diag_n);
   else build_inner();
   if (opt.inner == GKB_INNER_FGMRES) fgm.init(L64.nvel, opt.fgmres_restart);
   stats.tuned_inner_ms = tuned_ms;
@@ -1371,7 +1448,7 @@ void tune_read_file() {
 // time of a whole inner solve to tol_inner, and keep the fastest; results are
 // cached per device, grid, viscosity kind, precision, inner solver and gamma
 // decade, in the process and (GKB_TUNE_CACHE) in a text file.
-void Solver::autotune_inner(bool var_mu) {
+void Solver::autotune_inner(bool var_mu, bool weighted) {
   int dev = 0;
   GKB_CUDA(cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -1381,7 +1458,7 @@ void Solver::autotune_inner(bool var_mu) {
     if (c == ' ') c = '_';
   char key[512];
   snprintf(key, sizeof key, "%s|d%d|%dx%dx%d|%s|p%d|i%d|g%+.0f", name.c_str(), grid.dim, L64.n[0], L64.n[1], L64.n[2],
-           var_mu ? "varmu" : "mu", opt.precision, opt.inner, gamma > 0 ? std::floor(std::log10(gamma)) : -99.0);
+           var_mu ? (weighted ? "varmu-ndiag" : "varmu") : "mu", opt.precision, opt.inner, gamma > 0 ? std::floor(std::log10(gamma)) : -99.0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_read_file();
@@ -1759,6 +1836,18 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
   if (P) P->phase = saved;
 }
 
+// f = gamma A N^-1 r (the first term of Eq. (3)'s right-hand side) from the
+// staged r in ctmp; the diagonal-N form scales r into gq first
+void Solver::al_rhs(cudaStream_t s) {
+  const Lvl& L = L64;
+  if (diag_n) {
+    { ProfScope ps_(GKB_KC_GKB, s); k_cells_mul<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, nw64.p, gq.p); }
+    Ops<double>::grad(L, gq.p, f.p, gamma / n_scale, s);
+  } else {
+    Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
+  }
+}
+
 // AL transform, GKB initialisation and the while loop of Algorithm 1,
 // captured into the graph that s is capturing. Inputs: wtmp (g), ctmp (r);
 // outputs: u (velocity without y0), pp (pressure), y0.
@@ -1768,12 +1857,12 @@ void Solver::capture_core(cudaStream_t s, cudaStream_t sb1, cudaStream_t sb2) {
   GkbState* S = gkb_dev;
   double* red_out = (double*)((char*)gkb_dev + offsetof(GkbState, red));
   // AL transform (Eq. (3)): f = g + gamma A N^-1 r ; y0 = M^-1 f ; b = r - A^T y0
-  Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
+  al_rhs(s);
   Ops<double>::axpby(len, 1.0, wtmp.p, 1.0, f.p, s);
   capture_inner(s, sb1);
   GKB_CUDA(cudaMemcpyAsync(y0.p, x.p, len * sizeof(double), cudaMemcpyDeviceToDevice, s));
   // init: beta_1, q_1, w = M^-1 A q_1, alpha_1, v_1, zeta_1, d_1, p, u
-  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, S, red, red_out); }
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out); }
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S); }
   Ops<double>::grad(L, q.p, f.p, 1.0, s);
@@ -1885,6 +1974,9 @@ void Solver::init_state(double tol, int delay) {
   hs.tol = tol;
   hs.n_scale = n_scale;
   hs.ncells = (double)ncell;
+  hs.nd = diag_n ? nd64.p : nullptr;
+  hs.nsum = diag_n ? nsum : n_scale * (double)ncell;
+  hs.ninvsum = diag_n ? ninvsum : (double)ncell / n_scale;
   hs.delay = delay;
   hs.maxit = opt.maxit;
   hs.enclosed = enclosed ? 1 : 0;
@@ -1909,10 +2001,10 @@ void Solver::run_core_host() {
   const long long len = L.nvel;
   GkbState* S = gkb_dev;
   double* red_out = (double*)((char*)gkb_dev + offsetof(GkbState, red));
-  Ops<double>::grad(L, ctmp.p, f.p, gamma / n_scale, s);
+  al_rhs(s);
   Ops<double>::axpby(len, 1.0, wtmp.p, 1.0, f.p, s);
   inner_solve(f.p, y0.p);
-  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, red, red_out); }
+  { ProfScope ps_(GKB_KC_GKB, s); k_gkb_b<<<cgrid(L), dim3(32, 8), 0, s>>>(L, ctmp.p, y0.p, bc.p, S, red, red_out); }
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_scalar<<<1, 32, 0, s>>>(S_BETA1, S, red_out); }
   { ProfScope ps_(GKB_KC_GKB, s); k_gkb_q1<<<cgrid(L), dim3(32, 8), 0, s>>>(L, bc.p, q.p, S); }
   Ops<double>::grad(L, q.p, f.p, 1.0, s);

@@ -67,6 +67,7 @@ struct Gmg {
   struct Level {
     Lvl L;
     DevBuf<T> x, b, r, d, mu;
+    DevBuf<T> nw;               // coarsened grad-div weights (diagonal N)
     DevBuf<T> t2;               // second restriction scratch (3D coarse levels)
     DevBuf<T> sl;               // coarse slopes for the 3D prolongation
     DevBuf<T> table;            // patch class inverses (constant viscosity)
@@ -166,6 +167,12 @@ struct Solver {
   Lvl L64{}, L32{};              // finest level, FP64 / FP32 views
   DevBuf<double> mu64;
   DevBuf<float> mu32;
+  // diagonal N (gkb_set_problem_n): N per cell (padded, FP64), the relative
+  // grad-div weights n_scale / N in both precisions, sum N and sum 1/N
+  DevBuf<double> nd64, nw64;
+  DevBuf<float> nw32;
+  double nsum = 0, ninvsum = 0;
+  bool diag_n = false;
 
   // reduction scratch and device scalars
   DevBuf<double> red_partial;
@@ -206,12 +213,13 @@ struct Solver {
   double tuned_ms = 0;            // inner-solve time of the tuned configuration
   void build_inner();
   double time_inner_solve();
-  void autotune_inner(bool var_mu);
+  void autotune_inner(bool var_mu, bool weighted);
   void attach_net_levels();
   void refresh_net();
   void ensure_capture_streams();
   void build_solve_graph();
   // emitters shared by the graph capture and the host-sequenced path
+  void al_rhs(cudaStream_t s);
   void capture_core(cudaStream_t s, cudaStream_t sb1, cudaStream_t sb2);
   void capture_inner(cudaStream_t s, cudaStream_t sb);
   void stage_in(const double* g, const double* r, const double* w0, const double* p0);
@@ -219,7 +227,8 @@ struct Solver {
   void run_core_host();
   int finish(double* w_out, double* p_out, const double* w0, const double* p0, bool graph_run);
 
-  void set_problem(const gkb_grid* g, const double* viscosity, double mu0, double gamma, double n_scale);
+  void set_problem(const gkb_grid* g, const double* viscosity, double mu0, double gamma, double n_scale,
+                   const double* n_diag = nullptr);
   int solve(const double* g, const double* r, double tol, int delay, double* w_out, double* p_out,
             const double* w0, const double* p0);
   void apply(int op, const double* x, double* y);

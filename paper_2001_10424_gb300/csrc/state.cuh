@@ -153,8 +153,10 @@ struct GkbState {
   double zsum;               // sum_{j<=K} zeta_j^2
   double est;                // latest lower-bound estimate
   double tol;
-  double n_scale;            // N = n_scale * I
+  double n_scale;            // N = n_scale * I (nd == null)
   double ncells;             // number of cells (for the mean)
+  const double* nd;          // diagonal of N per padded cell, or null
+  double nsum, ninvsum;      // sum of N_i and of 1 / N_i over the cells
   double red[4];             // raw results of the last FIN_STORE reduction
   double ring[GKB_RING];     // zeta^2, indexed by K mod GKB_RING
   int delay, maxit, enclosed;

@@ -9,7 +9,7 @@ from oracle import mac
 
 def make_handle(gk, n, bc, mu=1.0, gamma=0.0, precision=0, inner=1, tol_inner=1e-11, maxit=1000,
                 maxit_inner=3000, coarse_max=8, degree=2, mixed_rtol=1e-3, use_graph=1, n_scale=0.0,
-                profile=0, kernel_variant=0, unet_side=0, net=None):
+                profile=0, kernel_variant=0, unet_side=0, net=None, n_diag=None):
     import torch
     opt = gk.gkb_default_options()
     opt.precision = precision
@@ -36,7 +36,11 @@ def make_handle(gk, n, bc, mu=1.0, gamma=0.0, precision=0, inner=1, tol_inner=1e
     else:
         # compact cell ordering: x fastest == Fortran order of an [x, y, z] array
         visc = np.ascontiguousarray(np.asarray(mu, dtype=np.float64).ravel(order="F"))
-    gk.gkb_set_problem(h, gk.make_grid(n, h_, bc), visc, mu0, gamma, n_scale)
+    if n_diag is not None:
+        nd = np.ascontiguousarray(np.asarray(n_diag, dtype=np.float64).ravel(order="F"))
+        gk.gkb_set_problem_n(h, gk.make_grid(n, h_, bc), nd, visc, mu0, gamma)
+    else:
+        gk.gkb_set_problem(h, gk.make_grid(n, h_, bc), visc, mu0, gamma, n_scale)
     return h
 
 

@@ -155,10 +155,16 @@ def _edge_mu(grid, mu, X, c, a, a_face):
     return total / count
 
 
-def assemble(grid, mu=1.0, gamma=0.0, n_scale=None, n_diag=None):
+def assemble(grid, mu=1.0, gamma=0.0, n_scale=None, n_diag=None, sym=False):
     """Assemble W, A (CSR), N and M = W + gamma A N^-1 A^T (Eq. (2)).
 
     ``mu`` is a scalar or an array of cell viscosities indexed [x, y(, z)].
+    ``sym`` selects the symmetric-gradient viscous operator
+    ``-div(2 mu eps(u))`` (every side Dirichlet): the normal links carry
+    ``2 mu``, and every interior node (2D) / edge (3D) between the axes
+    ``a`` and ``c`` adds the cross coupling of its energy
+    ``mu_e h^(d-2) (d_a u_c + d_c u_a)^2``, whose squares are the tangential
+    links already present.
     ``n_diag`` (optional, same indexing, every entry > 0) selects the diagonal
     ``N = diag(n_diag)``; otherwise ``N = n_scale * I``.
     Returns a dict with W, A, M (scipy CSR, FP64), n_scale, ``N`` (the scalar
@@ -220,7 +226,7 @@ def assemble(grid, mu=1.0, gamma=0.0, n_scale=None, n_diag=None):
             if a == c:
                 # normal link across the cell between the two faces
                 mu_l, _ = _cell_mu(grid, mu, Xl)
-                kap = scale * mu_l
+                kap = (2.0 if sym else 1.0) * scale * mu_l
             else:
                 mu_l = _edge_mu(grid, mu, Xl, c, a, Xl[a] + 1)
                 kap = scale * mu_l * area[tuple(sl1)]
@@ -249,6 +255,34 @@ def assemble(grid, mu=1.0, gamma=0.0, n_scale=None, n_diag=None):
                     kap = 2.0 * scale * mu_l * area[tuple(sl)]
                     act = ib >= 0
                     add_diag(ib[act], kap[act])  # wall (tangential) velocity is 0
+    if sym:
+        assert grid.enclosed, "the symmetric-gradient form needs Dirichlet velocity on every side"
+        for c in range(d):
+            for a in range(c):
+                # interior edges between axes a and c: node coordinates
+                # ka in 1..n_a-1, kc in 1..n_c-1, cell coordinates elsewhere
+                shape = list(grid.n)
+                shape[a] = grid.n[a] - 1
+                shape[c] = grid.n[c] - 1
+                E = np.indices(shape)
+                E[a] += 1
+                E[c] += 1
+                # u_c above / below the edge along a; u_a right / left along c
+                def faces(comp, axis, shift):
+                    X = [e.copy() for e in E]
+                    X[axis] = X[axis] + shift
+                    return grid.face_index[comp][tuple(X)]
+                cp, cm = faces(c, a, 0), faces(c, a, -1)
+                ap, am = faces(a, c, 0), faces(a, c, -1)
+                mu_e = _edge_mu(grid, mu, [e for e in E], c, a, E[a])
+                kap = (scale * mu_e).ravel()
+                g1 = ((cp.ravel(), 1.0), (cm.ravel(), -1.0))
+                g2 = ((ap.ravel(), 1.0), (am.ravel(), -1.0))
+                for i1, s1 in g1:
+                    for i2, s2 in g2:
+                        rows.extend([i1, i2])
+                        cols.extend([i2, i1])
+                        vals.extend([s1 * s2 * kap, s1 * s2 * kap])
     rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
     cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
     vals = np.concatenate(vals) if vals else np.zeros(0)

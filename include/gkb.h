@@ -85,6 +85,9 @@ extern "C" {
                                  unet_side cells as the starting guess of the
                                  ordinary cycle from that level down           */
 
+#define GKB_VISC_LAPLACE 0
+#define GKB_VISC_SYMGRAD 1
+
 #define GKB_OP_W   0          /* y = W x                 (m -> m) */
 #define GKB_OP_A   1          /* y = A x (gradient)      (n -> m) */
 #define GKB_OP_AT  2          /* y = A^T x (-divergence) (m -> n) */
@@ -163,6 +166,12 @@ typedef struct {
                              once, appended). gkb_get_options returns the
                              choice. Multigrid inner solvers only.           */
   void* stream;           /* cudaStream_t to run on (NULL: legacy stream)     */
+  int viscous_form;       /* GKB_VISC_LAPLACE (default): W is the component-
+                             wise -div(mu grad u_c); GKB_VISC_SYMGRAD: W is
+                             -div(2 mu eps(u)), eps(u) = (grad u + grad u^T)
+                             / 2, coupling the components through the
+                             node (2D) / edge (3D) viscosities; needs
+                             Dirichlet velocity on every side                 */
 } gkb_options;
 
 typedef struct {

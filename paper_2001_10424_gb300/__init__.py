@@ -35,6 +35,7 @@ GKB_INNER_FCG_UNET = 2
 GKB_INNER_FCG_UNET_MG = 3
 GKB_INNER_FGMRES = 4
 GKB_OP_W, GKB_OP_A, GKB_OP_AT, GKB_OP_M = 0, 1, 2, 3
+GKB_VISC_LAPLACE, GKB_VISC_SYMGRAD = 0, 1
 KERNEL_CLASSES = ["apply", "residual", "smooth", "restrict", "prolong", "coarse", "blas", "gkb", "layout", "unet"]
 
 STATUS_NAMES = {
@@ -66,7 +67,8 @@ class gkb_options(ctypes.Structure):
                 ("coarse_max", ctypes.c_int), ("mixed_rtol", ctypes.c_double), ("use_graph", ctypes.c_int),
                 ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("unet_side", ctypes.c_int),
                 ("fcg_rho", ctypes.c_double), ("fgmres_restart", ctypes.c_int), ("cheb_lo", ctypes.c_double),
-                ("cheb_hi", ctypes.c_double), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("cheb_hi", ctypes.c_double), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("viscous_form", ctypes.c_int)]
 
 
 class gkb_stats_t(ctypes.Structure):

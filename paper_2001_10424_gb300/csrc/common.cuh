@@ -36,6 +36,10 @@ struct Lvl {
   // variable-viscosity levels
   const double* nw64;
   const float* nw32;
+  // 1: W is -div(2 mu eps(u)) (normal links doubled, cross couplings at the
+  // interior nodes / edges); only on variable-viscosity levels, all sides
+  // Dirichlet
+  int sym;
   // derived constants (set by finish_level), in both precisions so that FP32
   // kernels never convert from double on the FP64 pipe
   int has_gd;         // gc != 0
@@ -208,17 +212,21 @@ __device__ __forceinline__ T neg_div(const Lvl& L, const T* x, int i, int j, int
 template <typename T, bool VarMu, int C, bool NC = true>
 __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T xf) {
   T acc = 0;
-  // normal links across the cells p[C]-1 and p[C]
+  const bool sym = VarMu && L.sym;
+  // normal links across the cells p[C]-1 and p[C] (conductance 2 mu in the
+  // symmetric-gradient form)
   {
     int q[3] = {p[0], p[1], p[2]};
     if (p[C] < L.n[C]) {
       q[C] = p[C] + 1;
       T mu = cell_mu<T, VarMu>(L, p[0], p[1], p[2]);
+      if (sym) mu += mu;
       acc = fma(mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
     }
     if (p[C] > 0) {
       q[C] = p[C] - 1;
       T mu = cell_mu<T, VarMu>(L, q[0], q[1], q[2]);
+      if (sym) mu += mu;
       acc = fma(mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
     }
   }
@@ -238,6 +246,16 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
       if (p[A] + 1 < L.n[A]) {
         q[A] = p[A] + 1;
         acc = fma(area * mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
+        if (sym) {
+          // cross coupling at the interior node / edge (A-node p[A]+1,
+          // C-node p[C]): -mu (u_A(p + e_A) - u_A(p + e_A - e_C))
+          int s[3] = {p[0], p[1], p[2]};
+          s[A] = p[A] + 1;
+          const T ap = ldv<T, NC>(x, L.off[A] + cix(L, s[0], s[1], s[2]));
+          s[C] = p[C] - 1;
+          const T am = ldv<T, NC>(x, L.off[A] + cix(L, s[0], s[1], s[2]));
+          acc = fma(-mu, ap - am, acc);
+        }
       } else if (!L.nat[2 * A + 1]) {
         acc = fma((T)2 * area * mu, xf, acc);
       }
@@ -251,6 +269,14 @@ __device__ __forceinline__ T w_row(const Lvl& L, const T* x, const int p[3], T x
       if (p[A] > 0) {
         q[A] = p[A] - 1;
         acc = fma(area * mu, xf - face_val<T, C, NC>(L, x, q[0], q[1], q[2]), acc);
+        if (sym) {
+          // cross coupling at (A-node p[A], C-node p[C]): +mu (u_A(p) - u_A(p - e_C))
+          int s[3] = {p[0], p[1], p[2]};
+          const T ap = ldv<T, NC>(x, L.off[A] + cix(L, s[0], s[1], s[2]));
+          s[C] = p[C] - 1;
+          const T am = ldv<T, NC>(x, L.off[A] + cix(L, s[0], s[1], s[2]));
+          acc = fma(mu, ap - am, acc);
+        }
       } else if (!L.nat[2 * A]) {
         acc = fma((T)2 * area * mu, xf, acc);
       }
@@ -269,6 +295,7 @@ __device__ __forceinline__ T w_diag(const Lvl& L, const int p[3]) {
     q[C] = p[C] - 1;
     acc += cell_mu<T, VarMu>(L, q[0], q[1], q[2]);
   }
+  if (VarMu && L.sym) acc += acc;  // normal conductance 2 mu
   const bool half = (p[C] == 0 && L.nat[2 * C]) || (p[C] == L.n[C] && L.nat[2 * C + 1]);
   const T area = half ? (T)0.5 : (T)1;
 #pragma unroll

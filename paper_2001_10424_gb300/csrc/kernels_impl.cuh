@@ -65,18 +65,25 @@ __device__ __forceinline__ T w_row_const(const Lvl& L, const T* x, const T* xc, 
 template <typename T, int C>
 __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* mc, T xf) {
   const long long sc = strd<C>(L);
+  const bool sym = L.sym;
   T acc = 0;
-  acc = fma(__ldg(mc), xf - __ldg(xc + sc), acc);
-  acc = fma(__ldg(mc - sc), xf - __ldg(xc - sc), acc);
+  T m0 = __ldg(mc), m1 = __ldg(mc - sc);
+  if (sym) { m0 += m0; m1 += m1; }
+  acc = fma(m0, xf - __ldg(xc + sc), acc);
+  acc = fma(m1, xf - __ldg(xc - sc), acc);
 #pragma unroll
   for (int A = 0; A < 3; ++A) {
     if (A == C || A >= L.dim) continue;
     const long long sa = A == 0 ? 1LL : (A == 1 ? (long long)L.P : L.S);
+    // u_A at the face's padded index (cross couplings of the symmetric form)
+    const T* xa = xc - L.off[C] + L.off[A];
     // node/edge means: cells at C-offsets -1, 0 and A-offsets (0, +1) / (-1, 0)
     const T mup = (((__ldg(mc - sc) + __ldg(mc - sc + sa)) + __ldg(mc)) + __ldg(mc + sa)) / (T)4;
     acc = fma(mup, xf - __ldg(xc + sa), acc);
+    if (sym) acc = fma(-mup, __ldg(xa + sa) - __ldg(xa + sa - sc), acc);
     const T mum = (((__ldg(mc - sc - sa) + __ldg(mc - sc)) + __ldg(mc - sa)) + __ldg(mc)) / (T)4;
     acc = fma(mum, xf - __ldg(xc - sa), acc);
+    if (sym) acc = fma(mum, __ldg(xa) - __ldg(xa - sc), acc);
   }
   return acc;
 }
@@ -266,6 +273,15 @@ __device__ void patch_matrix(const Lvl& L, const int e[3], T Mp[4][4], bool act[
     cc[a] = e[a]; cc[b] = e[b];
     if (act[1] && act[3] && cell_in(L, cc[0], cc[1], cc[2]))
       Mp[1][3] = Mp[3][1] = g * cell_nw<T, VarMu>(L, cix(L, cc[0], cc[1], cc[2]));
+  }
+  if (VarMu && L.sym && e[a] >= 1 && e[a] < L.n[a] && e[b] >= 1 && e[b] < L.n[b]) {
+    // symmetric form: the cross coupling of an interior node / edge, +-k
+    // with the same signs as the grad-div couplings
+    const T k = ws * edge_mu<T, VarMu, a, b>(L, e, e[b]);
+    Mp[0][2] += k; Mp[2][0] += k;
+    Mp[0][3] -= k; Mp[3][0] -= k;
+    Mp[1][2] -= k; Mp[2][1] -= k;
+    Mp[1][3] += k; Mp[3][1] += k;
   }
 }
 

@@ -62,6 +62,7 @@ Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
   L.mu32 = nullptr;
   L.nw64 = nullptr;
   L.nw32 = nullptr;
+  L.sym = 0;
   L.fast = 1;
   finish_level(L);
   return L;
@@ -331,6 +332,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
     Lvl Lc = make_level(Lf.dim, nc, 2.0 * Lf.h, Lf.nat, gc);
     Lc.mu0 = Lf.mu0;
     Lc.fast = Lf.fast;
+    Lc.sym = Lf.sym;
     finish_level(Lc);
     lev.emplace_back();
     Level& C = lev.back();
@@ -1218,19 +1220,24 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
     throw Error{GKB_ERR_INVALID_ARG, "the FGMRES inner solver runs in FP64"};
   if (use_gmg && !enclosed)
     throw Error{GKB_ERR_INVALID_ARG, "the multigrid preconditioner needs Dirichlet velocity on every side"};
+  const bool symgrad = opt.viscous_form == GKB_VISC_SYMGRAD;
+  if (symgrad && !enclosed)
+    throw Error{GKB_ERR_INVALID_ARG, "the symmetric-gradient form needs Dirichlet velocity on every side"};
   if (learned_inner() && g->dim != 2)
     throw Error{GKB_ERR_INVALID_ARG, "the learned inner solver is 2D only"};
   int n3[3] = {g->n[0], g->n[1], g->dim == 3 ? g->n[2] : 1};
   L64 = make_level(g->dim, n3, g->h, nat, gamma / n_scale);
   ncell = (int64_t)n3[0] * n3[1] * n3[2];
-  // a non-uniform N runs on the variable-viscosity kernels, which carry the
-  // per-cell weights: a constant viscosity becomes an array of mu0
+  // a non-uniform N and the symmetric-gradient form run on the
+  // variable-viscosity kernels, which carry the per-cell weights and the
+  // cross couplings: a constant viscosity becomes an array of mu0
   std::vector<double> mu_fill;
-  if (n_diag && !viscosity) {
+  if ((n_diag || symgrad) && !viscosity) {
     mu_fill.assign((size_t)ncell, mu0);
     viscosity = mu_fill.data();
   }
   L64.mu0 = viscosity ? 1.0 : mu0;
+  L64.sym = symgrad ? 1 : 0;
   // fast paths: measured faster in FP32, slower in FP64 (FP64-pipe bound)
   L64.fast = (opt.kernel_variant == 2) ? 1 : 0;
   finish_level(L64);
@@ -1325,7 +1332,7 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   hist_inner.alloc((size_t)opt.maxit + 4);
   // multigrid + CG (tuned first when asked)
   tuned_ms = 0;
-  if (opt.autotune && use_gmg && opt.inner != GKB_INNER_FGMRES) autotune_inner(viscosity != nullptr, diag_n);
+  if (opt.autotune && use_gmg && opt.inner != GKB_INNER_FGMRES) autotune_inner(viscosity != nullptr, diag_n ? 1 : 0);
   else build_inner();
   if (opt.inner == GKB_INNER_FGMRES) fgm.init(L64.nvel, opt.fgmres_restart);
   stats.tuned_inner_ms = tuned_ms;
@@ -1448,7 +1455,7 @@ void tune_read_file() {
 // time of a whole inner solve to tol_inner, and keep the fastest; results are
 // cached per device, grid, viscosity kind, precision, inner solver and gamma
 // decade, in the process and (GKB_TUNE_CACHE) in a text file.
-void Solver::autotune_inner(bool var_mu, bool weighted) {
+void Solver::autotune_inner(bool var_mu, int weighted) {
   int dev = 0;
   GKB_CUDA(cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -1458,7 +1465,8 @@ void Solver::autotune_inner(bool var_mu, bool weighted) {
     if (c == ' ') c = '_';
   char key[512];
   snprintf(key, sizeof key, "%s|d%d|%dx%dx%d|%s|p%d|i%d|g%+.0f", name.c_str(), grid.dim, L64.n[0], L64.n[1], L64.n[2],
-           var_mu ? (weighted ? "varmu-ndiag" : "varmu") : "mu", opt.precision, opt.inner, gamma > 0 ? std::floor(std::log10(gamma)) : -99.0);
+           var_mu ? (weighted ? (L64.sym ? "symgrad-ndiag" : "varmu-ndiag") : (L64.sym ? "symgrad" : "varmu")) : "mu",
+           opt.precision, opt.inner, gamma > 0 ? std::floor(std::log10(gamma)) : -99.0);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_read_file();
@@ -2189,6 +2197,7 @@ __global__ void k_boundary_rhs(Lvl L, Compact cmp, int side, const double* __res
 
 void Solver::boundary_rhs(int side, const double* ub, double* g, double* r) {
   if (!have_problem) throw Error{GKB_ERR_INVALID_ARG, "gkb_set_problem has not been called"};
+  if (L64.sym) throw Error{GKB_ERR_INVALID_ARG, "boundary data is not supported with the symmetric-gradient form"};
   if (side < 0 || side >= 2 * grid.dim) throw Error{GKB_ERR_INVALID_ARG, "side out of range"};
   if (grid.bc[side] != GKB_BC_DIRICHLET) throw Error{GKB_ERR_INVALID_ARG, "side is not Dirichlet"};
   if (!ub || !g || !r) throw Error{GKB_ERR_INVALID_ARG, "NULL vector"};

@@ -213,7 +213,7 @@ struct Solver {
   double tuned_ms = 0;            // inner-solve time of the tuned configuration
   void build_inner();
   double time_inner_solve();
-  void autotune_inner(bool var_mu, bool weighted);
+  void autotune_inner(bool var_mu, int weighted);
   void attach_net_levels();
   void refresh_net();
   void ensure_capture_streams();

@@ -9,7 +9,7 @@ from oracle import mac
 
 def make_handle(gk, n, bc, mu=1.0, gamma=0.0, precision=0, inner=1, tol_inner=1e-11, maxit=1000,
                 maxit_inner=3000, coarse_max=8, degree=2, mixed_rtol=1e-3, use_graph=1, n_scale=0.0,
-                profile=0, kernel_variant=0, unet_side=0, net=None, n_diag=None):
+                profile=0, kernel_variant=0, unet_side=0, net=None, n_diag=None, viscous_form=0):
     import torch
     opt = gk.gkb_default_options()
     opt.precision = precision
@@ -24,6 +24,7 @@ def make_handle(gk, n, bc, mu=1.0, gamma=0.0, precision=0, inner=1, tol_inner=1e
     opt.profile = profile
     opt.kernel_variant = kernel_variant
     opt.unet_side = unet_side
+    opt.viscous_form = viscous_form
     opt.stream = torch.cuda.current_stream().cuda_stream
     h = gk.gkb_create(opt)
     if net is not None:
@@ -49,9 +50,9 @@ def energy_rel(M, a, ref):
     return math.sqrt(max(float(e @ (M @ e)), 0.0)) / math.sqrt(float(ref @ (M @ ref)))
 
 
-def oracle_problem(n, bc, mu=1.0, gamma=0.0):
+def oracle_problem(n, bc, mu=1.0, gamma=0.0, **kw):
     grid = mac.MacGrid(n, 1.0 / n[0], bc)
-    ops = mac.assemble(grid, mu, gamma)
+    ops = mac.assemble(grid, mu, gamma, **kw)
     return grid, ops
 
 

@@ -55,7 +55,7 @@ def test_cavity2d_gamma_robust(lib):
 
 
 def test_varvisc2d_gamma_robust(lib):
-    _check(_sweep(lib, workloads.varvisc2d(256), precision=1), 30)
+    _check(_sweep(lib, workloads.varvisc2d(256)), 30)
 
 
 def test_cavity3d_gamma_robust(lib):

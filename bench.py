@@ -304,7 +304,10 @@ class Workload:
         return "solves/s" if self.batched else "s"
 
 
-def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, inner=None):
+def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, inner=None, variant=None):
+    """variant: None, or a combination of "ndiag" (N = h^d / mu, the
+    viscosity-weighted pressure mass matrix) and "symgrad" (the
+    symmetric-gradient viscous operator)."""
     opt = gk.gkb_default_options()
     opt.autotune = autotune
     if wk.kernel_variant is not None:
@@ -321,6 +324,8 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, in
         opt.unet_side = wk.unet_side
     if inner is not None:
         opt.inner = inner
+    if variant and "symgrad" in variant:
+        opt.viscous_form = gk.GKB_VISC_SYMGRAD
     h = gk.gkb_create(opt)
     if learned:
         gk.gkb_set_unet(h, wk.net)
@@ -328,6 +333,10 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, in
     import numpy as np
     if np.isscalar(mu):
         gk.gkb_set_problem(h, gk.make_grid(pr["n"], pr["h"], pr["bc"]), None, float(mu), pr["gamma"], 0.0)
+    elif variant and "ndiag" in variant:
+        visc = np.ascontiguousarray(np.asarray(mu).ravel(order="F"))
+        nd = np.ascontiguousarray(pr["h"] ** len(pr["n"]) / visc)
+        gk.gkb_set_problem_n(h, gk.make_grid(pr["n"], pr["h"], pr["bc"]), nd, visc, 1.0, pr["gamma"])
     else:
         visc = np.ascontiguousarray(np.asarray(mu).ravel(order="F"))
         gk.gkb_set_problem(h, gk.make_grid(pr["n"], pr["h"], pr["bc"]), visc, 1.0, pr["gamma"], 0.0)
@@ -337,13 +346,14 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, in
 class Bound:
     """Handles plus device/host buffers of a workload, and its step."""
 
-    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0, inner=None):
+    def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0, inner=None,
+                 variant=None):
         import numpy as np
         self.gk, self.torch, self.wk = gk, torch, wk
         probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
         self.probs = probs
         lf = wk.learned if learned == "default" else learned
-        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner) for pr in probs]
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner, variant) for pr in probs]
         self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
         for h, pr in zip(self.hs, probs):
             m, n = gk.gkb_layout(h)
@@ -627,10 +637,10 @@ def run_ours(args, ws, rank, local):
     rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
 
-    def time_form(form, learned, autotune=None, inner=None):
+    def time_form(form, learned, autotune=None, inner=None, variant=None):
         autotune = args.autotune if autotune is None else autotune
         t_setup = time.perf_counter()
-        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune, inner=inner)
+        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune, inner=inner, variant=variant)
         t_setup = time.perf_counter() - t_setup
         for _ in range(2):
             B2.step(args)
@@ -667,6 +677,10 @@ def run_ours(args, ws, rank, local):
             forms["learned_" + other + "_" + wk.form] = time_form(wk.form, other)
             forms["gmg_pcg_" + wk.form] = time_form(wk.form, None)
             forms["gmg_pcg_fp64"] = time_form("fp64", None)
+            # general N and the symmetric-gradient operator on the same instance
+            forms["gmg_pcg_" + wk.form + "_ndiag"] = time_form(wk.form, None, variant="ndiag")
+            forms["gmg_pcg_" + wk.form + "_symgrad"] = time_form(wk.form, None, variant="symgrad")
+            forms["gmg_pcg_" + wk.form + "_symgrad_ndiag"] = time_form(wk.form, None, variant="symgrad+ndiag")
         else:
             other = "mixed" if wk.form == "fp64" else "fp64"
             forms[other] = time_form(other, None)

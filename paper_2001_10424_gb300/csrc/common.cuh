@@ -36,6 +36,12 @@ struct Lvl {
   // variable-viscosity levels
   const double* nw64;
   const float* nw32;
+  // node (2D) / edge (3D) viscosities of variable-viscosity levels: one
+  // plane of em_plane() values per edge orientation E (the axis the edge
+  // runs along; 2D has only E = 2), indexed by the padded index of the edge's
+  // (node, node, cell) coordinates; null: computed from the cells on the fly
+  const double* em64;
+  const float* em32;
   // 1: W is -div(2 mu eps(u)) (normal links doubled, cross couplings at the
   // interior nodes / edges); only on variable-viscosity levels, all sides
   // Dirichlet
@@ -136,12 +142,20 @@ __device__ __forceinline__ T cell_nw(const Lvl& L, long long cb) {
   return w ? __ldg(w + cb) : (T)1;
 }
 
+__host__ __device__ __forceinline__ long long em_plane(const Lvl& L) {
+  return (L.dim == 3 ? (long long)(L.n[2] + 1) : 1LL) * L.S;
+}
+
+template <typename T> struct EmPtr;
+template <> struct EmPtr<double> { static __device__ __forceinline__ const double* get(const Lvl& L) { return L.em64; } };
+template <> struct EmPtr<float>  { static __device__ __forceinline__ const float*  get(const Lvl& L) { return L.em32; } };
+
 // mean viscosity of the in-domain cells around the node/edge crossed by a
 // tangential link of component C along axis A; the cells have C-coordinate
 // p[C]-1 and p[C], A-coordinate af-1 and af, other coordinates from p.
-template <typename T, bool VarMu, int C, int A>
-__device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
-  if (!VarMu) return Kc<T>::mu0(L);
+// Summed in the order (C-1, A-1), (C-1, A), (C, A-1), (C, A).
+template <typename T, int C, int A>
+__device__ __forceinline__ T edge_mu_cells(const Lvl& L, const int p[3], int af) {
   T s = 0;
   int cnt = 0;
 #pragma unroll
@@ -154,6 +168,21 @@ __device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
       if (cell_in(L, q[0], q[1], q[2])) { s += cell_mu<T, true>(L, q[0], q[1], q[2]); ++cnt; }
     }
   return s / (T)cnt;
+}
+
+// the same from the level's node/edge table when it has one (one value per
+// node/edge whichever component asks, so every path reads the same bits)
+template <typename T, bool VarMu, int C, int A>
+__device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
+  if (!VarMu) return Kc<T>::mu0(L);
+  const T* em = EmPtr<T>::get(L);
+  if (em) {
+    constexpr int E = 3 - C - A;
+    int q[3] = {p[0], p[1], p[2]};
+    q[A] = af;
+    return __ldg(em + (L.dim == 3 ? E : 0) * em_plane(L) + cix(L, q[0], q[1], q[2]));
+  }
+  return edge_mu_cells<T, C, A>(L, p, af);
 }
 
 // velocity loads: through the read-only path (NC, the default: the array is

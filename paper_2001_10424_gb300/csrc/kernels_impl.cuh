@@ -77,11 +77,18 @@ __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* 
     const long long sa = A == 0 ? 1LL : (A == 1 ? (long long)L.P : L.S);
     // u_A at the face's padded index (cross couplings of the symmetric form)
     const T* xa = xc - L.off[C] + L.off[A];
-    // node/edge means: cells at C-offsets -1, 0 and A-offsets (0, +1) / (-1, 0)
-    const T mup = (((__ldg(mc - sc) + __ldg(mc - sc + sa)) + __ldg(mc)) + __ldg(mc + sa)) / (T)4;
+    // node/edge means: from the level's table (the node/edge of the + link
+    // has the padded index of the face plus sa, that of the - link the
+    // face's), else from the cells at C-offsets -1, 0 and A-offsets (0, +1) /
+    // (-1, 0) in the order of edge_mu_cells
+    const T* em = EmPtr<T>::get(L);
+    const T* emp = em ? em + (L.dim == 3 ? 3 - C - A : 0) * em_plane(L) + (mc - MuPtr<T>::get(L)) : nullptr;
+    const T mup = em ? __ldg(emp + sa)
+                     : (((__ldg(mc - sc) + __ldg(mc - sc + sa)) + __ldg(mc)) + __ldg(mc + sa)) / (T)4;
     acc = fma(mup, xf - __ldg(xc + sa), acc);
     if (sym) acc = fma(-mup, __ldg(xa + sa) - __ldg(xa + sa - sc), acc);
-    const T mum = (((__ldg(mc - sc - sa) + __ldg(mc - sc)) + __ldg(mc - sa)) + __ldg(mc)) / (T)4;
+    const T mum = em ? __ldg(emp)
+                     : (((__ldg(mc - sc - sa) + __ldg(mc - sc)) + __ldg(mc - sa)) + __ldg(mc)) / (T)4;
     acc = fma(mum, xf - __ldg(xc - sa), acc);
     if (sym) acc = fma(mum, __ldg(xa) - __ldg(xa - sc), acc);
   }
@@ -659,6 +666,25 @@ __global__ void k_patch_table(Lvl L, T* table) {
   for (int r = 0; r < 4; ++r)
     for (int c = 0; c < 4; ++c)
       table[(size_t)t * 16 + r * 4 + c] = (act[r] && act[c]) ? (T)inv[r][c] : (T)0;
+}
+
+// Node (2D) / edge (3D) viscosity table of a variable-viscosity level: one
+// thread per position (e0, e1, e2) with e0 <= n0, e1 <= n1, e2 <= n2 (3D);
+// orientation E takes the positions with node coordinates along its two
+// other axes and a cell coordinate along E.
+template <typename T>
+__global__ void k_edge_mu(Lvl L, T* __restrict__ em) {
+  const int e[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
+                    (int)blockIdx.z};
+  if (e[0] > L.n[0] || e[1] > L.n[1]) return;
+  const long long Q = em_plane(L), id = cix(L, e[0], e[1], e[2]);
+  if (L.dim == 2) {
+    em[id] = edge_mu_cells<T, 0, 1>(L, e, e[1]);
+    return;
+  }
+  if (e[2] < L.n[2]) em[2 * Q + id] = edge_mu_cells<T, 0, 1>(L, e, e[1]);
+  if (e[0] < L.n[0]) em[0 * Q + id] = edge_mu_cells<T, 1, 2>(L, e, e[2]);
+  if (e[1] < L.n[1]) em[1 * Q + id] = edge_mu_cells<T, 0, 2>(L, e, e[2]);
 }
 
 // Per-patch inverses for variable viscosity (one thread per edge of

@@ -120,6 +120,18 @@ void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
 
 #if GKB_IN_PART(5)
 template <>
+long long Ops<KT>::edge_table_len(const Lvl& L) {
+  return (L.dim == 3 ? 3 : 1) * em_plane(L);
+}
+
+template <>
+void Ops<KT>::edge_table(const Lvl& L, KT* em, cudaStream_t s) {
+  ProfScope ps_(GKB_KC_LAYOUT, s);
+  const dim3 g((L.n[0] + 1 + 31) / 32, (L.n[1] + 1 + 7) / 8, L.dim == 3 ? L.n[2] + 1 : 1);
+  k_edge_mu<KT><<<g, dim3(32, 8), 0, s>>>(L, em);
+}
+
+template <>
 void Ops<KT>::grad(const Lvl& L, const KT* p, KT* y, KT scale, cudaStream_t s) {
   ProfScope ps_(GKB_KC_LAYOUT, s, lvl_unknowns(L));
   k_grad<KT><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, p, y, scale);

@@ -26,6 +26,9 @@ struct Ops {
   // (3*75*16 entries) for constant viscosity, every patch for variable
   static long long patch_table_len(const Lvl& L);
   static void patch_table(const Lvl& L, T* table, cudaStream_t s);
+  // node (2D) / edge (3D) viscosity table of a variable-viscosity level
+  static long long edge_table_len(const Lvl& L);
+  static void edge_table(const Lvl& L, T* em, cudaStream_t s);
   // y = scale * A p (faces from cells)
   static void grad(const Lvl& L, const T* p, T* y, T scale, cudaStream_t s);
   // y = scale * A^T x (cells from faces)

@@ -71,6 +71,9 @@ Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc) {
 template <typename T> static void set_mu(Lvl& L, const T* mu);
 template <> void set_mu<double>(Lvl& L, const double* mu) { L.mu64 = mu; L.mu32 = nullptr; }
 template <> void set_mu<float>(Lvl& L, const float* mu) { L.mu32 = mu; L.mu64 = nullptr; }
+template <typename T> static void set_em(Lvl& L, const T* e);
+template <> void set_em<double>(Lvl& L, const double* e) { L.em64 = e; L.em32 = nullptr; }
+template <> void set_em<float>(Lvl& L, const float* e) { L.em32 = e; L.em64 = nullptr; }
 template <typename T> static void set_nw(Lvl& L, const T* w);
 template <> void set_nw<double>(Lvl& L, const double* w) { L.nw64 = w; L.nw32 = nullptr; }
 template <> void set_nw<float>(Lvl& L, const float* w) { L.nw32 = w; L.nw64 = nullptr; }
@@ -344,6 +347,15 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
       { ProfScope ps_(GKB_KC_LAYOUT, s); k_mu_coarsen<T><<<g, dim3(32, 8), 0, s>>>(lev[lev.size() - 2].L, Lc, fmu, C.mu.p); }
       GKB_CUDA(cudaGetLastError());
       set_mu<T>(C.L, C.mu.p);
+      // FP64 levels read node / edge viscosities from a table (saves six
+      // FP64-pipe operations per link); FP32 levels are faster forming the
+      // means from the cells than streaming one more array
+      if (sizeof(T) == 8) {
+        C.em.alloc(Ops<T>::edge_table_len(Lc));
+        Ops<T>::edge_table(C.L, C.em.p, s);
+        GKB_CUDA(cudaGetLastError());
+        set_em<T>(C.L, C.em.p);
+      }
     }
     // diagonal N: the coarse weight is the mean of the 2^d children's, which
     // with gc / 2^d and the divergence-preserving transfers makes the coarse
@@ -1302,6 +1314,20 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   L32.mu32 = mu32.p;
   L32.nw64 = nullptr;
   L32.nw32 = nw32.p;
+  // node / edge viscosity table (variable viscosity, FP64 levels only: see
+  // Gmg<T>::build)
+  em64.release();
+  L64.em64 = nullptr;
+  L64.em32 = nullptr;
+  L32.em64 = nullptr;
+  L32.em32 = nullptr;
+  L64.sym = L32.sym = symgrad ? 1 : 0;
+  if (mu64.p) {
+    em64.alloc(Ops<double>::edge_table_len(L64));
+    Ops<double>::edge_table(L64, em64.p, stream);
+    L64.em64 = em64.p;
+  }
+  GKB_CUDA(cudaGetLastError());
   L32.fast = (opt.kernel_variant == 1) ? 0 : 1;
   // reduction scratch: enough partials for every launch shape used
   long long blocks = std::max<long long>(Ops<double>::face_blocks(L64), blas_blocks(L64.nvel));

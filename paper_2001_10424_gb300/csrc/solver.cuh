@@ -68,6 +68,7 @@ struct Gmg {
     Lvl L;
     DevBuf<T> x, b, r, d, mu;
     DevBuf<T> nw;               // coarsened grad-div weights (diagonal N)
+    DevBuf<T> em;               // node / edge viscosity table
     DevBuf<T> t2;               // second restriction scratch (3D coarse levels)
     DevBuf<T> sl;               // coarse slopes for the 3D prolongation
     DevBuf<T> table;            // patch class inverses (constant viscosity)
@@ -167,6 +168,7 @@ struct Solver {
   Lvl L64{}, L32{};              // finest level, FP64 / FP32 views
   DevBuf<double> mu64;
   DevBuf<float> mu32;
+  DevBuf<double> em64;           // node / edge viscosity table of the finest FP64 level
   // diagonal N (gkb_set_problem_n): N per cell (padded, FP64), the relative
   // grad-div weights n_scale / N in both precisions, sum N and sum 1/N
   DevBuf<double> nd64, nw64;

@@ -105,13 +105,41 @@ template <typename T, bool VarMu, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
                                                      T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
   __shared__ T Dt[2][BY + 1][BX + 1];
+  // variable-viscosity 2D blocks wholly in the deep interior: u, v and mu
+  // tiles with a one-cell halo (u, v faces and cells i0-1 .. i0+BX,
+  // j0-1 .. j0+BY)
+  __shared__ T Tl[VarMu ? 3 : 1][BY + 2][BX + 2];
   if (pred && !*pred) return;  // predicated launch (uniform over the grid)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k = blockIdx.z;
   const int i = i0 + tx, j = j0 + ty;
   const bool gd = L.has_gd && !wonly && x != nullptr;
   const int cur = (L.dim == 3) ? 1 : 0;
-  if (gd) {
+  const bool tile2d = VarMu && L.dim == 2 && L.fast && x != nullptr && EmPtr<T>::get(L) == nullptr && i0 >= 2 &&
+                      i0 + BX + 2 <= L.n[0] && j0 >= 2 && j0 + BY + 2 <= L.n[1];
+  if (tile2d) {
+    constexpr int TW = BX + 2, TN = (BY + 2) * (BX + 2);
+    const T* mu = MuPtr<T>::get(L);
+    for (int t = tid; t < TN; t += BX * BY) {
+      const int r = t / TW, c = t - r * TW;
+      const long long g = cix(L, i0 - 1 + c, j0 - 1 + r, 0);
+      Tl[0][r][c] = __ldg(x + L.off[0] + g);
+      Tl[1][r][c] = __ldg(x + L.off[1] + g);
+      Tl[VarMu ? 2 : 0][r][c] = __ldg(mu + g);
+    }
+    __syncthreads();
+    if (gd) {
+      // the divergences as neg_div_at forms them, from the tiles
+      const T* nw = NwPtr<T>::get(L);
+      for (int t = tid; t < (BY + 1) * (BX + 1); t += BX * BY) {
+        const int cj = t / (BX + 1), ci = t - cj * (BX + 1);
+        T dv = Tl[0][cj][ci] - Tl[0][cj][ci + 1] + Tl[1][cj][ci] - Tl[1][cj + 1][ci];
+        if (nw) dv *= __ldg(nw + cix(L, i0 - 1 + ci, j0 - 1 + cj, 0));
+        Dt[0][cj][ci] = dv;
+      }
+      __syncthreads();
+    }
+  } else if (gd) {
     const int nplanes = (L.dim == 3) ? 2 : 1;
     constexpr int TS = (BX + 1) * (BY + 1);
     for (int t = tid; t < nplanes * TS; t += BX * BY) {
@@ -134,7 +162,54 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
   const T g2 = Kc<T>::g2(L);
   const long long cb = cix(L, i, j, k);
   double dot = 0.0;
-  if (!VarMu && x != nullptr && deep_interior(L, i, j, k)) {
+  if (tile2d) {
+    // the operations and roundings of w_row_var_deep + GKB_TILE_VDEEP, with
+    // every operand from the tiles (bitwise equal to the general row)
+    const T ws = Kc<T>::ws(L);
+    const bool sym = L.sym;
+    const int c = tx + 1, r = ty + 1;
+    constexpr int MU = VarMu ? 2 : 0;
+    {  // u face (C = 0, A = 1)
+      const long long id = L.off[0] + cb;
+      const T xf = Tl[0][r][c];
+      T m0 = Tl[MU][r][c], m1 = Tl[MU][r][c - 1];
+      if (sym) { m0 += m0; m1 += m1; }
+      T acc = 0;
+      acc = fma(m0, xf - Tl[0][r][c + 1], acc);
+      acc = fma(m1, xf - Tl[0][r][c - 1], acc);
+      const T mup = (((Tl[MU][r][c - 1] + Tl[MU][r + 1][c - 1]) + Tl[MU][r][c]) + Tl[MU][r + 1][c]) / (T)4;
+      acc = fma(mup, xf - Tl[0][r + 1][c], acc);
+      if (sym) acc = fma(-mup, Tl[1][r + 1][c] - Tl[1][r + 1][c - 1], acc);
+      const T mum = (((Tl[MU][r - 1][c - 1] + Tl[MU][r][c - 1]) + Tl[MU][r - 1][c]) + Tl[MU][r][c]) / (T)4;
+      acc = fma(mum, xf - Tl[0][r - 1][c], acc);
+      if (sym) acc = fma(mum, Tl[1][r][c] - Tl[1][r][c - 1], acc);
+      T m = mul_rn(acc, ws);
+      if (gd) m = fma(g2, Dt[0][ty + 1][tx + 1] - Dt[0][ty + 1][tx], m);
+      const T val = (MODE == 0) ? b[id] - m : m;
+      if (DOT) dot += (double)xf * (double)val;
+      y[id] = val;
+    }
+    {  // v face (C = 1, A = 0)
+      const long long id = L.off[1] + cb;
+      const T xf = Tl[1][r][c];
+      T m0 = Tl[MU][r][c], m1 = Tl[MU][r - 1][c];
+      if (sym) { m0 += m0; m1 += m1; }
+      T acc = 0;
+      acc = fma(m0, xf - Tl[1][r + 1][c], acc);
+      acc = fma(m1, xf - Tl[1][r - 1][c], acc);
+      const T mup = (((Tl[MU][r - 1][c] + Tl[MU][r - 1][c + 1]) + Tl[MU][r][c]) + Tl[MU][r][c + 1]) / (T)4;
+      acc = fma(mup, xf - Tl[1][r][c + 1], acc);
+      if (sym) acc = fma(-mup, Tl[0][r][c + 1] - Tl[0][r - 1][c + 1], acc);
+      const T mum = (((Tl[MU][r - 1][c - 1] + Tl[MU][r - 1][c]) + Tl[MU][r][c - 1]) + Tl[MU][r][c]) / (T)4;
+      acc = fma(mum, xf - Tl[1][r][c - 1], acc);
+      if (sym) acc = fma(mum, Tl[0][r][c] - Tl[0][r - 1][c], acc);
+      T m = mul_rn(acc, ws);
+      if (gd) m = fma(g2, Dt[0][ty + 1][tx + 1] - Dt[0][ty][tx + 1], m);
+      const T val = (MODE == 0) ? b[id] - m : m;
+      if (DOT) dot += (double)xf * (double)val;
+      y[id] = val;
+    }
+  } else if (!VarMu && x != nullptr && deep_interior(L, i, j, k)) {
     const T wmu = Kc<T>::wmu(L);
     const T kd = (L.dim == 3) ? (T)6 : (T)4;
 #define GKB_TILE_DEEP(C, DPLUS, DMINUS)                                          \

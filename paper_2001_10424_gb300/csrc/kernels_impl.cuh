@@ -105,17 +105,16 @@ template <typename T, bool VarMu, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
                                                      T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
   __shared__ T Dt[2][BY + 1][BX + 1];
-  // variable-viscosity 2D blocks wholly in the deep interior: u, v and mu
-  // tiles with a one-cell halo (u, v faces and cells i0-1 .. i0+BX,
-  // j0-1 .. j0+BY)
-  __shared__ T Tl[VarMu ? 3 : 1][BY + 2][BX + 2];
+  // 2D blocks wholly in the deep interior: u, v (and mu) tiles with a
+  // one-cell halo (u, v faces and cells i0-1 .. i0+BX, j0-1 .. j0+BY)
+  __shared__ T Tl[VarMu ? 3 : 2][BY + 2][BX + 2];
   if (pred && !*pred) return;  // predicated launch (uniform over the grid)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k = blockIdx.z;
   const int i = i0 + tx, j = j0 + ty;
   const bool gd = L.has_gd && !wonly && x != nullptr;
   const int cur = (L.dim == 3) ? 1 : 0;
-  const bool tile2d = VarMu && L.dim == 2 && L.fast && x != nullptr && EmPtr<T>::get(L) == nullptr && i0 >= 2 &&
+  const bool tile2d = L.dim == 2 && L.fast && x != nullptr && (!VarMu || EmPtr<T>::get(L) == nullptr) && i0 >= 2 &&
                       i0 + BX + 2 <= L.n[0] && j0 >= 2 && j0 + BY + 2 <= L.n[1];
   if (tile2d) {
     constexpr int TW = BX + 2, TN = (BY + 2) * (BX + 2);
@@ -125,7 +124,7 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
       const long long g = cix(L, i0 - 1 + c, j0 - 1 + r, 0);
       Tl[0][r][c] = __ldg(x + L.off[0] + g);
       Tl[1][r][c] = __ldg(x + L.off[1] + g);
-      Tl[VarMu ? 2 : 0][r][c] = __ldg(mu + g);
+      if (VarMu) Tl[VarMu ? 2 : 0][r][c] = __ldg(mu + g);
     }
     __syncthreads();
     if (gd) {
@@ -162,7 +161,26 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
   const T g2 = Kc<T>::g2(L);
   const long long cb = cix(L, i, j, k);
   double dot = 0.0;
-  if (tile2d) {
+  if (tile2d && !VarMu) {
+    // GKB_TILE_DEEP with every operand from the tiles
+    const T wmu = Kc<T>::wmu(L);
+    const T kd = (T)4;
+    const int c = tx + 1, r = ty + 1;
+#define GKB_TILE_SMEM(C, DPLUS, DMINUS)                                          \
+    {                                                                            \
+      const long long id = L.off[C] + cb;                                        \
+      const T xf = Tl[C][r][c];                                                  \
+      T acc = Tl[C][r][c + 1] + Tl[C][r][c - 1] + Tl[C][r + 1][c] + Tl[C][r - 1][c]; \
+      T m = wmu * (kd * xf - acc);                                               \
+      if (gd) m += g2 * ((DPLUS) - (DMINUS));                                    \
+      const T val = (MODE == 0) ? b[id] - m : m;                                 \
+      if (DOT) dot += (double)xf * (double)val;                                  \
+      y[id] = val;                                                               \
+    }
+    GKB_TILE_SMEM(0, Dt[0][ty + 1][tx + 1], Dt[0][ty + 1][tx])
+    GKB_TILE_SMEM(1, Dt[0][ty + 1][tx + 1], Dt[0][ty][tx + 1])
+#undef GKB_TILE_SMEM
+  } else if (tile2d) {
     // the operations and roundings of w_row_var_deep + GKB_TILE_VDEEP, with
     // every operand from the tiles (bitwise equal to the general row)
     const T ws = Kc<T>::ws(L);

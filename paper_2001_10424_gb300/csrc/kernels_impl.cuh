@@ -25,6 +25,22 @@ __device__ __forceinline__ bool in_store(const Lvl& L, int i, int j, int k) {
   return C == 2 ? (k <= L.n[2]) : (k < L.n[2]);
 }
 
+// Position of a thread in its 32 x 8 block. 3D levels give every warp an
+// 8 x 4 patch of the block instead of a 32-wide row: on the short x rows of
+// 3D levels (a few warps per row) a row warp nearly always mixes the two
+// boundary cells of the row with interior ones, so it runs both the general
+// and the deep-interior path; an 8 x 4 warp meets a boundary 4x less often.
+__device__ __forceinline__ void block_xy(const Lvl& L, int& tx, int& ty) {
+  if (L.dim != 3) {
+    tx = threadIdx.x;
+    ty = threadIdx.y;
+    return;
+  }
+  const int t = threadIdx.y * BX + threadIdx.x, w = t >> 5, l = t & 31;
+  tx = ((w & 3) << 3) | (l & 7);
+  ty = ((w >> 2) << 2) | (l >> 3);
+}
+
 // A position whose coordinates lie in [2, n-3] on every axis: all its faces
 // are active, all their links regular and every patch containing one of its
 // faces is in the interior class. L.fast = 0 disables the fast paths (the
@@ -104,12 +120,16 @@ __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* 
 template <typename T, bool VarMu, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
                                                      T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
-  __shared__ T Dt[2][BY + 1][BX + 1];
+  // row stride 40 (>= BX + 1): conflict-free for the 8 x 4 warps of 3D levels
+  // (8r + c covers the 32 banks) as well as for 32-wide rows
+  __shared__ T Dt[2][BY + 1][40];
   // 2D blocks wholly in the deep interior: u, v (and mu) tiles with a
   // one-cell halo (u, v faces and cells i0-1 .. i0+BX, j0-1 .. j0+BY)
   __shared__ T Tl[VarMu ? 3 : 2][BY + 2][BX + 2];
   if (pred && !*pred) return;  // predicated launch (uniform over the grid)
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  int tx, ty;
+  block_xy(L, tx, ty);
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k = blockIdx.z;
   const int i = i0 + tx, j = j0 + ty;
   const bool gd = L.has_gd && !wonly && x != nullptr;
@@ -666,8 +686,10 @@ __global__ void k_patch_fold(Lvl L, T* table) {
 template <typename T, bool VarMu>
 __global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r, T* __restrict__ x,
                                                   T* __restrict__ d, T ca, T cb, int x_zero, const T* table) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+  int tx, ty;
+  block_xy(L, tx, ty);
+  const int i = blockIdx.x * BX + tx;
+  const int j = blockIdx.y * BY + ty;
   const int k = blockIdx.z;
   const int p[3] = {i, j, k};
   const long long pc = cix(L, i, j, k);

@@ -185,6 +185,7 @@ CASES = [
     ((64, 64), "grf", 100.0),
     ((16, 16, 16), "const", 100.0),
     ((24, 16, 20), "var", 10.0),
+    ((16, 16, 48), "const", 100.0),
 ]
 
 
@@ -314,7 +315,7 @@ def test_graph_and_host_loops_agree_bitwise(lib, prec):
 
 @pytest.mark.parametrize("n,prec,var", [((64, 48), FP64, 0), ((70, 66), MIXED, 0), ((14, 12, 10), FP64, 0),
                                         ((12, 14, 16), MIXED, 0), ((64, 48), FP64, 1), ((70, 66), MIXED, 1),
-                                        ((14, 12, 10), MIXED, 1)])
+                                        ((14, 12, 10), MIXED, 1), ((40, 36, 64), MIXED, 0), ((24, 20, 48), FP64, 0)])
 def test_fast_paths_match_general_paths_bitwise(lib, n, prec, var):
     """The deep-interior fast paths of the operator and smoother kernels must
     reproduce the general paths bit for bit: one V-cycle and one operator

@@ -265,7 +265,7 @@ int gkb_solve_preconditioned(gkb_handle h, const double* g, const double* r, dou
 
 /* Solve `count` independent problems in one CUDA graph launch (the batched
  * form; same method as gkb_solve for each). hs[i] is a handle set up with
- * gkb_set_problem, all on one device, with use_graph = 1 and profile = 0.
+ * gkb_set_problem or gkb_set_problem_n, all on one device, with use_graph = 1 and profile = 0.
  * g[i], r[i] (inputs) and w_out[i], p_out[i] (outputs) are problem i's
  * compact vectors, host or device memory. Every problem's whole solve, with
  * its device-side loops, is one branch of a single graph; the branches run

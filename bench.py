@@ -69,10 +69,13 @@ VARMU_SMOOTH_EXTRA = {2: 5.0, 3: 10.0}
 # ncu captures of the current kernels (cold cache), keyed by (workload, form,
 # kernel class); summarised under profiles/
 TRAFFIC = {
-    ("stokes2d", "fp64", "smooth"): 16.85e6 + 0.05e6,      # smoother_residual_stokes2d_1024_fp64_full.md
-    ("stokes2d", "fp64", "residual"): 33.71e6 + 0.04e6,
-    ("varvisc2d", "mixed", "smooth"): 203.01e6 + 47.88e6,  # varvisc_smoother_residual_2048_mixed_full.md
-    ("varvisc2d", "mixed", "residual"): 84.23e6 + 12.84e6,
+    ("stokes2d", "fp64", "smooth"): 16.86e6 + 0.05e6,      # smoother_residual_stokes2d_1024_fp64_full.md
+    ("stokes2d", "fp64", "residual"): 33.72e6 + 0.05e6,
+    ("varvisc2d", "mixed", "smooth"): 203.02e6 + 48.94e6,  # varvisc_smoother_residual_2048_mixed_full.md
+    ("varvisc2d", "mixed", "residual"): 84.25e6 + 12.06e6,
+    # smoother_stokes3d_160_mixed_full.md: 96.32 MB at 160^3 (12.21 M unknowns),
+    # scaled by the unknowns to 256^3 (50.14 M); the step's bytes are per unknown
+    ("stokes3d", "mixed", "smooth"): (50.48e6 + 45.84e6) * (3 * 255 * 256 ** 2) / (3 * 159 * 160 ** 2),
 }
 # algorithmic bytes of the captured finest-level launch per velocity unknown,
 # in elements (first Chebyshev step: r read, d and x written; residual: x, b

@@ -83,6 +83,22 @@ TRAFFIC = {
 CAPTURED_ELEMS = {"smooth": 3.0, "residual": 3.0}
 
 
+def host_cpu():
+    """Model of the host CPU and its core count (for the CPU baseline)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                if key.strip().lower() in ("model name", "cpu part") and model is None:
+                    model = val.strip()
+    except Exception:
+        pass
+    import platform
+    return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
+            "host_cores": os.cpu_count()}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -540,7 +556,7 @@ def run_reference(args, ws, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": bool(wk.batched), "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config(args, wk),
-        "cpu_baseline": {"value": val, "unit": wk.unit(), "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": wk.unit(), "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": "oracle GKB on %s, scaled x%.0f by the unknown ratio per step" % (desc, scale)},
         "e2e": {"value": val, "unit": wk.unit(), "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -699,6 +715,7 @@ def run_ours(args, ws, rank, local):
         t_cpu, scale, desc = cpu_oracle_sample(wk, args)
         cpu_step = t_cpu * scale
         cpu = {"value": len(wk.problems) / cpu_step if wk.batched else cpu_step, "unit": wk.unit(), "cores": 1,
+               "host": host_cpu(),
                "kind": "oracle",
                "sample": "oracle GKB on %s: %.1f s measured, x%.0f (unknown ratio) to the full step" % (desc, t_cpu, scale)}
     step_s = ms / 1e3

@@ -44,7 +44,9 @@ FP64_PEAK_TFLOPS = 1.258   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.
 FP32_PEAK_TFLOPS = 80.6    # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 
 # algorithmic work per velocity unknown of the launch's level, per kernel
-# class: (flops, element accesses); see DESIGN.md "Roofline accounting"
+# class: (flops, element accesses). Flops count what the definition needs
+# (one divergence per cell, the 2d-point W row, one row of each patch
+# inverse); accesses count the compulsory reads and writes of the vectors
 PER_UNIT = {
     2: {"apply": (14.0, 2.0), "residual": (14.0, 3.0), "smooth": (20.0, 4.5), "restrict": (1.5, 1.25),
         "prolong": (1.5, 2.25), "blas": (2.0, 3.0)},

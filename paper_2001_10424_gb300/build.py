@@ -2,7 +2,7 @@
 
 The translation units are compiled in parallel (one nvcc process each) and
 linked into ``paper_2001_10424_gb300/libgkb.so`` with the CUDA runtime linked
-statically, so loading the library needs nothing beyond the driver.
+statically, so loading the library needs nothing beyond the CUDA driver.
 """
 import concurrent.futures
 import os

@@ -62,3 +62,30 @@ def test_binding_rejects_non_float64():
         gk._ptr(np.zeros(4, dtype=np.float32))
     with pytest.raises(TypeError):
         gk._ptr(np.zeros((4, 4))[:, 1])
+
+
+def test_options_struct_layout_matches_the_header(libpath):
+    """gkb_default_options zeroes exactly sizeof(gkb_options) bytes before
+    filling the fields: over a larger buffer of 0xAB bytes the untouched tail
+    shows the C size, which the ctypes mirror must equal (the struct ends in
+    an int and padding, both zero)."""
+    import paper_2001_10424_gb300 as gk
+    lib = gk.load(libpath)
+    buf = (ctypes.c_ubyte * 1024)(*([0xAB] * 1024))
+    assert lib.gkb_default_options(ctypes.cast(buf, ctypes.POINTER(gk.gkb_options))) == gk.GKB_OK
+    raw = bytes(buf)
+    end = max(i for i, v in enumerate(raw) if v != 0xAB) + 1
+    c_size = (end + 7) // 8 * 8
+    assert c_size == ctypes.sizeof(gk.gkb_options)
+    o = gk.gkb_options.from_buffer_copy(raw[:ctypes.sizeof(gk.gkb_options)])
+    assert o.viscous_form == gk.GKB_VISC_LAPLACE and o.cheb_hi == 1.1 and o.fgmres_restart == 30
+
+
+def test_header_constants_match_the_binding():
+    import paper_2001_10424_gb300 as gk
+    src = open(os.path.join(ROOT, "include", "gkb.h")).read()
+    consts = dict((k, int(v)) for k, v in re.findall(r"#define\s+(GKB_[A-Z0-9_]+)\s+(-?\d+)\b", src))
+    assert "GKB_VISC_SYMGRAD" in consts and "GKB_INNER_FGMRES" in consts
+    for name, val in consts.items():
+        if hasattr(gk, name):
+            assert getattr(gk, name) == val, name

@@ -97,6 +97,9 @@ def host_cpu():
     except Exception:
         pass
     import platform
+    # Arm cores report a part number instead of a model name
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1"}
+    model = arm_parts.get(model, model)
     return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
             "host_cores": os.cpu_count()}
 

@@ -1309,16 +1309,19 @@ __global__ void __launch_bounds__(RB) k_cg_dir(long long len, T* __restrict__ p,
                                                 const CgState* cg, int first) {
   const T beta = first ? (T)0 : (T)cg->beta;
   const long long stride = (long long)gridDim.x * RB;
+  // the first direction never reads p: a non-finite p left by an earlier
+  // failed solve must not survive as 0 * NaN
   for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride)
-    p[t] = z[t] + beta * p[t];
+    p[t] = first ? z[t] : z[t] + beta * p[t];
 }
 
 // y = a x + b y (host scalars)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_axpby(long long len, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
   const long long stride = (long long)gridDim.x * RB;
+  // b = 0 overwrites y without reading it (y may hold stale non-finite values)
   for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride)
-    y[t] = a * x[t] + b * y[t];
+    y[t] = (b == (T)0) ? a * x[t] : a * x[t] + b * y[t];
 }
 
 }  // namespace gkb

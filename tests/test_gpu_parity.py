@@ -344,3 +344,30 @@ def test_fast_paths_match_general_paths_bitwise(lib, n, prec, var):
     else:
         assert np.array_equal(outs[0][0], outs[1][0])
     assert np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_non_finite_inputs_return_a_status(lib, prec):
+    """A NaN in g or an Inf in r ends the solve with a status (the norm and
+    reduction finalisers test every scalar for finiteness), not a hang or a
+    silent result."""
+    gk = lib
+    n, bc = (32, 32), (D,) * 4
+    grid, ops = oracle_problem(n, bc, 1.0, 10.0)
+    rng = np.random.default_rng(12)
+    for bad in ("g", "r"):
+        h = make_handle(gk, n, bc, 1.0, 10.0, precision=prec, maxit_inner=300)
+        try:
+            g = rng.standard_normal(grid.m)
+            r = np.zeros(grid.n_cells)
+            if bad == "g":
+                g[17] = np.nan
+            else:
+                r[40] = np.inf
+            try:
+                rc, _, _ = gpu_solve(gk, h, g, r)
+            except gk.GkbError as e:
+                rc = e.code
+            assert rc in (gk.GKB_ERR_NAN, gk.GKB_ERR_INNER_NOT_CONVERGED), rc
+        finally:
+            gk.gkb_destroy(h)

@@ -138,7 +138,9 @@ typedef struct {
                              the stream and report per-class totals in
                              gkb_stats (adds event overhead between kernels)  */
   int kernel_variant;     /* stencil kernels' deep-interior fast paths (same
-                             values bit for bit as the general paths):
+                             values bit for bit as the general paths, except
+                             the 3D constant-viscosity smoother's folded
+                             stencil, which agrees to rounding):
                              0: on in FP32, off in FP64 (measured fastest);
                              1: off everywhere; 2: on everywhere               */
   int unet_side;          /* GKB_INNER_FCG_UNET: longer side (cells) of the

@@ -109,3 +109,31 @@ def test_gkb_on_the_symmetric_form_reaches_the_dense_solution(n):
     w_ex, p_ex = dense_saddle_solve(grid, ops, g, r)
     assert m_norm(ops["M"], res["w"] - w_ex) <= 1e-9 * m_norm(ops["M"], w_ex)
     assert np.abs(res["p"] - p_ex).max() <= 1e-8 * np.abs(p_ex).max()
+
+
+def _manufactured3():
+    x, y, z = sympy.symbols("x y z")
+    mu = 1 + sympy.Rational(2, 5) * sympy.sin(2 * x + 1) * sympy.cos(y - z)
+    u = [sympy.sin(2 * x) * sympy.cos(y + 2 * z), sympy.cos(x + y) * sympy.sin(z + 1), sympy.sin(x * y + z)]
+    X = (x, y, z)
+    eps = [[(sympy.diff(u[a], X[b]) + sympy.diff(u[b], X[a])) / 2 for b in range(3)] for a in range(3)]
+    f = [-sum(sympy.diff(2 * mu * eps[a][b], X[b]) for b in range(3)) for a in range(3)]
+    lam = lambda e: sympy.lambdify((x, y, z), e, "numpy")
+    return lam(mu), [lam(e) for e in u], [lam(e) for e in f]
+
+
+def test_second_order_against_the_continuous_operator_3d():
+    """The same in 3D: all three cross couplings (edges along x, y and z)."""
+    mu_f, u_f, f_f = _manufactured3()
+    errs = []
+    for n in (16, 32):   # n = 8 is still pre-asymptotic (rate 1.4 to 16)
+        grid = mac.MacGrid((n, n, n), 1.0 / n)
+        C = grid.cell_centres()
+        W = mac.assemble(grid, mu_f(*C), 0.0, sym=True)["W"]
+        F = [grid.face_centres(c) for c in range(3)]
+        w = grid.join_velocity([u_f[c](*F[c]) for c in range(3)])
+        ref = grid.join_velocity([f_f[c](*F[c]) for c in range(3)])
+        rows = np.concatenate([_away_from_walls(grid, c, 2) for c in range(3)])
+        errs.append(np.abs((W @ w)[rows] / grid.h ** 3 - ref[rows]).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > 1.75, (errs, rate)

@@ -89,3 +89,16 @@ def test_header_constants_match_the_binding():
     for name, val in consts.items():
         if hasattr(gk, name):
             assert getattr(gk, name) == val, name
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the built library the binding raises."""
+    import subprocess
+    import sys
+    code = ("import paper_2001_10424_gb300 as gk\n"
+            "try:\n"
+            "    gk.load(%r)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', e)\n" % str(tmp_path / "libgkb.so"))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.startswith("raised"), out.stdout + out.stderr

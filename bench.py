@@ -67,16 +67,18 @@ UNET_UNITS_PER_PX = 4 + 3 / 4 + 2 / 16 + 2
 # per velocity unknown
 VARMU_SMOOTH_EXTRA = {2: 5.0, 3: 10.0}
 
-# DRAM traffic (bytes) of one finest-level launch of the dominant kernel from
-# ncu captures of the current kernels (cold cache), keyed by (workload, form,
-# kernel class); summarised under profiles/
+# DRAM traffic (bytes, read + write) of one finest-level launch of the
+# dominant kernel, from ncu captures of the current kernels (cold cache, one
+# launch each), keyed by (workload, form, kernel class)
 TRAFFIC = {
-    ("stokes2d", "fp64", "smooth"): 16.86e6 + 0.05e6,      # smoother_residual_stokes2d_1024_fp64_full.md
+    # 1024^2 FP64: first Chebyshev step (smooth) and residual of a V-cycle
+    ("stokes2d", "fp64", "smooth"): 16.86e6 + 0.05e6,
     ("stokes2d", "fp64", "residual"): 33.72e6 + 0.05e6,
-    ("varvisc2d", "mixed", "smooth"): 203.02e6 + 48.94e6,  # varvisc_smoother_residual_2048_mixed_full.md
+    # 2048^2 log-normal viscosity, mixed form
+    ("varvisc2d", "mixed", "smooth"): 203.02e6 + 48.94e6,
     ("varvisc2d", "mixed", "residual"): 84.25e6 + 12.06e6,
-    # smoother_stokes3d_160_mixed_full.md: 96.32 MB at 160^3 (12.21 M unknowns),
-    # scaled by the unknowns to 256^3 (50.14 M); the step's bytes are per unknown
+    # 3D smoother captured at 160^3 (12.21 M unknowns, 96.32 MB), scaled by
+    # the unknowns to 256^3 (50.14 M); the step's bytes are per unknown
     ("stokes3d", "mixed", "smooth"): (50.48e6 + 45.84e6) * (3 * 255 * 256 ** 2) / (3 * 159 * 160 ** 2),
 }
 # algorithmic bytes of the captured finest-level launch per velocity unknown,
@@ -430,6 +432,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     import numpy as np
     subset = list(range(min(len(wk.problems), 16))) if wk.batched else None
     B = Bound(gk, torch, wk, form, profile=1, subset=subset, autotune=args.autotune)
+    n_profiled = len(B.hs)
     ms, units, launches = {}, {}, {}
     for i, h in enumerate(B.hs):
         gk.gkb_solve(h, B.g[i], B.r[i], args.tol, args.delay, B.w[i], B.p[i], B.w0[i], B.p0[i])
@@ -458,7 +461,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
         rl["share_of_kernel_time"] = ms[top] / total_ms if total_ms else None
         rl["traffic"] = TRAFFIC.get((wk.name, form, top))
         rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
-        rl["profiled"] = "1 problem, profiled host-sequenced solve"
+        rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % n_profiled
         return rl
     varmu = any(not np.isscalar(p["mu"]) for p in wk.problems)
     per_unit_bytes = table[top][1] + (VARMU_SMOOTH_EXTRA[wk.dim] if (top == "smooth" and varmu) else 0.0)
@@ -483,8 +486,135 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
         rl["traffic_basis"] = "ncu DRAM read+write of one finest-level launch (cold cache)"
         rl["traffic_algorithmic"] = m0 * (CAPTURED_ELEMS.get(top, table[top][1]) + extra) * s
     rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
-    rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % len(ms and (subset or [0]))
+    rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % n_profiled
     return rl
+
+
+def _oracle_worker(conn, pr, inner, tol_inner):
+    """Spawned process holding the oracle's operators of one problem and its
+    inner solver (for ``inner="direct"`` the sparse LU of M, the oracle's
+    setup); each request runs Eq. (3), Algorithm 1 and Eq. (5) once."""
+    try:
+        import numpy as np
+
+        from oracle import gkb as ogkb
+        from oracle import mac
+        t0 = time.perf_counter()
+        grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+        ops = mac.assemble(grid, pr["mu"], pr["gamma"])
+        g, r = pr.get("g"), pr.get("r")
+        if "inflow" in pr:
+            g, r = mac.dirichlet_rhs(grid, ops, {0: pr["inflow"]})
+        t1 = time.perf_counter()
+        solver = ogkb.InnerSolver(ops["M"], inner, tol_inner)
+        t2 = time.perf_counter()
+        conn.send(("setup", t1 - t0, t2 - t1))
+        while True:
+            msg = conn.recv()
+            if msg[0] == "stop":
+                break
+            _, tol, delay, want = msg
+            ts = time.perf_counter()
+            res = ogkb.solve(grid, ops, g, r, tol=tol, delay=delay, w0=pr.get("w0"), p0=pr.get("p0"),
+                             solver=solver)
+            secs = time.perf_counter() - ts
+            out = {"seconds": secs, "outer_iterations": res["iterations"], "converged": bool(res["converged"]),
+                   "inner_iterations": int(sum(res["inner_iterations"]))}
+            if want:
+                out["w"], out["p"] = np.asarray(res["w"]), np.asarray(res["p"])
+            conn.send(("ok", out))
+    except Exception as e:  # reported to the parent, which raises
+        conn.send(("error", "%s: %s" % (type(e).__name__, e)))
+    finally:
+        conn.close()
+
+
+class OracleWorkers:
+    """The oracle on the workload's own problems at full size: one spawned
+    process per problem (SciPy's sparse LU and products are single-threaded,
+    so the problems run side by side, one host core each). Each process
+    assembles its operators and factorises M once (the oracle's setup, timed
+    apart like the GPU handles' setup); a step solves every problem once and
+    takes the wall time until the last one finishes."""
+
+    def __init__(self, problems, inner="direct", tol_inner=1e-12):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")   # never fork a process that holds a CUDA context
+        self.conns, self.procs = [], []
+        for pr in problems:
+            a, b = ctx.Pipe()
+            proc = ctx.Process(target=_oracle_worker, args=(b, pr, inner, tol_inner), daemon=True)
+            proc.start()
+            b.close()
+            self.conns.append(a)
+            self.procs.append(proc)
+        msgs = [self._recv(c) for c in self.conns]
+        self.assemble_s = [m[1] for m in msgs]
+        self.factor_s = [m[2] for m in msgs]
+
+    @staticmethod
+    def _recv(c):
+        msg = c.recv()
+        if msg[0] == "error":
+            raise RuntimeError("oracle worker: " + msg[1])
+        return msg
+
+    def step(self, tol, delay, want_solution=False):
+        t0 = time.perf_counter()
+        for c in self.conns:
+            c.send(("solve", tol, delay, want_solution))
+        outs = [self._recv(c)[1] for c in self.conns]
+        return time.perf_counter() - t0, outs
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+        self.conns, self.procs = [], []
+
+
+# workloads whose oracle runs at the benchmark's own size (the others run it
+# on a reduced member of the family and scale by the unknown ratio)
+FULL_SIZE_ORACLE = {"stokes2d": ("direct", 1e-12), "poiseuille": ("cg", 1e-12)}
+# tolerance of the oracle solution the GPU result is compared with
+TRUTH_TOL = 1e-13
+
+
+def oracle_full(wk, args, truth=False):
+    """Time one oracle step on the workload's problems at full size (after
+    its setup), and with ``truth`` also solve them to TRUTH_TOL; returns
+    (step seconds, per-problem outputs, truth outputs or None, setup dict)."""
+    inner, tol_inner = FULL_SIZE_ORACLE[wk.name]
+    W = OracleWorkers(wk.problems, inner, tol_inner)
+    try:
+        secs, outs = W.step(args.tol, args.delay)
+        ref = W.step(TRUTH_TOL, args.delay, want_solution=True)[1] if truth else None
+        setup = {"assemble_s": W.assemble_s, "factor_s": W.factor_s}
+    finally:
+        W.close()
+    return secs, outs, ref, setup
+
+
+def error_vs_oracle(wk, ws, ps, ref):
+    """Relative M-norm error of each GPU velocity against the oracle
+    solution, and the largest pressure difference relative to the largest
+    oracle pressure."""
+    import numpy as np
+
+    from oracle import mac
+    ev, ep = [], []
+    for pr, w, p, rf in zip(wk.problems, ws, ps, ref):
+        grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+        M = mac.assemble(grid, pr["mu"], pr["gamma"])["M"]
+        e = w - rf["w"]
+        ev.append(float(np.sqrt(max(float(e @ (M @ e)), 0.0) / float(rf["w"] @ (M @ rf["w"])))))
+        ep.append(float(np.abs(p - rf["p"]).max() / np.abs(rf["p"]).max()))
+    return {"velocity_m_norm_rel": ev, "pressure_max_rel": ep, "oracle_tol": TRUTH_TOL,
+            "oracle_inner": FULL_SIZE_ORACLE[wk.name][0], "size": "full (the timed problems)"}
 
 
 def cpu_oracle_sample(wk, args):
@@ -549,22 +679,49 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return 0
     wk = Workload(args)
-    times = []
-    for i in range(args.warmup + args.steps):
-        t, scale, desc = cpu_oracle_sample(wk, args)
-        if i >= args.warmup:
-            times.append(t * scale)
+    times, one_core, extra = [], [], {}
+    if wk.name in FULL_SIZE_ORACLE:
+        # the oracle at the benchmark's own size: setup (assembly, LU of M)
+        # once, then every step a whole solve of every problem
+        t0 = time.perf_counter()
+        inner, tol_inner = FULL_SIZE_ORACLE[wk.name]
+        W = OracleWorkers(wk.problems, inner, tol_inner)
+        extra["setup_s"] = time.perf_counter() - t0
+        try:
+            for i in range(args.warmup + args.steps):
+                t, outs = W.step(args.tol, args.delay)
+                if i >= args.warmup:
+                    times.append(t)
+                    one_core.append(sum(o["seconds"] for o in outs))
+            extra["outer_iterations"] = [o["outer_iterations"] for o in outs]
+            extra["converged"] = [o["converged"] for o in outs]
+            extra["factor_s"] = W.factor_s
+        finally:
+            W.close()
+        cores = len(wk.problems)
+        sample = ("oracle GKB (Eq. (3), Algorithm 1, Eq. (5); %s inner solves) on the workload's own %d "
+                  "problem(s) at full size, one process and host core per problem; every step a whole solve; "
+                  "assembly and factorisation are setup" % (inner, len(wk.problems)))
+    else:
+        for i in range(args.warmup + args.steps):
+            t, scale, desc = cpu_oracle_sample(wk, args)
+            if i >= args.warmup:
+                times.append(t * scale)
+        cores = 1
+        sample = "oracle GKB on %s, extrapolated: scaled x%.0f by the unknown ratio per step" % (desc, scale)
     step_s = statistics.mean(times)
     val = len(wk.problems) / step_s if wk.batched else step_s
+    cpu = {"value": val, "unit": wk.unit(), "cores": cores, "kind": "oracle", "host": host_cpu(), "sample": sample}
+    if one_core:
+        cpu["one_core_s"] = statistics.mean(one_core)
     line = {
         "impl": "reference", "metric": wk.metric(), "value": val, "unit": wk.unit(), "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": bool(wk.batched), "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config(args, wk),
-        "cpu_baseline": {"value": val, "unit": wk.unit(), "cores": 1, "kind": "oracle", "host": host_cpu(),
-                         "sample": "oracle GKB on %s, scaled x%.0f by the unknown ratio per step" % (desc, scale)},
+        "data": "synthetic", "config": config(args, wk), "cpu_baseline": cpu,
         "e2e": {"value": val, "unit": wk.unit(), "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    line.update(extra)
     print(json.dumps(line))
     return 0
 
@@ -653,6 +810,8 @@ def run_ours(args, ws, rank, local):
             e2e.append(t2 - t1)
     e2e_s = statistics.mean(e2e)
     finite = bool(all(np.isfinite(x.numpy()).all() for x in B.host[2]))
+    gpu_w = [x.numpy().copy() for x in B.host[2]]   # this run's solutions, for the oracle comparison
+    gpu_p = [x.numpy().copy() for x in B.host[3]]
     B.destroy()
     if rank != 0:
         if ws > 1:
@@ -716,13 +875,29 @@ def run_ours(args, ws, rank, local):
         else:
             forms[wk.form + "_autotuned"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=1)
     cpu = None
+    err = None
     if not args.no_cpu_baseline:
-        t_cpu, scale, desc = cpu_oracle_sample(wk, args)
-        cpu_step = t_cpu * scale
-        cpu = {"value": len(wk.problems) / cpu_step if wk.batched else cpu_step, "unit": wk.unit(), "cores": 1,
-               "host": host_cpu(),
-               "kind": "oracle",
-               "sample": "oracle GKB on %s: %.1f s measured, x%.0f (unknown ratio) to the full step" % (desc, t_cpu, scale)}
+        if wk.name in FULL_SIZE_ORACLE:
+            # the oracle on the timed problems themselves: one whole solve
+            # (timed), then a solve to TRUTH_TOL that the GPU solutions are
+            # compared with
+            secs, outs, ref, setup = oracle_full(wk, args, truth=True)
+            cpu = {"value": secs, "unit": wk.unit(), "cores": len(wk.problems), "host": host_cpu(), "kind": "oracle",
+                   "one_core_s": sum(o["seconds"] for o in outs),
+                   "outer_iterations": [o["outer_iterations"] for o in outs],
+                   "setup_s": setup,
+                   "sample": "oracle GKB (Eq. (3), Algorithm 1, Eq. (5); %s inner solves) on the timed problems at "
+                             "full size, one process and host core per problem, one whole solve; assembly and "
+                             "factorisation are setup" % FULL_SIZE_ORACLE[wk.name][0]}
+            err = error_vs_oracle(wk, gpu_w, gpu_p, ref)
+        else:
+            t_cpu, scale, desc = cpu_oracle_sample(wk, args)
+            cpu_step = t_cpu * scale
+            cpu = {"value": len(wk.problems) / cpu_step if wk.batched else cpu_step, "unit": wk.unit(), "cores": 1,
+                   "host": host_cpu(),
+                   "kind": "oracle",
+                   "sample": "oracle GKB on %s: %.1f s measured, extrapolated x%.0f (unknown ratio) to the full "
+                             "step" % (desc, t_cpu, scale)}
     step_s = ms / 1e3
     value = args.gpus * len(wk.problems) / step_s if wk.batched else step_s
     e2e_val = args.gpus * len(wk.problems) / e2e_s if wk.batched else e2e_s
@@ -739,6 +914,7 @@ def run_ours(args, ws, rank, local):
         "outer_iterations": outer if len(outer) <= 8 else {"min": min(outer), "max": max(outer), "sum": sum(outer)},
         "inner_iterations": inner if len(inner) <= 8 else {"min": min(inner), "max": max(inner), "sum": sum(inner)},
         "status": status, "setup_s": setup_s, "forms": forms, "finite_output": finite,
+        "error_vs_oracle": err,
     }
     if tuned:
         line["tuned_options"] = tuned

@@ -215,15 +215,21 @@ def gkb(M, A, N, b, solve_M, tol, delay, maxit, enclosed=False,
 
 def solve(grid, ops, g, r, tol=1e-8, delay=5, maxit=10000, inner="cg",
           tol_inner=1e-12, maxit_inner=100000, w0=None, p0=None,
-          squared=False, keep_bases=False):
+          squared=False, keep_bases=False, solver=None):
     """Solve [W A; A^T 0][w; p] = [g; r] with the AL transform and GKB.
 
-    ``ops`` comes from :func:`oracle.mac.assemble`. Returns the GKB dict with
-    ``w`` (velocity), ``p`` (pressure) and ``inner_iterations`` added.
+    ``ops`` comes from :func:`oracle.mac.assemble`. ``solver`` is an
+    :class:`InnerSolver` of ``ops["M"]`` built earlier (its factorisation is
+    then reused across solves), else one of kind ``inner`` is built here.
+    Returns the GKB dict with ``w`` (velocity), ``p`` (pressure) and
+    ``inner_iterations`` (of this solve) added.
     """
     W, A, M = ops["W"], ops["A"], ops["M"]
     N, gamma = ops.get("N", ops["n_scale"]), ops["gamma"]
-    solver = InnerSolver(M, inner, tol_inner, maxit_inner)
+    if solver is None:
+        solver = InnerSolver(M, inner, tol_inner, maxit_inner)
+    solver.iterations = []
+    solver.converged = True
     g = np.asarray(g, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64)
     if w0 is not None:

@@ -307,13 +307,18 @@ int gkb_precond(gkb_handle h, const double* r, double* z);
  * arrays live in one file-scope device array of 2 * GKB_NOALLOC_MAX_ELEMS
  * doubles (16 MiB), which every GPU that loads the library holds until the
  * process exits. A grid whose padded velocity or cell array exceeds
- * GKB_NOALLOC_MAX_ELEMS doubles (about 700 x 700 cells in 2D, 78^3 in 3D)
- * returns GKB_ERR_INVALID_ARG. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture. All calls share the array and each call clears what it
- * needs, so calls that overlap on the GPU (different streams or threads)
- * race and must be serialised by the caller. Runs on `stream` (cudaStream_t,
- * NULL: legacy stream) and returns after it has completed.
+ * GKB_NOALLOC_MAX_ELEMS doubles returns GKB_ERR_INVALID_ARG. The padded
+ * layout rounds every x row of n_x + 1 faces up to a multiple of 32
+ * elements, so the largest squares and cubes accepted are 711 x 711 cells
+ * (2 * 712 * 736 doubles) and 63^3 cells (190 * 64 * 64 doubles); a 64^3
+ * grid needs 193 * 65 * 96 = 1,204,320. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and keeps it for the
+ * process: make that first call before any stream capture, and do not use
+ * this entry point across a cudaDeviceReset. All calls share the array and
+ * each call clears what it needs, so calls that overlap on the GPU
+ * (different streams or threads) race and must be serialised by the
+ * caller. Runs on `stream` (cudaStream_t, NULL: legacy stream) and waits
+ * for that stream (cudaStreamSynchronize) before it returns.
  * Errors: INVALID_ARG (bad grid, sizes above the limit, host pointers),
  * CUDA. */
 #define GKB_NOALLOC_MAX_ELEMS 1048576

@@ -25,7 +25,9 @@ std::mutex g_noalloc_mutex;
 double* g_noalloc_addr[64] = {};
 
 // host-side address of the scratch array on the current device (looked up
-// once per device; the symbol's name on the host is not a device address)
+// once per device and process; the symbol's name on the host is not a device
+// address). A cudaDeviceReset reloads the module, possibly elsewhere, so the
+// cached address does not survive one.
 int noalloc_scratch(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
@@ -52,79 +54,6 @@ bool on_device(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-// compact ordering (include/gkb.h) <-> padded layout of one level
-struct Box {
-  int lo[3][3], ext[3][3];
-  long long base[3], m;
-};
-
-Box make_box(const gkb::Lvl& L) {
-  Box b{};
-  long long off = 0;
-  for (int c = 0; c < L.dim; ++c) {
-    for (int a = 0; a < 3; ++a) {
-      if (a >= L.dim) { b.lo[c][a] = 0; b.ext[c][a] = 1; continue; }
-      if (a == c) {
-        const int lo = L.nat[2 * a] ? 0 : 1, hi = L.nat[2 * a + 1] ? L.n[a] : L.n[a] - 1;
-        b.lo[c][a] = lo;
-        b.ext[c][a] = hi - lo + 1;
-      } else {
-        b.lo[c][a] = 0;
-        b.ext[c][a] = L.n[a];
-      }
-    }
-    b.base[c] = off;
-    off += (long long)b.ext[c][0] * b.ext[c][1] * b.ext[c][2];
-  }
-  b.m = off;
-  return b;
-}
-
-__device__ long long box_padded(const gkb::Lvl& L, const Box& b, long long t) {
-  int c = 0;
-  if (L.dim == 3 && t >= b.base[2]) c = 2;
-  else if (t >= b.base[1]) c = 1;
-  const long long l = t - b.base[c];
-  const long long row = l / b.ext[c][0];
-  const int i = (int)(l - row * b.ext[c][0]) + b.lo[c][0];
-  const long long pl = row / b.ext[c][1];
-  const int j = (int)(row - pl * b.ext[c][1]) + b.lo[c][1];
-  const int k = (int)pl + b.lo[c][2];
-  return L.off[c] + gkb::cix(L, i, j, k);
-}
-
-__device__ long long cell_padded(const gkb::Lvl& L, long long t) {
-  const long long row = t / L.n[0];
-  const int i = (int)(t - row * L.n[0]);
-  const int k = (int)(row / L.n[1]);
-  const int j = (int)(row - (long long)k * L.n[1]);
-  return gkb::cix(L, i, j, k);
-}
-
-// dir 0: compact src -> padded dst; dir 1: padded src -> compact dst
-__global__ void k_na_vel(gkb::Lvl L, Box b, int dir, const double* __restrict__ src, double* __restrict__ dst) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < b.m; t += (long long)gridDim.x * blockDim.x) {
-    const long long p = box_padded(L, b, t);
-    if (dir == 0) dst[p] = src[t];
-    else dst[t] = src[p];
-  }
-}
-
-__global__ void k_na_cell(gkb::Lvl L, int dir, const double* __restrict__ src, double* __restrict__ dst) {
-  const long long n = (long long)L.n[0] * L.n[1] * L.n[2];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const long long p = cell_padded(L, t);
-    if (dir == 0) dst[p] = src[t];
-    else dst[t] = src[p];
-  }
-}
-
-unsigned blocks_for(long long n) {
-  long long b = (n + 255) / 256;
-  if (b > 4096) b = 4096;
-  return (unsigned)(b < 1 ? 1 : b);
 }
 
 }  // namespace
@@ -157,8 +86,6 @@ extern "C" int gkb_apply_noalloc(const gkb_grid* grid, double mu0, double gamma,
   double* in = scratch;
   double* out = scratch + (size_t)GKB_NOALLOC_MAX_ELEMS;
   cudaStream_t s = (cudaStream_t)stream;
-  const Box b = make_box(L);
-  const long long ncells = (long long)n3[0] * n3[1] * n3[2];
   const bool in_cells = (op == GKB_OP_A), out_cells = (op == GKB_OP_AT);
   // the previous call's contents remain in the array: clear the input's
   // padding, which the operator kernels read as zero
@@ -166,16 +93,16 @@ extern "C" int gkb_apply_noalloc(const gkb_grid* grid, double mu0, double gamma,
     (void)cudaGetLastError();
     return GKB_ERR_CUDA;
   }
-  if (in_cells) k_na_cell<<<blocks_for(ncells), 256, 0, s>>>(L, 0, x, in);
-  else k_na_vel<<<blocks_for(b.m), 256, 0, s>>>(L, b, 0, x, in);
+  if (in_cells) gkb::pack_cells(L, x, in, s);
+  else gkb::pack_velocity(L, x, in, s);
   switch (op) {
     case GKB_OP_W: gkb::Ops<double>::apply(L, 0, in, out, s); break;
     case GKB_OP_M: gkb::Ops<double>::apply(L, 1, in, out, s); break;
     case GKB_OP_A: gkb::Ops<double>::grad(L, in, out, 1.0, s); break;
     default: gkb::Ops<double>::negdiv(L, in, out, 1.0, s); break;
   }
-  if (out_cells) k_na_cell<<<blocks_for(ncells), 256, 0, s>>>(L, 1, out, y);
-  else k_na_vel<<<blocks_for(b.m), 256, 0, s>>>(L, b, 1, out, y);
+  if (out_cells) gkb::unpack_cells(L, out, y, s);
+  else gkb::unpack_velocity(L, out, y, s);
   cudaError_t e = cudaStreamSynchronize(s);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {

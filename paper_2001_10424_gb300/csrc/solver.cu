@@ -1194,6 +1194,23 @@ static unsigned lin_blocks(long long n) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// compact ordering of include/gkb.h <-> padded layout of level L (the
+// layout kernels above, for callers outside this file)
+void pack_velocity(const Lvl& L, const double* compact, double* padded, cudaStream_t s) {
+  const Compact c = make_compact(L);
+  k_pack_vel<double><<<lin_blocks(c.m), 256, 0, s>>>(L, c, compact, padded);
+}
+void unpack_velocity(const Lvl& L, const double* padded, double* compact, cudaStream_t s) {
+  const Compact c = make_compact(L);
+  k_unpack_vel<<<lin_blocks(c.m), 256, 0, s>>>(L, c, padded, compact);
+}
+void pack_cells(const Lvl& L, const double* compact, double* padded, cudaStream_t s) {
+  k_pack_cell<double><<<lin_blocks((long long)L.n[0] * L.n[1] * L.n[2]), 256, 0, s>>>(L, compact, padded);
+}
+void unpack_cells(const Lvl& L, const double* padded, double* compact, cudaStream_t s) {
+  k_unpack_cell<<<lin_blocks((long long)L.n[0] * L.n[1] * L.n[2]), 256, 0, s>>>(L, padded, compact, 0.0);
+}
+
 Solver::~Solver() {
   sgraph.destroy();
   if (cg_host) cudaFreeHost(cg_host);

@@ -61,6 +61,13 @@ struct UnetAct;
 // Geometry of one level (both precisions share it; mu pointers differ).
 Lvl make_level(int dim, const int n[3], double h, const int nat[6], double gc);
 
+// Compact ordering of include/gkb.h <-> padded layout of level L, on stream
+// s. Packing writes only the active entries (the caller clears the rest).
+void pack_velocity(const Lvl& L, const double* compact, double* padded, cudaStream_t s);
+void unpack_velocity(const Lvl& L, const double* padded, double* compact, cudaStream_t s);
+void pack_cells(const Lvl& L, const double* compact, double* padded, cudaStream_t s);
+void unpack_cells(const Lvl& L, const double* padded, double* compact, cudaStream_t s);
+
 // Multigrid hierarchy in precision T for an all-Dirichlet grid.
 template <typename T>
 struct Gmg {

@@ -52,6 +52,48 @@ def test_noalloc_matches_handle_apply(lib, n, bc, mu0, gamma):
         gk.gkb_destroy(h)
 
 
+def test_noalloc_calls_allocate_no_device_memory(lib):
+    """The property the entry point exists for: after a first call (which
+    looks up the static array's address), further calls leave the device's
+    free memory unchanged."""
+    import torch
+    gk = lib
+    n = (96, 80)
+    grid = gk.make_grid(n, 1.0 / n[0])
+    m = 95 * 80 + 96 * 79
+    s = torch.cuda.current_stream().cuda_stream
+    x = torch.randn(m, dtype=torch.float64, device="cuda")
+    y = torch.empty(m, dtype=torch.float64, device="cuda")
+    assert gk.gkb_apply_noalloc(grid, 1.0, 10.0, 0.0, gk.GKB_OP_M, x, y, s) == gk.GKB_OK
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(20):
+        for op in (gk.GKB_OP_W, gk.GKB_OP_M):
+            assert gk.gkb_apply_noalloc(grid, 1.0, 10.0, 0.0, op, x, y, s) == gk.GKB_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+@pytest.mark.parametrize("n,ok", [((711, 711), True), ((712, 712), False), ((63, 63, 63), True),
+                                  ((64, 64, 64), False)])
+def test_noalloc_size_limit_at_the_boundary(lib, n, ok):
+    """The largest square and cube the static array holds (its padded rows
+    round n + 1 faces up to a multiple of 32) and the next size, refused."""
+    import torch
+    gk = lib
+    d = len(n)
+    m = d * (n[0] - 1) * n[0] ** (d - 1)
+    grid = gk.make_grid(n, 1.0 / n[0])
+    x = torch.randn(m, dtype=torch.float64, device="cuda")
+    y = torch.zeros(m, dtype=torch.float64, device="cuda")
+    rc = gk.gkb_apply_noalloc(grid, 1.0, 10.0, 0.0, gk.GKB_OP_M, x, y, torch.cuda.current_stream().cuda_stream)
+    if ok:
+        assert rc == gk.GKB_OK
+        assert torch.isfinite(y).all() and float(y.abs().max()) > 0
+    else:
+        assert rc == gk.GKB_ERR_INVALID_ARG
+
+
 def test_noalloc_rejects_grids_above_the_limit(lib):
     import torch
     gk = lib

@@ -44,15 +44,35 @@ FP64_PEAK_TFLOPS = 1.258   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (probe: 1.
 FP32_PEAK_TFLOPS = 80.6    # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz
 
 # algorithmic work per velocity unknown of the launch's level, per kernel
-# class: (flops, element accesses). Flops count what the definition needs
-# (one divergence per cell, the 2d-point W row, one row of each patch
-# inverse); accesses count the compulsory reads and writes of the vectors
+# class: (flops, element accesses). Flops count the arithmetic of the
+# definitions with constant viscosity: a W row is 2d+2 flops (2d-1 additions
+# of the neighbours, 2d x_f - sum as one fused multiply-add, the viscosity
+# scale); the divergence of a cell (2d-1 additions) is shared by its d
+# faces; the grad-div term adds 3 per face (difference of the two cell
+# divergences, scale, sum); the residual subtracts from b (1 more). The
+# smoother's count depends on the Chebyshev step (see SMOOTH_FLOPS).
+# Accesses count the compulsory reads and writes of the vectors.
 PER_UNIT = {
-    2: {"apply": (14.0, 2.0), "residual": (14.0, 3.0), "smooth": (20.0, 4.5), "restrict": (1.5, 1.25),
+    2: {"apply": (10.5, 2.0), "residual": (11.5, 3.0), "smooth": (None, 4.5), "restrict": (1.5, 1.25),
         "prolong": (1.5, 2.25), "blas": (2.0, 3.0)},
-    3: {"apply": (19.0, 2.0), "residual": (19.0, 3.0), "smooth": (35.0, 4.5), "restrict": (1.5, 1.125),
-        "prolong": (1.5, 2.125), "blas": (2.0, 3.0)},
+    3: {"apply": (8.0 + 5.0 / 3.0 + 3.0, 2.0), "residual": (9.0 + 5.0 / 3.0 + 3.0, 3.0), "smooth": (None, 4.5),
+        "restrict": (1.5, 1.125), "prolong": (1.5, 2.125), "blas": (2.0, 3.0)},
 }
+
+
+def smooth_flops(dim, degree):
+    """Flops per velocity unknown of one Chebyshev step of the patch
+    smoother, averaged over the 2 * degree steps of a V-cycle's pre- and
+    post-smoothing. A face lies in 2 patches (2D vertex patches) or 4 (3D
+    edge patches); its share of each is one row of the 4 x 4 patch inverse
+    (4 products, 3 sums), and the patches' contributions are summed:
+    z = 15 (2D) / 31 (3D) flops. The first pre-smoothing step (x = 0, no
+    previous direction) adds ca * z; the first post-smoothing step also adds
+    x + d; every other step forms d = ca z + cb d and x + d (4 more)."""
+    z = 15.0 if dim == 2 else 31.0
+    steps = [z + 1.0, z + 2.0] + [z + 4.0] * (2 * degree - 2)
+    return sum(steps) / len(steps)
+
 
 # U-Net forward: flops per pixel of the image (9 convolutions: 4 at full,
 # 3 at half, 2 at quarter resolution) and unit count per pixel of one
@@ -330,10 +350,12 @@ class Workload:
         return "solves/s" if self.batched else "s"
 
 
-def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, inner=None, variant=None):
+def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, inner=None, variant=None,
+                mixed_rtol=None, maxit=1000):
     """variant: None, or a combination of "ndiag" (N = h^d / mu, the
     viscosity-weighted pressure mass matrix) and "symgrad" (the
-    symmetric-gradient viscous operator)."""
+    symmetric-gradient viscous operator). mixed_rtol: the mixed form's
+    replacement trigger (0: the ablation without FP64 replacement)."""
     opt = gk.gkb_default_options()
     opt.autotune = autotune
     if wk.kernel_variant is not None:
@@ -341,7 +363,9 @@ def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, in
     opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
     opt.inner = wk.inner
     opt.tol_inner = wk.tol_inner
-    opt.maxit = 1000
+    opt.maxit = maxit
+    if mixed_rtol is not None:
+        opt.mixed_rtol = mixed_rtol
     opt.maxit_inner = 20000 if wk.inner == 0 else 5000
     opt.profile = profile
     opt.stream = torch.cuda.current_stream().cuda_stream
@@ -373,13 +397,14 @@ class Bound:
     """Handles plus device/host buffers of a workload, and its step."""
 
     def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0, inner=None,
-                 variant=None):
+                 variant=None, mixed_rtol=None, maxit=1000):
         import numpy as np
         self.gk, self.torch, self.wk = gk, torch, wk
         probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
         self.probs = probs
         lf = wk.learned if learned == "default" else learned
-        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner, variant) for pr in probs]
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner, variant, mixed_rtol, maxit)
+                   for pr in probs]
         self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
         for h, pr in zip(self.hs, probs):
             m, n = gk.gkb_layout(h)
@@ -434,6 +459,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     B = Bound(gk, torch, wk, form, profile=1, subset=subset, autotune=args.autotune)
     n_profiled = len(B.hs)
     ms, units, launches = {}, {}, {}
+    smooth_fl = 0.0    # smoother flops of all profiled handles (degree per handle)
     for i, h in enumerate(B.hs):
         gk.gkb_solve(h, B.g[i], B.r[i], args.tol, args.delay, B.w[i], B.p[i], B.w0[i], B.p0[i])
         st = gk.gkb_stats(h)
@@ -441,6 +467,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
             ms[k] = ms.get(k, 0.0) + st["kernel_ms"][k]
             units[k] = units.get(k, 0) + st["kernel_units"][k]
             launches[k] = launches.get(k, 0) + st["kernel_launches"][k]
+        smooth_fl += st["kernel_units"]["smooth"] * smooth_flops(wk.dim, gk.gkb_get_options(h).smoother_degree)
     B.destroy()
     table = PER_UNIT[wk.dim]
     cand = {k: v for k, v in ms.items() if k in table or (k == "unet" and wk.learned)}
@@ -465,7 +492,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
         return rl
     varmu = any(not np.isscalar(p["mu"]) for p in wk.problems)
     per_unit_bytes = table[top][1] + (VARMU_SMOOTH_EXTRA[wk.dim] if (top == "smooth" and varmu) else 0.0)
-    flops = units[top] * table[top][0]
+    flops = smooth_fl if top == "smooth" else units[top] * table[top][0]
     byts = units[top] * per_unit_bytes * s
     alu_peak = (FP64_PEAK_TFLOPS if form == "fp64" else FP32_PEAK_TFLOPS) * 1e12
     if form == "fp64" and flops / alu_peak > byts / (hbm_peak * 1e9):
@@ -487,6 +514,7 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
         rl["traffic_algorithmic"] = m0 * (CAPTURED_ELEMS.get(top, table[top][1]) + extra) * s
     rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
     rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % n_profiled
+    rl["flops_per_unit"] = flops / max(1, units[top])
     return rl
 
 
@@ -820,10 +848,14 @@ def run_ours(args, ws, rank, local):
     rl = roofline(gk, torch, wk, args, wk.form, hbm_peak, peak_kind)
     forms = {}
 
-    def time_form(form, learned, autotune=None, inner=None, variant=None):
+    keep = wk.name in FULL_SIZE_ORACLE and not args.no_cpu_baseline
+    form_solutions = {}
+
+    def time_form(form, learned, autotune=None, inner=None, variant=None, mixed_rtol=None, maxit=1000, name=None):
         autotune = args.autotune if autotune is None else autotune
         t_setup = time.perf_counter()
-        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune, inner=inner, variant=variant)
+        B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune, inner=inner, variant=variant,
+                   mixed_rtol=mixed_rtol, maxit=maxit)
         t_setup = time.perf_counter() - t_setup
         for _ in range(2):
             B2.step(args)
@@ -840,7 +872,11 @@ def run_ours(args, ws, rank, local):
         st2 = B2.stats()
         out = {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
                "inner_iterations": [s["inner_iterations"] for s in st2],
-               "inner_fallbacks": [s["inner_fallbacks"] for s in st2]}
+               "inner_fallbacks": [s["inner_fallbacks"] for s in st2],
+               "status": [s["status"] for s in st2]}
+        if keep and name:
+            torch.cuda.synchronize()
+            form_solutions[name] = ([x.cpu().numpy() for x in B2.w], [x.cpu().numpy() for x in B2.p])
         if autotune:
             out["setup_s_with_tuning"] = t_setup
             out["tuned"] = []
@@ -866,12 +902,18 @@ def run_ours(args, ws, rank, local):
             forms["gmg_pcg_" + wk.form + "_symgrad_ndiag"] = time_form(wk.form, None, variant="symgrad+ndiag")
         else:
             other = "mixed" if wk.form == "fp64" else "fp64"
-            forms[other] = time_form(other, None)
+            forms[other] = time_form(other, None, name=other)
             forms[wk.form] = head
+            # ablation: FP32 inner solves without the FP64 residual
+            # replacement (their error floor; the outer loop may not reach tau)
+            forms["mixed_no_replacement"] = time_form("mixed", None, mixed_rtol=0.0, maxit=100,
+                                                      name="mixed_no_replacement")
             if wk.dim == 2:   # the paper's other inner Krylov method (host-sequenced)
-                forms["fgmres_fp64"] = time_form("fp64", None, autotune=0, inner=gk.GKB_INNER_FGMRES)
+                forms["fgmres_fp64"] = time_form("fp64", None, autotune=0, inner=gk.GKB_INNER_FGMRES,
+                                                 name="fgmres_fp64")
         if args.autotune:
-            forms[wk.form + "_default_options"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=0)
+            forms[wk.form + "_default_options"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=0,
+                                                            name=wk.form + "_default_options")
         else:
             forms[wk.form + "_autotuned"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=1)
     cpu = None
@@ -890,6 +932,10 @@ def run_ours(args, ws, rank, local):
                              "full size, one process and host core per problem, one whole solve; assembly and "
                              "factorisation are setup" % FULL_SIZE_ORACLE[wk.name][0]}
             err = error_vs_oracle(wk, gpu_w, gpu_p, ref)
+            for nm, (fw, fp) in form_solutions.items():
+                e2 = error_vs_oracle(wk, fw, fp, ref)
+                forms[nm]["error_vs_oracle"] = {"velocity_m_norm_rel": e2["velocity_m_norm_rel"],
+                                                "pressure_max_rel": e2["pressure_max_rel"]}
         else:
             t_cpu, scale, desc = cpu_oracle_sample(wk, args)
             cpu_step = t_cpu * scale

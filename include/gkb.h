@@ -129,7 +129,13 @@ typedef struct {
                              (coarse_max / 2, at least 4, in 3D)              */
   double mixed_rtol;      /* GKB_PREC_MIXED: the FP32 CG recomputes its
                              residual in FP64 whenever it has dropped by this
-                             factor since the last recomputation               */
+                             factor since the last recomputation, and checks
+                             convergence on that FP64 residual; 0: ablation
+                             without replacement (the FP32 recursion's own
+                             convergence claim ends each inner solve, and the
+                             FP32 iterate is converted to FP64 once), for
+                             measuring the error floor that the replacement
+                             removes                                           */
   int use_graph;          /* 1: run every inner CG solve as one CUDA graph whose
                              while loop is a device-side conditional node;
                              0: host-sequenced loop (always used when

@@ -88,7 +88,7 @@ int gkb_create(gkb_handle* out, const gkb_options* opt) {
     return GKB_ERR_INVALID_ARG;
   if (!(opt->tol_inner > 0) || opt->maxit < 0 || opt->maxit > 100000000 || opt->maxit_inner < 1 ||
       opt->smoother_degree < 1 || opt->smoother_degree > 16 || opt->coarse_max < 4 ||
-      !(opt->mixed_rtol > 0 && opt->mixed_rtol < 1) || opt->kernel_variant < 0 || opt->kernel_variant > 2)
+      !(opt->mixed_rtol >= 0 && opt->mixed_rtol < 1) || opt->kernel_variant < 0 || opt->kernel_variant > 2)
     return GKB_ERR_INVALID_ARG;
   gkb_ctx* h = new (std::nothrow) gkb_ctx();
   if (!h) return GKB_ERR_OOM;

@@ -1705,7 +1705,7 @@ int Solver::mixed_solve(const double* f, double* x64, int* iters) {
   CgState h{};
   h.tol2 = opt.tol_inner * opt.tol_inner;
   h.maxit = opt.maxit_inner;
-  h.delta2 = opt.mixed_rtol * opt.mixed_rtol;
+  h.delta2 = opt.mixed_rtol > 0 ? opt.mixed_rtol * opt.mixed_rtol : -1.0;
   h.rho2 = c.flex ? c.rho2 : 0.0;
   GKB_CUDA(cudaMemcpyAsync(cg_dev, &h, sizeof(CgState), cudaMemcpyHostToDevice, s));
   GKB_CUDA(cudaMemsetAsync(x64, 0, len * sizeof(double), s));
@@ -1789,7 +1789,7 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
     Cg<float>& c = cg32;
     float* zp = c.pre ? c.z.p : c.r.p;
     const int* upd = &cg_dev->update;
-    const double delta2 = opt.mixed_rtol * opt.mixed_rtol;
+    const double delta2 = opt.mixed_rtol > 0 ? opt.mixed_rtol * opt.mixed_rtol : -1.0;
     capture_loop(
         s, sb, 3,
         [&](cudaStream_t st, cudaGraphConditionalHandle h) {

@@ -47,7 +47,7 @@ struct CgState {
   int solves;
   int update;       // mixed form: 1 when an FP64 residual recomputation is due
   double rmax2;     // mixed form: ||r||^2 at the last FP64 recomputation
-  double delta2;    // mixed form: trigger ratio squared
+  double delta2;    // mixed form: trigger ratio squared (< 0: no replacement)
   double rr64;      // mixed form: last true FP64 ||r||^2
   int graph_iters;  // loop-body executions of the graph form (device counted)
   int fallback;     // flexible form: 1 once the solve has switched to plain GMG-PCG
@@ -111,6 +111,14 @@ __device__ __forceinline__ void finalize(int op, const double* s, void* st) {
       c->it += 1;
       c->total_it += 1;
       if (!isfinite(s[0])) { cg_fail(c, ST_NAN); break; }
+      if (c->delta2 < 0.0) {
+        // ablation without FP64 residual replacement: the FP32 recursion's
+        // own convergence claim ends the solve
+        c->update = 0;
+        if (s[0] <= c->tol2 * c->ff) c->done = 1;
+        else if (c->it >= c->maxit) cg_fail(c, ST_INNER_NOT_CONVERGED);
+        break;
+      }
       c->update = (s[0] <= c->delta2 * c->rmax2 || s[0] <= c->tol2 * c->ff || c->it >= c->maxit) ? 1 : 0;
     } break;
     case FIN_MX_RR64: {

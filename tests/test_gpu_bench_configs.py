@@ -55,7 +55,7 @@ def bench_args(**kw):
     return args
 
 
-def run_bench_form(gk, args, autotune=1, learned="default"):
+def run_bench_form(gk, args, autotune=1, learned="default", mixed_rtol=None, maxit=1000):
     """One step of the workload as bench.py times it; returns the solutions,
     statuses and statistics of its problems."""
     import torch
@@ -63,7 +63,8 @@ def run_bench_form(gk, args, autotune=1, learned="default"):
     if wk.learned:
         wk.net, _ = bench.train_network(gk, torch, wk, args)
     try:
-        B = bench.Bound(gk, torch, wk, wk.form, autotune=autotune, learned=learned)
+        B = bench.Bound(gk, torch, wk, wk.form, autotune=autotune, learned=learned, mixed_rtol=mixed_rtol,
+                        maxit=maxit)
         try:
             status = B.step(args)
             torch.cuda.synchronize()
@@ -116,6 +117,33 @@ def test_precision_form_3d_64_within_1e8_of_the_oracle(lib):
     grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
     ops = mac.assemble(grid, 1.0, pr["gamma"])
     check_against(ops, ws[0], ps[0], ref["w"], ref["p"], "64^3 mixed")
+    # the same form without the FP64 residual replacement misses the bound
+    wk2, ws2, ps2, status2, stats2 = run_bench_form(lib, args, autotune=0, mixed_rtol=0.0, maxit=100)
+    e_abl = energy_rel(ops["M"], ws2[0], ref["w"])
+    print("64^3 mixed without replacement: %.3e (%d outer, status %d)" % (e_abl, stats2[0]["outer_iterations"],
+                                                                         status2[0]))
+    assert e_abl > 1e-8
+
+
+def test_fp32_inner_without_replacement_has_an_error_floor(lib):
+    """The ablation of the precision form's FP64 residual replacement: the
+    same mixed form with FP32 inner solves that end on the FP32 recursion's
+    own convergence claim. Without the replacement the velocity misses the
+    1e-8 bound (FP32 rounding of the inner solutions, unit roundoff 6e-8,
+    is not corrected); with it the bound holds on the same problem."""
+    args = bench_args(n=256, gammas=[100.0], form="mixed")
+    wk, ws, ps, status, stats = run_bench_form(lib, args, autotune=0)
+    wk2, ws2, ps2, status2, stats2 = run_bench_form(lib, args, autotune=0, mixed_rtol=0.0, maxit=100)
+    pr = wk.problems[0]
+    grid = mac.MacGrid(pr["n"], pr["h"], pr["bc"])
+    ops = mac.assemble(grid, 1.0, pr["gamma"])
+    ref = ogkb.solve(grid, ops, pr["g"], pr["r"], tol=1e-13, delay=5, inner="direct")
+    e_rep = energy_rel(ops["M"], ws[0], ref["w"])
+    e_abl = energy_rel(ops["M"], ws2[0], ref["w"])
+    print("256^2 mixed: with replacement %.3e (%d outer), without %.3e (%d outer, status %d)"
+          % (e_rep, stats[0]["outer_iterations"], e_abl, stats2[0]["outer_iterations"], status2[0]))
+    assert status[0] == 0 and e_rep <= 1e-8
+    assert e_abl > 1e-8 and e_abl > 10 * e_rep
 
 
 @pytest.mark.parametrize("form", ["replace", "composite"])

@@ -55,6 +55,21 @@ struct Lvl {
   float mu0f, wscalef, ascalef, g2f, wmuf;
 };
 
+// Coordinates of a thread block in the grid of one problem's launch and that
+// grid's extent. A kernel launched for one problem takes its own blockIdx /
+// gridDim; a lock-step batched launch (several problems in one grid) maps its
+// blocks to (problem, block of that problem's grid) and hands the body the
+// coordinates the problem's own launch would have had.
+struct Blk {
+  unsigned x, y, z, nx, ny, nz;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ Blk native_blk() {
+  return Blk{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
+}
+#endif
+
 inline void finish_level(Lvl& L) {
   L.has_gd = (L.gc != 0.0) ? 1 : 0;
   L.g2 = L.gc * L.ascale * L.ascale;

@@ -118,7 +118,7 @@ __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* 
 //   mode 0: y = b - M x   (x null: y = b)
 //   mode 1: y = M x       (wonly: y = W x), DOT: reduce x.y
 template <typename T, bool VarMu, int MODE, bool DOT>
-__global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
+__device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
                                                      T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
   // row stride 40 (>= BX + 1): conflict-free for the 8 x 4 warps of 3D levels
   // (8r + c covers the 32 banks) as well as for 32-wide rows
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
   const int tid = threadIdx.y * BX + threadIdx.x;
   int tx, ty;
   block_xy(L, tx, ty);
-  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY, k = blockIdx.z;
+  const int i0 = B.x * BX, j0 = B.y * BY, k = B.z;
   const int i = i0 + tx, j = j0 + ty;
   const bool gd = L.has_gd && !wonly && x != nullptr;
   const int cur = (L.dim == 3) ? 1 : 0;
@@ -313,8 +313,14 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
   }
   if (DOT) {
     double v[1] = {dot};
-    grid_reduce<1>(v, red, fin, st);
+    grid_reduce<1>(v, red, fin, st, B);
   }
+}
+
+template <typename T, bool VarMu, int MODE, bool DOT>
+__global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
+                                                     T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
+  mac_tile_body<T, VarMu, MODE, DOT>(native_blk(), L, wonly, x, b, y, red, fin, st, pred);
 }
 
 // ---------------------------------------------------------------------------
@@ -684,13 +690,13 @@ __global__ void k_patch_fold(Lvl L, T* table) {
 // One Chebyshev step of the patch-preconditioned smoother:
 //   z = C r;  d = ca * z + cb * d;  x = (x_zero ? 0 : x) + d
 template <typename T, bool VarMu>
-__global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r, T* __restrict__ x,
+__device__ __forceinline__ void cheb_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
                                                   T* __restrict__ d, T ca, T cb, int x_zero, const T* table) {
   int tx, ty;
   block_xy(L, tx, ty);
-  const int i = blockIdx.x * BX + tx;
-  const int j = blockIdx.y * BY + ty;
-  const int k = blockIdx.z;
+  const int i = B.x * BX + tx;
+  const int j = B.y * BY + ty;
+  const int k = B.z;
   const int p[3] = {i, j, k};
   const long long pc = cix(L, i, j, k);
   if (!VarMu && table != nullptr && deep_interior(L, i, j, k)) {
@@ -721,6 +727,12 @@ __global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r,
   GKB_CHEB_COMP(1)
   if (L.dim == 3) { GKB_CHEB_COMP(2) }
 #undef GKB_CHEB_COMP
+}
+
+template <typename T, bool VarMu>
+__global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r, T* __restrict__ x,
+                                                  T* __restrict__ d, T ca, T cb, int x_zero, const T* table) {
+  cheb_body<T, VarMu>(native_blk(), L, r, x, d, ca, cb, x_zero, table);
 }
 
 // z = C r (power iteration, tests)
@@ -843,10 +855,10 @@ __global__ void k_patch_vtab(Lvl L, T* __restrict__ vtab) {
 
 // y = s * A p  (faces from cells): y_f = s * ascale * (p_plus - p_minus)
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_grad(Lvl L, const T* __restrict__ pc, T* __restrict__ y, T s) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
-  const int k = blockIdx.z;
+__device__ __forceinline__ void grad_body(const Blk& B, const Lvl& L, const T* __restrict__ pc, T* __restrict__ y, T s) {
+  const int i = B.x * BX + threadIdx.x;
+  const int j = B.y * BY + threadIdx.y;
+  const int k = B.z;
   const T sc = s * Kc<T>::as(L);
 #define GKB_GRAD_COMP(C, DI, DJ, DK)                                             \
   if (in_store<C>(L, i, j, k)) {                                                 \
@@ -863,6 +875,11 @@ __global__ void __launch_bounds__(BX* BY) k_grad(Lvl L, const T* __restrict__ pc
   GKB_GRAD_COMP(1, 0, 1, 0)
   if (L.dim == 3) { GKB_GRAD_COMP(2, 0, 0, 1) }
 #undef GKB_GRAD_COMP
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_grad(Lvl L, const T* __restrict__ pc, T* __restrict__ y, T s) {
+  grad_body<T>(native_blk(), L, pc, y, s);
 }
 
 // y = s * A^T x  (cells from faces) = s * ascale * negdiv(x); padding untouched
@@ -942,13 +959,18 @@ __device__ __forceinline__ T prolong_flux_val(const Lvl& Lc, const T* xc, int pc
 
 // xf += P xc (2D)
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_prolong_flux2d(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
-  const int i = blockIdx.x * BX + threadIdx.x;
-  const int j = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void prolong_flux2d_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+  const int i = B.x * BX + threadIdx.x;
+  const int j = B.y * BY + threadIdx.y;
   if (in_store<0>(Lf, i, j, 0) && face_active<0>(Lf, i, j, 0))
     xf[Lf.off[0] + cix(Lf, i, j, 0)] += prolong_flux_val<T, 0>(Lc, xc, i, j);
   if (in_store<1>(Lf, i, j, 0) && face_active<1>(Lf, i, j, 0))
     xf[Lf.off[1] + cix(Lf, i, j, 0)] += prolong_flux_val<T, 1>(Lc, xc, j, i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_prolong_flux2d(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+  prolong_flux2d_body<T>(native_blk(), Lf, Lc, xc, xf);
 }
 
 template <typename T, int C>
@@ -983,10 +1005,10 @@ __device__ __forceinline__ void restrict_flux_gather(const Lvl& Lf, const T* rf,
 
 // pass a: bc = rU, tmp = rD  (launched over the coarse face grid)
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_a(Lvl Lf, Lvl Lc, const T* __restrict__ rf,
+__device__ __forceinline__ void restrict_flux2d_a_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* __restrict__ rf,
                                                                T* __restrict__ bc, T* __restrict__ tmp) {
-  const int I = blockIdx.x * BX + threadIdx.x;
-  const int J = blockIdx.y * BY + threadIdx.y;
+  const int I = B.x * BX + threadIdx.x;
+  const int J = B.y * BY + threadIdx.y;
   if (in_store<0>(Lc, I, J, 0)) {
     const long long id = Lc.off[0] + cix(Lc, I, J, 0);
     T rU = 0, rD = 0;
@@ -1001,6 +1023,12 @@ __global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_a(Lvl Lf, Lvl Lc, co
     bc[id] = rU;
     tmp[id] = rD;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_a(Lvl Lf, Lvl Lc, const T* __restrict__ rf,
+                                                               T* __restrict__ bc, T* __restrict__ tmp) {
+  restrict_flux2d_a_body<T>(native_blk(), Lf, Lc, rf, bc, tmp);
 }
 
 // pass b: bc += G^T tmp (transpose of the tangential slope, mirror walls)
@@ -1020,13 +1048,18 @@ __device__ __forceinline__ T slope_transpose(const Lvl& Lc, const T* d, int I, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_b(Lvl Lc, const T* __restrict__ tmp, T* __restrict__ bc) {
-  const int I = blockIdx.x * BX + threadIdx.x;
-  const int J = blockIdx.y * BY + threadIdx.y;
+__device__ __forceinline__ void restrict_flux2d_b_body(const Blk& B, const Lvl& Lc, const T* __restrict__ tmp, T* __restrict__ bc) {
+  const int I = B.x * BX + threadIdx.x;
+  const int J = B.y * BY + threadIdx.y;
   if (in_store<0>(Lc, I, J, 0) && face_active<0>(Lc, I, J, 0))
     bc[Lc.off[0] + cix(Lc, I, J, 0)] += slope_transpose<T, 0>(Lc, tmp, I, J);
   if (in_store<1>(Lc, I, J, 0) && face_active<1>(Lc, I, J, 0))
     bc[Lc.off[1] + cix(Lc, I, J, 0)] += slope_transpose<T, 1>(Lc, tmp, I, J);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_b(Lvl Lc, const T* __restrict__ tmp, T* __restrict__ bc) {
+  restrict_flux2d_b_body<T>(native_blk(), Lc, tmp, bc);
 }
 
 // ---- 3D flux-conserving, divergence-preserving transfers -----------------
@@ -1239,9 +1272,9 @@ __global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_b(Lvl Lc, const T* _
 
 // coarsest level: x[idx[r]] = sum_c Minv[r][c] b[idx[c]]; one warp per row
 template <typename T>
-__global__ void k_coarse_solve(int m, const T* __restrict__ Minv, const int* __restrict__ idx,
+__device__ __forceinline__ void coarse_solve_body(const Blk& B, int m, const T* __restrict__ Minv, const int* __restrict__ idx,
                                const T* __restrict__ b, T* __restrict__ x) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int warp = (B.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m) return;
   double acc = 0.0;
@@ -1249,6 +1282,12 @@ __global__ void k_coarse_solve(int m, const T* __restrict__ Minv, const int* __r
   for (int c = lane; c < m; c += 32) acc += (double)row[c] * (double)__ldg(b + idx[c]);
   acc = warp_sum(acc);
   if (lane == 0) x[idx[warp]] = (T)acc;
+}
+
+template <typename T>
+__global__ void k_coarse_solve(int m, const T* __restrict__ Minv, const int* __restrict__ idx,
+                               const T* __restrict__ b, T* __restrict__ x) {
+  coarse_solve_body<T>(native_blk(), m, Minv, idx, b, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1259,15 +1298,21 @@ constexpr int RB = 256;
 
 // sum a.b (and b.b when NV == 2)
 template <typename T>
-__global__ void __launch_bounds__(RB) k_dot(long long len, const T* __restrict__ a, const T* __restrict__ b,
+__device__ __forceinline__ void dot_body(const Blk& B, long long len, const T* __restrict__ a, const T* __restrict__ b,
                                              RedBuf red, int fin, void* st, const int* pred) {
   if (pred && !*pred) return;  // every block skips, so the ticket stays untouched
   T acc = 0;
-  const long long stride = (long long)gridDim.x * RB;
-  for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride)
+  const long long stride = (long long)B.nx * RB;
+  for (long long t = (long long)B.x * RB + threadIdx.x; t < len; t += stride)
     acc += a[t] * b[t];
   double v[1] = {(double)acc};
-  grid_reduce<1>(v, red, fin, st);
+  grid_reduce<1>(v, red, fin, st, B);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RB) k_dot(long long len, const T* __restrict__ a, const T* __restrict__ b,
+                                             RedBuf red, int fin, void* st, const int* pred) {
+  dot_body<T>(native_blk(), len, a, b, red, fin, st, pred);
 }
 
 // sums a.b and b.c in one pass
@@ -1287,41 +1332,59 @@ __global__ void __launch_bounds__(RB) k_dot2(long long len, const T* __restrict_
 
 // x += alpha p ; r -= alpha q ; sum r.r      (alpha from CgState)
 template <typename T>
-__global__ void __launch_bounds__(RB) k_cg_update(long long len, T* __restrict__ x, const T* __restrict__ p,
+__device__ __forceinline__ void cg_update_body(const Blk& B, long long len, T* __restrict__ x, const T* __restrict__ p,
                                                    T* __restrict__ r, const T* __restrict__ q,
                                                    const CgState* cg, RedBuf red, void* st, int fin) {
   const T alpha = (T)cg->alpha;
   T acc = 0;
-  const long long stride = (long long)gridDim.x * RB;
-  for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride) {
+  const long long stride = (long long)B.nx * RB;
+  for (long long t = (long long)B.x * RB + threadIdx.x; t < len; t += stride) {
     x[t] += alpha * p[t];
     const T rn = r[t] - alpha * q[t];
     r[t] = rn;
     acc += rn * rn;
   }
   double v[1] = {(double)acc};
-  grid_reduce<1>(v, red, fin, st);
+  grid_reduce<1>(v, red, fin, st, B);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RB) k_cg_update(long long len, T* __restrict__ x, const T* __restrict__ p,
+                                                   T* __restrict__ r, const T* __restrict__ q,
+                                                   const CgState* cg, RedBuf red, void* st, int fin) {
+  cg_update_body<T>(native_blk(), len, x, p, r, q, cg, red, st, fin);
 }
 
 // p = z + beta p   (beta from CgState; first: p = z)
 template <typename T>
-__global__ void __launch_bounds__(RB) k_cg_dir(long long len, T* __restrict__ p, const T* __restrict__ z,
+__device__ __forceinline__ void cg_dir_body(const Blk& B, long long len, T* __restrict__ p, const T* __restrict__ z,
                                                 const CgState* cg, int first) {
   const T beta = first ? (T)0 : (T)cg->beta;
-  const long long stride = (long long)gridDim.x * RB;
+  const long long stride = (long long)B.nx * RB;
   // the first direction never reads p: a non-finite p left by an earlier
   // failed solve must not survive as 0 * NaN
-  for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride)
+  for (long long t = (long long)B.x * RB + threadIdx.x; t < len; t += stride)
     p[t] = first ? z[t] : z[t] + beta * p[t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RB) k_cg_dir(long long len, T* __restrict__ p, const T* __restrict__ z,
+                                                const CgState* cg, int first) {
+  cg_dir_body<T>(native_blk(), len, p, z, cg, first);
 }
 
 // y = a x + b y (host scalars)
 template <typename T>
-__global__ void __launch_bounds__(RB) k_axpby(long long len, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
-  const long long stride = (long long)gridDim.x * RB;
+__device__ __forceinline__ void axpby_body(const Blk& B, long long len, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  const long long stride = (long long)B.nx * RB;
   // b = 0 overwrites y without reading it (y may hold stale non-finite values)
-  for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride)
+  for (long long t = (long long)B.x * RB + threadIdx.x; t < len; t += stride)
     y[t] = (b == (T)0) ? a * x[t] : a * x[t] + b * y[t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RB) k_axpby(long long len, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+  axpby_body<T>(native_blk(), len, a, x, b, y);
 }
 
 }  // namespace gkb

@@ -7,6 +7,7 @@
 // on the launch shape, so results are bitwise reproducible run to run.
 #pragma once
 #include <cuda_runtime.h>
+#include "common.cuh"
 #include "state.cuh"
 
 namespace gkb {
@@ -22,16 +23,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// All threads of every block must call this exactly once.
+// All threads of every block of the problem's grid B must call this exactly
+// once.
 template <int NV>
-__device__ void grid_reduce(double (&v)[NV], RedBuf red, int fin, void* st) {
+__device__ void grid_reduce(double (&v)[NV], RedBuf red, int fin, void* st, const Blk& B) {
   __shared__ double sh[NV][32];
   __shared__ bool am_last;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nthr = blockDim.x * blockDim.y * blockDim.z;
   const int lane = tid & 31, warp = tid >> 5, nwarp = (nthr + 31) >> 5;
-  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = B.x + B.nx * (B.y + B.ny * B.z);
+  const unsigned nblk = B.nx * B.ny * B.nz;
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
     double s = warp_sum(v[i]);
@@ -78,6 +80,12 @@ __device__ void grid_reduce(double (&v)[NV], RedBuf red, int fin, void* st) {
     finalize(fin, fin_v, st);
     *red.ticket = 0u;
   }
+}
+
+// the same over the launch's own grid
+template <int NV>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], RedBuf red, int fin, void* st) {
+  grid_reduce<NV>(v, red, fin, st, native_blk());
 }
 
 }  // namespace gkb

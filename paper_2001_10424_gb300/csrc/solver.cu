@@ -11,10 +11,13 @@
 #include <mutex>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 
 #include <cooperative_groups.h>
 
 #include "solver.cuh"
+#include "gkb_device.cuh"
+#include "lockstep.cuh"
 #include "prof.h"
 #include "unet.cuh"
 
@@ -694,44 +697,19 @@ template struct Cg<double>;
 template struct Cg<float>;
 
 // ---------------------------------------------------------------------------
-// GKB kernels (FP64)
+// GKB kernels (FP64): launch wrappers of the bodies in gkb_device.cuh
 // ---------------------------------------------------------------------------
-
-constexpr int CB = 256;
 
 static dim3 cgrid(const Lvl& L) { return dim3((L.n[0] + 31) / 32, (L.n[1] + 7) / 8, L.n[2]); }
 
-// b = r - A^T y0 ; reduce sum b^2 / N, sum b, sum b / N
 __global__ void __launch_bounds__(256) k_gkb_b(Lvl L, const double* __restrict__ rc, const double* __restrict__ y0,
                                                double* __restrict__ b, const GkbState* st, RedBuf red, double* out) {
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  double v[3] = {0.0, 0.0, 0.0};
-  if (i < L.n[0] && j < L.n[1]) {
-    const long long id = cix(L, i, j, k);
-    const double bv = rc[id] - L.ascale * neg_div<double>(L, y0, i, j, k);
-    const double ni = st->nd ? st->nd[id] : st->n_scale;
-    b[id] = bv;
-    v[0] = bv * bv / ni;
-    v[1] = bv;
-    v[2] = bv / ni;
-  }
-  grid_reduce<3>(v, red, FIN_STORE, out);
+  gkb_b_body(native_blk(), L, rc, y0, b, st, red, out);
 }
 
-// g = N^-1 A^T v - alpha q ; reduce sum N g^2, sum N g
 __global__ void __launch_bounds__(256) k_gk1(Lvl L, const double* __restrict__ v, const double* __restrict__ q,
                                              double* __restrict__ gq, const GkbState* st, RedBuf red, double* out) {
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  double acc[2] = {0.0, 0.0};
-  if (i < L.n[0] && j < L.n[1]) {
-    const long long id = cix(L, i, j, k);
-    const double ni = st->nd ? st->nd[id] : st->n_scale;
-    const double g = L.ascale * neg_div<double>(L, v, i, j, k) / ni - st->alpha * q[id];
-    gq[id] = g;
-    acc[0] = ni * g * g;
-    acc[1] = ni * g;
-  }
-  grid_reduce<2>(acc, red, FIN_STORE, out);
+  gk1_body(native_blk(), L, v, q, gq, st, red, out);
 }
 
 // out = w * a on the in-domain cells (N^-1 r of the right-hand-side transform)
@@ -743,165 +721,36 @@ __global__ void __launch_bounds__(256) k_cells_mul(Lvl L, const double* __restri
   out[id] = a[id] * w[id];
 }
 
-// f = A q_{k+1} with q_{k+1} = (g - mean) / beta (mean cancels on active faces)
 __global__ void __launch_bounds__(256) k_gk2(Lvl L, const double* __restrict__ gq, double* __restrict__ f,
                                              const GkbState* st) {
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  const double sc = (st->beta > 0.0 && !st->stop) ? L.ascale / st->beta : 0.0;
-  const double mean = st->mean;
-#define GKB_GK2(C, DI, DJ, DK)                                                   \
-  {                                                                              \
-    bool store = (L.dim == 2) ? (k == 0 && i <= L.n[0] && j <= L.n[1])           \
-                              : (i <= L.n[0] && j <= L.n[1] && (C == 2 ? k <= L.n[2] : k < L.n[2])); \
-    if (store) {                                                                 \
-      double val = 0.0;                                                          \
-      if (face_active<C>(L, i, j, k)) {                                          \
-        const double pp = cell_in(L, i, j, k) ? gq[cix(L, i, j, k)] - mean : 0.0; \
-        const double pm = cell_in(L, i - DI, j - DJ, k - DK) ? gq[cix(L, i - DI, j - DJ, k - DK)] - mean : 0.0; \
-        val = sc * (pp - pm);                                                    \
-      }                                                                          \
-      f[L.off[C] + cix(L, i, j, k)] = val;                                       \
-    }                                                                            \
-  }
-  GKB_GK2(0, 1, 0, 0)
-  GKB_GK2(1, 0, 1, 0)
-  if (L.dim == 3) GKB_GK2(2, 0, 0, 1)
-#undef GKB_GK2
+  gk2_body(native_blk(), L, gq, f, st);
 }
 
-// w = x - beta v
 __global__ void __launch_bounds__(CB) k_gk3(long long len, const double* __restrict__ x, const double* __restrict__ v,
                                             double* __restrict__ w, const GkbState* st) {
-  const double beta = st->stop && st->beta == 0.0 ? 0.0 : st->beta;
-  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB)
-    w[t] = x[t] - beta * v[t];
+  gk3_body(native_blk(), len, x, v, w, st);
 }
 
-// v = w / alpha ; u += zeta v     (first: u = zeta v)
 __global__ void __launch_bounds__(CB) k_gk4v(long long len, const double* __restrict__ w, double* __restrict__ v,
                                              double* __restrict__ u, const GkbState* st, int first) {
-  if (st->stop && st->converged && st->alpha == 0.0) return;
-  if (st->status != 0) return;
-  const double ia = 1.0 / st->alpha, z = st->zeta;
-  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB) {
-    const double vn = w[t] * ia;
-    v[t] = vn;
-    u[t] = first ? z * vn : u[t] + z * vn;
-  }
+  gk4v_body(native_blk(), len, w, v, u, st, first);
 }
 
-// q = (g - mean) / beta ; d = (q - beta d) / alpha ; p -= zeta d   (first: d = q / alpha, p = -zeta d)
 __global__ void __launch_bounds__(256) k_gk4c(Lvl L, const double* __restrict__ gq, double* __restrict__ q,
                                               double* __restrict__ d, double* __restrict__ p, const GkbState* st,
                                               int first) {
-  if (st->stop && st->converged && st->alpha == 0.0) return;
-  if (st->status != 0) return;
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  if (i >= L.n[0] || j >= L.n[1]) return;
-  const long long id = cix(L, i, j, k);
-  const double ia = 1.0 / st->alpha, z = st->zeta, beta = st->beta;
-  if (first) {
-    const double dn = q[id] * ia;
-    d[id] = dn;
-    p[id] = -z * dn;
-  } else {
-    const double qn = (gq[id] - st->mean) / beta;
-    q[id] = qn;
-    const double dn = (qn - beta * d[id]) * ia;
-    d[id] = dn;
-    p[id] -= z * dn;
-  }
+  gk4c_body(native_blk(), L, gq, q, d, p, st, first);
 }
 
-// q1 = N^-1 (b - mean) / beta1
 __global__ void __launch_bounds__(256) k_gkb_q1(Lvl L, const double* __restrict__ b, double* __restrict__ q,
                                                 const GkbState* st) {
-  const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  if (i >= L.n[0] || j >= L.n[1]) return;
-  const long long id = cix(L, i, j, k);
-  const double ni = st->nd ? st->nd[id] : st->n_scale;
-  q[id] = (st->beta > 0.0) ? (b[id] - st->mean) / (ni * st->beta) : 0.0;
-}
-
-enum { S_BETA1 = 0, S_ALPHA1 = 1, S_BETA = 2, S_ALPHA = 3 };
-
-__device__ void hist_put(double* h, int cap, int i, double v) {
-  if (h && i >= 0 && i < cap) h[i] = v;
+  gkb_q1_body(native_blk(), L, b, q, st);
 }
 
 // scalar part of Algorithm 1 and the stopping rule (single thread)
 __global__ void k_gkb_scalar(int op, GkbState* st, const double* red) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  GkbState& S = *st;
-  switch (op) {
-    case S_BETA1: {
-      // beta_1 = ||b||_{N^-1} on the mean-free b:
-      // sum (b - m)^2 / N = sum b^2 / N - 2 m sum b / N + m^2 sum 1 / N
-      const double mean = S.enclosed ? red[1] / S.ncells : 0.0;
-      double s2 = red[0] - 2.0 * mean * red[2] + mean * mean * S.ninvsum;
-      if (s2 < 0) s2 = 0;
-      S.mean = mean;
-      S.beta = sqrt(s2);
-      hist_put(S.h_beta, S.hcap, 0, S.beta);
-      if (!isfinite(S.beta)) { S.status = ST_NAN; S.stop = 1; }
-      else if (S.beta == 0.0) { S.stop = 1; S.converged = 1; }
-    } break;
-    case S_ALPHA1: {
-      const double a2 = red[0];
-      if (!isfinite(a2)) { S.status = ST_NAN; S.stop = 1; break; }
-      if (!(a2 > 0.0)) {
-        if (a2 < 0.0) S.status = ST_NOT_SPD;
-        S.alpha = 0.0; S.stop = 1; S.converged = (a2 == 0.0);
-        break;
-      }
-      S.alpha = sqrt(a2);
-      S.zeta = S.beta / S.alpha;
-      S.K = 1;
-      S.zsum = S.zeta * S.zeta;
-      S.ring[1 % GKB_RING] = S.zeta * S.zeta;
-      hist_put(S.h_alpha, S.hcap, 0, S.alpha);
-      hist_put(S.h_zeta, S.hcap, 0, S.zeta);
-      if (S.maxit <= 0) S.stop = 1;
-    } break;
-    case S_BETA: {
-      // beta_{k+1} = ||g - c||_N with c = sum N g / sum N, the N-weighted
-      // mean (the plain mean when N = n I): sum N g^2 - c^2 sum N
-      S.k += 1;
-      const double mean = S.enclosed ? red[1] / S.nsum : 0.0;
-      double s2 = red[0] - S.nsum * mean * mean;
-      if (s2 < 0) s2 = 0;
-      S.mean = mean;
-      S.beta = sqrt(s2);
-      hist_put(S.h_beta, S.hcap, S.k, S.beta);
-      if (!isfinite(S.beta)) { S.status = ST_NAN; S.stop = 1; }
-      else if (S.beta == 0.0) { S.stop = 1; S.converged = 1; S.alpha = 0.0; }
-    } break;
-    case S_ALPHA: {
-      if (S.stop) break;  // breakdown already handled
-      const double a2 = red[0];
-      if (!isfinite(a2)) { S.status = ST_NAN; S.stop = 1; break; }
-      if (!(a2 > 0.0)) {
-        if (a2 < 0.0) S.status = ST_NOT_SPD;
-        S.alpha = 0.0; S.stop = 1; S.converged = (a2 == 0.0);
-        break;
-      }
-      S.alpha = sqrt(a2);
-      S.zeta = -S.beta / S.alpha * S.zeta;
-      S.K += 1;
-      const double z2 = S.zeta * S.zeta;
-      S.zsum += z2;
-      S.ring[S.K % GKB_RING] = z2;
-      double tail = 0.0;
-      const int j0 = (S.K - S.delay > 1) ? S.K - S.delay : 1;
-      for (int j = j0; j <= S.K; ++j) tail += S.ring[j % GKB_RING];
-      S.est = sqrt(tail / S.zsum);
-      hist_put(S.h_alpha, S.hcap, S.k, S.alpha);
-      hist_put(S.h_zeta, S.hcap, S.K - 1, S.zeta);
-      hist_put(S.h_est, S.hcap, S.k - 1, S.est);
-      if (S.est <= S.tol) { S.converged = 1; S.stop = 1; }
-      else if (S.k >= S.maxit) S.stop = 1;
-    } break;
-  }
+  gkb_scalar_op(op, st, red);
 }
 
 // pressure sum for the mean-zero projection
@@ -912,20 +761,15 @@ __global__ void __launch_bounds__(256) k_cell_sum(Lvl L, const double* __restric
   grid_reduce<1>(v, red, FIN_STORE, out);
 }
 
-// mixed precision: r32 = (float) r64 ; x64 += x32, x32 = 0
 __global__ void __launch_bounds__(CB) k_cvt_f32(long long len, const double* __restrict__ r, float* __restrict__ o,
                                                 const int* pred) {
-  if (pred && !*pred) return;
-  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB)
-    o[t] = (float)r[t];
+  cvt_f32_body(native_blk(), len, r, o, pred);
 }
+
+
 __global__ void __launch_bounds__(CB) k_mixed_accum(long long len, float* __restrict__ x32, double* __restrict__ x64,
                                                     const int* pred) {
-  if (pred && !*pred) return;
-  for (long long t = blockIdx.x * (long long)CB + threadIdx.x; t < len; t += (long long)gridDim.x * CB) {
-    x64[t] += (double)x32[t];
-    x32[t] = 0.0f;
-  }
+  mixed_accum_body(native_blk(), len, x32, x64, pred);
 }
 
 // ---- device-side control of the graph form --------------------------------
@@ -2395,14 +2239,27 @@ int Solver::harvest(const double* fin, int max_pairs, float* x_img, float* t_img
 
 namespace {
 
+// one graph per batch: either every problem's whole solve as a branch, or
+// the lock-step form (lockstep.cu) where each step is one launch over all
+// problems
 struct BatchGraph {
   std::vector<const Solver*> members;
   std::vector<int> gens;
   cudaGraphExec_t exec = nullptr;
+  Lockstep* lock = nullptr;
   ~BatchGraph() {
     if (exec) cudaGraphExecDestroy(exec);
+    delete lock;
   }
 };
+
+// GKB_BATCH_MODE=branches keeps the one-branch-per-problem form for batches
+// the lock-step form could take (for comparisons)
+bool lockstep_wanted(Solver** S, int count) {
+  const char* m = getenv("GKB_BATCH_MODE");
+  if (m && strcmp(m, "branches") == 0) return false;
+  return lockstep_eligible(S, count);
+}
 
 std::mutex g_batch_mutex;
 std::vector<BatchGraph*> g_batches;
@@ -2429,6 +2286,20 @@ static BatchGraph* build_batch(Solver** S, int count, cudaStream_t origin) {
   for (int i = 0; i < count; ++i) {
     B->members.push_back(S[i]);
     B->gens.push_back(S[i]->generation);
+  }
+  if (lockstep_wanted(S, count)) {
+    Profiler* saved = g_prof;
+    g_prof = nullptr;
+    try {
+      S[0]->ensure_capture_streams();
+      B->lock = new Lockstep(S, count, origin, S[0]->cap2, S[0]->cap3);
+    } catch (...) {
+      g_prof = saved;
+      delete B;
+      throw;
+    }
+    g_prof = saved;
+    return B;
   }
   std::vector<cudaStream_t> br(count, nullptr);
   std::vector<cudaEvent_t> ev(count + 1, nullptr);
@@ -2514,10 +2385,17 @@ int solve_batched(Solver** S, int count, const double* const* g, const double* c
       S[i]->init_state(tol, delay);
       S[i]->refresh_net();
     }
-    GKB_CUDA(cudaGraphLaunch(B->exec, st));
+    if (B->lock) B->lock->launch(st);
+    else GKB_CUDA(cudaGraphLaunch(B->exec, st));
     for (int i = 0; i < count; ++i) {
-      const int si = S[i]->finish(w[i], p[i], nullptr, nullptr, true);
+      const int si = S[i]->finish(w[i], p[i], nullptr, nullptr, B->lock == nullptr);
       if (status == GKB_OK && si != GKB_OK) status = si;
+    }
+    if (B->lock) {
+      // the batch's launches (each covers every problem) go to the first handle
+      long long lc[GKB_KC_COUNT];
+      B->lock->launch_counts(st, lc);
+      for (int k = 0; k < GKB_KC_COUNT; ++k) S[0]->stats.kernel_launches[k] += lc[k];
     }
   } catch (...) {
     for (int i = 0; i < count; ++i) S[i]->stream = own[i];

@@ -1,7 +1,11 @@
 """Batched form: many independent cavities solved in one graph launch.
 
-Every problem's whole solve is one branch of a single CUDA graph; the
-branches use per-problem reductions and states, so each problem must match
+Eligible batches (2D, constant viscosity per problem, GMG-PCG) run in lock
+step: every step of the solve is one launch over all problems, with each
+problem's blocks running the body of its own launch (same grid, same
+reduction buffers) and per-problem snapshot flags deciding which problems
+take part in each loop iteration. Other batches capture every problem's
+whole solve as one branch of the graph. Either way each problem must match
 its own individual solve bit for bit, and the oracle within the FP64 bound.
 """
 import numpy as np
@@ -80,3 +84,73 @@ def test_batched_argument_errors(lib):
     finally:
         gk.gkb_destroy(h)
         gk.gkb_destroy(h2)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lockstep_batch_with_uneven_problems(lib, prec):
+    """Problems that stop at very different points in one lock-step batch: a
+    zero right-hand side (Algorithm 1 stops at beta_1 = 0), gammas from 1 to
+    1e4 (outer iteration counts from many to few), sides whose hierarchies
+    have 3 to 6 levels; every problem equals its individual solve bit for
+    bit and the launches of the batch are counted."""
+    import torch
+    gk = lib
+    sides = [64, 32, 96, 160, 48, 64, 128]
+    gammas = [100.0, 1.0, 1e4, 10.0, 100.0, 1000.0, 100.0]
+    probs = workloads.batched2d(count=len(sides), seed_offset=61, sides=sides)
+    probs[5]["g"] = np.zeros_like(probs[5]["g"])
+    hs = [make_handle(gk, pr["n"], pr["bc"], pr["mu"], gm, precision=prec, tol_inner=1e-11)
+          for pr, gm in zip(probs, gammas)]
+    try:
+        g = [torch.tensor(pr["g"], device="cuda") for pr in probs]
+        r = [torch.tensor(pr["r"], device="cuda") for pr in probs]
+        w = [torch.empty(pr["m"], dtype=torch.float64, device="cuda") for pr in probs]
+        p = [torch.empty(pr["ncells"], dtype=torch.float64, device="cuda") for pr in probs]
+        rc = gk.gkb_solve_batched(hs, g, r, 1e-8, 5, w, p)
+        assert rc == gk.GKB_OK, gk.gkb_last_error(hs[0])
+        stats_b = [gk.gkb_stats(h) for h in hs]
+        assert sum(stats_b[0]["kernel_launches"].values()) > 0
+        wb = [x.cpu().numpy() for x in w]
+        pb = [x.cpu().numpy() for x in p]
+        assert not np.any(wb[5]) and not np.any(pb[5])
+        outer = []
+        for i, h in enumerate(hs):
+            wi = torch.empty_like(w[i])
+            pi = torch.empty_like(p[i])
+            assert gk.gkb_solve(h, g[i], r[i], 1e-8, 5, wi, pi) == gk.GKB_OK
+            st = gk.gkb_stats(h)
+            outer.append(st["outer_iterations"])
+            assert st["outer_iterations"] == stats_b[i]["outer_iterations"], i
+            assert st["inner_iterations"] == stats_b[i]["inner_iterations"], i
+            assert np.array_equal(wi.cpu().numpy(), wb[i]) and np.array_equal(pi.cpu().numpy(), pb[i]), i
+        assert max(outer) >= 2 * min(o for o in outer if o > 0)
+        pr = probs[3]
+        grid, ops = oracle_problem(pr["n"], pr["bc"], pr["mu"], gammas[3])
+        ref = oracle_truth(grid, ops, pr["g"], pr["r"])
+        assert energy_rel(ops["M"], wb[3], ref["w"]) <= 1e-8
+    finally:
+        for h in hs:
+            gk.gkb_destroy(h)
+
+
+def test_variable_viscosity_batch_uses_graph_branches(lib):
+    """A batch the lock-step form does not take (per-cell viscosity) still
+    solves every problem exactly as its individual solve."""
+    import torch
+    gk = lib
+    probs = [workloads.varvisc2d(32, seed_offset=70 + 2 * i) for i in range(3)]
+    hs = [make_handle(gk, pr["n"], pr["bc"], pr["mu"], 100.0, precision=1, tol_inner=1e-11) for pr in probs]
+    try:
+        g = [torch.tensor(pr["g"], device="cuda") for pr in probs]
+        r = [torch.tensor(pr["r"], device="cuda") for pr in probs]
+        w = [torch.empty(pr["m"], dtype=torch.float64, device="cuda") for pr in probs]
+        p = [torch.empty(pr["ncells"], dtype=torch.float64, device="cuda") for pr in probs]
+        assert gk.gkb_solve_batched(hs, g, r, 1e-8, 5, w, p) == gk.GKB_OK
+        for i, h in enumerate(hs):
+            wi = torch.empty_like(w[i])
+            pi = torch.empty_like(p[i])
+            assert gk.gkb_solve(h, g[i], r[i], 1e-8, 5, wi, pi) == gk.GKB_OK
+            assert torch.equal(wi, w[i]) and torch.equal(pi, p[i])
+    finally:
+        for h in hs:
+            gk.gkb_destroy(h)

@@ -687,6 +687,181 @@ __global__ void k_patch_fold(Lvl L, T* table) {
   f[0] = (T)self;
 }
 
+// ---- 3D constant viscosity: folded stencils for every position class ------
+// Per axis a position (face index along the face's normal axis, cell index
+// along the others) falls in one of seven classes: 0, 1, 2 (its distance
+// from the low side), 3 (interior), 4, 5, 6 (n - 2, n - 1, n). With at least
+// six cells on the axis, the classes of a position fix the classes and the
+// activity of every patch through its faces (their edges lie within one
+// cell of it), so (C r) at a face of component C is one 13-point stencil per
+// (position class, C): the face itself and, for each orientation E != C, the
+// six other faces of its two patches (the offsets of patch_apply_fold). The
+// stencils follow the interior table after PATCH_FOLD_OFF.
+constexpr int FOLD3_OFF = PATCH_FOLD_OFF + 3 * 16;
+constexpr int FOLD3_CLASSES = 343;
+constexpr int FOLD3_INTERIOR = (3 * 7 + 3) * 7 + 3;
+
+__host__ __device__ __forceinline__ int cls7(int x, int n) {
+  return x <= 2 ? x : (x >= n - 2 ? x - n + 6 : 3);
+}
+__host__ __device__ __forceinline__ int rep7(int c, int n) {
+  return c <= 3 ? c : n + c - 6;
+}
+
+// the two patches of orientation E through a face of component C at p: their
+// rows of the class inverses, scattered into the stencil slots t..t+5 and the
+// face's own slot 0 (inactive faces contribute nothing)
+template <typename T, int E>
+__device__ void fold3_orient(const Lvl& L, const T* __restrict__ inv, const int p[3], int C, double acc[13], int t) {
+  constexpr int a = EAx<E>::a, b = EAx<E>::b;
+  int e0[3] = {p[0], p[1], p[2]};
+  int e1[3] = {p[0], p[1], p[2]};
+  bool act0[4], act1[4];
+  if (C == a) {
+    e1[b] += 1;
+    patch_active<E>(L, e0, act0);
+    patch_active<E>(L, e1, act1);
+    const T* R0 = inv + (size_t)(E * 75 + patch_class<E>(L, e0)) * 16 + 1 * 4;  // slot 1 of patch p
+    const T* R1 = inv + (size_t)(E * 75 + patch_class<E>(L, e1)) * 16 + 0 * 4;  // slot 0 of patch p + e_b
+    if (act0[0]) acc[t + 0] += (double)R0[0];
+    if (act0[1]) acc[0] += (double)R0[1];
+    if (act0[2]) acc[t + 1] += (double)R0[2];
+    if (act0[3]) acc[t + 2] += (double)R0[3];
+    if (act1[0]) acc[0] += (double)R1[0];
+    if (act1[1]) acc[t + 3] += (double)R1[1];
+    if (act1[2]) acc[t + 4] += (double)R1[2];
+    if (act1[3]) acc[t + 5] += (double)R1[3];
+  } else {
+    e1[a] += 1;
+    patch_active<E>(L, e0, act0);
+    patch_active<E>(L, e1, act1);
+    const T* R0 = inv + (size_t)(E * 75 + patch_class<E>(L, e0)) * 16 + 3 * 4;  // slot 3 of patch p
+    const T* R1 = inv + (size_t)(E * 75 + patch_class<E>(L, e1)) * 16 + 2 * 4;  // slot 2 of patch p + e_a
+    if (act0[0]) acc[t + 0] += (double)R0[0];
+    if (act0[1]) acc[t + 1] += (double)R0[1];
+    if (act0[2]) acc[t + 2] += (double)R0[2];
+    if (act0[3]) acc[0] += (double)R0[3];
+    if (act1[0]) acc[t + 3] += (double)R1[0];
+    if (act1[1]) acc[t + 4] += (double)R1[1];
+    if (act1[2]) acc[0] += (double)R1[2];
+    if (act1[3]) acc[t + 5] += (double)R1[3];
+  }
+}
+
+// the stencils of all position classes (one thread per class and component),
+// from the class inverses at the start of the same table (k_patch_table),
+// summed in FP64
+template <typename T>
+__global__ void k_fold3_table(Lvl L, T* table) {
+  const T* inv = table;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L.dim != 3 || t >= FOLD3_CLASSES * 3) return;
+  const int C = t % 3, pc = t / 3;
+  const int p[3] = {rep7(pc / 49, L.n[0]), rep7((pc / 7) % 7, L.n[1]), rep7(pc % 7, L.n[2])};
+  double acc[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) acc[q] = 0.0;
+  int slot = 1;
+  if (C != 0) { fold3_orient<T, 0>(L, inv, p, C, acc, slot); slot += 6; }
+  if (C != 1) { fold3_orient<T, 1>(L, inv, p, C, acc, slot); slot += 6; }
+  if (C != 2) { fold3_orient<T, 2>(L, inv, p, C, acc, slot); }
+  T* f = table + FOLD3_OFF + (size_t)t * 16;
+  for (int q = 0; q < 13; ++q) f[q] = (T)acc[q];
+  f[13] = f[14] = f[15] = (T)0;
+}
+
+// the interior class's stencils as a kernel parameter (read from the
+// constant bank, no load instructions)
+template <typename T>
+struct Fold3In {
+  T c[3][13];
+};
+
+// (C r) at an active face of component C by the stencil f (13 entries);
+// near a side (Inner == false) only faces with a nonzero coefficient are
+// read, which are active faces inside the arrays. Offsets are 32-bit (the
+// padded arrays hold fewer than 2^31 entries).
+template <typename T, int C, bool Inner, class Coef>
+__device__ __forceinline__ T fold3_apply(const Lvl& L, const T* __restrict__ r, int cb, Coef f) {
+  const int P = L.P, S = (int)L.S;
+  const T* rc = r + L.off[C] + cb;
+  T acc = f(0) * __ldg(rc);
+  int t = 1;
+#pragma unroll
+  for (int E = 0; E < 3; ++E) {
+    if (E == C) continue;
+    const int a = (E == 0) ? 1 : 0, b = (E == 2) ? 1 : 2;
+    const int sa = a == 0 ? 1 : (a == 1 ? P : S), sb = b == 1 ? P : S;
+    const T* ra = r + L.off[a] + cb;
+    const T* rb = r + L.off[b] + cb;
+    int o[6];
+    const T* base[6];
+    if (C == a) {
+      base[0] = ra; o[0] = -sb; base[1] = rb; o[1] = -sa; base[2] = rb; o[2] = 0;
+      base[3] = ra; o[3] = sb; base[4] = rb; o[4] = sb - sa; base[5] = rb; o[5] = sb;
+    } else {
+      base[0] = ra; o[0] = -sb; base[1] = ra; o[1] = 0; base[2] = rb; o[2] = -sa;
+      base[3] = ra; o[3] = sa - sb; base[4] = ra; o[4] = sa; base[5] = rb; o[5] = sa;
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      const T c = f(t + u);
+      if (Inner || c != (T)0) acc += c * __ldg(base[u] + o[u]);
+    }
+    t += 6;
+  }
+  return acc;
+}
+
+// one Chebyshev step of the 3D constant-viscosity smoother through the class
+// stencils (levels with at least six cells on every axis): interior
+// positions take the stencils from the kernel parameter, the others from the
+// table; d and x are read before the stencil so that their loads overlap it
+template <typename T>
+__device__ __forceinline__ void cheb3_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
+                                           T* __restrict__ d, T ca, T cb, int x_zero, const T* __restrict__ table,
+                                           const Fold3In<T>& fin) {
+  const int i = B.x * BX + threadIdx.x;
+  const int j = B.y * BY + threadIdx.y;
+  const int k = B.z;
+  if (i > L.n[0] || j > L.n[1]) return;
+  const int pc = (cls7(i, L.n[0]) * 7 + cls7(j, L.n[1])) * 7 + cls7(k, L.n[2]);
+  const int p0 = (int)cix(L, i, j, k);
+  const T* fold = table + FOLD3_OFF + (size_t)pc * 48;
+#define GKB_CHEB3(C)                                                                     \
+  if (in_store<C>(L, i, j, k) && face_active<C>(L, i, j, k)) {                           \
+    const int id = (int)L.off[C] + p0;                                                   \
+    const T dold = (cb != (T)0) ? d[id] : (T)0;                                          \
+    const T xold = x_zero ? (T)0 : x[id];                                                \
+    T z;                                                                                 \
+    if (pc == FOLD3_INTERIOR)                                                            \
+      z = fold3_apply<T, C, true>(L, r, p0, [&](int q) { return fin.c[C][q]; });        \
+    else                                                                                 \
+      z = fold3_apply<T, C, false>(L, r, p0, [&](int q) { return __ldg(fold + C * 16 + q); }); \
+    const T dn = (cb != (T)0) ? ca * z + cb * dold : ca * z;                             \
+    d[id] = dn;                                                                          \
+    x[id] = x_zero ? dn : xold + dn;                                                     \
+  }
+  GKB_CHEB3(0)
+  GKB_CHEB3(1)
+  GKB_CHEB3(2)
+#undef GKB_CHEB3
+}
+
+// the class stencils serve 3D constant-viscosity levels with the fast paths
+// on and at least six cells on every axis
+inline bool cheb3_level(const Lvl& L) {
+  return L.dim == 3 && L.fast && L.n[0] >= 6 && L.n[1] >= 6 && L.n[2] >= 6;
+}
+inline bool cheb3_applies(const Lvl& L, const void* table) { return table != nullptr && cheb3_level(L); }
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_cheb3(Lvl L, const T* __restrict__ r, T* __restrict__ x,
+                                                   T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
+                                                   const __grid_constant__ Fold3In<T> fin) {
+  cheb3_body<T>(native_blk(), L, r, x, d, ca, cb, x_zero, table, fin);
+}
+
 // One Chebyshev step of the patch-preconditioned smoother:
 //   z = C r;  d = ca * z + cb * d;  x = (x_zero ? 0 : x) + d
 template <typename T, bool VarMu>

@@ -62,10 +62,18 @@ void launch_patch_varmu(const Lvl& L, const KT* r, KT* z, const KT* vtab, cudaSt
 #if GKB_IN_PART(3)
 template <>
 void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_zero, const KT* table,
-                   cudaStream_t s) {
+                   cudaStream_t s, const double* fold_in) {
   ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
-  if (GKB_VARMU(L)) launch_cheb_varmu(L, r, x, d, ca, cb, x_zero, table, s);
-  else k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
+  if (GKB_VARMU(L)) {
+    launch_cheb_varmu(L, r, x, d, ca, cb, x_zero, table, s);
+  } else if (fold_in && cheb3_applies(L, table)) {
+    Fold3In<KT> f;
+    for (int c = 0; c < 3; ++c)
+      for (int q = 0; q < 13; ++q) f.c[c][q] = (KT)fold_in[c * 16 + q];
+    k_cheb3<KT><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);
+  } else {
+    k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
+  }
 }
 #endif
 
@@ -92,8 +100,15 @@ void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStrea
 
 template <>
 long long Ops<KT>::patch_table_len(const Lvl& L) {
-  if (!GKB_VARMU(L)) return PATCH_FOLD_OFF + 3 * 16;  // class inverses, then the 3D folded stencils
+  // class inverses, the 3D interior stencils, then the 3D class stencils
+  if (!GKB_VARMU(L)) return FOLD3_OFF + (L.dim == 3 ? FOLD3_CLASSES * 3 * 16 : 0);
   return (L.dim == 3 ? 3 : 1) * 10 * vtab_plane(L);
+}
+
+template <>
+long long Ops<KT>::fold3_interior_offset(const Lvl& L) {
+  if (GKB_VARMU(L) || !cheb3_level(L)) return -1;
+  return FOLD3_OFF + 48LL * FOLD3_INTERIOR;
 }
 
 template <>
@@ -101,7 +116,10 @@ void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
   ProfScope ps_(GKB_KC_LAYOUT, s, 0);
   if (!GKB_VARMU(L)) {
     k_patch_table<KT><<<1, 256, 0, s>>>(L, table);
-    if (L.dim == 3) k_patch_fold<KT><<<1, 32, 0, s>>>(L, table);
+    if (L.dim == 3) {
+      k_patch_fold<KT><<<1, 32, 0, s>>>(L, table);
+      k_fold3_table<KT><<<(FOLD3_CLASSES * 3 + 127) / 128, 128, 0, s>>>(L, table);
+    }
     return;
   }
   // variable viscosity: the per-patch inverses (entries never written stay 0)

@@ -74,20 +74,22 @@ __device__ __forceinline__ Blk job_blk(const JobHead& h) {
   return B;
 }
 
-// this block's job (map: job of every block of the launch), copied into
-// shared memory so that the body reads the level descriptor and pointers
-// from there; returns from the kernel when the job is gated off
+// this block's job (map: job of every block of the launch): its gate is
+// read first (gated-off blocks exit after two dependent loads), then the job
+// is copied into shared memory so that the body reads the level descriptor
+// and pointers from there
 #define LS_RUN(JT, ...)                                                  \
   __shared__ __align__(16) unsigned js_raw[sizeof(JT) / 4];              \
   {                                                                      \
-    const unsigned* jg = (const unsigned*)(jobs + map[blockIdx.x]);      \
+    const JT* jg_ = jobs + map[blockIdx.x];                              \
+    if (!job_on(jg_->h)) return;                                         \
+    const unsigned* jw_ = (const unsigned*)jg_;                          \
     const int tid_ = threadIdx.x + blockDim.x * threadIdx.y;             \
     for (int w_ = tid_; w_ < (int)(sizeof(JT) / 4); w_ += blockDim.x * blockDim.y) \
-      js_raw[w_] = jg[w_];                                               \
+      js_raw[w_] = jw_[w_];                                              \
   }                                                                      \
   __syncthreads();                                                       \
   const JT& job = *(const JT*)js_raw;                                    \
-  if (!job_on(job.h)) return;                                            \
   const Blk B = job_blk(job.h);                                          \
   __VA_ARGS__;
 
@@ -267,7 +269,7 @@ __global__ void kb_serial(const JSer* jobs, int n, int op, int arg) {
 // solve ended takes its next GKB steps in the same iteration and starts its
 // next inner solve, without waiting for the others.
 enum { EV_AL = 1, EV_INIT = 2, EV_OUTER = 3 };
-enum { K_INIT = 0, K_PRE, K_OUTER, K_START, K_POST };
+enum { K_INIT = 0, K_PRE, K_OUTER, K_START, K_POST, K_UPD };
 struct Flat {
   GkbState** S;
   CgState** cg;
@@ -276,7 +278,7 @@ struct Flat {
   int* ended;        // Algorithm 1 has ended for this problem
   // this iteration's steps
   int *body, *fin, *al, *init, *outer, *start_outer, *start_cg, *pc;
-  unsigned long long* counts;  // [0] iterations, [1..6] taken conditional sections
+  unsigned long long* counts;  // [0] iterations, [1..7] taken conditional sections
 };
 struct Handles {
   cudaGraphConditionalHandle h[4];
@@ -324,6 +326,9 @@ __global__ void __launch_bounds__(1024) kb_ctl(int op, Flat f, int n, int hard_o
       }
       f.start_outer[p] = cont;
       any[0] |= cont;
+    } else if (op == K_UPD) {
+      // a mixed-form FP64 residual replacement is due in some CG iteration
+      any[0] |= f.body[p] && f.cg[p]->update;
     } else if (op == K_START) {
       const int st = f.al[p] || f.start_outer[p];
       f.start_cg[p] = st;
@@ -353,6 +358,7 @@ __global__ void __launch_bounds__(1024) kb_ctl(int op, Flat f, int n, int hard_o
       for (int i = 0; i < 4; ++i) f.counts[1 + i] += any[i];
     if (op == K_OUTER) f.counts[5] += any[0];
     if (op == K_START) f.counts[6] += any[0];
+    if (op == K_UPD) f.counts[7] += any[0];
     for (int i = 0; i < H.nh; ++i) cudaGraphSetConditional(H.h[i], any[i] ? 1u : 0u);
   }
 }
@@ -392,9 +398,9 @@ struct Lockstep::Impl {
   DevBuf<CgState*> cp;
   std::vector<DevBuf<unsigned char>> store;
   std::map<std::vector<unsigned>, const unsigned*> maps;
-  // launches captured, by section (0 once, 1 every iteration, 2..7 the
+  // launches captured, by section (0 once, 1 every iteration, 2..8 the
   // conditional sections, each counted when taken) and kernel class
-  long long cl[8][GKB_KC_COUNT] = {};
+  long long cl[9][GKB_KC_COUNT] = {};
   int sect = 0;
   cudaGraphExec_t exec = nullptr;
   Flat F{};
@@ -617,7 +623,8 @@ struct Lockstep::Impl {
 
   // the steps of the flattened solve (lockstep.cu, below)
   void cg_prefix(cudaStream_t st);   // [D] start the inner solves flagged start_cg
-  void cg_body(cudaStream_t st);     // [A] first half of a CG iteration (flag body)
+  void cg_body(cudaStream_t st, cudaStream_t sc);  // [A] first half of a CG iteration (flag body)
+  void replace64(cudaStream_t su);   // the mixed form's FP64 reliable update
   void cg_precond(cudaStream_t st);  // [E] preconditioner, r.z, direction (flag pc)
   void cg_suffix(cudaStream_t st);   // [B] end the inner solves flagged fin
   void capture(cudaStream_t st, cudaStream_t sb, cudaStream_t sc);
@@ -731,10 +738,49 @@ void Lockstep::Impl::cg_prefix(cudaStream_t st) {
   }
 }
 
+// the mixed form's FP64 residual replacement (x64 += x32, r64 = f - M x64,
+// r32 = r64, r64.r64), gated per problem by its finaliser's update flag
+void Lockstep::Impl::replace64(cudaStream_t su) {
+  const std::vector<int> ps = all();
+  const int* G = F.body;
+  auto vlen = [](Solver& s) { return (long long)s.L64.nvel; };
+  auto upd = [](Solver& s) { return (const int*)&s.cg_dev->update; };
+  launch<JCvt>(su, GKB_KC_LAYOUT, ps, dim3(CB), [&](int p, JCvt& j) {
+    Solver& s = *S[p];
+    j.h.active = G + p;
+    j.h.pred = upd(s);
+    j.len = s.L64.nvel;
+    j.x32 = s.x32.p;
+    j.x64 = s.x.p;
+    return dim3(lin_blocks_ls(j.len));
+  }, kb_accum);
+  launch<JTile<double>>(su, GKB_KC_RESIDUAL, ps, dim3(BX, BY), [&](int p, JTile<double>& j) {
+    Solver& s = *S[p];
+    j.h.active = G + p;
+    j.h.pred = upd(s);
+    j.L = s.L64;
+    j.x = s.x.p;
+    j.b = s.f.p;
+    j.y = s.r64.p;
+    return face_grid(s.L64);
+  }, kb_tile<double, 0, false>);
+  launch<JCvt>(su, GKB_KC_LAYOUT, ps, dim3(CB), [&](int p, JCvt& j) {
+    Solver& s = *S[p];
+    j.h.active = G + p;
+    j.h.pred = upd(s);
+    j.len = s.L64.nvel;
+    j.r = s.r64.p;
+    j.o = s.cg32.r.p;
+    return dim3(lin_blocks_ls(j.len));
+  }, kb_cvt);
+  dot<double>(su, GKB_KC_BLAS, G, upd, vlen, [&](int p) { return (const double*)S[p]->r64.p; },
+              [&](int p) { return (const double*)S[p]->r64.p; }, FIN_MX_RR64);
+}
+
 // [A] operator product, step and residual update of a CG iteration (and the
 // mixed form's FP64 reliable update where its finaliser asks for one), for
 // the problems flagged body
-void Lockstep::Impl::cg_body(cudaStream_t st) {
+void Lockstep::Impl::cg_body(cudaStream_t st, cudaStream_t sc) {
   const std::vector<int> ps = all();
   const int* G = F.body;
   auto vlen = [](Solver& s) { return (long long)s.L64.nvel; };
@@ -764,37 +810,11 @@ void Lockstep::Impl::cg_body(cudaStream_t st) {
       j.fin = FIN_MX_RR;
       return dim3((unsigned)blas_blocks(j.len));
     }, kb_cg_update<float>);
-    auto upd = [](Solver& s) { return (const int*)&s.cg_dev->update; };
-    launch<JCvt>(st, GKB_KC_LAYOUT, ps, dim3(CB), [&](int p, JCvt& j) {
-      Solver& s = *S[p];
-      j.h.active = G + p;
-      j.h.pred = upd(s);
-      j.len = s.L64.nvel;
-      j.x32 = s.x32.p;
-      j.x64 = s.x.p;
-      return dim3(lin_blocks_ls(j.len));
-    }, kb_accum);
-    launch<JTile<double>>(st, GKB_KC_RESIDUAL, ps, dim3(BX, BY), [&](int p, JTile<double>& j) {
-      Solver& s = *S[p];
-      j.h.active = G + p;
-      j.h.pred = upd(s);
-      j.L = s.L64;
-      j.x = s.x.p;
-      j.b = s.f.p;
-      j.y = s.r64.p;
-      return face_grid(s.L64);
-    }, kb_tile<double, 0, false>);
-    launch<JCvt>(st, GKB_KC_LAYOUT, ps, dim3(CB), [&](int p, JCvt& j) {
-      Solver& s = *S[p];
-      j.h.active = G + p;
-      j.h.pred = upd(s);
-      j.len = s.L64.nvel;
-      j.r = s.r64.p;
-      j.o = s.cg32.r.p;
-      return dim3(lin_blocks_ls(j.len));
-    }, kb_cvt);
-    dot<double>(st, GKB_KC_BLAS, G, upd, vlen, [&](int p) { return (const double*)S[p]->r64.p; },
-                [&](int p) { return (const double*)S[p]->r64.p; }, FIN_MX_RR64);
+    // the FP64 residual replacement under a conditional node: most
+    // iterations need it in no problem
+    const cudaGraphConditionalHandle hu = new_handle(st);
+    ctl(st, K_UPD, {hu});
+    if_node(st, sc, hu, 8, [&](cudaStream_t su) { replace64(su); });
   } else {
     launch<JTile<double>>(st, GKB_KC_APPLY, ps, dim3(BX, BY), [&](int p, JTile<double>& j) {
       Solver& s = *S[p];
@@ -974,7 +994,7 @@ void Lockstep::Impl::capture(cudaStream_t st, cudaStream_t sb, cudaStream_t sc) 
   const cudaGraphConditionalHandle h_fin = new_handle(sb), h_al = new_handle(sb), h_init = new_handle(sb),
                                    h_outer = new_handle(sb), h_next = new_handle(sb), h_start = new_handle(sb);
   ctl(sb, K_PRE, {h_fin, h_al, h_init, h_outer});
-  cg_body(sb);
+  cg_body(sb, sc);
   if_node(sb, sc, h_fin, 2, [&](cudaStream_t s_) { cg_suffix(s_); });
   // after the inner solve of Eq. (3): b = r - A^T y0, beta_1, q_1, f = A q_1
   if_node(sb, sc, h_al, 3, [&](cudaStream_t s_) {
@@ -1091,7 +1111,7 @@ Lockstep::Lockstep(Solver* const* S, int count, cudaStream_t cap1, cudaStream_t 
   M.n = count;
   M.mixed = S[0]->opt.precision == GKB_PREC_MIXED;
   M.state.alloc(11 * (size_t)count);
-  M.counts.alloc(8);
+  M.counts.alloc(9);
   std::vector<GkbState*> sp(count);
   std::vector<CgState*> cp(count);
   for (int p = 0; p < count; ++p) {
@@ -1141,18 +1161,18 @@ Lockstep::~Lockstep() {
 }
 
 void Lockstep::launch(cudaStream_t s) {
-  GKB_CUDA(cudaMemsetAsync(I->counts.p, 0, 8 * sizeof(unsigned long long), s));
+  GKB_CUDA(cudaMemsetAsync(I->counts.p, 0, 9 * sizeof(unsigned long long), s));
   GKB_CUDA(cudaGraphLaunch(I->exec, s));
 }
 
 void Lockstep::launch_counts(cudaStream_t s, long long out[GKB_KC_COUNT]) {
-  unsigned long long c[8] = {};
+  unsigned long long c[9] = {};
   GKB_CUDA(cudaMemcpyAsync(c, I->counts.p, sizeof(c), cudaMemcpyDeviceToHost, s));
   GKB_CUDA(cudaStreamSynchronize(s));
-  // section 0 once; 1 every iteration; 2..7 when taken (c[1..6])
+  // section 0 once; 1 every iteration; 2..8 when taken (c[1..7])
   for (int k = 0; k < GKB_KC_COUNT; ++k) {
     long long v = I->cl[0][k] + (long long)c[0] * I->cl[1][k];
-    for (int t = 2; t < 8; ++t) v += (long long)c[t - 1] * I->cl[t][k];
+    for (int t = 2; t < 9; ++t) v += (long long)c[t - 1] * I->cl[t][k];
     out[k] = v;
   }
 }

@@ -392,6 +392,14 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
       V.table.alloc(Ops<T>::patch_table_len(V.L));
       Ops<T>::patch_table(V.L, V.table.p, s);
       GKB_CUDA(cudaGetLastError());
+      const long long fo = Ops<T>::fold3_interior_offset(V.L);
+      V.fold_in.clear();
+      if (fo >= 0) {
+        std::vector<T> h(48);
+        GKB_CUDA(cudaMemcpyAsync(h.data(), V.table.p + fo, 48 * sizeof(T), cudaMemcpyDeviceToHost, s));
+        GKB_CUDA(cudaStreamSynchronize(s));
+        V.fold_in.assign(h.begin(), h.end());
+      }
     }
   }
   // power iteration for lambda_max(C M) on every smoothing level
@@ -550,7 +558,8 @@ void Gmg<T>::smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s) {
       Ops<T>::residual(V.L, x, b, V.r.p, s);
       r = V.r.p;
     }
-    Ops<T>::cheb(V.L, r, x, V.d.p, (T)V.ca[k], (T)V.cb[k], (k == 0 && x_zero) ? 1 : 0, V.table.p, s);
+    Ops<T>::cheb(V.L, r, x, V.d.p, (T)V.ca[k], (T)V.cb[k], (k == 0 && x_zero) ? 1 : 0, V.table.p, s,
+                 V.fold_in.empty() ? nullptr : V.fold_in.data());
   }
 }
 

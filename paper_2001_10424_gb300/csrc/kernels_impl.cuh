@@ -813,39 +813,73 @@ __device__ __forceinline__ T fold3_apply(const Lvl& L, const T* __restrict__ r, 
   return acc;
 }
 
+// one Chebyshev step at one position: d, x are read before the stencil so
+// that their loads overlap it
+template <typename T, int C, bool Inner, class Coef>
+__device__ __forceinline__ void cheb3_face(const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
+                                           T* __restrict__ d, T ca, T cb, int x_zero, int p0, Coef f) {
+  const int id = (int)L.off[C] + p0;
+  const T dold = (cb != (T)0) ? d[id] : (T)0;
+  const T xold = x_zero ? (T)0 : x[id];
+  const T z = fold3_apply<T, C, Inner>(L, r, p0, f);
+  const T dn = (cb != (T)0) ? ca * z + cb * dold : ca * z;
+  d[id] = dn;
+  x[id] = x_zero ? dn : xold + dn;
+}
+
 // one Chebyshev step of the 3D constant-viscosity smoother through the class
-// stencils (levels with at least six cells on every axis): interior
-// positions take the stencils from the kernel parameter, the others from the
-// table; d and x are read before the stencil so that their loads overlap it
+// stencils (levels with at least six cells on every axis). Every thread
+// walks CHEB3_KZ planes; blocks whose positions are all interior take the
+// interior stencils from the kernel parameter (the constant bank) with no
+// per-face checks, the others the table's stencil of each position's class.
+constexpr int CHEB3_KZ = 4;
+
 template <typename T>
 __device__ __forceinline__ void cheb3_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
                                            T* __restrict__ d, T ca, T cb, int x_zero, const T* __restrict__ table,
                                            const Fold3In<T>& fin) {
-  const int i = B.x * BX + threadIdx.x;
-  const int j = B.y * BY + threadIdx.y;
-  const int k = B.z;
-  if (i > L.n[0] || j > L.n[1]) return;
-  const int pc = (cls7(i, L.n[0]) * 7 + cls7(j, L.n[1])) * 7 + cls7(k, L.n[2]);
-  const int p0 = (int)cix(L, i, j, k);
-  const T* fold = table + FOLD3_OFF + (size_t)pc * 48;
-#define GKB_CHEB3(C)                                                                     \
-  if (in_store<C>(L, i, j, k) && face_active<C>(L, i, j, k)) {                           \
-    const int id = (int)L.off[C] + p0;                                                   \
-    const T dold = (cb != (T)0) ? d[id] : (T)0;                                          \
-    const T xold = x_zero ? (T)0 : x[id];                                                \
-    T z;                                                                                 \
-    if (pc == FOLD3_INTERIOR)                                                            \
-      z = fold3_apply<T, C, true>(L, r, p0, [&](int q) { return fin.c[C][q]; });        \
-    else                                                                                 \
-      z = fold3_apply<T, C, false>(L, r, p0, [&](int q) { return __ldg(fold + C * 16 + q); }); \
-    const T dn = (cb != (T)0) ? ca * z + cb * dold : ca * z;                             \
-    d[id] = dn;                                                                          \
-    x[id] = x_zero ? dn : xold + dn;                                                     \
+  const int i0 = B.x * BX, j0 = B.y * BY, k0 = B.z * CHEB3_KZ;
+  const int i = i0 + threadIdx.x;
+  const int j = j0 + threadIdx.y;
+  const bool inner = i0 >= 3 && i0 + BX - 1 <= L.n[0] - 3 && j0 >= 3 && j0 + BY - 1 <= L.n[1] - 3 && k0 >= 3 &&
+                     k0 + CHEB3_KZ - 1 <= L.n[2] - 3;
+  const int P = L.P, S = (int)L.S;
+  if (inner) {
+#pragma unroll
+    for (int kk = 0; kk < CHEB3_KZ; ++kk) {
+      const int p0 = (k0 + kk) * S + j * P + i;
+      cheb3_face<T, 0, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[0][q]; });
+      cheb3_face<T, 1, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[1][q]; });
+      cheb3_face<T, 2, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[2][q]; });
+    }
+    return;
   }
-  GKB_CHEB3(0)
-  GKB_CHEB3(1)
-  GKB_CHEB3(2)
-#undef GKB_CHEB3
+  if (i > L.n[0] || j > L.n[1]) return;
+  const int cxy = (cls7(i, L.n[0]) * 7 + cls7(j, L.n[1])) * 7;
+  for (int kk = 0; kk < CHEB3_KZ; ++kk) {
+    const int k = k0 + kk;
+    if (k > L.n[2]) break;
+    const int pc = cxy + cls7(k, L.n[2]);
+    const int p0 = k * S + j * P + i;
+    const T* fold = table + FOLD3_OFF + (size_t)pc * 48;
+    if (pc == FOLD3_INTERIOR) {
+      cheb3_face<T, 0, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[0][q]; });
+      cheb3_face<T, 1, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[1][q]; });
+      cheb3_face<T, 2, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[2][q]; });
+      continue;
+    }
+    if (in_store<0>(L, i, j, k) && face_active<0>(L, i, j, k))
+      cheb3_face<T, 0, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + q); });
+    if (in_store<1>(L, i, j, k) && face_active<1>(L, i, j, k))
+      cheb3_face<T, 1, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 16 + q); });
+    if (in_store<2>(L, i, j, k) && face_active<2>(L, i, j, k))
+      cheb3_face<T, 2, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 32 + q); });
+  }
+}
+
+// the launch grid of k_cheb3: 32 x 8 positions per block, CHEB3_KZ planes
+inline dim3 cheb3_grid(const Lvl& L) {
+  return dim3((L.n[0] + 1 + BX - 1) / BX, (L.n[1] + 1 + BY - 1) / BY, (L.n[2] + 1 + CHEB3_KZ - 1) / CHEB3_KZ);
 }
 
 // the class stencils serve 3D constant-viscosity levels with the fast paths

@@ -882,6 +882,125 @@ inline dim3 cheb3_grid(const Lvl& L) {
   return dim3((L.n[0] + 1 + BX - 1) / BX, (L.n[1] + 1 + BY - 1) / BY, (L.n[2] + 1 + CHEB3_KZ - 1) / CHEB3_KZ);
 }
 
+// ---- 2D constant viscosity: folded stencils for every position class ------
+// The same construction with one orientation (vertex patches, E = 2): per
+// (position class, component) a 7-point stencil, the face itself and the six
+// other faces of its two patches, after FOLD3_OFF with the 3D layout (48
+// entries per class, 16 per component).
+constexpr int FOLD2_CLASSES = 49;
+constexpr int FOLD2_INTERIOR = 3 * 7 + 3;
+
+template <typename T>
+__global__ void k_fold2_table(Lvl L, T* table) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (L.dim != 2 || t >= FOLD2_CLASSES * 2) return;
+  const int C = t % 2, pc = t / 2;
+  const int p[3] = {rep7(pc / 7, L.n[0]), rep7(pc % 7, L.n[1]), 0};
+  double acc[13];
+#pragma unroll
+  for (int q = 0; q < 13; ++q) acc[q] = 0.0;
+  fold3_orient<T, 2>(L, table, p, C, acc, 1);
+  T* f = table + FOLD3_OFF + (size_t)pc * 48 + C * 16;
+  for (int q = 0; q < 16; ++q) f[q] = q < 7 ? (T)acc[q] : (T)0;
+}
+
+// the interior class's 2D stencils scaled by the Chebyshev step's ca, as a
+// kernel parameter
+template <typename T>
+struct Fold2In {
+  T c[2][7];
+};
+
+// (C r) at an active face of component C by the 7-point stencil f (2D);
+// Inner == false reads only faces with nonzero coefficients
+template <typename T, int C, bool Inner, class Coef>
+__device__ __forceinline__ T fold2_apply(const Lvl& L, const T* __restrict__ r, int cb, Coef f) {
+  const int P = L.P;
+  const T* ra = r + L.off[0] + cb;
+  const T* rb = r + L.off[1] + cb;
+  T acc = f(0) * __ldg(C == 0 ? ra : rb);
+  const T* base[6];
+  int o[6];
+  if (C == 0) {
+    base[0] = ra; o[0] = -P; base[1] = rb; o[1] = -1; base[2] = rb; o[2] = 0;
+    base[3] = ra; o[3] = P; base[4] = rb; o[4] = P - 1; base[5] = rb; o[5] = P;
+  } else {
+    base[0] = ra; o[0] = -P; base[1] = ra; o[1] = 0; base[2] = rb; o[2] = -1;
+    base[3] = ra; o[3] = 1 - P; base[4] = ra; o[4] = 1; base[5] = rb; o[5] = 1;
+  }
+#pragma unroll
+  for (int u = 0; u < 6; ++u) {
+    const T c = f(1 + u);
+    if (Inner || c != (T)0) acc += c * __ldg(base[u] + o[u]);
+  }
+  return acc;
+}
+
+// one Chebyshev step of the 2D constant-viscosity smoother through the class
+// stencils (levels with at least six cells per axis). Blocks whose positions
+// are all interior use the kernel parameter's stencils, already scaled by
+// ca (d = z + cb d); the others each position's class stencil from the table.
+template <typename T>
+__device__ __forceinline__ void cheb2_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
+                                           T* __restrict__ d, T ca, T cb, int x_zero, const T* __restrict__ table,
+                                           const Fold2In<T>& fs) {
+  const int i0 = B.x * BX, j0 = B.y * BY;
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  const int P = L.P;
+  if (i0 >= 3 && i0 + BX - 1 <= L.n[0] - 3 && j0 >= 3 && j0 + BY - 1 <= L.n[1] - 3) {
+    const int p0 = j * P + i;
+#define GKB_CHEB2_IN(C)                                                                  \
+    {                                                                                    \
+      const int id = (int)L.off[C] + p0;                                                 \
+      const T dold = (cb != (T)0) ? d[id] : (T)0;                                        \
+      const T xold = x_zero ? (T)0 : x[id];                                              \
+      const T zs = fold2_apply<T, C, true>(L, r, p0, [&](int q) { return fs.c[C][q]; }); \
+      const T dn = (cb != (T)0) ? fma(cb, dold, zs) : zs;                                \
+      d[id] = dn;                                                                        \
+      x[id] = x_zero ? dn : xold + dn;                                                   \
+    }
+    GKB_CHEB2_IN(0)
+    GKB_CHEB2_IN(1)
+#undef GKB_CHEB2_IN
+    return;
+  }
+  if (i > L.n[0] || j > L.n[1]) return;
+  const int pc = cls7(i, L.n[0]) * 7 + cls7(j, L.n[1]);
+  const int p0 = j * P + i;
+  const T* fold = table + FOLD3_OFF + (size_t)pc * 48;
+#define GKB_CHEB2(C)                                                                              \
+  if (in_store<C>(L, i, j, 0) && face_active<C>(L, i, j, 0)) {                                    \
+    const int id = (int)L.off[C] + p0;                                                            \
+    const T dold = (cb != (T)0) ? d[id] : (T)0;                                                   \
+    const T xold = x_zero ? (T)0 : x[id];                                                         \
+    const T z = fold2_apply<T, C, false>(L, r, p0, [&](int q) { return __ldg(fold + C * 16 + q); }); \
+    const T dn = (cb != (T)0) ? ca * z + cb * dold : ca * z;                                      \
+    d[id] = dn;                                                                                   \
+    x[id] = x_zero ? dn : xold + dn;                                                              \
+  }
+  GKB_CHEB2(0)
+  GKB_CHEB2(1)
+#undef GKB_CHEB2
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY) k_cheb2(Lvl L, const T* __restrict__ r, T* __restrict__ x,
+                                                   T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
+                                                   const __grid_constant__ Fold2In<T> fs) {
+  cheb2_body<T>(native_blk(), L, r, x, d, ca, cb, x_zero, table, fs);
+}
+
+inline bool cheb2_level(const Lvl& L) { return L.dim == 2 && L.fast && L.n[0] >= 6 && L.n[1] >= 6; }
+
+// the interior stencils of a 2D level (host copy, 2 x 16 values) scaled by ca
+template <typename T>
+inline Fold2In<T> fold2_scaled(const double* fold_in, double ca) {
+  Fold2In<T> f;
+  for (int c = 0; c < 2; ++c)
+    for (int q = 0; q < 7; ++q) f.c[c][q] = (T)(ca * fold_in[c * 16 + q]);
+  return f;
+}
+
 // the class stencils serve 3D constant-viscosity levels with the fast paths
 // on and at least six cells on every axis
 inline bool cheb3_level(const Lvl& L) {

@@ -66,11 +66,14 @@ void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_
   ProfScope ps_(GKB_KC_SMOOTH, s, lvl_unknowns(L));
   if (GKB_VARMU(L)) {
     launch_cheb_varmu(L, r, x, d, ca, cb, x_zero, table, s);
-  } else if (fold_in && cheb3_applies(L, table)) {
+  } else if (fold_in && table && cheb3_level(L)) {
     Fold3In<KT> f;
     for (int c = 0; c < 3; ++c)
       for (int q = 0; q < 13; ++q) f.c[c][q] = (KT)fold_in[c * 16 + q];
     k_cheb3<KT><<<cheb3_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);
+  } else if (fold_in && table && cheb2_level(L)) {
+    const Fold2In<KT> f = fold2_scaled<KT>(fold_in, (double)ca);
+    k_cheb2<KT><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);
   } else {
     k_cheb<KT, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table);
   }
@@ -101,14 +104,16 @@ void Ops<KT>::patch(const Lvl& L, const KT* r, KT* z, const KT* table, cudaStrea
 template <>
 long long Ops<KT>::patch_table_len(const Lvl& L) {
   // class inverses, the 3D interior stencils, then the 3D class stencils
-  if (!GKB_VARMU(L)) return FOLD3_OFF + (L.dim == 3 ? FOLD3_CLASSES * 3 * 16 : 0);
+  if (!GKB_VARMU(L)) return FOLD3_OFF + 48LL * (L.dim == 3 ? FOLD3_CLASSES : FOLD2_CLASSES);
   return (L.dim == 3 ? 3 : 1) * 10 * vtab_plane(L);
 }
 
 template <>
-long long Ops<KT>::fold3_interior_offset(const Lvl& L) {
-  if (GKB_VARMU(L) || !cheb3_level(L)) return -1;
-  return FOLD3_OFF + 48LL * FOLD3_INTERIOR;
+long long Ops<KT>::fold_interior_offset(const Lvl& L) {
+  if (GKB_VARMU(L)) return -1;
+  if (cheb3_level(L)) return FOLD3_OFF + 48LL * FOLD3_INTERIOR;
+  if (cheb2_level(L)) return FOLD3_OFF + 48LL * FOLD2_INTERIOR;
+  return -1;
 }
 
 template <>
@@ -119,6 +124,8 @@ void Ops<KT>::patch_table(const Lvl& L, KT* table, cudaStream_t s) {
     if (L.dim == 3) {
       k_patch_fold<KT><<<1, 32, 0, s>>>(L, table);
       k_fold3_table<KT><<<(FOLD3_CLASSES * 3 + 127) / 128, 128, 0, s>>>(L, table);
+    } else {
+      k_fold2_table<KT><<<1, 128, 0, s>>>(L, table);
     }
     return;
   }

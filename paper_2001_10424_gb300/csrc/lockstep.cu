@@ -100,11 +100,17 @@ __global__ void __launch_bounds__(BX* BY) kb_tile(const JTile<T>* jobs, const un
   LS_RUN(JTile<T>, mac_tile_body<T, false, MODE, DOT>(B, job.L, job.wonly, job.x, job.b, job.y, job.red, job.fin, job.st, nullptr))
 }
 
+// use2: the level takes the class-stencil smoother (as Ops::cheb decides)
 template <typename T>
-struct JCheb { JobHead h; Lvl L; const T* r; T* x; T* d; T ca, cb; int x_zero; const T* table; };
+struct JCheb { JobHead h; Lvl L; const T* r; T* x; T* d; T ca, cb; int x_zero, use2; const T* table; Fold2In<T> fs; };
+template <typename T>
+__device__ __forceinline__ void cheb_job(const Blk& B, const JCheb<T>& job) {
+  if (job.use2) cheb2_body<T>(B, job.L, job.r, job.x, job.d, job.ca, job.cb, job.x_zero, job.table, job.fs);
+  else cheb_body<T, false>(B, job.L, job.r, job.x, job.d, job.ca, job.cb, job.x_zero, job.table);
+}
 template <typename T>
 __global__ void __launch_bounds__(BX* BY) kb_cheb(const JCheb<T>* jobs, const unsigned* map) {
-  LS_RUN(JCheb<T>, cheb_body<T, false>(B, job.L, job.r, job.x, job.d, job.ca, job.cb, job.x_zero, job.table))
+  LS_RUN(JCheb<T>, cheb_job<T>(B, job))
 }
 
 template <typename T>
@@ -518,6 +524,9 @@ struct Lockstep::Impl {
         j.cb = (T)V.cb[k];
         j.x_zero = first ? 1 : 0;
         j.table = V.table.p;
+        j.use2 = (!V.fold_in.empty() && V.table.p && cheb2_level(V.L)) ? 1 : 0;
+        // the same rounded ca as the single-problem launch (Ops::cheb gets T)
+        if (j.use2) j.fs = fold2_scaled<T>(V.fold_in.data(), (double)(T)V.ca[k]);
         return face_grid(V.L);
       }, kb_cheb<T>);
     }

@@ -18,9 +18,9 @@ struct Ops {
   // r = b - M x (x null: r = b); pred: device flag, launch is a no-op when 0
   static void residual(const Lvl& L, const T* x, const T* b, T* r, cudaStream_t s, const int* pred = nullptr);
   // one Chebyshev step of the patch smoother
-  // (fold_in: the 3D constant-viscosity class stencils of the interior class,
-  // 3 x 16 values of the table at fold3_interior_offset, read back at setup;
-  // null: the general kernel)
+  // (fold_in: the constant-viscosity class stencils of the interior class,
+  // 2 or 3 x 16 values of the table at fold_interior_offset, read back at
+  // setup; null: the general kernel)
   static void cheb(const Lvl& L, const T* r, T* x, T* d, T ca, T cb, int x_zero, const T* table,
                    cudaStream_t s, const double* fold_in = nullptr);
   // z = C r (additive patch preconditioner)
@@ -28,9 +28,9 @@ struct Ops {
   // length of the smoother's inverse table of level L: the patch classes
   // (3*75*16 entries) for constant viscosity, every patch for variable
   static long long patch_table_len(const Lvl& L);
-  // where the table holds the interior class's 3D stencils (-1: no such
-  // stencils on this level)
-  static long long fold3_interior_offset(const Lvl& L);
+  // where the table holds the interior class's 2D or 3D stencils (-1: no
+  // such stencils on this level)
+  static long long fold_interior_offset(const Lvl& L);
   static void patch_table(const Lvl& L, T* table, cudaStream_t s);
   // node (2D) / edge (3D) viscosity table of a variable-viscosity level
   static long long edge_table_len(const Lvl& L);

@@ -392,7 +392,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
       V.table.alloc(Ops<T>::patch_table_len(V.L));
       Ops<T>::patch_table(V.L, V.table.p, s);
       GKB_CUDA(cudaGetLastError());
-      const long long fo = Ops<T>::fold3_interior_offset(V.L);
+      const long long fo = Ops<T>::fold_interior_offset(V.L);
       V.fold_in.clear();
       if (fo >= 0) {
         std::vector<T> h(48);

@@ -80,7 +80,7 @@ struct Gmg {
     DevBuf<T> sl;               // coarse slopes for the 3D prolongation
     DevBuf<T> table;            // patch class inverses (constant viscosity)
     std::vector<double> ca, cb; // Chebyshev coefficients per step
-    std::vector<double> fold_in; // 3D constant viscosity: the interior class stencils (host copy)
+    std::vector<double> fold_in; // constant viscosity: the interior class stencils (host copy)
     double lam_max = 0;
   };
   std::vector<Level> lev;

@@ -908,9 +908,8 @@ def run_ours(args, ws, rank, local):
             # replacement (their error floor; the outer loop may not reach tau)
             forms["mixed_no_replacement"] = time_form("mixed", None, mixed_rtol=0.0, maxit=100,
                                                       name="mixed_no_replacement")
-            if wk.dim == 2:   # the paper's other inner Krylov method (host-sequenced)
-                forms["fgmres_fp64"] = time_form("fp64", None, autotune=0, inner=gk.GKB_INNER_FGMRES,
-                                                 name="fgmres_fp64")
+            if wk.dim == 2:   # the paper's other inner Krylov method (FGMRES(30), device-resident)
+                forms["fgmres_fp64"] = time_form("fp64", None, inner=gk.GKB_INNER_FGMRES, name="fgmres_fp64")
         if args.autotune:
             forms[wk.form + "_default_options"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=0,
                                                             name=wk.form + "_default_options")

@@ -263,6 +263,13 @@ static void capture_loop(cudaStream_t s, cudaStream_t sb, int body_phase, Pre pr
   post(s);
 }
 
+void capture_while(cudaStream_t s, cudaStream_t sb, int body_phase,
+                   const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& pre,
+                   const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& body,
+                   const std::function<void(cudaStream_t)>& post) {
+  capture_loop(s, sb, body_phase, pre, body, post);
+}
+
 // end any capture still open on these streams (error paths)
 static void abandon_captures(std::initializer_list<cudaStream_t> ss) {
   for (cudaStream_t st : ss) {
@@ -1071,6 +1078,7 @@ Solver::~Solver() {
   if (cap1) cudaStreamDestroy(cap1);
   if (cap2) cudaStreamDestroy(cap2);
   if (cap3) cudaStreamDestroy(cap3);
+  if (cap4) cudaStreamDestroy(cap4);
 }
 
 void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_, double gamma_, double n_scale_,
@@ -1226,11 +1234,12 @@ void Solver::set_problem(const gkb_grid* g, const double* viscosity, double mu0_
   stage_n.alloc(ncell);
   hist.alloc(4 * (size_t)(opt.maxit + 2));
   hist_inner.alloc((size_t)opt.maxit + 4);
-  // multigrid + CG (tuned first when asked)
+  // multigrid + CG (tuned first when asked; the FGMRES work space first, as
+  // the tuner times whole inner solves)
   tuned_ms = 0;
-  if (opt.autotune && use_gmg && opt.inner != GKB_INNER_FGMRES) autotune_inner(viscosity != nullptr, diag_n ? 1 : 0);
-  else build_inner();
   if (opt.inner == GKB_INNER_FGMRES) fgm.init(L64.nvel, opt.fgmres_restart);
+  if (opt.autotune && use_gmg) autotune_inner(viscosity != nullptr, diag_n ? 1 : 0);
+  else build_inner();
   stats.tuned_inner_ms = tuned_ms;
   attach_net_levels();
   GKB_CUDA(cudaStreamSynchronize(stream));
@@ -1288,7 +1297,7 @@ double Solver::time_inner_solve() {
     GKB_CUDA(cudaGraphInstantiate(&ge, g, 0));
   } catch (...) {
     if (P) P->phase = saved;
-    abandon_captures({cap2, cap1});
+    abandon_captures({cap4, cap3, cap2, cap1});
     if (g) cudaGraphDestroy(g);
     throw;
   }
@@ -1626,6 +1635,7 @@ void Solver::ensure_capture_streams() {
   if (!cap1) GKB_CUDA(cudaStreamCreateWithFlags(&cap1, cudaStreamNonBlocking));
   if (!cap2) GKB_CUDA(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
   if (!cap3) GKB_CUDA(cudaStreamCreateWithFlags(&cap3, cudaStreamNonBlocking));
+  if (!cap4) GKB_CUDA(cudaStreamCreateWithFlags(&cap4, cudaStreamNonBlocking));
 }
 
 // One inner solve x = M^-1 f in graph form (prefix; while; suffix), then its
@@ -1638,7 +1648,9 @@ void Solver::capture_inner(cudaStream_t s, cudaStream_t sb) {
   const long long len = L64.nvel;
   const double tol2 = opt.tol_inner * opt.tol_inner;
   const int maxit = opt.maxit_inner;
-  if (opt.precision == GKB_PREC_MIXED) {
+  if (opt.inner == GKB_INNER_FGMRES) {
+    capture_fgmres(*this, s, sb, sb == cap3 ? cap4 : cap3);
+  } else if (opt.precision == GKB_PREC_MIXED) {
     Cg<float>& c = cg32;
     float* zp = c.pre ? c.z.p : c.r.p;
     const int* upd = &cg_dev->update;
@@ -1801,7 +1813,7 @@ void Solver::capture_core(cudaStream_t s, cudaStream_t sb1, cudaStream_t sb2) {
 
 void Solver::build_solve_graph() {
   sgraph.destroy();
-  if (!opt.use_graph || opt.profile || opt.inner == GKB_INNER_FGMRES) return;  // FGMRES: host-sequenced
+  if (!opt.use_graph || opt.profile) return;
   ensure_capture_streams();
   Profiler* P = g_prof;
   if (P) {
@@ -1818,7 +1830,7 @@ void Solver::build_solve_graph() {
     GKB_CUDA(cudaGraphInstantiate(&sgraph.exec, g, 0));
   } catch (...) {
     if (P) P->phase = -1;
-    abandon_captures({cap3, cap2, cap1});
+    abandon_captures({cap4, cap3, cap2, cap1});
     if (g) cudaGraphDestroy(g);
     sgraph.exec = nullptr;
     throw;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -153,12 +154,25 @@ struct Fgmres {
   int m = 0;
   long long len = 0;
   DevBuf<double> V, Z, w, r, h, h2, y, part;
+  DevBuf<double> state;    // device-resident form: its state, H, cs, sn, g
+  DevBuf<double> vin, zt;  // the current basis vector and its V-cycle (fixed graph arguments)
   void init(long long len, int m);
 };
 
 struct Solver;
-// x = M^-1 f by FGMRES(m) with one V-cycle as right preconditioner (FP64)
+// x = M^-1 f by FGMRES(m) with one V-cycle as right preconditioner (FP64),
+// host-sequenced
 int fgmres_solve(Solver& S, const double* f, double* x, int* iters);
+// the same inner solve (S.f -> S.x) captured on the graph stream s capturing,
+// device-resident: its restart loop's body on sb, the Arnoldi loop's on sc;
+// the outcome goes to S.cg_dev as a CG solve's would
+void capture_fgmres(Solver& S, cudaStream_t s, cudaStream_t sb, cudaStream_t sc);
+// "pre; while (cond) body; post" on the graph stream s is capturing (body on
+// sb; pre ends by setting the condition, body with the kernel that updates it)
+void capture_while(cudaStream_t s, cudaStream_t sb, int body_phase,
+                   const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& pre,
+                   const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& body,
+                   const std::function<void(cudaStream_t)>& post);
 // [W A; A^T 0][w; p] = [g; r] by FGMRES(restart) with GKB to pc_tol as the
 // preconditioner; stops at ||b - K z||_2 <= tol ||b||_2 (compact I/O)
 int solve_preconditioned(Solver& S, const double* g, const double* r, double tol, int restart, int maxit,
@@ -213,7 +227,7 @@ struct Solver {
   DevBuf<double> stage_m, stage_n;             // compact staging for host I/O
   gkb_stats_t stats{};
   Profiler prof;
-  cudaStream_t cap1 = nullptr, cap2 = nullptr, cap3 = nullptr;  // private capture streams
+  cudaStream_t cap1 = nullptr, cap2 = nullptr, cap3 = nullptr, cap4 = nullptr;  // private capture streams
   SolveGraph sgraph;              // whole solve as one graph (use_graph, no profiling)
   DevBuf<int> hist_inner;         // CG iterations of each inner solve
   int generation = 0;             // bumped by every set_problem

@@ -1,6 +1,8 @@
 """The FGMRES(m) inner solver with a V-cycle as right preconditioner: GKB with
 it reaches the oracle's solution, with inner-iteration counts comparable to
-GMG-PCG, also when short restarts force several cycles."""
+GMG-PCG, also when short restarts force several cycles; the device-resident
+form (inside the whole-solve graph) takes the same iterations as the
+host-sequenced one."""
 import numpy as np
 import pytest
 
@@ -13,11 +15,12 @@ pytestmark = pytest.mark.gpu
 D = mac.DIRICHLET
 
 
-def _fgmres_handle(gk, n, mu, gamma, restart=30, precision=0):
+def _fgmres_handle(gk, n, mu, gamma, restart=30, precision=0, use_graph=1):
     import torch
     opt = gk.gkb_default_options()
     opt.inner = gk.GKB_INNER_FGMRES
     opt.precision = precision
+    opt.use_graph = use_graph
     opt.tol_inner = 1e-11
     opt.fgmres_restart = restart
     opt.stream = torch.cuda.current_stream().cuda_stream
@@ -66,3 +69,32 @@ def test_fgmres_argument_errors(lib):
         gk.gkb_create(opt)
     with pytest.raises(gk.GkbError):  # FP64 only
         _fgmres_handle(gk, (16, 16), 1.0, 10.0, precision=1)
+
+
+@pytest.mark.parametrize("restart", [30, 5])
+def test_device_resident_fgmres_matches_host_sequenced(lib, restart):
+    """The graph form keeps the Hessenberg column, the Givens rotations, the
+    back substitution and the restart test on the device; it must take the
+    host loop's iterations (outer and inner, restarts included) and reach
+    the same solution to rounding."""
+    gk = lib
+    n = (48, 40)
+    mu = np.exp(0.5 * np.random.default_rng(8).standard_normal(n))
+    grid, ops = oracle_problem(n, (D,) * 4, mu, 100.0)
+    g = np.random.default_rng(9).standard_normal(grid.m)
+    r = np.zeros(grid.n_cells)
+    out = []
+    for use_graph in (1, 0):
+        h = _fgmres_handle(gk, n, mu, 100.0, restart, use_graph=use_graph)
+        try:
+            rc, w, p = gpu_solve(gk, h, g, r, 1e-8, 5)
+            assert rc == gk.GKB_OK, gk.gkb_last_error(h)
+            st = gk.gkb_stats(h)
+            out.append((w, p, st["outer_iterations"], st["inner_iterations"], st["inner_solves"]))
+        finally:
+            gk.gkb_destroy(h)
+    (w1, p1, o1, i1, s1), (w0, p0, o0, i0, s0) = out
+    assert (o1, i1, s1) == (o0, i0, s0)
+    assert energy_rel(ops["M"], w1, w0) <= 1e-12
+    ref = oracle_truth(grid, ops, g, r)
+    assert energy_rel(ops["M"], w1, ref["w"]) <= 1e-8

@@ -351,13 +351,15 @@ class Workload:
 
 
 def make_handle(gk, torch, pr, wk, form, profile=0, learned=None, autotune=0, inner=None, variant=None,
-                mixed_rtol=None, maxit=1000):
+                mixed_rtol=None, maxit=1000, lockstep=0):
     """variant: None, or a combination of "ndiag" (N = h^d / mu, the
     viscosity-weighted pressure mass matrix) and "symgrad" (the
     symmetric-gradient viscous operator). mixed_rtol: the mixed form's
-    replacement trigger (0: the ablation without FP64 replacement)."""
+    replacement trigger (0: the ablation without FP64 replacement).
+    lockstep: the batch_lockstep option of gkb_solve_batched."""
     opt = gk.gkb_default_options()
     opt.autotune = autotune
+    opt.batch_lockstep = lockstep
     if wk.kernel_variant is not None:
         opt.kernel_variant = wk.kernel_variant
     opt.precision = gk.GKB_PREC_FP64 if form == "fp64" else gk.GKB_PREC_MIXED
@@ -397,14 +399,14 @@ class Bound:
     """Handles plus device/host buffers of a workload, and its step."""
 
     def __init__(self, gk, torch, wk, form, profile=0, subset=None, learned="default", autotune=0, inner=None,
-                 variant=None, mixed_rtol=None, maxit=1000):
+                 variant=None, mixed_rtol=None, maxit=1000, concurrent=True, lockstep=0):
         import numpy as np
         self.gk, self.torch, self.wk = gk, torch, wk
         probs = wk.problems if subset is None else [wk.problems[i] for i in subset]
         self.probs = probs
         lf = wk.learned if learned == "default" else learned
-        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner, variant, mixed_rtol, maxit)
-                   for pr in probs]
+        self.hs = [make_handle(gk, torch, pr, wk, form, profile, lf, autotune, inner, variant, mixed_rtol, maxit,
+                               lockstep) for pr in probs]
         self.g, self.r, self.w, self.p, self.w0, self.p0 = [], [], [], [], [], []
         for h, pr in zip(self.hs, probs):
             m, n = gk.gkb_layout(h)
@@ -420,6 +422,11 @@ class Bound:
             self.w0.append(torch.tensor(pr["w0"], device="cuda") if "w0" in pr else None)
             self.p0.append(torch.tensor(pr["p0"], device="cuda") if "p0" in pr else None)
         self.host = None
+        # several problems without initial guesses: one gkb_solve_batched
+        # call (a graph branch per problem, run concurrently), else one
+        # gkb_solve per problem in turn
+        self.batched = wk.batched or (concurrent and not profile and len(self.hs) > 1
+                                      and all(x is None for x in self.w0 + self.p0))
 
     def step(self, args, host=False):
         gk = self.gk
@@ -427,7 +434,7 @@ class Bound:
         w0 = [None if x is None else (x.cpu().pin_memory() if host else x) for x in self.w0] if host else self.w0
         p0 = [None if x is None else (x.cpu().pin_memory() if host else x) for x in self.p0] if host else self.p0
         status = []
-        if self.wk.batched:
+        if self.batched:
             status.append(gk.gkb_solve_batched(self.hs, g, r, args.tol, args.delay, w, p))
         else:
             for i, h in enumerate(self.hs):
@@ -761,6 +768,10 @@ def config(args, wk):
          "n_scale": "h^d", "l2": "flushed between steps (1 GiB write)",
          "parallelism": "replicas" if args.gpus > 1 else "single",
          "autotune": bool(getattr(args, "autotune", 0) > 0)}
+    if len(wk.problems) > 1:
+        c["solve"] = ("gkb_solve_batched: one graph launch, a branch per problem, run concurrently"
+                      if (wk.batched or all("w0" not in p and "p0" not in p for p in wk.problems))
+                      else "gkb_solve per problem, in turn")
     if len(sizes) <= 4:
         c["grid"] = [list(s) for s in sizes]
     else:
@@ -851,11 +862,12 @@ def run_ours(args, ws, rank, local):
     keep = wk.name in FULL_SIZE_ORACLE and not args.no_cpu_baseline
     form_solutions = {}
 
-    def time_form(form, learned, autotune=None, inner=None, variant=None, mixed_rtol=None, maxit=1000, name=None):
+    def time_form(form, learned, autotune=None, inner=None, variant=None, mixed_rtol=None, maxit=1000, name=None,
+                  concurrent=True, lockstep=0):
         autotune = args.autotune if autotune is None else autotune
         t_setup = time.perf_counter()
         B2 = Bound(gk, torch, wk, form, learned=learned, autotune=autotune, inner=inner, variant=variant,
-                   mixed_rtol=mixed_rtol, maxit=maxit)
+                   mixed_rtol=mixed_rtol, maxit=maxit, concurrent=concurrent, lockstep=lockstep)
         t_setup = time.perf_counter() - t_setup
         for _ in range(2):
             B2.step(args)
@@ -870,10 +882,18 @@ def run_ours(args, ws, rank, local):
             e1.synchronize()
             vals.append(e0.elapsed_time(e1) / 1e3)
         st2 = B2.stats()
-        out = {"s_per_step": statistics.mean(vals), "outer_iterations": [s["outer_iterations"] for s in st2],
-               "inner_iterations": [s["inner_iterations"] for s in st2],
-               "inner_fallbacks": [s["inner_fallbacks"] for s in st2],
-               "status": [s["status"] for s in st2]}
+        out = {"s_per_step": statistics.mean(vals)}
+        if wk.batched:
+            out["solves_per_s"] = len(st2) / out["s_per_step"]
+            out["inner_iterations_sum"] = sum(s["inner_iterations"] for s in st2)
+            out["launches_per_step"] = sum(sum(s["kernel_launches"].values()) for s in st2)
+        else:
+            out.update({"outer_iterations": [s["outer_iterations"] for s in st2],
+                        "inner_iterations": [s["inner_iterations"] for s in st2],
+                        "inner_fallbacks": [s["inner_fallbacks"] for s in st2],
+                        "status": [s["status"] for s in st2]})
+        if len(st2) > 1:
+            out["problems_concurrent"] = B2.batched
         if keep and name:
             torch.cuda.synchronize()
             form_solutions[name] = ([x.cpu().numpy() for x in B2.w], [x.cpu().numpy() for x in B2.p])
@@ -887,6 +907,9 @@ def run_ours(args, ws, rank, local):
         B2.destroy()
         return out
 
+    if not args.no_forms and wk.batched:
+        # the lock-step batched form on the same problems
+        forms["lockstep"] = time_form(wk.form, None, lockstep=1)
     if not args.no_forms and not wk.batched and wk.inner == 1:
         head = {"s_per_step": ms / 1e3, "outer_iterations": outer, "inner_iterations": inner,
                 "inner_fallbacks": [s["inner_fallbacks"] for s in stats]}
@@ -910,6 +933,8 @@ def run_ours(args, ws, rank, local):
                                                       name="mixed_no_replacement")
             if wk.dim == 2:   # the paper's other inner Krylov method (FGMRES(30), device-resident)
                 forms["fgmres_fp64"] = time_form("fp64", None, inner=gk.GKB_INNER_FGMRES, name="fgmres_fp64")
+            if len(wk.problems) > 1:   # the same problems solved one after another
+                forms[wk.form + "_sequential"] = time_form(wk.form, None, concurrent=False)
         if args.autotune:
             forms[wk.form + "_default_options"] = time_form(wk.form, None if not wk.learned else wk.learned, autotune=0,
                                                             name=wk.form + "_default_options")

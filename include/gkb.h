@@ -180,6 +180,14 @@ typedef struct {
                              / 2, coupling the components through the
                              node (2D) / edge (3D) viscosities; needs
                              Dirichlet velocity on every side                 */
+  int batch_lockstep;     /* gkb_solve_batched, read from hs[0]: 0 (default)
+                             captures every problem as one branch of the
+                             batch's graph; 1 runs a batch that qualifies
+                             (2D, GMG-PCG, Laplacian form, constant
+                             viscosity per problem, N = n I, one precision,
+                             smoother degree and iteration limits) in lock
+                             step: each step one kernel launch over all
+                             problems; other batches keep the branches     */
 } gkb_options;
 
 typedef struct {
@@ -272,16 +280,19 @@ int gkb_solve_preconditioned(gkb_handle h, const double* g, const double* r, dou
                              double pc_tol, int delay, double* w_out, double* p_out, int* iterations);
 
 /* Solve `count` independent problems in one CUDA graph launch (the batched
- * form; same method as gkb_solve for each). hs[i] is a handle set up with
- * gkb_set_problem or gkb_set_problem_n, all on one device, with use_graph = 1 and profile = 0.
- * g[i], r[i] (inputs) and w_out[i], p_out[i] (outputs) are problem i's
- * compact vectors, host or device memory. Every problem's whole solve, with
- * its device-side loops, is one branch of a single graph; the branches run
- * concurrently and each stops on its own estimate. The graph for a list of
- * handles is captured at its first call and reused while none of the handles
- * is re-set or destroyed. Runs on the stream of hs[0]. Returns OK when every
- * problem returned OK, else the first non-OK status; per-problem statistics
- * via gkb_stats(hs[i]). */
+ * form; same method as gkb_solve for each, and the same result bit for bit).
+ * hs[i] is a handle set up with gkb_set_problem or gkb_set_problem_n, all on
+ * one device, with use_graph = 1 and profile = 0. g[i], r[i] (inputs) and
+ * w_out[i], p_out[i] (outputs) are problem i's compact vectors, host or device
+ * memory. By default every problem's whole solve, with its device-side loops,
+ * is one branch of a single graph; the branches run concurrently (one
+ * problem's latency-bound coarse levels overlap another's fine levels) and
+ * each stops on its own estimate. With hs[0]'s batch_lockstep = 1 a batch
+ * that qualifies runs in lock step instead (see gkb_options). The graph for a
+ * list of handles is captured at its first call and reused while none of the
+ * handles is re-set or destroyed. Runs on the stream of hs[0]. Returns OK when
+ * every problem returned OK, else the first non-OK status; per-problem
+ * statistics via gkb_stats(hs[i]). */
 int gkb_solve_batched(gkb_handle* hs, int count, const double* const* g, const double* const* r,
                       double tol, int delay, double* const* w_out, double* const* p_out);
 

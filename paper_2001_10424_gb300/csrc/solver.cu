@@ -2274,12 +2274,10 @@ struct BatchGraph {
   }
 };
 
-// GKB_BATCH_MODE=branches keeps the one-branch-per-problem form for batches
-// the lock-step form could take (for comparisons)
+// the first handle's batch_lockstep option asks for the lock-step form; a
+// batch that does not qualify keeps one graph branch per problem
 bool lockstep_wanted(Solver** S, int count) {
-  const char* m = getenv("GKB_BATCH_MODE");
-  if (m && strcmp(m, "branches") == 0) return false;
-  return lockstep_eligible(S, count);
+  return S[0]->opt.batch_lockstep == 1 && lockstep_eligible(S, count);
 }
 
 std::mutex g_batch_mutex;

@@ -1,12 +1,13 @@
 """Batched form: many independent cavities solved in one graph launch.
 
-Eligible batches (2D, constant viscosity per problem, GMG-PCG) run in lock
-step: every step of the solve is one launch over all problems, with each
-problem's blocks running the body of its own launch (same grid, same
-reduction buffers) and per-problem snapshot flags deciding which problems
-take part in each loop iteration. Other batches capture every problem's
-whole solve as one branch of the graph. Either way each problem must match
-its own individual solve bit for bit, and the oracle within the FP64 bound.
+By default every problem's whole solve is one branch of the graph. With the
+batch_lockstep option, batches that qualify (2D, constant viscosity per
+problem, GMG-PCG) run in lock step instead: every step of the solve is one
+launch over all problems, with each problem's blocks running the body of its
+own launch (same grid, same reduction buffers) and per-problem snapshot flags
+deciding which problems take part in each loop iteration. Either way each
+problem must match its own individual solve bit for bit, and the oracle
+within the FP64 bound.
 """
 import numpy as np
 import pytest
@@ -99,7 +100,7 @@ def test_lockstep_batch_with_uneven_problems(lib, prec):
     gammas = [100.0, 1.0, 1e4, 10.0, 100.0, 1000.0, 100.0]
     probs = workloads.batched2d(count=len(sides), seed_offset=61, sides=sides)
     probs[5]["g"] = np.zeros_like(probs[5]["g"])
-    hs = [make_handle(gk, pr["n"], pr["bc"], pr["mu"], gm, precision=prec, tol_inner=1e-11)
+    hs = [make_handle(gk, pr["n"], pr["bc"], pr["mu"], gm, precision=prec, tol_inner=1e-11, batch_lockstep=1)
           for pr, gm in zip(probs, gammas)]
     try:
         g = [torch.tensor(pr["g"], device="cuda") for pr in probs]
@@ -109,11 +110,13 @@ def test_lockstep_batch_with_uneven_problems(lib, prec):
         rc = gk.gkb_solve_batched(hs, g, r, 1e-8, 5, w, p)
         assert rc == gk.GKB_OK, gk.gkb_last_error(hs[0])
         stats_b = [gk.gkb_stats(h) for h in hs]
-        assert sum(stats_b[0]["kernel_launches"].values()) > 0
+        launches_b = sum(sum(st["kernel_launches"].values()) for st in stats_b)
+        assert launches_b > 0
         wb = [x.cpu().numpy() for x in w]
         pb = [x.cpu().numpy() for x in p]
         assert not np.any(wb[5]) and not np.any(pb[5])
         outer = []
+        launches_i = 0
         for i, h in enumerate(hs):
             wi = torch.empty_like(w[i])
             pi = torch.empty_like(p[i])
@@ -123,7 +126,11 @@ def test_lockstep_batch_with_uneven_problems(lib, prec):
             assert st["outer_iterations"] == stats_b[i]["outer_iterations"], i
             assert st["inner_iterations"] == stats_b[i]["inner_iterations"], i
             assert np.array_equal(wi.cpu().numpy(), wb[i]) and np.array_equal(pi.cpu().numpy(), pb[i]), i
+            launches_i += sum(st["kernel_launches"].values())
         assert max(outer) >= 2 * min(o for o in outer if o > 0)
+        # lock step: one launch per step for all problems, far fewer than
+        # the individual solves' launches together
+        assert launches_b < launches_i / 2, (launches_b, launches_i)
         pr = probs[3]
         grid, ops = oracle_problem(pr["n"], pr["bc"], pr["mu"], gammas[3])
         ref = oracle_truth(grid, ops, pr["g"], pr["r"])

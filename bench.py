@@ -467,6 +467,10 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     n_profiled = len(B.hs)
     ms, units, launches = {}, {}, {}
     smooth_fl = 0.0    # smoother flops of all profiled handles (degree per handle)
+    # the profiled solves are the capture range of a profiler started with
+    # its collection off (ncu --profile-from-start off); no-ops otherwise
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     for i, h in enumerate(B.hs):
         gk.gkb_solve(h, B.g[i], B.r[i], args.tol, args.delay, B.w[i], B.p[i], B.w0[i], B.p0[i])
         st = gk.gkb_stats(h)
@@ -475,6 +479,8 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
             units[k] = units.get(k, 0) + st["kernel_units"][k]
             launches[k] = launches.get(k, 0) + st["kernel_launches"][k]
         smooth_fl += st["kernel_units"]["smooth"] * smooth_flops(wk.dim, gk.gkb_get_options(h).smoother_degree)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     B.destroy()
     table = PER_UNIT[wk.dim]
     cand = {k: v for k, v in ms.items() if k in table or (k == "unet" and wk.learned)}

@@ -52,7 +52,8 @@ struct Lvl {
   int fast;           // deep-interior fast paths enabled
   double g2;          // gc * ascale^2: grad-div coupling of two faces of a cell
   double wmu;         // wscale * mu0
-  float mu0f, wscalef, ascalef, g2f, wmuf;
+  double wkd;         // 2d * wmu: the diagonal of a regular constant-viscosity W row
+  float mu0f, wscalef, ascalef, g2f, wmuf, wkdf;
 };
 
 // Coordinates of a thread block in the grid of one problem's launch and that
@@ -74,11 +75,13 @@ inline void finish_level(Lvl& L) {
   L.has_gd = (L.gc != 0.0) ? 1 : 0;
   L.g2 = L.gc * L.ascale * L.ascale;
   L.wmu = L.wscale * L.mu0;
+  L.wkd = (L.dim == 3 ? 6.0 : 4.0) * L.wmu;
   L.mu0f = (float)L.mu0;
   L.wscalef = (float)L.wscale;
   L.ascalef = (float)L.ascale;
   L.g2f = (float)L.g2;
   L.wmuf = (float)L.wmu;
+  L.wkdf = (float)L.wkd;
 }
 
 // per-precision level constants
@@ -89,6 +92,7 @@ template <> struct Kc<double> {
   static __host__ __device__ __forceinline__ double as(const Lvl& L) { return L.ascale; }
   static __host__ __device__ __forceinline__ double g2(const Lvl& L) { return L.g2; }
   static __host__ __device__ __forceinline__ double wmu(const Lvl& L) { return L.wmu; }
+  static __host__ __device__ __forceinline__ double wkd(const Lvl& L) { return L.wkd; }
 };
 template <> struct Kc<float> {
   static __host__ __device__ __forceinline__ float mu0(const Lvl& L) { return L.mu0f; }
@@ -96,6 +100,7 @@ template <> struct Kc<float> {
   static __host__ __device__ __forceinline__ float as(const Lvl& L) { return L.ascalef; }
   static __host__ __device__ __forceinline__ float g2(const Lvl& L) { return L.g2f; }
   static __host__ __device__ __forceinline__ float wmu(const Lvl& L) { return L.wmuf; }
+  static __host__ __device__ __forceinline__ float wkd(const Lvl& L) { return L.wkdf; }
 };
 
 // number of velocity unknowns (active faces) of a level

@@ -55,23 +55,43 @@ __device__ __forceinline__ bool deep_interior(const Lvl& L, int i, int j, int k)
 // velocity -> velocity stencils
 // ---------------------------------------------------------------------------
 
-// W row for constant viscosity: faces whose links are all regular (no wall,
-// no natural side) take wmu * (2d x_f - sum of the 2d neighbours); the rest
-// fall back to the general link-by-link row.
-template <typename T, int C>
-__device__ __forceinline__ T w_row_const(const Lvl& L, const T* x, const T* xc, const int p[3], T xf) {
+// A constant-viscosity face whose links are all regular (no wall, no
+// natural side): its W row is wmu * (2d x_f - sum of the 2d neighbours).
+template <int C>
+__device__ __forceinline__ bool const_regular(const Lvl& L, const int p[3]) {
   bool interior = p[C] >= 1 && p[C] <= L.n[C] - 1;
 #pragma unroll
   for (int A = 0; A < 3; ++A)
     if (A != C && A < L.dim) interior = interior && p[A] >= 1 && p[A] <= L.n[A] - 2;
-  if (interior) {
-    // xc points at this face; neighbours are +-1 (x), +-P (y), +-S (z)
-    T acc = __ldg(xc + 1) + __ldg(xc - 1) + __ldg(xc + L.P) + __ldg(xc - L.P);
-    if (L.dim == 3) acc += __ldg(xc + L.S) + __ldg(xc - L.S);
-    const T kd = (L.dim == 3) ? (T)6 : (T)4;
-    return Kc<T>::wmu(L) * (kd * xf - acc);
+  return interior;
+}
+
+// sum of the 2d neighbours of the face xc points at (+-1 in x, +-P in y,
+// +-S in z), in the order every path uses
+template <typename T>
+__device__ __forceinline__ T nb_sum(const Lvl& L, const T* xc) {
+  T acc = __ldg(xc + 1) + __ldg(xc - 1) + __ldg(xc + L.P) + __ldg(xc - L.P);
+  if (L.dim == 3) acc += __ldg(xc + L.S) + __ldg(xc - L.S);
+  return acc;
+}
+
+// M row of a regular constant-viscosity face, wmu (2d x_f - acc) +
+// g2 (dp - dm) (acc: nb_sum; dp, dm: the negative divergences of the cells
+// after and before the face; gd: with the grad-div term), as b - row (MODE 0)
+// or the row (MODE 1), in multiply-adds in one fixed order: every path that
+// forms this row (shared-memory tile, deep interior, general) computes it bit
+// for bit alike, with one FP64-pipe operation fewer than the factored form.
+template <typename T, int MODE>
+__device__ __forceinline__ T const_row(const Lvl& L, T b, T xf, T acc, bool gd, T dp, T dm) {
+  const T wmu = Kc<T>::wmu(L), wkd = Kc<T>::wkd(L), g2 = Kc<T>::g2(L);
+  if (MODE == 0) {
+    T t = gd ? fma(-g2, dp - dm, b) : b;
+    t = fma(wmu, acc, t);
+    return fma(-wkd, xf, t);
   }
-  return w_row<T, false, C>(L, x, p, xf) * Kc<T>::ws(L);
+  T t = gd ? g2 * (dp - dm) : (T)0;
+  t = fma(-wmu, acc, t);
+  return fma(wkd, xf, t);
 }
 
 // W row for variable viscosity at a deep-interior face (all links regular,
@@ -183,17 +203,13 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
   double dot = 0.0;
   if (tile2d && !VarMu) {
     // GKB_TILE_DEEP with every operand from the tiles
-    const T wmu = Kc<T>::wmu(L);
-    const T kd = (T)4;
     const int c = tx + 1, r = ty + 1;
 #define GKB_TILE_SMEM(C, DPLUS, DMINUS)                                          \
     {                                                                            \
       const long long id = L.off[C] + cb;                                        \
       const T xf = Tl[C][r][c];                                                  \
       T acc = Tl[C][r][c + 1] + Tl[C][r][c - 1] + Tl[C][r + 1][c] + Tl[C][r - 1][c]; \
-      T m = wmu * (kd * xf - acc);                                               \
-      if (gd) m += g2 * ((DPLUS) - (DMINUS));                                    \
-      const T val = (MODE == 0) ? b[id] - m : m;                                 \
+      const T val = const_row<T, MODE>(L, (MODE == 0) ? b[id] : (T)0, xf, acc, gd, DPLUS, DMINUS); \
       if (DOT) dot += (double)xf * (double)val;                                  \
       y[id] = val;                                                               \
     }
@@ -248,18 +264,13 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
       y[id] = val;
     }
   } else if (!VarMu && x != nullptr && deep_interior(L, i, j, k)) {
-    const T wmu = Kc<T>::wmu(L);
-    const T kd = (L.dim == 3) ? (T)6 : (T)4;
 #define GKB_TILE_DEEP(C, DPLUS, DMINUS)                                          \
     {                                                                            \
       const long long id = L.off[C] + cb;                                        \
       const T* xc = x + id;                                                      \
       const T xf = __ldg(xc);                                                    \
-      T acc = __ldg(xc + 1) + __ldg(xc - 1) + __ldg(xc + L.P) + __ldg(xc - L.P); \
-      if (L.dim == 3) acc += __ldg(xc + L.S) + __ldg(xc - L.S);                  \
-      T m = wmu * (kd * xf - acc);                                               \
-      if (gd) m += g2 * ((DPLUS) - (DMINUS));                                    \
-      const T val = (MODE == 0) ? b[id] - m : m;                                 \
+      const T acc = nb_sum<T>(L, xc);                                            \
+      const T val = const_row<T, MODE>(L, (MODE == 0) ? b[id] : (T)0, xf, acc, gd, DPLUS, DMINUS); \
       if (DOT) dot += (double)xf * (double)val;                                  \
       y[id] = val;                                                               \
     }
@@ -291,17 +302,21 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
     T val = 0;                                                                   \
     if (face_active<C>(L, i, j, k)) {                                            \
       T m = 0, xf = 0;                                                           \
+      bool fused = false;                                                        \
       if (x) {                                                                   \
         xf = x[id];                                                              \
         if (VarMu) {                                                             \
           m = mul_rn(w_row<T, VarMu, C>(L, x, p, xf), Kc<T>::ws(L));             \
           if (gd) m = fma(g2, (DPLUS) - (DMINUS), m);                            \
+        } else if (const_regular<C>(L, p)) {                                     \
+          fused = true;                                                          \
+          m = const_row<T, MODE>(L, (MODE == 0) ? b[id] : (T)0, xf, nb_sum<T>(L, x + id), gd, DPLUS, DMINUS); \
         } else {                                                                 \
-          m = w_row_const<T, C>(L, x, x + id, p, xf);                            \
+          m = w_row<T, false, C>(L, x, p, xf) * Kc<T>::ws(L);                    \
           if (gd) m += g2 * ((DPLUS) - (DMINUS));                                \
         }                                                                        \
       }                                                                          \
-      val = (MODE == 0) ? b[id] - m : m;                                         \
+      val = (MODE == 0 && !fused) ? b[id] - m : m;                               \
       if (DOT) dot += (double)xf * (double)val;                                  \
     }                                                                            \
     y[id] = val;                                                                 \
@@ -1285,15 +1300,59 @@ __device__ __forceinline__ T prolong_flux_val(const Lvl& Lc, const T* xc, int pc
   return (T)0.5 * (line_val(I) + line_val(I + 1)) + fix;
 }
 
-// xf += P xc (2D)
+// xf += P xc (2D), one thread per coarse cell (I, J): the cell's left and
+// bottom coarse faces and their tangential slopes are formed once and give
+// its 2 x 2 fine u faces (fine columns 2I, 2I+1) and v faces (fine rows 2J,
+// 2J+1) with the operations of prolong_flux_val; the extra column I = n_x
+// and row J = n_y of threads take the fine faces on the last coarse lines.
 template <typename T>
 __device__ __forceinline__ void prolong_flux2d_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* __restrict__ xc, T* __restrict__ xf) {
-  const int i = B.x * BX + threadIdx.x;
-  const int j = B.y * BY + threadIdx.y;
-  if (in_store<0>(Lf, i, j, 0) && face_active<0>(Lf, i, j, 0))
-    xf[Lf.off[0] + cix(Lf, i, j, 0)] += prolong_flux_val<T, 0>(Lc, xc, i, j);
-  if (in_store<1>(Lf, i, j, 0) && face_active<1>(Lf, i, j, 0))
-    xf[Lf.off[1] + cix(Lf, i, j, 0)] += prolong_flux_val<T, 1>(Lc, xc, j, i);
+  const int I = B.x * BX + threadIdx.x;
+  const int J = B.y * BY + threadIdx.y;
+  if (I > Lc.n[0] || J > Lc.n[1]) return;
+  const bool inx = I < Lc.n[0], iny = J < Lc.n[1];
+  auto add = [&](int C, int i, int j, T v) {
+    if (C == 0 ? (in_store<0>(Lf, i, j, 0) && face_active<0>(Lf, i, j, 0))
+               : (in_store<1>(Lf, i, j, 0) && face_active<1>(Lf, i, j, 0)))
+      xf[Lf.off[C] + cix(Lf, i, j, 0)] += v;
+  };
+  // u slopes (along y) on the cell's left and right faces, v slopes (along x)
+  // on its bottom and top faces
+  const T du0 = iny ? coarse_slope<T, 0>(Lc, xc, I, J) : (T)0;
+  const T du1 = (iny && inx) ? coarse_slope<T, 0>(Lc, xc, I + 1, J) : (T)0;
+  const T dv0 = inx ? coarse_slope<T, 1>(Lc, xc, I, J) : (T)0;
+  const T dv1 = (inx && iny) ? coarse_slope<T, 1>(Lc, xc, I, J + 1) : (T)0;
+  if (iny) {
+    const T u0 = coarse_face<T, 0>(Lc, xc, I, J, 0);
+    const T lo0 = u0 + (T)-1 * du0, hi0 = u0 + (T)1 * du0;  // coarse line I at fine rows 2J, 2J+1
+    add(0, 2 * I, 2 * J, lo0);
+    add(0, 2 * I, 2 * J + 1, hi0);
+    if (inx) {
+      const T u1 = coarse_face<T, 0>(Lc, xc, I + 1, J, 0);
+      const T lo1 = u1 + (T)-1 * du1, hi1 = u1 + (T)1 * du1;
+      const T fix = (T)0.5 * (dv1 - dv0);
+      add(0, 2 * I + 1, 2 * J, (T)0.5 * (lo0 + lo1) + fix);
+      add(0, 2 * I + 1, 2 * J + 1, (T)0.5 * (hi0 + hi1) + fix);
+    }
+  }
+  if (inx) {
+    const T v0 = coarse_face<T, 1>(Lc, xc, I, J, 0);
+    const T lo0 = v0 + (T)-1 * dv0, hi0 = v0 + (T)1 * dv0;  // coarse line J at fine columns 2I, 2I+1
+    add(1, 2 * I, 2 * J, lo0);
+    add(1, 2 * I + 1, 2 * J, hi0);
+    if (iny) {
+      const T v1 = coarse_face<T, 1>(Lc, xc, I, J + 1, 0);
+      const T lo1 = v1 + (T)-1 * dv1, hi1 = v1 + (T)1 * dv1;
+      const T fix = (T)0.5 * (du1 - du0);
+      add(1, 2 * I, 2 * J + 1, (T)0.5 * (lo0 + lo1) + fix);
+      add(1, 2 * I + 1, 2 * J + 1, (T)0.5 * (hi0 + hi1) + fix);
+    }
+  }
+}
+
+// launch grid of the 2D prolongation: the coarse cells plus one column and row
+inline dim3 prolong2d_grid(const Lvl& Lc) {
+  return dim3((Lc.n[0] + 1 + BX - 1) / BX, (Lc.n[1] + 1 + BY - 1) / BY, 1);
 }
 
 template <typename T>

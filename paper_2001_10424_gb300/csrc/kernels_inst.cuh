@@ -172,7 +172,7 @@ template <>
 void Ops<KT>::prolong(const Lvl& Lf, const Lvl& Lc, const KT* xc, KT* xf, KT* slopes, cudaStream_t s) {
   if (Lf.dim == 2) {
     ProfScope ps_(GKB_KC_PROLONG, s, lvl_unknowns(Lf));
-    k_prolong_flux2d<KT><<<face_grid(Lf), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
+    k_prolong_flux2d<KT><<<prolong2d_grid(Lc), dim3(BX, BY), 0, s>>>(Lf, Lc, xc, xf);
     return;
   }
   { ProfScope ps_(GKB_KC_PROLONG, s, 0); k_slopes3d<KT><<<face_grid(Lc), dim3(BX, BY), 0, s>>>(Lc, xc, slopes); }

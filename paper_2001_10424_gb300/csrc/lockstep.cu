@@ -607,7 +607,7 @@ struct Lockstep::Impl {
         j.Lc = G.lev[d + 1].L;
         j.xc = G.lev[d + 1].x.p;
         j.xf = xf(p);
-        return face_grid(j.Lf);
+        return prolong2d_grid(j.Lc);
       }, kb_prolong<T>);
       smooth<T>(st, ps, d, F, bf, xf, false);
     }

@@ -66,11 +66,12 @@ def run_bench_form(gk, args, autotune=1, learned="default", mixed_rtol=None, max
         B = bench.Bound(gk, torch, wk, wk.form, autotune=autotune, learned=learned, mixed_rtol=mixed_rtol,
                         maxit=maxit)
         try:
-            status = B.step(args)
+            B.step(args)
             torch.cuda.synchronize()
             ws = [x.cpu().numpy() for x in B.w]
             ps = [x.cpu().numpy() for x in B.p]
             stats = B.stats()
+            status = [st["status"] for st in stats]   # per problem (one batched call may cover several)
         finally:
             B.destroy()
     finally:

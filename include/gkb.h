@@ -166,7 +166,9 @@ typedef struct {
                              kernel_variant (0..2), coarse_max (8, 16, 32) and
                              cheb_lo (0.05, 0.1, 0.2, 0.3), one after another,
                              for the fastest inner solve (device time of one
-                             GMG-PCG solve to tol_inner) and keeps it; results
+                             GMG-PCG solve to tol_inner, best of three; within
+                             2 % of each other, the candidate with fewer
+                             iterations) and keeps it; results
                              are cached per device, grid, viscosity kind,
                              precision, inner solver and gamma decade in the
                              process and, when the environment variable

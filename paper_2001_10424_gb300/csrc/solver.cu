@@ -1278,7 +1278,7 @@ void Solver::build_inner() {
 // Device time (ms) of one inner solve M x = f, run as a captured graph like
 // the solver's own; +inf when it fails. f = A A^T h for a fixed pseudo-random
 // h lies in the range of A like the right-hand sides A q of the GKB loop.
-double Solver::time_inner_solve() {
+double Solver::time_inner_solve(int* its) {
   ensure_capture_streams();
   { ProfScope ps_(GKB_KC_LAYOUT, stream); k_fill_hash<double><<<fgrid(L64), dim3(32, 8), 0, stream>>>(L64, wtmp.p); }
   Ops<double>::negdiv(L64, wtmp.p, ctmp.p, 1.0, stream);
@@ -1308,7 +1308,7 @@ double Solver::time_inner_solve() {
   GKB_CUDA(cudaEventCreate(&e0));
   GKB_CUDA(cudaEventCreate(&e1));
   bool ok = true;
-  for (int rep = 0; rep < 3 && ok; ++rep) {
+  for (int rep = 0; rep < 4 && ok; ++rep) {
     GKB_CUDA(cudaEventRecord(e0, stream));
     GKB_CUDA(cudaGraphLaunch(ge, stream));
     GKB_CUDA(cudaEventRecord(e1, stream));
@@ -1318,6 +1318,7 @@ double Solver::time_inner_solve() {
     GKB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     ok = cg_host->status == ST_OK;
     if (rep > 0) best = std::min(best, (double)ms);  // the first launch warms up
+    if (its) *its = cg_host->it;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1329,6 +1330,7 @@ namespace {
 struct Tuned {
   int degree, variant, coarse_max;
   double lo, ms;
+  int its = 0;   // iterations of the timed solve (tie-break; not stored in the file)
 };
 std::mutex g_tune_mutex;
 std::map<std::string, Tuned> g_tune_cache;
@@ -1387,19 +1389,27 @@ void Solver::autotune_inner(bool var_mu, int weighted) {
     }
   }
   Tuned best{opt.smoother_degree, opt.kernel_variant, opt.coarse_max, opt.cheb_lo, 1e300};
+  // a candidate replaces the best when it is faster by more than the timing
+  // noise (2 %), or when the two are within it and the candidate needs fewer
+  // iterations (a stronger preconditioner: more work per launch, which also
+  // holds up better when several solves share the GPU)
   auto trial = [&](int deg, int var, int cmax, double lo) {
     opt.smoother_degree = deg;
     opt.kernel_variant = var;
     opt.coarse_max = cmax;
     opt.cheb_lo = lo;
     double ms = 1e300;
+    int its = 0;
     try {
       build_inner();
-      ms = time_inner_solve();
+      ms = time_inner_solve(&its);
     } catch (const Error& e) {
       if (e.code != GKB_ERR_INVALID_ARG) throw;  // an infeasible candidate (coarse level too large)
     }
-    if (ms < best.ms) best = Tuned{deg, var, cmax, lo, ms};
+    if (!(ms < 1e300)) return;
+    const bool faster = ms < 0.98 * best.ms;
+    const bool tie = !faster && ms <= 1.02 * best.ms && its < best.its;
+    if (faster || tie) best = Tuned{deg, var, cmax, lo, ms, its};
   };
   const double lo0 = best.lo;
   trial(best.degree, best.variant, best.coarse_max, lo0);

@@ -236,7 +236,7 @@ struct Solver {
   void set_net(Unet* u);
   double tuned_ms = 0;            // inner-solve time of the tuned configuration
   void build_inner();
-  double time_inner_solve();
+  double time_inner_solve(int* its = nullptr);  // device ms of one inner solve (best of 3)
   void autotune_inner(bool var_mu, int weighted);
   void attach_net_levels();
   void refresh_net();

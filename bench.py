@@ -91,9 +91,11 @@ VARMU_SMOOTH_EXTRA = {2: 5.0, 3: 10.0}
 # dominant kernel, from ncu captures of the current kernels (cold cache, one
 # launch each), keyed by (workload, form, kernel class)
 TRAFFIC = {
-    # 1024^2 FP64: first Chebyshev step (smooth) and residual of a V-cycle
-    ("stokes2d", "fp64", "smooth"): 16.86e6 + 0.05e6,
-    ("stokes2d", "fp64", "residual"): 33.72e6 + 0.05e6,
+    # 1024^2 FP64: first Chebyshev step (smooth, k_cheb2) and residual of a
+    # V-cycle (reads exactly the algorithmic vectors; the writes include
+    # lines left dirty before the launch)
+    ("stokes2d", "fp64", "smooth"): 16.79e6 + 45.57e6,
+    ("stokes2d", "fp64", "residual"): 33.72e6 + 34.30e6,
     # 2048^2 log-normal viscosity, mixed form
     ("varvisc2d", "mixed", "smooth"): 203.02e6 + 48.94e6,
     ("varvisc2d", "mixed", "residual"): 84.25e6 + 12.06e6,

@@ -339,6 +339,213 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
 }
 
 // ---------------------------------------------------------------------------
+// 3D constant-viscosity operator (mode 0: b - M x; mode 1: M x), split by
+// geometry. The box kernel takes the positions [1, n-2] on every axis, where
+// every face of every component is active and all its links are regular: a
+// block of 32 x 8 threads walks MAC3_KZ planes of a 32 x 8 column, keeping x of
+// three planes (u, v, w with a one-position halo) and the negative cell
+// divergences of two cell planes in shared memory as rings, the next plane's x
+// fetched into registers while the current one is computed; every face forms
+// the fused row (const_row) without tests. The shell kernel takes the other
+// positions, one thread each, with the general link-by-link row. Both use the
+// operations and roundings of k_mac_tile, so the results are bit for bit its.
+// ---------------------------------------------------------------------------
+constexpr int MAC3_KZ = 8;
+
+// levels that take the split kernels (smaller ones stay with k_mac_tile)
+inline bool mac3_level(const Lvl& L) {
+  return L.dim == 3 && L.n[0] >= 16 && L.n[1] >= 16 && L.n[2] >= 16;
+}
+inline dim3 mac3_grid(const Lvl& L) {
+  return dim3((L.n[0] - 2 + BX - 1) / BX, (L.n[1] - 2 + BY - 1) / BY, (L.n[2] - 2 + MAC3_KZ - 1) / MAC3_KZ);
+}
+// positions of the shell: the planes 0, n-1, n whole; on the other planes
+// the rows 0, n-1, n whole and the positions 0, n-1, n of the other rows
+inline long long mac3_shell_count(const Lvl& L) {
+  const long long nx = L.n[0] + 1, ny = L.n[1] + 1;
+  return 3 * nx * ny + (long long)(L.n[2] - 2) * (3 * nx + 3 * (ny - 3));
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wonly, const T* __restrict__ x,
+                                              const T* __restrict__ b, T* __restrict__ y) {
+  constexpr int TW = BX + 2, TH = BY + 2;
+  __shared__ T Xt[3][3][TH][TW];      // [plane slot][component][row][col]: position (i0-1+col, j0-1+row)
+  __shared__ T Dv[2][BY + 1][BX + 1];  // [cell plane parity][row][col]: cell (i0-1+col, j0-1+row)
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int i0 = 1 + (int)B.x * BX, j0 = 1 + (int)B.y * BY, k0 = 1 + (int)B.z * MAC3_KZ;
+  const int i = i0 + tx, j = j0 + ty;
+  const int kend = min(k0 + MAC3_KZ, L.n[2] - 1);  // planes k0 .. kend-1 (uniform over the block)
+  const bool mine = i <= L.n[0] - 2 && j <= L.n[1] - 2;
+  const bool gd = L.has_gd && !wonly;
+  auto slot = [](int k) { return k % 3; };   // k >= 0
+  // this thread's tile entries: (col, row) = (tx, ty), (tx + BX, ty) for
+  // tx < 2, (tx, ty + BY) and (tx + BX, ty + BY) for ty < 2; the planes
+  // k0-1 .. kend lie in [0, n-1], held by every component's box, so only x
+  // and y are tested (once); offsets relative to the corner (i0-1, j0-1)
+  const long long tb = (long long)(j0 - 1) * L.P + (i0 - 1);
+  int tofs[4];
+  bool tin[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int q = tx + (m & 1) * BX, r = ty + (m >> 1) * BY;
+    tin[m] = (q < TW) && (r < TH) && i0 - 1 + q <= L.n[0] && j0 - 1 + r <= L.n[1];
+    tofs[m] = r * L.P + q;
+  }
+  T pre[3][4];
+  auto fetch = [&](int k) {
+    const long long ks = (long long)k * L.S + tb;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const long long base = L.off[c] + ks;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pre[c][m] = tin[m] ? x[base + tofs[m]] : (T)0;
+    }
+  };
+  auto commit = [&](int k) {
+    const int sl = slot(k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Xt[sl][c][ty][tx] = pre[c][0];
+      if (tx < 2) Xt[sl][c][ty][tx + BX] = pre[c][1];
+      if (ty < 2) {
+        Xt[sl][c][ty + BY][tx] = pre[c][2];
+        if (tx < 2) Xt[sl][c][ty + BY][tx + BX] = pre[c][3];
+      }
+    }
+  };
+  // the cells this thread forms divergences for: (tx, ty); row BY for tid <
+  // BX; column BX for BX <= tid < BX + BY + 1 (cell planes k0-1 .. kend-1 lie
+  // in [0, n-2]; x and y tested once)
+  const int dci1 = (tid < BX) ? tid : BX, dcj1 = (tid < BX) ? BY : tid - BX;
+  const bool has1 = tid < BX + BY + 1;
+  const bool cin0 = i0 - 1 + tx < L.n[0] && j0 - 1 + ty < L.n[1];
+  const bool cin1 = has1 && i0 - 1 + dci1 < L.n[0] && j0 - 1 + dcj1 < L.n[1];
+  auto div_cell = [&](int kc, int ci, int cj, bool in) {
+    const int s0 = slot(kc), s1 = slot(kc + 1);
+    T dv = (T)0;
+    if (in) {
+      // the cell's low faces sit at tile [cj][ci] (neg_div_at's order)
+      dv = Xt[s0][0][cj][ci] - Xt[s0][0][cj][ci + 1] + Xt[s0][1][cj][ci] - Xt[s0][1][cj + 1][ci];
+      dv += Xt[s0][2][cj][ci] - Xt[s1][2][cj][ci];
+    }
+    Dv[kc & 1][cj][ci] = dv;
+  };
+  auto div_plane = [&](int kc) {
+    div_cell(kc, tx, ty, cin0);
+    if (has1) div_cell(kc, dci1, dcj1, cin1);
+  };
+  fetch(k0 - 1);
+  commit(k0 - 1);
+  fetch(k0);
+  commit(k0);
+  fetch(k0 + 1);
+  if (gd) {
+    __syncthreads();
+    div_plane(k0 - 1);
+  }
+  for (int k = k0; k < kend; ++k) {
+    const long long cb = cix(L, i, j, k);
+    T bv[3] = {(T)0, (T)0, (T)0};
+    commit(k + 1);
+    if (k + 1 < kend) fetch(k + 2);
+    if (MODE == 0 && mine) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) bv[c] = b[L.off[c] + cb];
+    }
+    __syncthreads();
+    if (gd) {
+      div_plane(k);
+      __syncthreads();
+    }
+    if (mine) {
+      const int sc = slot(k), su = slot(k + 1), sd = slot(k - 1);
+#define GKB_MAC3_FACE(C, DPLUS, DMINUS)                                                        \
+      {                                                                                        \
+        const T xf = Xt[sc][C][ty + 1][tx + 1];                                                \
+        T acc = Xt[sc][C][ty + 1][tx + 2] + Xt[sc][C][ty + 1][tx] + Xt[sc][C][ty + 2][tx + 1] + \
+                Xt[sc][C][ty][tx + 1];                                                         \
+        acc += Xt[su][C][ty + 1][tx + 1] + Xt[sd][C][ty + 1][tx + 1];                          \
+        y[L.off[C] + cb] = const_row<T, MODE>(L, bv[C], xf, acc, gd, gd ? (DPLUS) : (T)0,      \
+                                              gd ? (DMINUS) : (T)0);                           \
+      }
+      GKB_MAC3_FACE(0, Dv[k & 1][ty + 1][tx + 1], Dv[k & 1][ty + 1][tx])
+      GKB_MAC3_FACE(1, Dv[k & 1][ty + 1][tx + 1], Dv[k & 1][ty][tx + 1])
+      GKB_MAC3_FACE(2, Dv[k & 1][ty + 1][tx + 1], Dv[(k - 1) & 1][ty + 1][tx + 1])
+#undef GKB_MAC3_FACE
+    }
+    __syncthreads();  // the next plane's load and divergences overwrite slot k-1 and parity k-1
+  }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(BX* BY, 4) k_mac3_box(Lvl L, int wonly, const T* __restrict__ x,
+                                                        const T* __restrict__ b, T* __restrict__ y) {
+  mac3_box_body<T, MODE>(native_blk(), L, wonly, x, b, y);
+}
+
+// the shell: one thread per position, the three faces as k_mac_tile's
+// general path forms them (divergences from neg_div)
+template <typename T, int MODE>
+__global__ void k_mac3_shell(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
+                             T* __restrict__ y, long long count) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int nx = L.n[0] + 1, ny = L.n[1] + 1;
+  const long long full = (long long)nx * ny, ring = 3LL * nx + 3LL * (ny - 3);
+  int i, j, k;
+  if (t < 3 * full) {  // planes 0, n-1, n
+    const int pl = (int)(t / full);
+    const long long r = t - pl * full;
+    k = pl == 0 ? 0 : L.n[2] - 2 + pl;
+    j = (int)(r / nx);
+    i = (int)(r - (long long)j * nx);
+  } else {             // planes 1 .. n-2: rows 0, n-1, n, then the ends of the others
+    const long long u = t - 3 * full;
+    k = 1 + (int)(u / ring);
+    const long long r = u - (long long)(k - 1) * ring;
+    if (r < 3LL * nx) {
+      const int rw = (int)(r / nx);
+      j = rw == 0 ? 0 : L.n[1] - 2 + rw;
+      i = (int)(r - (long long)rw * nx);
+    } else {
+      const int e = (int)(r - 3LL * nx);
+      j = 1 + e / 3;
+      const int c = e - (j - 1) * 3;
+      i = c == 0 ? 0 : L.n[0] - 2 + c;
+    }
+  }
+  const bool gd = L.has_gd && !wonly;
+  const T g2 = Kc<T>::g2(L);
+  const int p[3] = {i, j, k};
+  const long long cb = cix(L, i, j, k);
+  const T d0 = gd ? neg_div<T>(L, x, i, j, k) : (T)0;
+#define GKB_MAC3_SHELL(C, DMINUS)                                                              \
+  if (in_store<C>(L, i, j, k)) {                                                               \
+    const long long id = L.off[C] + cb;                                                        \
+    T val = 0;                                                                                 \
+    if (face_active<C>(L, i, j, k)) {                                                          \
+      const T xf = x[id];                                                                      \
+      const T dm = gd ? (DMINUS) : (T)0;                                                       \
+      const T bb = (MODE == 0) ? b[id] : (T)0;                                                 \
+      if (const_regular<C>(L, p)) {                                                            \
+        val = const_row<T, MODE>(L, bb, xf, nb_sum<T>(L, x + id), gd, d0, dm);                 \
+      } else {                                                                                 \
+        T m = w_row<T, false, C>(L, x, p, xf) * Kc<T>::ws(L);                                  \
+        if (gd) m += g2 * (d0 - dm);                                                           \
+        val = (MODE == 0) ? bb - m : m;                                                        \
+      }                                                                                        \
+    }                                                                                          \
+    y[id] = val;                                                                               \
+  }
+  GKB_MAC3_SHELL(0, neg_div<T>(L, x, i - 1, j, k))
+  GKB_MAC3_SHELL(1, neg_div<T>(L, x, i, j - 1, k))
+  GKB_MAC3_SHELL(2, neg_div<T>(L, x, i, j, k - 1))
+#undef GKB_MAC3_SHELL
+}
+
+
+// ---------------------------------------------------------------------------
 // vertex (2D) / edge (3D) patch smoother: additive Schwarz over the patches
 // of faces around each node (2D) or edge (3D); the faces of one patch carry
 // the discrete curl of that node's / edge's hat function, i.e. a local

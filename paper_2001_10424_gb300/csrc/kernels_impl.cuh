@@ -350,20 +350,26 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
 // positions, one thread each, with the general link-by-link row. Both use the
 // operations and roundings of k_mac_tile, so the results are bit for bit its.
 // ---------------------------------------------------------------------------
-constexpr int MAC3_KZ = 8;
+constexpr int MAC3_KZ = 16;
 
 // levels that take the split kernels (smaller ones stay with k_mac_tile)
 inline bool mac3_level(const Lvl& L) {
   return L.dim == 3 && L.n[0] >= 16 && L.n[1] >= 16 && L.n[2] >= 16;
 }
-inline dim3 mac3_grid(const Lvl& L) {
-  return dim3((L.n[0] - 2 + BX - 1) / BX, (L.n[1] - 2 + BY - 1) / BY, (L.n[2] - 2 + MAC3_KZ - 1) / MAC3_KZ);
-}
 // positions of the shell: the planes 0, n-1, n whole; on the other planes
 // the rows 0, n-1, n whole and the positions 0, n-1, n of the other rows
-inline long long mac3_shell_count(const Lvl& L) {
+__host__ __device__ __forceinline__ long long mac3_shell_count(const Lvl& L) {
   const long long nx = L.n[0] + 1, ny = L.n[1] + 1;
   return 3 * nx * ny + (long long)(L.n[2] - 2) * (3 * nx + 3 * (ny - 3));
+}
+// z extent of the box part of the launch; z slices beyond it are the shell's
+__host__ __device__ __forceinline__ int mac3_box_z(const Lvl& L) { return (L.n[2] - 2 + MAC3_KZ - 1) / MAC3_KZ; }
+// one launch: the box's blocks, then enough z slices of blocks for one
+// thread per shell position
+inline dim3 mac3_grid(const Lvl& L) {
+  const unsigned gx = (L.n[0] - 2 + BX - 1) / BX, gy = (L.n[1] - 2 + BY - 1) / BY;
+  const long long per_slice = (long long)gx * gy * BX * BY;
+  return dim3(gx, gy, mac3_box_z(L) + (unsigned)((mac3_shell_count(L) + per_slice - 1) / per_slice));
 }
 
 template <typename T, int MODE>
@@ -379,40 +385,44 @@ __device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wo
   const bool mine = i <= L.n[0] - 2 && j <= L.n[1] - 2;
   const bool gd = L.has_gd && !wonly;
   auto slot = [](int k) { return k % 3; };   // k >= 0
-  // this thread's tile entries: (col, row) = (tx, ty), (tx + BX, ty) for
-  // tx < 2, (tx, ty + BY) and (tx + BX, ty + BY) for ty < 2; the planes
-  // k0-1 .. kend lie in [0, n-1], held by every component's box, so only x
-  // and y are tested (once); offsets relative to the corner (i0-1, j0-1)
-  const long long tb = (long long)(j0 - 1) * L.P + (i0 - 1);
-  int tofs[4];
-  bool tin[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    const int q = tx + (m & 1) * BX, r = ty + (m >> 1) * BY;
-    tin[m] = (q < TW) && (r < TH) && i0 - 1 + q <= L.n[0] && j0 - 1 + r <= L.n[1];
-    tofs[m] = r * L.P + q;
+  // this thread's tile entries: (col, row) = (tx, ty) of every component,
+  // and for tid < 3 * HALO one entry of the halo (rows BY, BY+1 and columns
+  // BX, BX+1 of component tid / HALO); the planes k0-1 .. kend lie in
+  // [0, n-1], held by every component's box, so only x and y are tested
+  // (once). xp[c] points at this thread's main entry of component c in the
+  // plane to fetch next, xh at its halo entry; both advance by S per plane.
+  constexpr int HALO = 2 * TW + 2 * BY;
+  const bool tin0 = i0 - 1 + tx <= L.n[0] && j0 - 1 + ty <= L.n[1];
+  int hc = 0, hr = 0, hq = 0;
+  bool hin = false;
+  if (tid < 3 * HALO) {
+    hc = tid / HALO;
+    const int h = tid - hc * HALO;
+    if (h < 2 * TW) { hr = BY + h / TW; hq = h - (hr - BY) * TW; }
+    else { hr = (h - 2 * TW) >> 1; hq = BX + ((h - 2 * TW) & 1); }
+    hin = i0 - 1 + hq <= L.n[0] && j0 - 1 + hr <= L.n[1];
   }
-  T pre[3][4];
-  auto fetch = [&](int k) {
-    const long long ks = (long long)k * L.S + tb;
+  const T* xp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) xp[c] = x + L.off[c] + cix(L, i0 - 1 + tx, j0 - 1 + ty, k0 - 1);
+  const T* xh = x + L.off[hc] + cix(L, i0 - 1 + hq, j0 - 1 + hr, k0 - 1);
+  T pre[3], preh = (T)0;
+  auto fetch = [&]() {  // the next plane in order (k0-1, k0, ...)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const long long base = L.off[c] + ks;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) pre[c][m] = tin[m] ? x[base + tofs[m]] : (T)0;
+      pre[c] = tin0 ? *xp[c] : (T)0;
+      xp[c] += L.S;
+    }
+    if (tid < 3 * HALO) {
+      preh = hin ? *xh : (T)0;
+      xh += L.S;
     }
   };
   auto commit = [&](int k) {
     const int sl = slot(k);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      Xt[sl][c][ty][tx] = pre[c][0];
-      if (tx < 2) Xt[sl][c][ty][tx + BX] = pre[c][1];
-      if (ty < 2) {
-        Xt[sl][c][ty + BY][tx] = pre[c][2];
-        if (tx < 2) Xt[sl][c][ty + BY][tx + BX] = pre[c][3];
-      }
-    }
+    for (int c = 0; c < 3; ++c) Xt[sl][c][ty][tx] = pre[c];
+    if (tid < 3 * HALO) Xt[sl][hc][hr][hq] = preh;
   };
   // the cells this thread forms divergences for: (tx, ty); row BY for tid <
   // BX; column BX for BX <= tid < BX + BY + 1 (cell planes k0-1 .. kend-1 lie
@@ -435,20 +445,21 @@ __device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wo
     div_cell(kc, tx, ty, cin0);
     if (has1) div_cell(kc, dci1, dcj1, cin1);
   };
-  fetch(k0 - 1);
+  fetch();
   commit(k0 - 1);
-  fetch(k0);
+  fetch();
   commit(k0);
-  fetch(k0 + 1);
+  fetch();
   if (gd) {
     __syncthreads();
     div_plane(k0 - 1);
   }
-  for (int k = k0; k < kend; ++k) {
-    const long long cb = cix(L, i, j, k);
+  // this thread's faces of plane k: index cb in every component's block
+  long long cb = cix(L, i, j, k0);
+  for (int k = k0; k < kend; ++k, cb += L.S) {
     T bv[3] = {(T)0, (T)0, (T)0};
     commit(k + 1);
-    if (k + 1 < kend) fetch(k + 2);
+    if (k + 1 < kend) fetch();
     if (MODE == 0 && mine) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) bv[c] = b[L.off[c] + cb];
@@ -478,19 +489,13 @@ __device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wo
   }
 }
 
+// the shell: one thread per position (t = its index in the shell's order),
+// the three faces as k_mac_tile's general path forms them (divergences from
+// neg_div)
 template <typename T, int MODE>
-__global__ void __launch_bounds__(BX* BY, 4) k_mac3_box(Lvl L, int wonly, const T* __restrict__ x,
-                                                        const T* __restrict__ b, T* __restrict__ y) {
-  mac3_box_body<T, MODE>(native_blk(), L, wonly, x, b, y);
-}
-
-// the shell: one thread per position, the three faces as k_mac_tile's
-// general path forms them (divergences from neg_div)
-template <typename T, int MODE>
-__global__ void k_mac3_shell(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
-                             T* __restrict__ y, long long count) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
+__device__ __forceinline__ void mac3_shell_body(const Lvl& L, int wonly, const T* __restrict__ x,
+                                                const T* __restrict__ b, T* __restrict__ y, long long t) {
+  if (t >= mac3_shell_count(L)) return;
   const int nx = L.n[0] + 1, ny = L.n[1] + 1;
   const long long full = (long long)nx * ny, ring = 3LL * nx + 3LL * (ny - 3);
   int i, j, k;
@@ -542,6 +547,18 @@ __global__ void k_mac3_shell(Lvl L, int wonly, const T* __restrict__ x, const T*
   GKB_MAC3_SHELL(1, neg_div<T>(L, x, i, j - 1, k))
   GKB_MAC3_SHELL(2, neg_div<T>(L, x, i, j, k - 1))
 #undef GKB_MAC3_SHELL
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(BX* BY, 4) k_mac3(Lvl L, int wonly, const T* __restrict__ x,
+                                                    const T* __restrict__ b, T* __restrict__ y) {
+  const int bz = mac3_box_z(L);
+  if ((int)blockIdx.z < bz) {
+    mac3_box_body<T, MODE>(native_blk(), L, wonly, x, b, y);
+  } else {
+    const long long blk = ((long long)(blockIdx.z - bz) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    mac3_shell_body<T, MODE>(L, wonly, x, b, y, blk * (BX * BY) + threadIdx.y * BX + threadIdx.x);
+  }
 }
 
 

@@ -30,11 +30,8 @@ void Ops<KT>::apply(const Lvl& L, int mode, const KT* x, KT* y, cudaStream_t s) 
   ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
   RedBuf red{nullptr, nullptr};
   const int wonly = (mode == 0);
-  if (mac3_level(L) && !GKB_VARMU(L) && x) {
-    k_mac3_box<KT, 1><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y);
-    const long long sc = mac3_shell_count(L);
-    k_mac3_shell<KT, 1><<<(unsigned)((sc + 255) / 256), 256, 0, s>>>(L, wonly, x, nullptr, y, sc);
-  } else if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
+  if (mac3_level(L) && !GKB_VARMU(L) && x) k_mac3<KT, 1><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y);
+  else if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
   else k_mac_tile<KT, false, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
 }
 
@@ -53,11 +50,8 @@ template <>
 void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s, const int* pred) {
   ProfScope ps_(GKB_KC_RESIDUAL, s, lvl_unknowns(L));
   RedBuf red{nullptr, nullptr};
-  if (mac3_level(L) && !GKB_VARMU(L) && x && !pred) {
-    k_mac3_box<KT, 0><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r);
-    const long long sc = mac3_shell_count(L);
-    k_mac3_shell<KT, 0><<<(unsigned)((sc + 255) / 256), 256, 0, s>>>(L, 0, x, b, r, sc);
-  } else if (GKB_VARMU(L)) k_mac_tile<KT, true, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
+  if (mac3_level(L) && !GKB_VARMU(L) && x && !pred) k_mac3<KT, 0><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r);
+  else if (GKB_VARMU(L)) k_mac_tile<KT, true, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
   else k_mac_tile<KT, false, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
 }
 #endif

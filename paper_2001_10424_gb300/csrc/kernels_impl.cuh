@@ -372,9 +372,9 @@ inline dim3 mac3_grid(const Lvl& L) {
   return dim3(gx, gy, mac3_box_z(L) + (unsigned)((mac3_shell_count(L) + per_slice - 1) / per_slice));
 }
 
-template <typename T, int MODE>
-__device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wonly, const T* __restrict__ x,
-                                              const T* __restrict__ b, T* __restrict__ y) {
+template <typename T, int MODE, bool DOT>
+__device__ __forceinline__ double mac3_box_body(const Blk& B, const Lvl& L, int wonly, const T* __restrict__ x,
+                                                const T* __restrict__ b, T* __restrict__ y) {
   constexpr int TW = BX + 2, TH = BY + 2;
   __shared__ T Xt[3][3][TH][TW];      // [plane slot][component][row][col]: position (i0-1+col, j0-1+row)
   __shared__ T Dv[2][BY + 1][BX + 1];  // [cell plane parity][row][col]: cell (i0-1+col, j0-1+row)
@@ -456,6 +456,7 @@ __device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wo
   }
   // this thread's faces of plane k: index cb in every component's block
   long long cb = cix(L, i, j, k0);
+  double dot = 0.0;
   for (int k = k0; k < kend; ++k, cb += L.S) {
     T bv[3] = {(T)0, (T)0, (T)0};
     commit(k + 1);
@@ -477,8 +478,10 @@ __device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wo
         T acc = Xt[sc][C][ty + 1][tx + 2] + Xt[sc][C][ty + 1][tx] + Xt[sc][C][ty + 2][tx + 1] + \
                 Xt[sc][C][ty][tx + 1];                                                         \
         acc += Xt[su][C][ty + 1][tx + 1] + Xt[sd][C][ty + 1][tx + 1];                          \
-        y[L.off[C] + cb] = const_row<T, MODE>(L, bv[C], xf, acc, gd, gd ? (DPLUS) : (T)0,      \
-                                              gd ? (DMINUS) : (T)0);                           \
+        const T val = const_row<T, MODE>(L, bv[C], xf, acc, gd, gd ? (DPLUS) : (T)0,           \
+                                         gd ? (DMINUS) : (T)0);                                \
+        if (DOT) dot += (double)xf * (double)val;                                              \
+        y[L.off[C] + cb] = val;                                                                \
       }
       GKB_MAC3_FACE(0, Dv[k & 1][ty + 1][tx + 1], Dv[k & 1][ty + 1][tx])
       GKB_MAC3_FACE(1, Dv[k & 1][ty + 1][tx + 1], Dv[k & 1][ty][tx + 1])
@@ -487,15 +490,16 @@ __device__ __forceinline__ void mac3_box_body(const Blk& B, const Lvl& L, int wo
     }
     __syncthreads();  // the next plane's load and divergences overwrite slot k-1 and parity k-1
   }
+  return dot;
 }
 
 // the shell: one thread per position (t = its index in the shell's order),
 // the three faces as k_mac_tile's general path forms them (divergences from
 // neg_div)
-template <typename T, int MODE>
-__device__ __forceinline__ void mac3_shell_body(const Lvl& L, int wonly, const T* __restrict__ x,
-                                                const T* __restrict__ b, T* __restrict__ y, long long t) {
-  if (t >= mac3_shell_count(L)) return;
+template <typename T, int MODE, bool DOT>
+__device__ __forceinline__ double mac3_shell_body(const Lvl& L, int wonly, const T* __restrict__ x,
+                                                  const T* __restrict__ b, T* __restrict__ y, long long t) {
+  if (t >= mac3_shell_count(L)) return 0.0;
   const int nx = L.n[0] + 1, ny = L.n[1] + 1;
   const long long full = (long long)nx * ny, ring = 3LL * nx + 3LL * (ny - 3);
   int i, j, k;
@@ -525,6 +529,7 @@ __device__ __forceinline__ void mac3_shell_body(const Lvl& L, int wonly, const T
   const int p[3] = {i, j, k};
   const long long cb = cix(L, i, j, k);
   const T d0 = gd ? neg_div<T>(L, x, i, j, k) : (T)0;
+  double dot = 0.0;
 #define GKB_MAC3_SHELL(C, DMINUS)                                                              \
   if (in_store<C>(L, i, j, k)) {                                                               \
     const long long id = L.off[C] + cb;                                                        \
@@ -540,6 +545,7 @@ __device__ __forceinline__ void mac3_shell_body(const Lvl& L, int wonly, const T
         if (gd) m += g2 * (d0 - dm);                                                           \
         val = (MODE == 0) ? bb - m : m;                                                        \
       }                                                                                        \
+      if (DOT) dot += (double)xf * (double)val;                                                \
     }                                                                                          \
     y[id] = val;                                                                               \
   }
@@ -547,17 +553,25 @@ __device__ __forceinline__ void mac3_shell_body(const Lvl& L, int wonly, const T
   GKB_MAC3_SHELL(1, neg_div<T>(L, x, i, j - 1, k))
   GKB_MAC3_SHELL(2, neg_div<T>(L, x, i, j, k - 1))
 #undef GKB_MAC3_SHELL
+  return dot;
 }
 
-template <typename T, int MODE>
+// DOT: x . y over box and shell, reduced through finaliser fin on st
+template <typename T, int MODE, bool DOT>
 __global__ void __launch_bounds__(BX* BY, 4) k_mac3(Lvl L, int wonly, const T* __restrict__ x,
-                                                    const T* __restrict__ b, T* __restrict__ y) {
+                                                    const T* __restrict__ b, T* __restrict__ y, RedBuf red,
+                                                    int fin, void* st) {
   const int bz = mac3_box_z(L);
+  double dot;
   if ((int)blockIdx.z < bz) {
-    mac3_box_body<T, MODE>(native_blk(), L, wonly, x, b, y);
+    dot = mac3_box_body<T, MODE, DOT>(native_blk(), L, wonly, x, b, y);
   } else {
     const long long blk = ((long long)(blockIdx.z - bz) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    mac3_shell_body<T, MODE>(L, wonly, x, b, y, blk * (BX * BY) + threadIdx.y * BX + threadIdx.x);
+    dot = mac3_shell_body<T, MODE, DOT>(L, wonly, x, b, y, blk * (BX * BY) + threadIdx.y * BX + threadIdx.x);
+  }
+  if (DOT) {
+    double v[1] = {dot};
+    grid_reduce<1>(v, red, fin, st);
   }
 }
 

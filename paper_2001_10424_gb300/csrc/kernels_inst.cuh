@@ -30,7 +30,7 @@ void Ops<KT>::apply(const Lvl& L, int mode, const KT* x, KT* y, cudaStream_t s) 
   ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
   RedBuf red{nullptr, nullptr};
   const int wonly = (mode == 0);
-  if (mac3_level(L) && !GKB_VARMU(L) && x) k_mac3<KT, 1><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y);
+  if (mac3_level(L) && !GKB_VARMU(L) && x) k_mac3<KT, 1, false><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr);
   else if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
   else k_mac_tile<KT, false, 1, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, 0, nullptr, nullptr);
 }
@@ -40,7 +40,8 @@ void Ops<KT>::apply_dot(const Lvl& L, int mode, const KT* x, KT* y, const RedBuf
                         cudaStream_t s) {
   ProfScope ps_(GKB_KC_APPLY, s, lvl_unknowns(L));
   const int wonly = (mode == 0);
-  if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
+  if (mac3_level(L) && !GKB_VARMU(L) && x) k_mac3<KT, 1, true><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st);
+  else if (GKB_VARMU(L)) k_mac_tile<KT, true, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
   else k_mac_tile<KT, false, 1, true><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, wonly, x, nullptr, y, red, fin, st, nullptr);
 }
 #endif
@@ -50,7 +51,7 @@ template <>
 void Ops<KT>::residual(const Lvl& L, const KT* x, const KT* b, KT* r, cudaStream_t s, const int* pred) {
   ProfScope ps_(GKB_KC_RESIDUAL, s, lvl_unknowns(L));
   RedBuf red{nullptr, nullptr};
-  if (mac3_level(L) && !GKB_VARMU(L) && x && !pred) k_mac3<KT, 0><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r);
+  if (mac3_level(L) && !GKB_VARMU(L) && x && !pred) k_mac3<KT, 0, false><<<mac3_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr);
   else if (GKB_VARMU(L)) k_mac_tile<KT, true, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
   else k_mac_tile<KT, false, 0, false><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, 0, x, b, r, red, 0, nullptr, pred);
 }

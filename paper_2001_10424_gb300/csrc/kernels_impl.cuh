@@ -356,12 +356,41 @@ constexpr int MAC3_KZ = 16;
 inline bool mac3_level(const Lvl& L) {
   return L.dim == 3 && L.n[0] >= 16 && L.n[1] >= 16 && L.n[2] >= 16;
 }
-// positions of the shell: the planes 0, n-1, n whole; on the other planes
-// the rows 0, n-1, n whole and the positions 0, n-1, n of the other rows
-__host__ __device__ __forceinline__ long long mac3_shell_count(const Lvl& L) {
-  const long long nx = L.n[0] + 1, ny = L.n[1] + 1;
-  return 3 * nx * ny + (long long)(L.n[2] - 2) * (3 * nx + 3 * (ny - 3));
+// The shell of positions around the box [lo, n - hi] (every axis) of a 3D
+// level, in a fixed order: the lo + hi outer planes whole, then on every
+// other plane the lo + hi outer rows whole and the lo + hi outer positions
+// of the other rows.
+__host__ __device__ __forceinline__ long long shell_count(const Lvl& L, int lo, int hi) {
+  const long long nx = L.n[0] + 1, ny = L.n[1] + 1, w = lo + hi;
+  return w * nx * ny + (L.n[2] + 1 - w) * (w * nx + w * (ny - w));
 }
+__device__ __forceinline__ void shell_ijk(const Lvl& L, int lo, int hi, long long t, int& i, int& j, int& k) {
+  const int nx = L.n[0] + 1, ny = L.n[1] + 1, w = lo + hi;
+  const long long full = (long long)nx * ny, ring = (long long)w * nx + (long long)w * (ny - w);
+  if (t < w * full) {
+    const int pl = (int)(t / full);
+    const long long r = t - pl * full;
+    k = pl < lo ? pl : L.n[2] - hi + 1 + (pl - lo);
+    j = (int)(r / nx);
+    i = (int)(r - (long long)j * nx);
+  } else {
+    const long long u = t - w * full;
+    k = lo + (int)(u / ring);
+    const long long r = u - (long long)(k - lo) * ring;
+    if (r < (long long)w * nx) {
+      const int rw = (int)(r / nx);
+      j = rw < lo ? rw : L.n[1] - hi + 1 + (rw - lo);
+      i = (int)(r - (long long)rw * nx);
+    } else {
+      const int e = (int)(r - (long long)w * nx);
+      j = lo + e / w;
+      const int c = e - (j - lo) * w;
+      i = c < lo ? c : L.n[0] - hi + 1 + (c - lo);
+    }
+  }
+}
+// the shell of the operator's box [1, n-2]
+__host__ __device__ __forceinline__ long long mac3_shell_count(const Lvl& L) { return shell_count(L, 1, 2); }
 // z extent of the box part of the launch; z slices beyond it are the shell's
 __host__ __device__ __forceinline__ int mac3_box_z(const Lvl& L) { return (L.n[2] - 2 + MAC3_KZ - 1) / MAC3_KZ; }
 // one launch: the box's blocks, then enough z slices of blocks for one
@@ -500,30 +529,8 @@ template <typename T, int MODE, bool DOT>
 __device__ __forceinline__ double mac3_shell_body(const Lvl& L, int wonly, const T* __restrict__ x,
                                                   const T* __restrict__ b, T* __restrict__ y, long long t) {
   if (t >= mac3_shell_count(L)) return 0.0;
-  const int nx = L.n[0] + 1, ny = L.n[1] + 1;
-  const long long full = (long long)nx * ny, ring = 3LL * nx + 3LL * (ny - 3);
   int i, j, k;
-  if (t < 3 * full) {  // planes 0, n-1, n
-    const int pl = (int)(t / full);
-    const long long r = t - pl * full;
-    k = pl == 0 ? 0 : L.n[2] - 2 + pl;
-    j = (int)(r / nx);
-    i = (int)(r - (long long)j * nx);
-  } else {             // planes 1 .. n-2: rows 0, n-1, n, then the ends of the others
-    const long long u = t - 3 * full;
-    k = 1 + (int)(u / ring);
-    const long long r = u - (long long)(k - 1) * ring;
-    if (r < 3LL * nx) {
-      const int rw = (int)(r / nx);
-      j = rw == 0 ? 0 : L.n[1] - 2 + rw;
-      i = (int)(r - (long long)rw * nx);
-    } else {
-      const int e = (int)(r - 3LL * nx);
-      j = 1 + e / 3;
-      const int c = e - (j - 1) * 3;
-      i = c == 0 ? 0 : L.n[0] - 2 + c;
-    }
-  }
+  shell_ijk(L, 1, 2, t, i, j, k);
   const bool gd = L.has_gd && !wonly;
   const T g2 = Kc<T>::g2(L);
   const int p[3] = {i, j, k};
@@ -1266,6 +1273,183 @@ __global__ void __launch_bounds__(BX* BY) k_cheb3(Lvl L, const T* __restrict__ r
                                                    T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
                                                    const __grid_constant__ Fold3In<T> fin) {
   cheb3_body<T>(native_blk(), L, r, x, d, ca, cb, x_zero, table, fin);
+}
+
+// ---------------------------------------------------------------------------
+// The same step split by geometry (levels of at least 16 cells per axis): the
+// box [3, n-3]^3, where every position is of the interior class, walks planes
+// like k_mac3's box (r of three planes with a one-position halo in shared
+// memory, the next plane fetched into registers, d and x of the plane read
+// before its barriers) and applies the interior stencils in fold3_apply's
+// order; the shell (three positions deep) takes the class table one thread
+// per position. Bit for bit the values of k_cheb3.
+// ---------------------------------------------------------------------------
+constexpr int CHEB3S_KZ = 16;
+
+inline bool cheb3s_level(const Lvl& L) {
+  return L.dim == 3 && L.n[0] >= 16 && L.n[1] >= 16 && L.n[2] >= 16;
+}
+__host__ __device__ __forceinline__ int cheb3s_box_z(const Lvl& L) { return (L.n[2] - 5 + CHEB3S_KZ - 1) / CHEB3S_KZ; }
+inline dim3 cheb3s_grid(const Lvl& L) {
+  const unsigned gx = (L.n[0] - 5 + BX - 1) / BX, gy = (L.n[1] - 5 + BY - 1) / BY;
+  const long long per_slice = (long long)gx * gy * BX * BY;
+  return dim3(gx, gy, cheb3s_box_z(L) + (unsigned)((shell_count(L, 3, 3) + per_slice - 1) / per_slice));
+}
+
+// fold3_apply's interior stencil of component C at tile position (tx, ty)
+// of plane slot s0 (planes below / above: sm, sp)
+template <typename T, int C>
+__device__ __forceinline__ T fold3_tile(const T (*Rt)[3][BY + 2][BX + 2], int sm, int s0, int sp, int tx, int ty,
+                                        const T* f) {
+  auto R = [&](int comp, const int dl[3]) -> T {
+    return Rt[dl[2] < 0 ? sm : (dl[2] > 0 ? sp : s0)][comp][ty + 1 + dl[1]][tx + 1 + dl[0]];
+  };
+  const int z0[3] = {0, 0, 0};
+  T acc = f[0] * R(C, z0);
+  int t = 1;
+#pragma unroll
+  for (int E = 0; E < 3; ++E) {
+    if (E == C) continue;
+    const int a = (E == 0) ? 1 : 0, b = (E == 2) ? 1 : 2;
+    int mb[3] = {0, 0, 0}, ma[3] = {0, 0, 0}, pb[3] = {0, 0, 0}, pa[3] = {0, 0, 0}, ba[3] = {0, 0, 0}, ab[3] = {0, 0, 0};
+    mb[b] = -1; ma[a] = -1; pb[b] = 1; pa[a] = 1; ba[b] = 1; ba[a] = -1; ab[a] = 1; ab[b] = -1;
+    if (C == a) {
+      acc += f[t + 0] * R(a, mb);
+      acc += f[t + 1] * R(b, ma);
+      acc += f[t + 2] * R(b, z0);
+      acc += f[t + 3] * R(a, pb);
+      acc += f[t + 4] * R(b, ba);
+      acc += f[t + 5] * R(b, pb);
+    } else {
+      acc += f[t + 0] * R(a, mb);
+      acc += f[t + 1] * R(a, z0);
+      acc += f[t + 2] * R(b, ma);
+      acc += f[t + 3] * R(a, ab);
+      acc += f[t + 4] * R(a, pa);
+      acc += f[t + 5] * R(b, pa);
+    }
+    t += 6;
+  }
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ void cheb3s_box_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
+                                                T* __restrict__ d, T ca, T cb, int x_zero, const Fold3In<T>& fin) {
+  constexpr int TW = BX + 2, TH = BY + 2;
+  __shared__ T Rt[3][3][TH][TW];   // [plane slot][component][row][col]: position (i0-1+col, j0-1+row)
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int i0 = 3 + (int)B.x * BX, j0 = 3 + (int)B.y * BY, k0 = 3 + (int)B.z * CHEB3S_KZ;
+  const int i = i0 + tx, j = j0 + ty;
+  const int kend = min(k0 + CHEB3S_KZ, L.n[2] - 2);  // planes k0 .. kend-1 (uniform over the block)
+  const bool mine = i <= L.n[0] - 3 && j <= L.n[1] - 3;
+  auto slot = [](int k) { return k % 3; };
+  // tile entries as in k_mac3's box (planes k0-1 .. kend lie in [2, n-2])
+  constexpr int HALO = 2 * TW + 2 * BY;
+  const bool tin0 = i0 - 1 + tx <= L.n[0] && j0 - 1 + ty <= L.n[1];
+  int hc = 0, hr = 0, hq = 0;
+  bool hin = false;
+  if (tid < 3 * HALO) {
+    hc = tid / HALO;
+    const int h = tid - hc * HALO;
+    if (h < 2 * TW) { hr = BY + h / TW; hq = h - (hr - BY) * TW; }
+    else { hr = (h - 2 * TW) >> 1; hq = BX + ((h - 2 * TW) & 1); }
+    hin = i0 - 1 + hq <= L.n[0] && j0 - 1 + hr <= L.n[1];
+  }
+  const T* rp[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) rp[c] = r + L.off[c] + cix(L, i0 - 1 + tx, j0 - 1 + ty, k0 - 1);
+  const T* rh = r + L.off[hc] + cix(L, i0 - 1 + hq, j0 - 1 + hr, k0 - 1);
+  T pre[3], preh = (T)0;
+  auto fetch = [&]() {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pre[c] = tin0 ? *rp[c] : (T)0;
+      rp[c] += L.S;
+    }
+    if (tid < 3 * HALO) {
+      preh = hin ? *rh : (T)0;
+      rh += L.S;
+    }
+  };
+  auto commit = [&](int k) {
+    const int sl = slot(k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Rt[sl][c][ty][tx] = pre[c];
+    if (tid < 3 * HALO) Rt[sl][hc][hr][hq] = preh;
+  };
+  fetch();
+  commit(k0 - 1);
+  fetch();
+  commit(k0);
+  fetch();
+  long long cbk = cix(L, i, j, k0);
+  for (int k = k0; k < kend; ++k, cbk += L.S) {
+    commit(k + 1);
+    if (k + 1 < kend) fetch();
+    T dold[3] = {(T)0, (T)0, (T)0}, xold[3] = {(T)0, (T)0, (T)0};
+    if (mine) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (cb != (T)0) dold[c] = d[L.off[c] + cbk];
+        if (!x_zero) xold[c] = x[L.off[c] + cbk];
+      }
+    }
+    __syncthreads();
+    if (mine) {
+      const int sc = slot(k), su = slot(k + 1), sd = slot(k - 1);
+#define GKB_CHEB3S_FACE(C)                                                                     \
+      {                                                                                        \
+        const T z = fold3_tile<T, C>(Rt, sd, sc, su, tx, ty, fin.c[C]);                         \
+        const T dn = (cb != (T)0) ? ca * z + cb * dold[C] : ca * z;                            \
+        d[L.off[C] + cbk] = dn;                                                                \
+        x[L.off[C] + cbk] = x_zero ? dn : xold[C] + dn;                                        \
+      }
+      GKB_CHEB3S_FACE(0)
+      GKB_CHEB3S_FACE(1)
+      GKB_CHEB3S_FACE(2)
+#undef GKB_CHEB3S_FACE
+    }
+    __syncthreads();  // the next plane's load overwrites slot k-1
+  }
+}
+
+// one position of the shell [3, n-3]: the class path of cheb3_body
+template <typename T>
+__device__ __forceinline__ void cheb3s_shell_body(const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
+                                                  T* __restrict__ d, T ca, T cb, int x_zero,
+                                                  const T* __restrict__ table, const Fold3In<T>& fin, long long t) {
+  if (t >= shell_count(L, 3, 3)) return;
+  int i, j, k;
+  shell_ijk(L, 3, 3, t, i, j, k);
+  const int pc = (cls7(i, L.n[0]) * 7 + cls7(j, L.n[1])) * 7 + cls7(k, L.n[2]);
+  const int p0 = k * (int)L.S + j * L.P + i;
+  const T* fold = table + FOLD3_OFF + (size_t)pc * 48;
+  if (pc == FOLD3_INTERIOR) {
+    cheb3_face<T, 0, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[0][q]; });
+    cheb3_face<T, 1, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[1][q]; });
+    cheb3_face<T, 2, true>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return fin.c[2][q]; });
+    return;
+  }
+  if (in_store<0>(L, i, j, k) && face_active<0>(L, i, j, k))
+    cheb3_face<T, 0, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + q); });
+  if (in_store<1>(L, i, j, k) && face_active<1>(L, i, j, k))
+    cheb3_face<T, 1, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 16 + q); });
+  if (in_store<2>(L, i, j, k) && face_active<2>(L, i, j, k))
+    cheb3_face<T, 2, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 32 + q); });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BX* BY, 4) k_cheb3s(Lvl L, const T* __restrict__ r, T* __restrict__ x,
+                                                      T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
+                                                      const __grid_constant__ Fold3In<T> fin) {
+  const int bz = cheb3s_box_z(L);
+  if ((int)blockIdx.z < bz) {
+    cheb3s_box_body<T>(native_blk(), L, r, x, d, ca, cb, x_zero, fin);
+  } else {
+    const long long blk = ((long long)(blockIdx.z - bz) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    cheb3s_shell_body<T>(L, r, x, d, ca, cb, x_zero, table, fin, blk * (BX * BY) + threadIdx.y * BX + threadIdx.x);
+  }
 }
 
 // One Chebyshev step of the patch-preconditioned smoother:

@@ -73,7 +73,8 @@ void Ops<KT>::cheb(const Lvl& L, const KT* r, KT* x, KT* d, KT ca, KT cb, int x_
     Fold3In<KT> f;
     for (int c = 0; c < 3; ++c)
       for (int q = 0; q < 13; ++q) f.c[c][q] = (KT)fold_in[c * 16 + q];
-    k_cheb3<KT><<<cheb3_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);
+    if (cheb3s_level(L)) k_cheb3s<KT><<<cheb3s_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);
+    else k_cheb3<KT><<<cheb3_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);
   } else if (fold_in && table && cheb2_level(L)) {
     const Fold2In<KT> f = fold2_scaled<KT>(fold_in, (double)ca);
     k_cheb2<KT><<<face_grid(L), dim3(BX, BY), 0, s>>>(L, r, x, d, ca, cb, x_zero, table, f);

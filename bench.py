@@ -473,14 +473,22 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     # its collection off (ncu --profile-from-start off); no-ops otherwise
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
+    # the launches of each class at its largest work per launch (the finest
+    # level): count, summed work, summed time, smoother flops
+    top_n, top_u, top_ms, top_sfl = {}, {}, {}, 0.0
     for i, h in enumerate(B.hs):
         gk.gkb_solve(h, B.g[i], B.r[i], args.tol, args.delay, B.w[i], B.p[i], B.w0[i], B.p0[i])
         st = gk.gkb_stats(h)
+        sfl = smooth_flops(wk.dim, gk.gkb_get_options(h).smoother_degree)
         for k in gk.KERNEL_CLASSES:
             ms[k] = ms.get(k, 0.0) + st["kernel_ms"][k]
             units[k] = units.get(k, 0) + st["kernel_units"][k]
             launches[k] = launches.get(k, 0) + st["kernel_launches"][k]
-        smooth_fl += st["kernel_units"]["smooth"] * smooth_flops(wk.dim, gk.gkb_get_options(h).smoother_degree)
+            top_n[k] = top_n.get(k, 0) + st["kernel_top_launches"][k]
+            top_u[k] = top_u.get(k, 0) + st["kernel_top_launches"][k] * st["kernel_top_units"][k]
+            top_ms[k] = top_ms.get(k, 0.0) + st["kernel_top_ms"][k]
+        smooth_fl += st["kernel_units"]["smooth"] * sfl
+        top_sfl += st["kernel_top_launches"]["smooth"] * st["kernel_top_units"]["smooth"] * sfl
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     B.destroy()
@@ -530,6 +538,19 @@ def roofline(gk, torch, wk, args, form, hbm_peak, peak_kind):
     rl["class_ms"] = {k: round(v, 3) for k, v in ms.items()}
     rl["profiled"] = "%d problem(s), profiled host-sequenced solve" % n_profiled
     rl["flops_per_unit"] = flops / max(1, units[top])
+    # the same class restricted to its finest-level launches (the level the
+    # ncu captures look at; the class figure above averages every level,
+    # coarse launches included), where they are a real share of the class
+    if top_n.get(top) and top_ms.get(top) and ms[top] and top_ms[top] >= 0.25 * ms[top]:
+        tf = top_ms[top] * 1e-3
+        if rl["bound"] == "alu":
+            ach = (top_sfl if top == "smooth" else top_u[top] * table[top][0]) / tf / 1e12
+        else:
+            ach = top_u[top] * per_unit_bytes * s / tf / 1e9
+        rl["finest_level"] = {"launches": top_n[top], "unknowns_per_launch": top_u[top] // top_n[top],
+                              "avg_launch_us": top_ms[top] * 1e3 / top_n[top],
+                              "share_of_class_time": top_ms[top] / ms[top] if ms[top] else None,
+                              "achieved": ach, "frac": ach / rl["peak"]}
     return rl
 
 

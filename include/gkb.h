@@ -210,6 +210,11 @@ typedef struct {
                                              BLAS, rows for the coarse solve) */
   double kernel_ms[GKB_KC_COUNT];         /* summed kernel time per class (ms)
                                              when profiling, else 0          */
+  int64_t kernel_top_launches[GKB_KC_COUNT]; /* profiling: the class's timed
+                                             launches of its largest work per
+                                             launch (the finest level)       */
+  int64_t kernel_top_units[GKB_KC_COUNT]; /* that work per launch            */
+  double kernel_top_ms[GKB_KC_COUNT];     /* their summed kernel time (ms)   */
 } gkb_stats_t;
 
 /* Fill *opt with defaults: FP64, GMG-PCG, tol_inner 1e-10, maxit 1000,

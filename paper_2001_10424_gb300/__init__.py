@@ -77,7 +77,9 @@ class gkb_stats_t(ctypes.Structure):
                 ("setup_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
                 ("levels", ctypes.c_int), ("inner_fallbacks", ctypes.c_int), ("tuned_inner_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64 * 10),
-                ("kernel_units", ctypes.c_int64 * 10), ("kernel_ms", ctypes.c_double * 10)]
+                ("kernel_units", ctypes.c_int64 * 10), ("kernel_ms", ctypes.c_double * 10),
+                ("kernel_top_launches", ctypes.c_int64 * 10), ("kernel_top_units", ctypes.c_int64 * 10),
+                ("kernel_top_ms", ctypes.c_double * 10)]
 
 
 class GkbError(RuntimeError):
@@ -233,6 +235,9 @@ def gkb_stats(h):
     out["kernel_launches"] = dict(zip(KERNEL_CLASSES, list(s.kernel_launches)))
     out["kernel_units"] = dict(zip(KERNEL_CLASSES, list(s.kernel_units)))
     out["kernel_ms"] = dict(zip(KERNEL_CLASSES, list(s.kernel_ms)))
+    out["kernel_top_launches"] = dict(zip(KERNEL_CLASSES, list(s.kernel_top_launches)))
+    out["kernel_top_units"] = dict(zip(KERNEL_CLASSES, list(s.kernel_top_units)))
+    out["kernel_top_ms"] = dict(zip(KERNEL_CLASSES, list(s.kernel_top_ms)))
     return out
 
 

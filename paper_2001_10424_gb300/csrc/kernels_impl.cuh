@@ -565,7 +565,7 @@ __device__ __forceinline__ double mac3_shell_body(const Lvl& L, int wonly, const
 
 // DOT: x . y over box and shell, reduced through finaliser fin on st
 template <typename T, int MODE, bool DOT>
-__global__ void __launch_bounds__(BX* BY, 4) k_mac3(Lvl L, int wonly, const T* __restrict__ x,
+__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_mac3(Lvl L, int wonly, const T* __restrict__ x,
                                                     const T* __restrict__ b, T* __restrict__ y, RedBuf red,
                                                     int fin, void* st) {
   const int bz = mac3_box_z(L);
@@ -1384,17 +1384,29 @@ __device__ __forceinline__ void cheb3s_box_body(const Blk& B, const Lvl& L, cons
   commit(k0);
   fetch();
   long long cbk = cix(L, i, j, k0);
-  for (int k = k0; k < kend; ++k, cbk += L.S) {
-    commit(k + 1);
-    if (k + 1 < kend) fetch();
-    T dold[3] = {(T)0, (T)0, (T)0}, xold[3] = {(T)0, (T)0, (T)0};
+  // d and x of the faces: those of plane k+1 are fetched while plane k is
+  // computed
+  T dnx[3] = {(T)0, (T)0, (T)0}, xnx[3] = {(T)0, (T)0, (T)0};
+  auto fetch_dx = [&](long long at) {
     if (mine) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        if (cb != (T)0) dold[c] = d[L.off[c] + cbk];
-        if (!x_zero) xold[c] = x[L.off[c] + cbk];
+        if (cb != (T)0) dnx[c] = d[L.off[c] + at];
+        if (!x_zero) xnx[c] = x[L.off[c] + at];
       }
     }
+  };
+  fetch_dx(cbk);
+  for (int k = k0; k < kend; ++k, cbk += L.S) {
+    commit(k + 1);
+    if (k + 1 < kend) fetch();
+    T dold[3], xold[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      dold[c] = dnx[c];
+      xold[c] = xnx[c];
+    }
+    if (k + 1 < kend) fetch_dx(cbk + L.S);
     __syncthreads();
     if (mine) {
       const int sc = slot(k), su = slot(k + 1), sd = slot(k - 1);
@@ -1440,7 +1452,7 @@ __device__ __forceinline__ void cheb3s_shell_body(const Lvl& L, const T* __restr
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY, 4) k_cheb3s(Lvl L, const T* __restrict__ r, T* __restrict__ x,
+__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_cheb3s(Lvl L, const T* __restrict__ r, T* __restrict__ x,
                                                       T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
                                                       const __grid_constant__ Fold3In<T> fin) {
   const int bz = cheb3s_box_z(L);

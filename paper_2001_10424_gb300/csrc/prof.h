@@ -18,8 +18,15 @@ struct Profiler {
   long long launches[GKB_KC_COUNT] = {};
   long long units[GKB_KC_COUNT] = {};   // unknowns (or elements) processed
   double ms[GKB_KC_COUNT] = {};
+  // timed launches of each class's largest work per launch (its finest
+  // level): count, that work, summed time
+  long long top_launches[GKB_KC_COUNT] = {};
+  long long top_units[GKB_KC_COUNT] = {};
+  double top_ms[GKB_KC_COUNT] = {};
   std::vector<cudaEvent_t> pool;
   std::vector<int> rec_class;
+  std::vector<long long> rec_work;
+  long long cur_work = 0;
   size_t used = 0;  // events used (pairs)
   int cur = -1;
   int phase = -1;   // >= 0 while a graph is captured: launches go to cap[phase]
@@ -35,9 +42,13 @@ struct Profiler {
     }
   }
   void reset() {
-    for (int k = 0; k < GKB_KC_COUNT; ++k) { launches[k] = 0; ms[k] = 0; units[k] = 0; }
+    for (int k = 0; k < GKB_KC_COUNT; ++k) {
+      launches[k] = 0; ms[k] = 0; units[k] = 0;
+      top_launches[k] = 0; top_units[k] = 0; top_ms[k] = 0;
+    }
     used = 0;
     rec_class.clear();
+    rec_work.clear();
   }
   void pre(int kc, cudaStream_t s, long long work) {
     if (phase >= 0) {
@@ -52,12 +63,14 @@ struct Profiler {
     if (timing && 2 * used + 1 < pool.size()) {
       cudaEventRecord(pool[2 * used], s);
       cur = kc;
+      cur_work = work;
     }
   }
   void post(int kc, cudaStream_t s) {
     if (cur == kc && timing) {
       cudaEventRecord(pool[2 * used + 1], s);
       rec_class.push_back(kc);
+      rec_work.push_back(cur_work);
       used += 1;
     }
     cur = -1;
@@ -66,11 +79,24 @@ struct Profiler {
   void collect() {
     for (size_t i = 0; i < used; ++i) {
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) == cudaSuccess) ms[rec_class[i]] += t;
+      if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) != cudaSuccess) continue;
+      const int kc = rec_class[i];
+      const long long w = rec_work[i];
+      ms[kc] += t;
+      if (w > top_units[kc]) {   // a larger level than seen so far: restart its sums
+        top_units[kc] = w;
+        top_launches[kc] = 0;
+        top_ms[kc] = 0;
+      }
+      if (w == top_units[kc]) {
+        top_launches[kc] += 1;
+        top_ms[kc] += t;
+      }
     }
     (void)cudaGetLastError();
     used = 0;
     rec_class.clear();
+    rec_work.clear();
   }
   ~Profiler() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);

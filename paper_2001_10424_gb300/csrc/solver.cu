@@ -2015,6 +2015,9 @@ int Solver::finish(double* w_out, double* p_out, const double* w0, const double*
     stats.kernel_launches[kc] = prof.launches[kc];
     stats.kernel_units[kc] = prof.units[kc];
     stats.kernel_ms[kc] = prof.ms[kc];
+    stats.kernel_top_launches[kc] = prof.top_launches[kc];
+    stats.kernel_top_units[kc] = prof.top_units[kc];
+    stats.kernel_top_ms[kc] = prof.top_ms[kc];
   }
   stats.status = status;
   stats.outer_iterations = H.k;

@@ -348,6 +348,28 @@ def test_fast_paths_match_general_paths_bitwise(lib, n, prec, var):
     assert np.array_equal(outs[0][1], outs[1][1])
 
 
+def test_profiled_solve_reports_the_finest_level(lib):
+    """A profiled solve times every launch; per kernel class it also reports
+    the launches at the class's largest work per launch, which for the
+    stencil classes is the finest level (work = its velocity unknowns)."""
+    gk = lib
+    n, bc = (64, 48), (D,) * 4
+    grid, _ = oracle_problem(n, bc, 1.0, 100.0)
+    h = make_handle(gk, n, bc, 1.0, 100.0, profile=1, use_graph=0)
+    try:
+        m, _ = gk.gkb_layout(h)
+        gvec = np.random.default_rng(17).standard_normal(grid.m)
+        rc, _, _ = gpu_solve(gk, h, gvec, np.zeros(grid.n_cells))
+        assert rc == gk.GKB_OK
+        st = gk.gkb_stats(h)
+        for k in ("residual", "smooth"):
+            assert st["kernel_top_units"][k] == m, k
+            assert 0 < st["kernel_top_launches"][k] < st["kernel_launches"][k], k
+            assert 0 < st["kernel_top_ms"][k] <= st["kernel_ms"][k], k
+    finally:
+        gk.gkb_destroy(h)
+
+
 @pytest.mark.parametrize("prec", [FP64, MIXED])
 def test_non_finite_inputs_return_a_status(lib, prec):
     """A NaN in g or an Inf in r ends the solve with a status (the norm and

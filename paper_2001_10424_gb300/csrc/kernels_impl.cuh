@@ -483,16 +483,26 @@ __device__ __forceinline__ double mac3_box_body(const Blk& B, const Lvl& L, int 
     __syncthreads();
     div_plane(k0 - 1);
   }
-  // this thread's faces of plane k: index cb in every component's block
+  // this thread's faces of plane k: index cb in every component's block;
+  // b of plane k+1 is fetched while plane k is computed
   long long cb = cix(L, i, j, k0);
   double dot = 0.0;
-  for (int k = k0; k < kend; ++k, cb += L.S) {
-    T bv[3] = {(T)0, (T)0, (T)0};
-    commit(k + 1);
-    if (k + 1 < kend) fetch();
+  T bnx[3] = {(T)0, (T)0, (T)0};
+  auto fetch_b = [&](long long at) {
     if (MODE == 0 && mine) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) bv[c] = b[L.off[c] + cb];
+      for (int c = 0; c < 3; ++c) bnx[c] = b[L.off[c] + at];
+    }
+  };
+  fetch_b(cb);
+  for (int k = k0; k < kend; ++k, cb += L.S) {
+    T bv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) bv[c] = bnx[c];
+    commit(k + 1);
+    if (k + 1 < kend) {
+      fetch();
+      fetch_b(cb + L.S);
     }
     __syncthreads();
     if (gd) {

@@ -836,7 +836,7 @@ def run_ours(args, ws, rank, local):
         for h in B.hs[:8]:
             o = gk.gkb_get_options(h)
             tuned.append({"smoother_degree": o.smoother_degree, "kernel_variant": o.kernel_variant,
-                          "coarse_max": o.coarse_max, "cheb_lo": o.cheb_lo})
+                          "coarse_max": o.coarse_max, "cheb_lo": o.cheb_lo, "tail_side": o.tail_side})
     flush = torch.empty(1 << 28, dtype=torch.float32, device="cuda")  # 1 GiB > L2
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -932,7 +932,7 @@ def run_ours(args, ws, rank, local):
             for h in B2.hs:
                 o = gk.gkb_get_options(h)
                 out["tuned"].append({"smoother_degree": o.smoother_degree, "kernel_variant": o.kernel_variant,
-                                     "coarse_max": o.coarse_max, "cheb_lo": o.cheb_lo})
+                                     "coarse_max": o.coarse_max, "cheb_lo": o.cheb_lo, "tail_side": o.tail_side})
         B2.destroy()
         return out
 

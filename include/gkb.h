@@ -165,10 +165,11 @@ typedef struct {
   int autotune;           /* 1: gkb_set_problem searches smoother_degree (1..3),
                              kernel_variant (0..2), coarse_max (8, 16, 32) and
                              cheb_lo (0.05, 0.1, 0.2, 0.3), one after another,
-                             for the fastest inner solve (device time of one
-                             GMG-PCG solve to tol_inner, best of three; within
-                             2 % of each other, the candidate with fewer
-                             iterations) and keeps it; results
+                             then tail_side (0, 64; with 64, coarse_max
+                             again), for the fastest inner solve (device
+                             time of one GMG-PCG solve to tol_inner, best of
+                             three; within 2 % of each other, the candidate
+                             with fewer iterations) and keeps it; results
                              are cached per device, grid, viscosity kind,
                              precision, inner solver and gamma decade in the
                              process and, when the environment variable
@@ -190,6 +191,17 @@ typedef struct {
                              smoother degree and iteration limits) in lock
                              step: each step one kernel launch over all
                              problems; other batches keep the branches     */
+  int tail_side;          /* 2D constant viscosity, multigrid inner solvers:
+                             the levels from the first one whose longer side
+                             is at most tail_side down to the coarsest run
+                             as one thread-block-cluster kernel (smoothing,
+                             residuals, transfers and the dense coarse solve
+                             with cluster barriers between the steps; the same
+                             values as separate launches); 0 (default): off.
+                             The autotuner tries 64 (on a GB300 it measured
+                             slower than separate launches: each fused step
+                             still pays its memory round trips, plus the
+                             barrier, on 16 SMs).                           */
 } gkb_options;
 
 typedef struct {

@@ -68,7 +68,7 @@ class gkb_options(ctypes.Structure):
                 ("profile", ctypes.c_int), ("kernel_variant", ctypes.c_int), ("unet_side", ctypes.c_int),
                 ("fcg_rho", ctypes.c_double), ("fgmres_restart", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("viscous_form", ctypes.c_int), ("batch_lockstep", ctypes.c_int)]
+                ("viscous_form", ctypes.c_int), ("batch_lockstep", ctypes.c_int), ("tail_side", ctypes.c_int)]
 
 
 class gkb_stats_t(ctypes.Structure):

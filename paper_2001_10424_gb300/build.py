@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libgkb.so")
 # GKB_PART into units that compile in parallel
 SOURCES = ([("kernels_f64.cu", ["-DGKB_PART=%d" % k]) for k in range(1, 8)]
            + [("kernels_f32.cu", ["-DGKB_PART=%d" % k]) for k in range(1, 8)]
-           + [(f, []) for f in ("solver.cu", "api.cu", "noalloc.cu", "unet.cu", "fgmres.cu", "lockstep.cu")])
+           + [(f, []) for f in ("solver.cu", "api.cu", "noalloc.cu", "unet.cu", "fgmres.cu", "lockstep.cu", "tail.cu")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -73,6 +73,7 @@ int gkb_default_options(gkb_options* opt) {
   opt->stream = nullptr;
   opt->viscous_form = GKB_VISC_LAPLACE;
   opt->batch_lockstep = 0;
+  opt->tail_side = 0;
   return GKB_OK;
 }
 
@@ -85,7 +86,7 @@ int gkb_create(gkb_handle* out, const gkb_options* opt) {
     return GKB_ERR_INVALID_ARG;
   if (!(opt->cheb_lo > 0 && opt->cheb_lo < opt->cheb_hi && opt->cheb_hi < 10)) return GKB_ERR_INVALID_ARG;
   if (opt->viscous_form != GKB_VISC_LAPLACE && opt->viscous_form != GKB_VISC_SYMGRAD) return GKB_ERR_INVALID_ARG;
-  if (opt->batch_lockstep < 0 || opt->batch_lockstep > 1) return GKB_ERR_INVALID_ARG;
+  if (opt->batch_lockstep < 0 || opt->batch_lockstep > 1 || opt->tail_side < 0) return GKB_ERR_INVALID_ARG;
   if (opt->unet_side < 0 || !(opt->fcg_rho >= 0 && opt->fcg_rho < 1) || opt->autotune < 0 || opt->autotune > 1)
     return GKB_ERR_INVALID_ARG;
   if (!(opt->tol_inner > 0) || opt->maxit < 0 || opt->maxit > 100000000 || opt->maxit_inner < 1 ||

@@ -10,6 +10,19 @@
 //   are kept exactly zero by every kernel, so flat BLAS-1 over the whole
 //   array equals BLAS-1 over the unknowns.
 #pragma once
+
+// Read-only loads and pointer qualifiers of the kernel bodies. By default the
+// bodies read their inputs through the read-only (non-coherent) path, which
+// is valid because no launch writes what it reads that way. A translation
+// unit that runs several dependent steps inside one kernel (writing arrays
+// that later steps read) defines both before including the headers, to plain
+// coherent loads and no restrict.
+#ifndef GKB_LDG
+#define GKB_LDG(p) __ldg(p)
+#endif
+#ifndef GKB_RESTRICT
+#define GKB_RESTRICT __restrict__
+#endif
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -147,7 +160,7 @@ template <> struct MuPtr<float>  { static __device__ __forceinline__ const float
 template <typename T, bool VarMu>
 __device__ __forceinline__ T cell_mu(const Lvl& L, int i, int j, int k) {
   if (!VarMu) return Kc<T>::mu0(L);
-  return __ldg(MuPtr<T>::get(L) + cix(L, i, j, k));
+  return GKB_LDG(MuPtr<T>::get(L) + cix(L, i, j, k));
 }
 
 template <typename T> struct NwPtr;
@@ -159,7 +172,7 @@ template <typename T, bool VarMu>
 __device__ __forceinline__ T cell_nw(const Lvl& L, long long cb) {
   if (!VarMu) return (T)1;
   const T* w = NwPtr<T>::get(L);
-  return w ? __ldg(w + cb) : (T)1;
+  return w ? GKB_LDG(w + cb) : (T)1;
 }
 
 __host__ __device__ __forceinline__ long long em_plane(const Lvl& L) {
@@ -200,7 +213,7 @@ __device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
     constexpr int E = 3 - C - A;
     int q[3] = {p[0], p[1], p[2]};
     q[A] = af;
-    return __ldg(em + (L.dim == 3 ? E : 0) * em_plane(L) + cix(L, q[0], q[1], q[2]));
+    return GKB_LDG(em + (L.dim == 3 ? E : 0) * em_plane(L) + cix(L, q[0], q[1], q[2]));
   }
   return edge_mu_cells<T, C, A>(L, p, af);
 }
@@ -210,7 +223,7 @@ __device__ __forceinline__ T edge_mu(const Lvl& L, const int p[3], int af) {
 // update the array they read between their own barriers)
 template <typename T, bool NC = true>
 __device__ __forceinline__ T ldv(const T* x, long long idx) {
-  if (NC) return __ldg(x + idx);
+  if (NC) return GKB_LDG(x + idx);
   return x[idx];
 }
 

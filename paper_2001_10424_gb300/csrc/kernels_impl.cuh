@@ -70,8 +70,8 @@ __device__ __forceinline__ bool const_regular(const Lvl& L, const int p[3]) {
 // +-S in z), in the order every path uses
 template <typename T>
 __device__ __forceinline__ T nb_sum(const Lvl& L, const T* xc) {
-  T acc = __ldg(xc + 1) + __ldg(xc - 1) + __ldg(xc + L.P) + __ldg(xc - L.P);
-  if (L.dim == 3) acc += __ldg(xc + L.S) + __ldg(xc - L.S);
+  T acc = GKB_LDG(xc + 1) + GKB_LDG(xc - 1) + GKB_LDG(xc + L.P) + GKB_LDG(xc - L.P);
+  if (L.dim == 3) acc += GKB_LDG(xc + L.S) + GKB_LDG(xc - L.S);
   return acc;
 }
 
@@ -103,10 +103,10 @@ __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* 
   const long long sc = strd<C>(L);
   const bool sym = L.sym;
   T acc = 0;
-  T m0 = __ldg(mc), m1 = __ldg(mc - sc);
+  T m0 = GKB_LDG(mc), m1 = GKB_LDG(mc - sc);
   if (sym) { m0 += m0; m1 += m1; }
-  acc = fma(m0, xf - __ldg(xc + sc), acc);
-  acc = fma(m1, xf - __ldg(xc - sc), acc);
+  acc = fma(m0, xf - GKB_LDG(xc + sc), acc);
+  acc = fma(m1, xf - GKB_LDG(xc - sc), acc);
 #pragma unroll
   for (int A = 0; A < 3; ++A) {
     if (A == C || A >= L.dim) continue;
@@ -119,14 +119,14 @@ __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* 
     // (-1, 0) in the order of edge_mu_cells
     const T* em = EmPtr<T>::get(L);
     const T* emp = em ? em + (L.dim == 3 ? 3 - C - A : 0) * em_plane(L) + (mc - MuPtr<T>::get(L)) : nullptr;
-    const T mup = em ? __ldg(emp + sa)
-                     : (((__ldg(mc - sc) + __ldg(mc - sc + sa)) + __ldg(mc)) + __ldg(mc + sa)) / (T)4;
-    acc = fma(mup, xf - __ldg(xc + sa), acc);
-    if (sym) acc = fma(-mup, __ldg(xa + sa) - __ldg(xa + sa - sc), acc);
-    const T mum = em ? __ldg(emp)
-                     : (((__ldg(mc - sc - sa) + __ldg(mc - sc)) + __ldg(mc - sa)) + __ldg(mc)) / (T)4;
-    acc = fma(mum, xf - __ldg(xc - sa), acc);
-    if (sym) acc = fma(mum, __ldg(xa) - __ldg(xa - sc), acc);
+    const T mup = em ? GKB_LDG(emp + sa)
+                     : (((GKB_LDG(mc - sc) + GKB_LDG(mc - sc + sa)) + GKB_LDG(mc)) + GKB_LDG(mc + sa)) / (T)4;
+    acc = fma(mup, xf - GKB_LDG(xc + sa), acc);
+    if (sym) acc = fma(-mup, GKB_LDG(xa + sa) - GKB_LDG(xa + sa - sc), acc);
+    const T mum = em ? GKB_LDG(emp)
+                     : (((GKB_LDG(mc - sc - sa) + GKB_LDG(mc - sc)) + GKB_LDG(mc - sa)) + GKB_LDG(mc)) / (T)4;
+    acc = fma(mum, xf - GKB_LDG(xc - sa), acc);
+    if (sym) acc = fma(mum, GKB_LDG(xa) - GKB_LDG(xa - sc), acc);
   }
   return acc;
 }
@@ -138,8 +138,8 @@ __device__ __forceinline__ T w_row_var_deep(const Lvl& L, const T* xc, const T* 
 //   mode 0: y = b - M x   (x null: y = b)
 //   mode 1: y = M x       (wonly: y = W x), DOT: reduce x.y
 template <typename T, bool VarMu, int MODE, bool DOT>
-__device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
-                                                     T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
+__device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wonly, const T* GKB_RESTRICT x, const T* GKB_RESTRICT b,
+                                                     T* GKB_RESTRICT y, RedBuf red, int fin, void* st, const int* pred) {
   // row stride 40 (>= BX + 1): conflict-free for the 8 x 4 warps of 3D levels
   // (8r + c covers the 32 banks) as well as for 32-wide rows
   __shared__ T Dt[2][BY + 1][40];
@@ -162,9 +162,9 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
     for (int t = tid; t < TN; t += BX * BY) {
       const int r = t / TW, c = t - r * TW;
       const long long g = cix(L, i0 - 1 + c, j0 - 1 + r, 0);
-      Tl[0][r][c] = __ldg(x + L.off[0] + g);
-      Tl[1][r][c] = __ldg(x + L.off[1] + g);
-      if (VarMu) Tl[VarMu ? 2 : 0][r][c] = __ldg(mu + g);
+      Tl[0][r][c] = GKB_LDG(x + L.off[0] + g);
+      Tl[1][r][c] = GKB_LDG(x + L.off[1] + g);
+      if (VarMu) Tl[VarMu ? 2 : 0][r][c] = GKB_LDG(mu + g);
     }
     __syncthreads();
     if (gd) {
@@ -173,7 +173,7 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
       for (int t = tid; t < (BY + 1) * (BX + 1); t += BX * BY) {
         const int cj = t / (BX + 1), ci = t - cj * (BX + 1);
         T dv = Tl[0][cj][ci] - Tl[0][cj][ci + 1] + Tl[1][cj][ci] - Tl[1][cj + 1][ci];
-        if (nw) dv *= __ldg(nw + cix(L, i0 - 1 + ci, j0 - 1 + cj, 0));
+        if (nw) dv *= GKB_LDG(nw + cix(L, i0 - 1 + ci, j0 - 1 + cj, 0));
         Dt[0][cj][ci] = dv;
       }
       __syncthreads();
@@ -189,7 +189,7 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
       if (cell_in(L, gi, gj, gk)) {
         const long long cc = cix(L, gi, gj, gk);
         T dv = neg_div_at<T>(L, x, cc);
-        if (VarMu && NwPtr<T>::get(L)) dv *= __ldg(NwPtr<T>::get(L) + cc);
+        if (VarMu && NwPtr<T>::get(L)) dv *= GKB_LDG(NwPtr<T>::get(L) + cc);
         Dt[pl][cj][ci] = dv;
       } else {
         Dt[pl][cj][ci] = (T)0;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
     {                                                                            \
       const long long id = L.off[C] + cb;                                        \
       const T* xc = x + id;                                                      \
-      const T xf = __ldg(xc);                                                    \
+      const T xf = GKB_LDG(xc);                                                    \
       const T acc = nb_sum<T>(L, xc);                                            \
       const T val = const_row<T, MODE>(L, (MODE == 0) ? b[id] : (T)0, xf, acc, gd, DPLUS, DMINUS); \
       if (DOT) dot += (double)xf * (double)val;                                  \
@@ -284,7 +284,7 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
 #define GKB_TILE_VDEEP(C, DPLUS, DMINUS)                                         \
     {                                                                            \
       const long long id = L.off[C] + cb;                                        \
-      const T xf = __ldg(x + id);                                                \
+      const T xf = GKB_LDG(x + id);                                                \
       T m = mul_rn(w_row_var_deep<T, C>(L, x + id, mc, xf), ws);                 \
       if (gd) m = fma(g2, (DPLUS) - (DMINUS), m);                                \
       const T val = (MODE == 0) ? b[id] - m : m;                                 \
@@ -333,8 +333,8 @@ __device__ __forceinline__ void mac_tile_body(const Blk& B, const Lvl& L, int wo
 }
 
 template <typename T, bool VarMu, int MODE, bool DOT>
-__global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* __restrict__ x, const T* __restrict__ b,
-                                                     T* __restrict__ y, RedBuf red, int fin, void* st, const int* pred) {
+__global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* GKB_RESTRICT x, const T* GKB_RESTRICT b,
+                                                     T* GKB_RESTRICT y, RedBuf red, int fin, void* st, const int* pred) {
   mac_tile_body<T, VarMu, MODE, DOT>(native_blk(), L, wonly, x, b, y, red, fin, st, pred);
 }
 
@@ -402,8 +402,8 @@ inline dim3 mac3_grid(const Lvl& L) {
 }
 
 template <typename T, int MODE, bool DOT>
-__device__ __forceinline__ double mac3_box_body(const Blk& B, const Lvl& L, int wonly, const T* __restrict__ x,
-                                                const T* __restrict__ b, T* __restrict__ y) {
+__device__ __forceinline__ double mac3_box_body(const Blk& B, const Lvl& L, int wonly, const T* GKB_RESTRICT x,
+                                                const T* GKB_RESTRICT b, T* GKB_RESTRICT y) {
   constexpr int TW = BX + 2, TH = BY + 2;
   __shared__ T Xt[3][3][TH][TW];      // [plane slot][component][row][col]: position (i0-1+col, j0-1+row)
   __shared__ T Dv[2][BY + 1][BX + 1];  // [cell plane parity][row][col]: cell (i0-1+col, j0-1+row)
@@ -536,8 +536,8 @@ __device__ __forceinline__ double mac3_box_body(const Blk& B, const Lvl& L, int 
 // the three faces as k_mac_tile's general path forms them (divergences from
 // neg_div)
 template <typename T, int MODE, bool DOT>
-__device__ __forceinline__ double mac3_shell_body(const Lvl& L, int wonly, const T* __restrict__ x,
-                                                  const T* __restrict__ b, T* __restrict__ y, long long t) {
+__device__ __forceinline__ double mac3_shell_body(const Lvl& L, int wonly, const T* GKB_RESTRICT x,
+                                                  const T* GKB_RESTRICT b, T* GKB_RESTRICT y, long long t) {
   if (t >= mac3_shell_count(L)) return 0.0;
   int i, j, k;
   shell_ijk(L, 1, 2, t, i, j, k);
@@ -575,8 +575,8 @@ __device__ __forceinline__ double mac3_shell_body(const Lvl& L, int wonly, const
 
 // DOT: x . y over box and shell, reduced through finaliser fin on st
 template <typename T, int MODE, bool DOT>
-__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_mac3(Lvl L, int wonly, const T* __restrict__ x,
-                                                    const T* __restrict__ b, T* __restrict__ y, RedBuf red,
+__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_mac3(Lvl L, int wonly, const T* GKB_RESTRICT x,
+                                                    const T* GKB_RESTRICT b, T* GKB_RESTRICT y, RedBuf red,
                                                     int fin, void* st) {
   const int bz = mac3_box_z(L);
   double dot;
@@ -722,10 +722,10 @@ __device__ __forceinline__ void patch_rhs(const Lvl& L, const T* r, long long ce
   constexpr int a = EAx<E>::a, b = EAx<E>::b;
   const T* ra = r + L.off[a] + ce;
   const T* rb = r + L.off[b] + ce;
-  out[0] = act[0] ? __ldg(ra - strd<b>(L)) : (T)0;
-  out[1] = act[1] ? __ldg(ra) : (T)0;
-  out[2] = act[2] ? __ldg(rb - strd<a>(L)) : (T)0;
-  out[3] = act[3] ? __ldg(rb) : (T)0;
+  out[0] = act[0] ? GKB_LDG(ra - strd<b>(L)) : (T)0;
+  out[1] = act[1] ? GKB_LDG(ra) : (T)0;
+  out[2] = act[2] ? GKB_LDG(rb - strd<a>(L)) : (T)0;
+  out[3] = act[3] ? GKB_LDG(rb) : (T)0;
 }
 
 template <int E>
@@ -775,17 +775,17 @@ __host__ __device__ __forceinline__ int sym4(int r, int c) {
 // row `slot` of the stored inverse of patch e applied to the patch residual
 template <typename T, int E>
 __device__ __forceinline__ T patch_vtab_row(const Lvl& L, const T* r, const int e[3], long long ce, int slot,
-                                            const T* __restrict__ vtab) {
+                                            const T* GKB_RESTRICT vtab) {
   constexpr int a = EAx<E>::a, b = EAx<E>::b;
   const long long Q = vtab_plane(L);
   const T* t = vtab + (size_t)(L.dim == 3 ? E : 0) * 10 * Q + ce;
   const T* ra = r + L.off[a] + ce;
   const T* rb = r + L.off[b] + ce;
   // faces outside the store (below the first node) are inactive: coefficient 0
-  const T r0 = e[b] > 0 ? __ldg(ra - strd<b>(L)) : (T)0;
-  const T r2 = e[a] > 0 ? __ldg(rb - strd<a>(L)) : (T)0;
-  return __ldg(t + sym4(slot, 0) * Q) * r0 + __ldg(t + sym4(slot, 1) * Q) * __ldg(ra) +
-         __ldg(t + sym4(slot, 2) * Q) * r2 + __ldg(t + sym4(slot, 3) * Q) * __ldg(rb);
+  const T r0 = e[b] > 0 ? GKB_LDG(ra - strd<b>(L)) : (T)0;
+  const T r2 = e[a] > 0 ? GKB_LDG(rb - strd<a>(L)) : (T)0;
+  return GKB_LDG(t + sym4(slot, 0) * Q) * r0 + GKB_LDG(t + sym4(slot, 1) * Q) * GKB_LDG(ra) +
+         GKB_LDG(t + sym4(slot, 2) * Q) * r2 + GKB_LDG(t + sym4(slot, 3) * Q) * GKB_LDG(rb);
 }
 
 // contribution of the patch of edge e (padded index ce) to slot `slot` of z = C r
@@ -793,7 +793,7 @@ __device__ __forceinline__ T patch_vtab_row(const Lvl& L, const T* r, const int 
 // for variable viscosity)
 template <typename T, bool VarMu, int E>
 __device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e[3], long long ce, int slot,
-                                           const T* __restrict__ table) {
+                                           const T* GKB_RESTRICT table) {
   bool act[4];
   T rp[4];
   if (VarMu) return patch_vtab_row<T, E>(L, r, e, ce, slot, table);
@@ -804,7 +804,7 @@ __device__ __forceinline__ T patch_contrib(const Lvl& L, const T* r, const int e
   patch_active<E>(L, e, act);
   patch_rhs<T, E>(L, r, ce, act, rp);
   const T* row = table + (size_t)(E * 75 + patch_class<E>(L, e)) * 16 + slot * 4;
-  return __ldg(row + 0) * rp[0] + __ldg(row + 1) * rp[1] + __ldg(row + 2) * rp[2] + __ldg(row + 3) * rp[3];
+  return GKB_LDG(row + 0) * rp[0] + GKB_LDG(row + 1) * rp[1] + GKB_LDG(row + 2) * rp[2] + GKB_LDG(row + 3) * rp[3];
 }
 
 // the two patches of orientation E that contain a face of component C at
@@ -855,8 +855,8 @@ __device__ __forceinline__ T patch_deep(const Lvl& L, const T* r, long long ce, 
   constexpr int a = EAx<E>::a, b = EAx<E>::b;
   const T* ra = r + L.off[a] + ce;
   const T* rb = r + L.off[b] + ce;
-  return __ldg(row + 0) * __ldg(ra - strd<b>(L)) + __ldg(row + 1) * __ldg(ra) + __ldg(row + 2) * __ldg(rb - strd<a>(L)) +
-         __ldg(row + 3) * __ldg(rb);
+  return GKB_LDG(row + 0) * GKB_LDG(ra - strd<b>(L)) + GKB_LDG(row + 1) * GKB_LDG(ra) + GKB_LDG(row + 2) * GKB_LDG(rb - strd<a>(L)) +
+         GKB_LDG(row + 3) * GKB_LDG(rb);
 }
 
 template <typename T, int C, int E>
@@ -885,11 +885,11 @@ __device__ __forceinline__ T patch_apply_deep(const Lvl& L, const T* r, long lon
 constexpr int PATCH_FOLD_OFF = 3 * 75 * 16;
 
 template <typename T, int C>
-__device__ __forceinline__ T patch_apply_fold(const Lvl& L, const T* __restrict__ r, long long cb,
-                                              const T* __restrict__ fold) {
+__device__ __forceinline__ T patch_apply_fold(const Lvl& L, const T* GKB_RESTRICT r, long long cb,
+                                              const T* GKB_RESTRICT fold) {
   const T* f = fold + C * 16;
   const T* rc = r + L.off[C] + cb;
-  T acc = __ldg(f) * __ldg(rc);
+  T acc = GKB_LDG(f) * GKB_LDG(rc);
   int t = 1;
 #pragma unroll
   for (int E = 0; E < 3; ++E) {
@@ -899,19 +899,19 @@ __device__ __forceinline__ T patch_apply_fold(const Lvl& L, const T* __restrict_
     const T* ra = r + L.off[a] + cb;
     const T* rb = r + L.off[b] + cb;
     if (C == a) {
-      acc += __ldg(f + t + 0) * __ldg(ra - sb);
-      acc += __ldg(f + t + 1) * __ldg(rb - sa);
-      acc += __ldg(f + t + 2) * __ldg(rb);
-      acc += __ldg(f + t + 3) * __ldg(ra + sb);
-      acc += __ldg(f + t + 4) * __ldg(rb + sb - sa);
-      acc += __ldg(f + t + 5) * __ldg(rb + sb);
+      acc += GKB_LDG(f + t + 0) * GKB_LDG(ra - sb);
+      acc += GKB_LDG(f + t + 1) * GKB_LDG(rb - sa);
+      acc += GKB_LDG(f + t + 2) * GKB_LDG(rb);
+      acc += GKB_LDG(f + t + 3) * GKB_LDG(ra + sb);
+      acc += GKB_LDG(f + t + 4) * GKB_LDG(rb + sb - sa);
+      acc += GKB_LDG(f + t + 5) * GKB_LDG(rb + sb);
     } else {
-      acc += __ldg(f + t + 0) * __ldg(ra - sb);
-      acc += __ldg(f + t + 1) * __ldg(ra);
-      acc += __ldg(f + t + 2) * __ldg(rb - sa);
-      acc += __ldg(f + t + 3) * __ldg(ra + sa - sb);
-      acc += __ldg(f + t + 4) * __ldg(ra + sa);
-      acc += __ldg(f + t + 5) * __ldg(rb + sa);
+      acc += GKB_LDG(f + t + 0) * GKB_LDG(ra - sb);
+      acc += GKB_LDG(f + t + 1) * GKB_LDG(ra);
+      acc += GKB_LDG(f + t + 2) * GKB_LDG(rb - sa);
+      acc += GKB_LDG(f + t + 3) * GKB_LDG(ra + sa - sb);
+      acc += GKB_LDG(f + t + 4) * GKB_LDG(ra + sa);
+      acc += GKB_LDG(f + t + 5) * GKB_LDG(rb + sa);
     }
     t += 6;
   }
@@ -982,7 +982,7 @@ __host__ __device__ __forceinline__ int rep7(int c, int n) {
 // rows of the class inverses, scattered into the stencil slots t..t+5 and the
 // face's own slot 0 (inactive faces contribute nothing)
 template <typename T, int E>
-__device__ void fold3_orient(const Lvl& L, const T* __restrict__ inv, const int p[3], int C, double acc[13], int t) {
+__device__ void fold3_orient(const Lvl& L, const T* GKB_RESTRICT inv, const int p[3], int C, double acc[13], int t) {
   constexpr int a = EAx<E>::a, b = EAx<E>::b;
   int e0[3] = {p[0], p[1], p[2]};
   int e1[3] = {p[0], p[1], p[2]};
@@ -1052,10 +1052,10 @@ struct Fold3In {
 // read, which are active faces inside the arrays. Offsets are 32-bit (the
 // padded arrays hold fewer than 2^31 entries).
 template <typename T, int C, bool Inner, class Coef>
-__device__ __forceinline__ T fold3_apply(const Lvl& L, const T* __restrict__ r, int cb, Coef f) {
+__device__ __forceinline__ T fold3_apply(const Lvl& L, const T* GKB_RESTRICT r, int cb, Coef f) {
   const int P = L.P, S = (int)L.S;
   const T* rc = r + L.off[C] + cb;
-  T acc = f(0) * __ldg(rc);
+  T acc = f(0) * GKB_LDG(rc);
   int t = 1;
 #pragma unroll
   for (int E = 0; E < 3; ++E) {
@@ -1076,7 +1076,7 @@ __device__ __forceinline__ T fold3_apply(const Lvl& L, const T* __restrict__ r, 
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
       const T c = f(t + u);
-      if (Inner || c != (T)0) acc += c * __ldg(base[u] + o[u]);
+      if (Inner || c != (T)0) acc += c * GKB_LDG(base[u] + o[u]);
     }
     t += 6;
   }
@@ -1086,8 +1086,8 @@ __device__ __forceinline__ T fold3_apply(const Lvl& L, const T* __restrict__ r, 
 // one Chebyshev step at one position: d, x are read before the stencil so
 // that their loads overlap it
 template <typename T, int C, bool Inner, class Coef>
-__device__ __forceinline__ void cheb3_face(const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
-                                           T* __restrict__ d, T ca, T cb, int x_zero, int p0, Coef f) {
+__device__ __forceinline__ void cheb3_face(const Lvl& L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                           T* GKB_RESTRICT d, T ca, T cb, int x_zero, int p0, Coef f) {
   const int id = (int)L.off[C] + p0;
   const T dold = (cb != (T)0) ? d[id] : (T)0;
   const T xold = x_zero ? (T)0 : x[id];
@@ -1105,8 +1105,8 @@ __device__ __forceinline__ void cheb3_face(const Lvl& L, const T* __restrict__ r
 constexpr int CHEB3_KZ = 4;
 
 template <typename T>
-__device__ __forceinline__ void cheb3_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
-                                           T* __restrict__ d, T ca, T cb, int x_zero, const T* __restrict__ table,
+__device__ __forceinline__ void cheb3_body(const Blk& B, const Lvl& L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                           T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* GKB_RESTRICT table,
                                            const Fold3In<T>& fin) {
   const int i0 = B.x * BX, j0 = B.y * BY, k0 = B.z * CHEB3_KZ;
   const int i = i0 + threadIdx.x;
@@ -1139,11 +1139,11 @@ __device__ __forceinline__ void cheb3_body(const Blk& B, const Lvl& L, const T* 
       continue;
     }
     if (in_store<0>(L, i, j, k) && face_active<0>(L, i, j, k))
-      cheb3_face<T, 0, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + q); });
+      cheb3_face<T, 0, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return GKB_LDG(fold + q); });
     if (in_store<1>(L, i, j, k) && face_active<1>(L, i, j, k))
-      cheb3_face<T, 1, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 16 + q); });
+      cheb3_face<T, 1, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return GKB_LDG(fold + 16 + q); });
     if (in_store<2>(L, i, j, k) && face_active<2>(L, i, j, k))
-      cheb3_face<T, 2, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 32 + q); });
+      cheb3_face<T, 2, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return GKB_LDG(fold + 32 + q); });
   }
 }
 
@@ -1184,11 +1184,11 @@ struct Fold2In {
 // (C r) at an active face of component C by the 7-point stencil f (2D);
 // Inner == false reads only faces with nonzero coefficients
 template <typename T, int C, bool Inner, class Coef>
-__device__ __forceinline__ T fold2_apply(const Lvl& L, const T* __restrict__ r, int cb, Coef f) {
+__device__ __forceinline__ T fold2_apply(const Lvl& L, const T* GKB_RESTRICT r, int cb, Coef f) {
   const int P = L.P;
   const T* ra = r + L.off[0] + cb;
   const T* rb = r + L.off[1] + cb;
-  T acc = f(0) * __ldg(C == 0 ? ra : rb);
+  T acc = f(0) * GKB_LDG(C == 0 ? ra : rb);
   const T* base[6];
   int o[6];
   if (C == 0) {
@@ -1201,7 +1201,7 @@ __device__ __forceinline__ T fold2_apply(const Lvl& L, const T* __restrict__ r, 
 #pragma unroll
   for (int u = 0; u < 6; ++u) {
     const T c = f(1 + u);
-    if (Inner || c != (T)0) acc += c * __ldg(base[u] + o[u]);
+    if (Inner || c != (T)0) acc += c * GKB_LDG(base[u] + o[u]);
   }
   return acc;
 }
@@ -1211,8 +1211,8 @@ __device__ __forceinline__ T fold2_apply(const Lvl& L, const T* __restrict__ r, 
 // are all interior use the kernel parameter's stencils, already scaled by
 // ca (d = z + cb d); the others each position's class stencil from the table.
 template <typename T>
-__device__ __forceinline__ void cheb2_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
-                                           T* __restrict__ d, T ca, T cb, int x_zero, const T* __restrict__ table,
+__device__ __forceinline__ void cheb2_body(const Blk& B, const Lvl& L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                           T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* GKB_RESTRICT table,
                                            const Fold2In<T>& fs) {
   const int i0 = B.x * BX, j0 = B.y * BY;
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
@@ -1243,7 +1243,7 @@ __device__ __forceinline__ void cheb2_body(const Blk& B, const Lvl& L, const T* 
     const int id = (int)L.off[C] + p0;                                                            \
     const T dold = (cb != (T)0) ? d[id] : (T)0;                                                   \
     const T xold = x_zero ? (T)0 : x[id];                                                         \
-    const T z = fold2_apply<T, C, false>(L, r, p0, [&](int q) { return __ldg(fold + C * 16 + q); }); \
+    const T z = fold2_apply<T, C, false>(L, r, p0, [&](int q) { return GKB_LDG(fold + C * 16 + q); }); \
     const T dn = (cb != (T)0) ? ca * z + cb * dold : ca * z;                                      \
     d[id] = dn;                                                                                   \
     x[id] = x_zero ? dn : xold + dn;                                                              \
@@ -1254,8 +1254,8 @@ __device__ __forceinline__ void cheb2_body(const Blk& B, const Lvl& L, const T* 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_cheb2(Lvl L, const T* __restrict__ r, T* __restrict__ x,
-                                                   T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
+__global__ void __launch_bounds__(BX* BY) k_cheb2(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                   T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* table,
                                                    const __grid_constant__ Fold2In<T> fs) {
   cheb2_body<T>(native_blk(), L, r, x, d, ca, cb, x_zero, table, fs);
 }
@@ -1279,8 +1279,8 @@ inline bool cheb3_level(const Lvl& L) {
 inline bool cheb3_applies(const Lvl& L, const void* table) { return table != nullptr && cheb3_level(L); }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_cheb3(Lvl L, const T* __restrict__ r, T* __restrict__ x,
-                                                   T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
+__global__ void __launch_bounds__(BX* BY) k_cheb3(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                   T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* table,
                                                    const __grid_constant__ Fold3In<T> fin) {
   cheb3_body<T>(native_blk(), L, r, x, d, ca, cb, x_zero, table, fin);
 }
@@ -1344,8 +1344,8 @@ __device__ __forceinline__ T fold3_tile(const T (*Rt)[3][BY + 2][BX + 2], int sm
 }
 
 template <typename T>
-__device__ __forceinline__ void cheb3s_box_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
-                                                T* __restrict__ d, T ca, T cb, int x_zero, const Fold3In<T>& fin) {
+__device__ __forceinline__ void cheb3s_box_body(const Blk& B, const Lvl& L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                T* GKB_RESTRICT d, T ca, T cb, int x_zero, const Fold3In<T>& fin) {
   constexpr int TW = BX + 2, TH = BY + 2;
   __shared__ T Rt[3][3][TH][TW];   // [plane slot][component][row][col]: position (i0-1+col, j0-1+row)
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
@@ -1438,9 +1438,9 @@ __device__ __forceinline__ void cheb3s_box_body(const Blk& B, const Lvl& L, cons
 
 // one position of the shell [3, n-3]: the class path of cheb3_body
 template <typename T>
-__device__ __forceinline__ void cheb3s_shell_body(const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
-                                                  T* __restrict__ d, T ca, T cb, int x_zero,
-                                                  const T* __restrict__ table, const Fold3In<T>& fin, long long t) {
+__device__ __forceinline__ void cheb3s_shell_body(const Lvl& L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                  T* GKB_RESTRICT d, T ca, T cb, int x_zero,
+                                                  const T* GKB_RESTRICT table, const Fold3In<T>& fin, long long t) {
   if (t >= shell_count(L, 3, 3)) return;
   int i, j, k;
   shell_ijk(L, 3, 3, t, i, j, k);
@@ -1454,16 +1454,16 @@ __device__ __forceinline__ void cheb3s_shell_body(const Lvl& L, const T* __restr
     return;
   }
   if (in_store<0>(L, i, j, k) && face_active<0>(L, i, j, k))
-    cheb3_face<T, 0, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + q); });
+    cheb3_face<T, 0, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return GKB_LDG(fold + q); });
   if (in_store<1>(L, i, j, k) && face_active<1>(L, i, j, k))
-    cheb3_face<T, 1, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 16 + q); });
+    cheb3_face<T, 1, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return GKB_LDG(fold + 16 + q); });
   if (in_store<2>(L, i, j, k) && face_active<2>(L, i, j, k))
-    cheb3_face<T, 2, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return __ldg(fold + 32 + q); });
+    cheb3_face<T, 2, false>(L, r, x, d, ca, cb, x_zero, p0, [&](int q) { return GKB_LDG(fold + 32 + q); });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_cheb3s(Lvl L, const T* __restrict__ r, T* __restrict__ x,
-                                                      T* __restrict__ d, T ca, T cb, int x_zero, const T* table,
+__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_cheb3s(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                      T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* table,
                                                       const __grid_constant__ Fold3In<T> fin) {
   const int bz = cheb3s_box_z(L);
   if ((int)blockIdx.z < bz) {
@@ -1477,8 +1477,8 @@ __global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_cheb3s(Lvl L
 // One Chebyshev step of the patch-preconditioned smoother:
 //   z = C r;  d = ca * z + cb * d;  x = (x_zero ? 0 : x) + d
 template <typename T, bool VarMu>
-__device__ __forceinline__ void cheb_body(const Blk& B, const Lvl& L, const T* __restrict__ r, T* __restrict__ x,
-                                                  T* __restrict__ d, T ca, T cb, int x_zero, const T* table) {
+__device__ __forceinline__ void cheb_body(const Blk& B, const Lvl& L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                  T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* table) {
   int tx, ty;
   block_xy(L, tx, ty);
   const int i = B.x * BX + tx;
@@ -1517,14 +1517,14 @@ __device__ __forceinline__ void cheb_body(const Blk& B, const Lvl& L, const T* _
 }
 
 template <typename T, bool VarMu>
-__global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* __restrict__ r, T* __restrict__ x,
-                                                  T* __restrict__ d, T ca, T cb, int x_zero, const T* table) {
+__global__ void __launch_bounds__(BX* BY) k_cheb(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+                                                  T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* table) {
   cheb_body<T, VarMu>(native_blk(), L, r, x, d, ca, cb, x_zero, table);
 }
 
 // z = C r (power iteration, tests)
 template <typename T, bool VarMu>
-__global__ void __launch_bounds__(BX* BY) k_patch(Lvl L, const T* __restrict__ r, T* __restrict__ z, const T* table) {
+__global__ void __launch_bounds__(BX* BY) k_patch(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT z, const T* table) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
@@ -1587,7 +1587,7 @@ __global__ void k_patch_table(Lvl L, T* table) {
 // orientation E takes the positions with node coordinates along its two
 // other axes and a cell coordinate along E.
 template <typename T>
-__global__ void k_edge_mu(Lvl L, T* __restrict__ em) {
+__global__ void k_edge_mu(Lvl L, T* GKB_RESTRICT em) {
   const int e[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
                     (int)blockIdx.z};
   if (e[0] > L.n[0] || e[1] > L.n[1]) return;
@@ -1605,7 +1605,7 @@ __global__ void k_edge_mu(Lvl L, T* __restrict__ em) {
 // orientation E; e[a] in [0, n_a], e[b] in [0, n_b], e[E] in [0, n_E - 1]):
 // the patch matrix in the level's precision, Gauss-Jordan in FP64.
 template <typename T, int E>
-__global__ void k_patch_vtab(Lvl L, T* __restrict__ vtab) {
+__global__ void k_patch_vtab(Lvl L, T* GKB_RESTRICT vtab) {
   constexpr int a = EAx<E>::a, b = EAx<E>::b;
   const int e[3] = {(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(blockIdx.y * blockDim.y + threadIdx.y),
                     (int)blockIdx.z};
@@ -1642,7 +1642,7 @@ __global__ void k_patch_vtab(Lvl L, T* __restrict__ vtab) {
 
 // y = s * A p  (faces from cells): y_f = s * ascale * (p_plus - p_minus)
 template <typename T>
-__device__ __forceinline__ void grad_body(const Blk& B, const Lvl& L, const T* __restrict__ pc, T* __restrict__ y, T s) {
+__device__ __forceinline__ void grad_body(const Blk& B, const Lvl& L, const T* GKB_RESTRICT pc, T* GKB_RESTRICT y, T s) {
   const int i = B.x * BX + threadIdx.x;
   const int j = B.y * BY + threadIdx.y;
   const int k = B.z;
@@ -1652,8 +1652,8 @@ __device__ __forceinline__ void grad_body(const Blk& B, const Lvl& L, const T* _
     const long long id = L.off[C] + cix(L, i, j, k);                             \
     T val = 0;                                                                   \
     if (face_active<C>(L, i, j, k)) {                                            \
-      const T pp = cell_in(L, i, j, k) ? __ldg(pc + cix(L, i, j, k)) : (T)0;     \
-      const T pm = cell_in(L, i - DI, j - DJ, k - DK) ? __ldg(pc + cix(L, i - DI, j - DJ, k - DK)) : (T)0; \
+      const T pp = cell_in(L, i, j, k) ? GKB_LDG(pc + cix(L, i, j, k)) : (T)0;     \
+      const T pm = cell_in(L, i - DI, j - DJ, k - DK) ? GKB_LDG(pc + cix(L, i - DI, j - DJ, k - DK)) : (T)0; \
       val = sc * (pp - pm);                                                      \
     }                                                                            \
     y[id] = val;                                                                 \
@@ -1665,13 +1665,13 @@ __device__ __forceinline__ void grad_body(const Blk& B, const Lvl& L, const T* _
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_grad(Lvl L, const T* __restrict__ pc, T* __restrict__ y, T s) {
+__global__ void __launch_bounds__(BX* BY) k_grad(Lvl L, const T* GKB_RESTRICT pc, T* GKB_RESTRICT y, T s) {
   grad_body<T>(native_blk(), L, pc, y, s);
 }
 
 // y = s * A^T x  (cells from faces) = s * ascale * negdiv(x); padding untouched
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_negdiv(Lvl L, const T* __restrict__ x, T* __restrict__ y, T s) {
+__global__ void __launch_bounds__(BX* BY) k_negdiv(Lvl L, const T* GKB_RESTRICT x, T* GKB_RESTRICT y, T s) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
@@ -1686,13 +1686,13 @@ __global__ void __launch_bounds__(BX* BY) k_negdiv(Lvl L, const T* __restrict__ 
 template <typename T, int C>
 __device__ __forceinline__ T coarse_face(const Lvl& Lc, const T* xc, int I, int J, int K) {
   if (!face_active<C>(Lc, I, J, K)) return (T)0;
-  return __ldg(xc + Lc.off[C] + cix(Lc, I, J, K));
+  return GKB_LDG(xc + Lc.off[C] + cix(Lc, I, J, K));
 }
 
 template <typename T, int C>
 __device__ __forceinline__ T fine_face(const Lvl& Lf, const T* rf, int i, int j, int k) {
   if (!face_active<C>(Lf, i, j, k)) return (T)0;
-  return __ldg(rf + Lf.off[C] + cix(Lf, i, j, k));
+  return GKB_LDG(rf + Lf.off[C] + cix(Lf, i, j, k));
 }
 
 // ---- 2D flux-conserving, divergence-preserving transfers -----------------
@@ -1715,7 +1715,7 @@ __device__ __forceinline__ T coarse_slope(const Lvl& Lc, const T* xc, int I, int
   constexpr int t = 1 - C;
   int P[3] = {I, J, 0};
   if (!face_active<C>(Lc, P[0], P[1], 0)) return (T)0;
-  const T u0 = __ldg(xc + Lc.off[C] + cix(Lc, P[0], P[1], 0));
+  const T u0 = GKB_LDG(xc + Lc.off[C] + cix(Lc, P[0], P[1], 0));
   int Pp[3] = {P[0], P[1], 0}, Pm[3] = {P[0], P[1], 0};
   Pp[t] += 1;
   Pm[t] -= 1;
@@ -1750,7 +1750,7 @@ __device__ __forceinline__ T prolong_flux_val(const Lvl& Lc, const T* xc, int pc
 // 2J+1) with the operations of prolong_flux_val; the extra column I = n_x
 // and row J = n_y of threads take the fine faces on the last coarse lines.
 template <typename T>
-__device__ __forceinline__ void prolong_flux2d_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+__device__ __forceinline__ void prolong_flux2d_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* GKB_RESTRICT xc, T* GKB_RESTRICT xf) {
   const int I = B.x * BX + threadIdx.x;
   const int J = B.y * BY + threadIdx.y;
   if (I > Lc.n[0] || J > Lc.n[1]) return;
@@ -1800,7 +1800,7 @@ inline dim3 prolong2d_grid(const Lvl& Lc) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_prolong_flux2d(Lvl Lf, Lvl Lc, const T* __restrict__ xc, T* __restrict__ xf) {
+__global__ void __launch_bounds__(BX* BY) k_prolong_flux2d(Lvl Lf, Lvl Lc, const T* GKB_RESTRICT xc, T* GKB_RESTRICT xf) {
   prolong_flux2d_body<T>(native_blk(), Lf, Lc, xc, xf);
 }
 
@@ -1836,8 +1836,8 @@ __device__ __forceinline__ void restrict_flux_gather(const Lvl& Lf, const T* rf,
 
 // pass a: bc = rU, tmp = rD  (launched over the coarse face grid)
 template <typename T>
-__device__ __forceinline__ void restrict_flux2d_a_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* __restrict__ rf,
-                                                               T* __restrict__ bc, T* __restrict__ tmp) {
+__device__ __forceinline__ void restrict_flux2d_a_body(const Blk& B, const Lvl& Lf, const Lvl& Lc, const T* GKB_RESTRICT rf,
+                                                               T* GKB_RESTRICT bc, T* GKB_RESTRICT tmp) {
   const int I = B.x * BX + threadIdx.x;
   const int J = B.y * BY + threadIdx.y;
   if (in_store<0>(Lc, I, J, 0)) {
@@ -1857,8 +1857,8 @@ __device__ __forceinline__ void restrict_flux2d_a_body(const Blk& B, const Lvl& 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_a(Lvl Lf, Lvl Lc, const T* __restrict__ rf,
-                                                               T* __restrict__ bc, T* __restrict__ tmp) {
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_a(Lvl Lf, Lvl Lc, const T* GKB_RESTRICT rf,
+                                                               T* GKB_RESTRICT bc, T* GKB_RESTRICT tmp) {
   restrict_flux2d_a_body<T>(native_blk(), Lf, Lc, rf, bc, tmp);
 }
 
@@ -1870,16 +1870,16 @@ __device__ __forceinline__ T slope_transpose(const Lvl& Lc, const T* d, int I, i
   const int q = P[t], Nt = Lc.n[t];
   T acc = 0;
   int Q[3] = {P[0], P[1], 0};
-  if (q - 1 >= 0) { Q[t] = q - 1; acc += __ldg(d + Lc.off[C] + cix(Lc, Q[0], Q[1], 0)); }
-  if (q + 1 < Nt) { Q[t] = q + 1; acc -= __ldg(d + Lc.off[C] + cix(Lc, Q[0], Q[1], 0)); }
-  const T own = __ldg(d + Lc.off[C] + cix(Lc, I, J, 0));
+  if (q - 1 >= 0) { Q[t] = q - 1; acc += GKB_LDG(d + Lc.off[C] + cix(Lc, Q[0], Q[1], 0)); }
+  if (q + 1 < Nt) { Q[t] = q + 1; acc -= GKB_LDG(d + Lc.off[C] + cix(Lc, Q[0], Q[1], 0)); }
+  const T own = GKB_LDG(d + Lc.off[C] + cix(Lc, I, J, 0));
   if (q == 0) acc += own;
   if (q == Nt - 1) acc -= own;
   return acc * (T)0.125;
 }
 
 template <typename T>
-__device__ __forceinline__ void restrict_flux2d_b_body(const Blk& B, const Lvl& Lc, const T* __restrict__ tmp, T* __restrict__ bc) {
+__device__ __forceinline__ void restrict_flux2d_b_body(const Blk& B, const Lvl& Lc, const T* GKB_RESTRICT tmp, T* GKB_RESTRICT bc) {
   const int I = B.x * BX + threadIdx.x;
   const int J = B.y * BY + threadIdx.y;
   if (in_store<0>(Lc, I, J, 0) && face_active<0>(Lc, I, J, 0))
@@ -1889,7 +1889,7 @@ __device__ __forceinline__ void restrict_flux2d_b_body(const Blk& B, const Lvl& 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_b(Lvl Lc, const T* __restrict__ tmp, T* __restrict__ bc) {
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux2d_b(Lvl Lc, const T* GKB_RESTRICT tmp, T* GKB_RESTRICT bc) {
   restrict_flux2d_b_body<T>(native_blk(), Lc, tmp, bc);
 }
 
@@ -1914,7 +1914,7 @@ template <typename T, int C, int A>
 __device__ __forceinline__ T slope3(const Lvl& Lc, const T* xc, const int P[3]) {
   if (!face_active<C>(Lc, P[0], P[1], P[2])) return (T)0;
   const T* u = xc + Lc.off[C] + cix(Lc, P[0], P[1], P[2]);
-  const T u0 = __ldg(u);
+  const T u0 = GKB_LDG(u);
   int Pp[3] = {P[0], P[1], P[2]}, Pm[3] = {P[0], P[1], P[2]};
   Pp[A] += 1;
   Pm[A] -= 1;
@@ -1927,7 +1927,7 @@ __device__ __forceinline__ T slope3(const Lvl& Lc, const T* xc, const int P[3]) 
 // sl[kk * nvel + index of face P of component C] = slope3<C, Oth<C, kk>>(P)
 // (0 on inactive faces, which are never written and stay 0).
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_slopes3d(Lvl Lc, const T* __restrict__ xc, T* __restrict__ sl) {
+__global__ void __launch_bounds__(BX* BY) k_slopes3d(Lvl Lc, const T* GKB_RESTRICT xc, T* GKB_RESTRICT sl) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
@@ -1946,9 +1946,9 @@ __global__ void __launch_bounds__(BX* BY) k_slopes3d(Lvl Lc, const T* __restrict
 
 // slope / 8 of component C along axis A at coarse face P, from the table
 template <typename T, int C, int A>
-__device__ __forceinline__ T slope3_at(const Lvl& Lc, const T* __restrict__ sl, const int P[3]) {
+__device__ __forceinline__ T slope3_at(const Lvl& Lc, const T* GKB_RESTRICT sl, const int P[3]) {
   constexpr int kk = (Oth<C, 0>::v == A) ? 0 : 1;
-  return __ldg(sl + kk * Lc.nvel + Lc.off[C] + cix(Lc, P[0], P[1], P[2]));
+  return GKB_LDG(sl + kk * Lc.nvel + Lc.off[C] + cix(Lc, P[0], P[1], P[2]));
 }
 
 // value of the prolongation at fine face p of component C: on a coarse face,
@@ -1981,8 +1981,8 @@ __device__ __forceinline__ T prolong3_val_tab(const Lvl& Lc, const T* xc, const 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_prolong_flux3d(Lvl Lf, Lvl Lc, const T* __restrict__ xc,
-                                                           const T* __restrict__ sl, T* __restrict__ xf) {
+__global__ void __launch_bounds__(BX* BY) k_prolong_flux3d(Lvl Lf, Lvl Lc, const T* GKB_RESTRICT xc,
+                                                           const T* GKB_RESTRICT sl, T* GKB_RESTRICT xf) {
   const int i = blockIdx.x * BX + threadIdx.x;
   const int j = blockIdx.y * BY + threadIdx.y;
   const int k = blockIdx.z;
@@ -2050,8 +2050,8 @@ __device__ __forceinline__ void restrict3_gather(const Lvl& Lf, const T* rf, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_a(Lvl Lf, Lvl Lc, const T* __restrict__ rf, T* __restrict__ bc,
-                                                               T* __restrict__ d1, T* __restrict__ d2) {
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_a(Lvl Lf, Lvl Lc, const T* GKB_RESTRICT rf, T* GKB_RESTRICT bc,
+                                                               T* GKB_RESTRICT d1, T* GKB_RESTRICT d2) {
   const int I = blockIdx.x * BX + threadIdx.x;
   const int J = blockIdx.y * BY + threadIdx.y;
   const int K = blockIdx.z;
@@ -2076,17 +2076,17 @@ __device__ __forceinline__ T slope3_transpose(const Lvl& Lc, const T* d, const i
   const int q = Q[A], Nt = Lc.n[A];
   T acc = 0;
   int R[3] = {Q[0], Q[1], Q[2]};
-  if (q - 1 >= 0) { R[A] = q - 1; acc += __ldg(d + Lc.off[C] + cix(Lc, R[0], R[1], R[2])); }
-  if (q + 1 < Nt) { R[A] = q + 1; acc -= __ldg(d + Lc.off[C] + cix(Lc, R[0], R[1], R[2])); }
-  const T own = __ldg(d + Lc.off[C] + cix(Lc, Q[0], Q[1], Q[2]));
+  if (q - 1 >= 0) { R[A] = q - 1; acc += GKB_LDG(d + Lc.off[C] + cix(Lc, R[0], R[1], R[2])); }
+  if (q + 1 < Nt) { R[A] = q + 1; acc -= GKB_LDG(d + Lc.off[C] + cix(Lc, R[0], R[1], R[2])); }
+  const T own = GKB_LDG(d + Lc.off[C] + cix(Lc, Q[0], Q[1], Q[2]));
   if (q == 0) acc += own;
   if (q == Nt - 1) acc -= own;
   return acc * (T)0.125;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_b(Lvl Lc, const T* __restrict__ d1, const T* __restrict__ d2,
-                                                               T* __restrict__ bc) {
+__global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_b(Lvl Lc, const T* GKB_RESTRICT d1, const T* GKB_RESTRICT d2,
+                                                               T* GKB_RESTRICT bc) {
   const int I = blockIdx.x * BX + threadIdx.x;
   const int J = blockIdx.y * BY + threadIdx.y;
   const int K = blockIdx.z;
@@ -2103,21 +2103,21 @@ __global__ void __launch_bounds__(BX* BY) k_restrict_flux3d_b(Lvl Lc, const T* _
 
 // coarsest level: x[idx[r]] = sum_c Minv[r][c] b[idx[c]]; one warp per row
 template <typename T>
-__device__ __forceinline__ void coarse_solve_body(const Blk& B, int m, const T* __restrict__ Minv, const int* __restrict__ idx,
-                               const T* __restrict__ b, T* __restrict__ x) {
+__device__ __forceinline__ void coarse_solve_body(const Blk& B, int m, const T* GKB_RESTRICT Minv, const int* GKB_RESTRICT idx,
+                               const T* GKB_RESTRICT b, T* GKB_RESTRICT x) {
   const int warp = (B.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= m) return;
   double acc = 0.0;
   const T* row = Minv + (size_t)warp * m;
-  for (int c = lane; c < m; c += 32) acc += (double)row[c] * (double)__ldg(b + idx[c]);
+  for (int c = lane; c < m; c += 32) acc += (double)row[c] * (double)GKB_LDG(b + idx[c]);
   acc = warp_sum(acc);
   if (lane == 0) x[idx[warp]] = (T)acc;
 }
 
 template <typename T>
-__global__ void k_coarse_solve(int m, const T* __restrict__ Minv, const int* __restrict__ idx,
-                               const T* __restrict__ b, T* __restrict__ x) {
+__global__ void k_coarse_solve(int m, const T* GKB_RESTRICT Minv, const int* GKB_RESTRICT idx,
+                               const T* GKB_RESTRICT b, T* GKB_RESTRICT x) {
   coarse_solve_body<T>(native_blk(), m, Minv, idx, b, x);
 }
 
@@ -2129,7 +2129,7 @@ constexpr int RB = 256;
 
 // sum a.b (and b.b when NV == 2)
 template <typename T>
-__device__ __forceinline__ void dot_body(const Blk& B, long long len, const T* __restrict__ a, const T* __restrict__ b,
+__device__ __forceinline__ void dot_body(const Blk& B, long long len, const T* GKB_RESTRICT a, const T* GKB_RESTRICT b,
                                              RedBuf red, int fin, void* st, const int* pred) {
   if (pred && !*pred) return;  // every block skips, so the ticket stays untouched
   T acc = 0;
@@ -2141,15 +2141,15 @@ __device__ __forceinline__ void dot_body(const Blk& B, long long len, const T* _
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RB) k_dot(long long len, const T* __restrict__ a, const T* __restrict__ b,
+__global__ void __launch_bounds__(RB) k_dot(long long len, const T* GKB_RESTRICT a, const T* GKB_RESTRICT b,
                                              RedBuf red, int fin, void* st, const int* pred) {
   dot_body<T>(native_blk(), len, a, b, red, fin, st, pred);
 }
 
 // sums a.b and b.c in one pass
 template <typename T>
-__global__ void __launch_bounds__(RB) k_dot2(long long len, const T* __restrict__ a, const T* __restrict__ b,
-                                              const T* __restrict__ c, RedBuf red, int fin, void* st) {
+__global__ void __launch_bounds__(RB) k_dot2(long long len, const T* GKB_RESTRICT a, const T* GKB_RESTRICT b,
+                                              const T* GKB_RESTRICT c, RedBuf red, int fin, void* st) {
   T ab = 0, bc = 0;
   const long long stride = (long long)gridDim.x * RB;
   for (long long t = (long long)blockIdx.x * RB + threadIdx.x; t < len; t += stride) {
@@ -2163,8 +2163,8 @@ __global__ void __launch_bounds__(RB) k_dot2(long long len, const T* __restrict_
 
 // x += alpha p ; r -= alpha q ; sum r.r      (alpha from CgState)
 template <typename T>
-__device__ __forceinline__ void cg_update_body(const Blk& B, long long len, T* __restrict__ x, const T* __restrict__ p,
-                                                   T* __restrict__ r, const T* __restrict__ q,
+__device__ __forceinline__ void cg_update_body(const Blk& B, long long len, T* GKB_RESTRICT x, const T* GKB_RESTRICT p,
+                                                   T* GKB_RESTRICT r, const T* GKB_RESTRICT q,
                                                    const CgState* cg, RedBuf red, void* st, int fin) {
   const T alpha = (T)cg->alpha;
   T acc = 0;
@@ -2180,15 +2180,15 @@ __device__ __forceinline__ void cg_update_body(const Blk& B, long long len, T* _
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RB) k_cg_update(long long len, T* __restrict__ x, const T* __restrict__ p,
-                                                   T* __restrict__ r, const T* __restrict__ q,
+__global__ void __launch_bounds__(RB) k_cg_update(long long len, T* GKB_RESTRICT x, const T* GKB_RESTRICT p,
+                                                   T* GKB_RESTRICT r, const T* GKB_RESTRICT q,
                                                    const CgState* cg, RedBuf red, void* st, int fin) {
   cg_update_body<T>(native_blk(), len, x, p, r, q, cg, red, st, fin);
 }
 
 // p = z + beta p   (beta from CgState; first: p = z)
 template <typename T>
-__device__ __forceinline__ void cg_dir_body(const Blk& B, long long len, T* __restrict__ p, const T* __restrict__ z,
+__device__ __forceinline__ void cg_dir_body(const Blk& B, long long len, T* GKB_RESTRICT p, const T* GKB_RESTRICT z,
                                                 const CgState* cg, int first) {
   const T beta = first ? (T)0 : (T)cg->beta;
   const long long stride = (long long)B.nx * RB;
@@ -2199,14 +2199,14 @@ __device__ __forceinline__ void cg_dir_body(const Blk& B, long long len, T* __re
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RB) k_cg_dir(long long len, T* __restrict__ p, const T* __restrict__ z,
+__global__ void __launch_bounds__(RB) k_cg_dir(long long len, T* GKB_RESTRICT p, const T* GKB_RESTRICT z,
                                                 const CgState* cg, int first) {
   cg_dir_body<T>(native_blk(), len, p, z, cg, first);
 }
 
 // y = a x + b y (host scalars)
 template <typename T>
-__device__ __forceinline__ void axpby_body(const Blk& B, long long len, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+__device__ __forceinline__ void axpby_body(const Blk& B, long long len, T a, const T* GKB_RESTRICT x, T b, T* GKB_RESTRICT y) {
   const long long stride = (long long)B.nx * RB;
   // b = 0 overwrites y without reading it (y may hold stale non-finite values)
   for (long long t = (long long)B.x * RB + threadIdx.x; t < len; t += stride)
@@ -2214,7 +2214,7 @@ __device__ __forceinline__ void axpby_body(const Blk& B, long long len, T a, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(RB) k_axpby(long long len, T a, const T* __restrict__ x, T b, T* __restrict__ y) {
+__global__ void __launch_bounds__(RB) k_axpby(long long len, T a, const T* GKB_RESTRICT x, T b, T* GKB_RESTRICT y) {
   axpby_body<T>(native_blk(), len, a, x, b, y);
 }
 

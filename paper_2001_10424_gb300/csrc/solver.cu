@@ -553,6 +553,7 @@ void Gmg<T>::build(const Lvl& fine, const T* fine_mu, int coarse_max, int deg, c
   coarse_idx.alloc(m);
   GKB_CUDA(cudaMemcpyAsync(coarse_idx.p, idx32.data(), m * sizeof(int), cudaMemcpyHostToDevice, s));
   GKB_CUDA(cudaStreamSynchronize(s));
+  gmg_tail_setup<T>(*this, tail_side, s);
 }
 
 template <typename T>
@@ -612,7 +613,10 @@ void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s, bool use_net) {
   auto net_at = [&](int l) {
     unet_correct<T>(*net, *net_act, lev[l].L, lvl_b(l), lvl_x(l), net_q.p, net_img.p, net_nrm.p, red, s);
   };
-  for (int l = 0; l < lc; ++l) {
+  // the fused coarse end: levels from tail_level on run in one cluster kernel
+  const bool tail = !with_net && tail_level > 0 && tail_buf.p;
+  const int ld = tail ? tail_level : lc;  // levels handled by separate launches
+  for (int l = 0; l < ld; ++l) {
     bool x_zero = true;
     if (with_net && l == net_level) {  // composite form
       net_at(l);
@@ -622,9 +626,10 @@ void Gmg<T>::vcycle(const T* r0, T* z0, cudaStream_t s, bool use_net) {
     Ops<T>::residual(lev[l].L, lvl_x(l), lvl_b(l), lev[l].r.p, s);
     Ops<T>::restrict_(lev[l].L, lev[l + 1].L, lev[l].r.p, lev[l + 1].b.p, lev[l + 1].x.p, lev[l + 1].t2.p, s);
   }
-  if (replace) net_at(lc);
+  if (tail) gmg_tail_launch<T>(*this, s);
+  else if (replace) net_at(lc);
   else Ops<T>::coarse(coarse_m, coarse_inv.p, coarse_idx.p, lvl_b(lc), lvl_x(lc), s);
-  for (int l = lc - 1; l >= 0; --l) {
+  for (int l = ld - 1; l >= 0; --l) {
     Ops<T>::prolong(lev[l].L, lev[l + 1].L, lev[l + 1].x.p, lvl_x(l), lev[l + 1].sl.p, s);
     smooth(l, lvl_b(l), lvl_x(l), false, s);
   }
@@ -1260,6 +1265,7 @@ void Solver::build_inner() {
   L32.fast = (opt.kernel_variant == 1) ? 0 : 1;
   gmg32.cheb_lo = gmg64.cheb_lo = opt.cheb_lo;
   gmg32.cheb_hi = gmg64.cheb_hi = opt.cheb_hi;
+  gmg32.tail_side = gmg64.tail_side = opt.tail_side;
   if (mixed) {
     if (use_gmg) gmg32.build(L32, mu32.p, opt.coarse_max, opt.smoother_degree, red, scal.p, stream);
     cg32.init(L32, use_gmg ? &gmg32 : nullptr, red, cg_dev, cg_host);
@@ -1331,6 +1337,7 @@ struct Tuned {
   int degree, variant, coarse_max;
   double lo, ms;
   int its = 0;   // iterations of the timed solve (tie-break; not stored in the file)
+  int tail = 0;  // tail_side
 };
 std::mutex g_tune_mutex;
 std::map<std::string, Tuned> g_tune_cache;
@@ -1348,10 +1355,16 @@ void tune_read_file() {
   if (!path) return;
   FILE* fp = fopen(path, "r");
   if (!fp) return;
-  char key[512];
-  Tuned t{};
-  while (fscanf(fp, "%511s %d %d %d %lf %lf", key, &t.degree, &t.variant, &t.coarse_max, &t.lo, &t.ms) == 6)
+  // one entry per line: key degree variant coarse_max cheb_lo ms [tail_side]
+  char line[1024], key[512];
+  while (fgets(line, sizeof line, fp)) {
+    Tuned t{};
+    const int n = sscanf(line, "%511s %d %d %d %lf %lf %d", key, &t.degree, &t.variant, &t.coarse_max, &t.lo, &t.ms,
+                         &t.tail);
+    if (n < 6) break;
+    if (n == 6) t.tail = 0;
     g_tune_cache[key] = t;
+  }
   fclose(fp);
 }
 }  // namespace
@@ -1383,21 +1396,23 @@ void Solver::autotune_inner(bool var_mu, int weighted) {
       opt.kernel_variant = it->second.variant;
       opt.coarse_max = it->second.coarse_max;
       opt.cheb_lo = it->second.lo;
+      opt.tail_side = it->second.tail;
       tuned_ms = it->second.ms;
       build_inner();
       return;
     }
   }
-  Tuned best{opt.smoother_degree, opt.kernel_variant, opt.coarse_max, opt.cheb_lo, 1e300};
+  Tuned best{opt.smoother_degree, opt.kernel_variant, opt.coarse_max, opt.cheb_lo, 1e300, 0, opt.tail_side};
   // a candidate replaces the best when it is faster by more than the timing
   // noise (2 %), or when the two are within it and the candidate needs fewer
   // iterations (a stronger preconditioner: more work per launch, which also
   // holds up better when several solves share the GPU)
-  auto trial = [&](int deg, int var, int cmax, double lo) {
+  auto trial = [&](int deg, int var, int cmax, double lo, int tail) {
     opt.smoother_degree = deg;
     opt.kernel_variant = var;
     opt.coarse_max = cmax;
     opt.cheb_lo = lo;
+    opt.tail_side = tail;
     double ms = 1e300;
     int its = 0;
     try {
@@ -1409,33 +1424,46 @@ void Solver::autotune_inner(bool var_mu, int weighted) {
     if (!(ms < 1e300)) return;
     const bool faster = ms < 0.98 * best.ms;
     const bool tie = !faster && ms <= 1.02 * best.ms && its < best.its;
-    if (faster || tie) best = Tuned{deg, var, cmax, lo, ms, its};
+    if (faster || tie) best = Tuned{deg, var, cmax, lo, ms, its, tail};
   };
   const double lo0 = best.lo;
-  trial(best.degree, best.variant, best.coarse_max, lo0);
+  const int t0 = best.tail;
+  trial(best.degree, best.variant, best.coarse_max, lo0, t0);
   for (int v = 0; v <= 2; ++v)
-    if (v != best.variant) trial(best.degree, v, best.coarse_max, lo0);
+    if (v != best.variant) trial(best.degree, v, best.coarse_max, lo0, t0);
   const int v0 = best.variant;
   for (int deg = 1; deg <= 3; ++deg)
-    if (deg != best.degree) trial(deg, v0, best.coarse_max, lo0);
+    if (deg != best.degree) trial(deg, v0, best.coarse_max, lo0, t0);
   const int d0 = best.degree;
   for (int cmax : {8, 16, 32})
-    if (cmax != best.coarse_max) trial(d0, v0, cmax, lo0);
+    if (cmax != best.coarse_max) trial(d0, v0, cmax, lo0, t0);
   const int c0 = best.coarse_max;
   for (double lo : {0.05, 0.1, 0.2, 0.3})
-    if (lo != best.lo && lo < opt.cheb_hi) trial(d0, v0, c0, lo);
+    if (lo != best.lo && lo < opt.cheb_hi) trial(d0, v0, c0, lo, t0);
+  // the fused coarse end (2D, constant viscosity); with it the coarse size
+  // is tried again (deeper hierarchies cost less when their end is fused)
+  if (grid.dim == 2 && !var_mu) {
+    const double l0 = best.lo;
+    const int tb = best.tail == 64 ? 0 : 64;
+    trial(d0, v0, c0, l0, tb);
+    if (best.tail == 64)
+      for (int cmax : {8, 16, 32})
+        if (cmax != best.coarse_max) trial(d0, v0, cmax, l0, 64);
+  }
   if (!(best.ms < 1e300)) throw Error{GKB_ERR_INNER_NOT_CONVERGED, "no autotuning candidate converged"};
   opt.smoother_degree = best.degree;
   opt.kernel_variant = best.variant;
   opt.coarse_max = best.coarse_max;
   opt.cheb_lo = best.lo;
+  opt.tail_side = best.tail;
   tuned_ms = best.ms;
   build_inner();
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune_cache[key] = best;
   if (const char* path = tune_file()) {
     if (FILE* fp = fopen(path, "a")) {
-      fprintf(fp, "%s %d %d %d %.4f %.6f\n", key, best.degree, best.variant, best.coarse_max, best.lo, best.ms);
+      fprintf(fp, "%s %d %d %d %.4f %.6f %d\n", key, best.degree, best.variant, best.coarse_max, best.lo, best.ms,
+              best.tail);
       fclose(fp);
     }
   }

@@ -101,6 +101,13 @@ struct Gmg {
   DevBuf<float> net_img;
   DevBuf<double> net_nrm;
   DevBuf<T> net_q;             // M z of the network's correction
+  // the coarse end of the V-cycle as one cluster kernel (2D, constant
+  // viscosity): levels from tail_level on (the first whose longer side is at
+  // most tail_side) run inside k_vtail; -1: off
+  int tail_side = 0;
+  int tail_level = -1;
+  int tail_cs = 0;
+  DevBuf<unsigned char> tail_buf;
   void attach_net(Unet* u, int level, bool composite, cudaStream_t s);
   void detach_net();
   Gmg() = default;
@@ -115,6 +122,12 @@ struct Gmg {
   void vcycle(const T* r, T* z, cudaStream_t s, bool use_net = true);
   void smooth(int l, const T* b, T* x, bool x_zero, cudaStream_t s);
 };
+
+// plan and launch of the fused coarse end (tail.cu)
+template <typename T>
+void gmg_tail_setup(Gmg<T>& G, int side, cudaStream_t s);
+template <typename T>
+void gmg_tail_launch(const Gmg<T>& G, cudaStream_t s);
 
 // An instantiated graph of a whole solve with the launch counts of its
 // parts recorded at capture time: [0] once, [1] per outer iteration,

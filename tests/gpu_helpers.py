@@ -10,7 +10,7 @@ from oracle import mac
 def make_handle(gk, n, bc, mu=1.0, gamma=0.0, precision=0, inner=1, tol_inner=1e-11, maxit=1000,
                 maxit_inner=3000, coarse_max=8, degree=2, mixed_rtol=1e-3, use_graph=1, n_scale=0.0,
                 profile=0, kernel_variant=0, unet_side=0, net=None, n_diag=None, viscous_form=0,
-                batch_lockstep=0):
+                batch_lockstep=0, tail_side=0):
     import torch
     opt = gk.gkb_default_options()
     opt.precision = precision
@@ -27,6 +27,7 @@ def make_handle(gk, n, bc, mu=1.0, gamma=0.0, precision=0, inner=1, tol_inner=1e
     opt.unet_side = unet_side
     opt.viscous_form = viscous_form
     opt.batch_lockstep = batch_lockstep
+    opt.tail_side = tail_side
     opt.stream = torch.cuda.current_stream().cuda_stream
     h = gk.gkb_create(opt)
     if net is not None:

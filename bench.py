@@ -798,9 +798,10 @@ def config(args, wk):
          "parallelism": "replicas" if args.gpus > 1 else "single",
          "autotune": bool(getattr(args, "autotune", 0) > 0)}
     if len(wk.problems) > 1:
-        c["solve"] = ("gkb_solve_batched: one graph launch, a branch per problem, run concurrently"
+        c["solve"] = ("problems solved concurrently (GPU: gkb_solve_batched, one graph launch with a branch per "
+                      "problem; CPU oracle: one process per problem)"
                       if (wk.batched or all("w0" not in p and "p0" not in p for p in wk.problems))
-                      else "gkb_solve per problem, in turn")
+                      else "problems solved in turn")
     if len(sizes) <= 4:
         c["grid"] = [list(s) for s in sizes]
     else:

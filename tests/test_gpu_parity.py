@@ -38,6 +38,10 @@ def _mu(kind, n, seed=0):
     ((9, 11, 7), (D,) * 6, "var", 3.0),
     ((16, 16, 16), (D,) * 6, "const", 0.0),
     ((35, 6), (Nat, D, D, Nat), "var", 2.0),
+    # 3D levels of at least 16 cells per axis take the box / shell operator
+    # kernel: odd sizes with the grad-div coupling, and a natural side
+    ((18, 16, 17), (D,) * 6, "const", 50.0),
+    ((16, 20, 24), (D, Nat, D, D, D, D), "const", 7.0),
 ])
 def test_operators_match_oracle(lib, n, bc, mukind, gamma):
     gk = lib
@@ -98,17 +102,20 @@ def test_boundary_rhs_matches_oracle(lib):
         gk.gkb_destroy(h)
 
 
-@pytest.mark.parametrize("n,mukind,gamma,prec", [
-    ((64, 64), "const", 10.0, FP64),
-    ((48, 40), "var", 100.0, FP64),
-    ((16, 16, 16), "const", 5.0, FP64),
-    ((64, 64), "const", 1000.0, MIXED),
+@pytest.mark.parametrize("n,mukind,gamma,prec,variant", [
+    ((64, 64), "const", 10.0, FP64, 0),
+    ((48, 40), "var", 100.0, FP64, 0),
+    ((16, 16, 16), "const", 5.0, FP64, 0),
+    ((64, 64), "const", 1000.0, MIXED, 0),
+    # the 3D box / shell smoother and operator (levels of at least 16 cells)
+    ((18, 16, 20), "const", 50.0, MIXED, 0),
+    ((20, 18, 16), "const", 30.0, FP64, 2),
 ])
-def test_vcycle_is_symmetric_positive(lib, n, mukind, gamma, prec):
+def test_vcycle_is_symmetric_positive(lib, n, mukind, gamma, prec, variant):
     """PCG needs an SPD preconditioner: <B x, y> = <x, B y>, <B x, x> > 0."""
     gk = lib
     bc = (D,) * (2 * len(n))
-    h = make_handle(gk, n, bc, _mu(mukind, n), gamma, precision=prec)
+    h = make_handle(gk, n, bc, _mu(mukind, n), gamma, precision=prec, kernel_variant=variant)
     try:
         m, _ = gk.gkb_layout(h)
         rng = np.random.default_rng(4)

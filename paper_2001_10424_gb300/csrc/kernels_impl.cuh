@@ -1462,7 +1462,7 @@ __device__ __forceinline__ void cheb3s_shell_body(const Lvl& L, const T* GKB_RES
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 3 : 4) k_cheb3s(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
+__global__ void __launch_bounds__(BX* BY, sizeof(T) == 8 ? 2 : 4) k_cheb3s(Lvl L, const T* GKB_RESTRICT r, T* GKB_RESTRICT x,
                                                       T* GKB_RESTRICT d, T ca, T cb, int x_zero, const T* table,
                                                       const __grid_constant__ Fold3In<T> fin) {
   const int bz = cheb3s_box_z(L);

@@ -339,16 +339,18 @@ __global__ void __launch_bounds__(BX* BY) k_mac_tile(Lvl L, int wonly, const T* 
 }
 
 // ---------------------------------------------------------------------------
-// 3D constant-viscosity operator (mode 0: b - M x; mode 1: M x), split by
-// geometry. The box kernel takes the positions [1, n-2] on every axis, where
-// every face of every component is active and all its links are regular: a
-// block of 32 x 8 threads walks MAC3_KZ planes of a 32 x 8 column, keeping x of
-// three planes (u, v, w with a one-position halo) and the negative cell
-// divergences of two cell planes in shared memory as rings, the next plane's x
-// fetched into registers while the current one is computed; every face forms
-// the fused row (const_row) without tests. The shell kernel takes the other
-// positions, one thread each, with the general link-by-link row. Both use the
-// operations and roundings of k_mac_tile, so the results are bit for bit its.
+// 3D constant-viscosity operator (mode 0: b - M x; mode 1: M x; DOT: with
+// the fused x . y), one launch split by geometry. Box blocks take the
+// positions [1, n-2] on every axis, where every face of every component is
+// active and all its links are regular: a block of 32 x 8 threads walks
+// MAC3_KZ planes of a 32 x 8 column, keeping x of three planes (u, v, w with a
+// one-position halo) and the negative cell divergences of two cell planes in
+// shared memory as rings, with x and b of the next plane fetched into
+// registers while the current one is computed; every face forms the fused
+// row (const_row) without tests. Shell blocks (the extra z slices of the
+// grid) take the other positions, one thread each, with the general
+// link-by-link row. Both use the operations and roundings of k_mac_tile, so
+// the values are bit for bit its (the dot sums in another order).
 // ---------------------------------------------------------------------------
 constexpr int MAC3_KZ = 16;
 
@@ -1289,10 +1291,11 @@ __global__ void __launch_bounds__(BX* BY) k_cheb3(Lvl L, const T* GKB_RESTRICT r
 // The same step split by geometry (levels of at least 16 cells per axis): the
 // box [3, n-3]^3, where every position is of the interior class, walks planes
 // like k_mac3's box (r of three planes with a one-position halo in shared
-// memory, the next plane fetched into registers, d and x of the plane read
-// before its barriers) and applies the interior stencils in fold3_apply's
-// order; the shell (three positions deep) takes the class table one thread
-// per position. Bit for bit the values of k_cheb3.
+// memory; r, d and x of the next plane fetched into registers while the
+// current one is computed) and applies the interior stencils in
+// fold3_apply's order; the shell (three positions deep, the extra z slices of
+// the same launch) takes the class table one thread per position. The same
+// operations as k_cheb3 for every face.
 // ---------------------------------------------------------------------------
 constexpr int CHEB3S_KZ = 16;
 
